@@ -1,0 +1,273 @@
+/*
+ * CPU oracle for the HPSCD column sweep (Algorithm 1 of "Algorithmic Solution
+ * for Systems of Linear Equations, in O(mn) time").
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path links, loads or calls
+ * this file: only the tests, the smoke check and the benchmark's CPU-baseline
+ * leg do.  It shares no code, header or constant with the CUDA library.
+ *
+ * Arithmetic: IEEE float64 throughout, strictly sequential summation order
+ * (i = 0..m-1), true division.  X is read in its stored type (float32,
+ * bfloat16 bit patterns or float64) and promoted exactly to float64, so the
+ * system being solved is exactly the stored one.
+ *
+ * Readings of the paper taken here (each is listed in the design notes):
+ *   - the residual is e = y - X·a (Algorithm 1, the initialisation of e, and
+ *     Sec. 3), not X·a - y as the prose of Sec. 2 once writes it;
+ *   - a column with <X_j,X_j> = 0 is skipped (da = 0): the paper is silent;
+ *   - the stopping test ("break if under a certain threshold", Sec. 2) runs
+ *     once per sweep, after column n, on r_s = ||e_s||_2 / ||y||_2
+ *     (r_s = ||e_s||_2 when y = 0);
+ *       REL_RES:    stop after sweep s >= 0 when r_s <= tol
+ *       REL_CHANGE: stop after sweep s >= 1 when |r_{s-1} - r_s| < tol * r_{s-1}
+ *                   (or when r_{s-1} == 0)
+ *       NONE:       run exactly max_sweeps sweeps;
+ *   - hist[0] is the residual of the initial guess (before any sweep).
+ * Parity status: pinned (closed forms, Gaussian elimination, normal-equation
+ * least squares, orthogonality and monotonicity invariants, Gauss-Seidel
+ * equivalence), see tests/test_oracle_pins.py.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_F32 0
+#define OR_BF16 1
+#define OR_F64 2
+#define OR_COL 0
+#define OR_ROW 1
+#define OR_STOP_REL_RES 0
+#define OR_STOP_REL_CHANGE 1
+#define OR_STOP_NONE 2
+#define OR_OK 0
+#define OR_INVALID 1
+#define OR_NOT_CONVERGED 2
+#define OR_NONFINITE 3
+#define OR_NOMEM 4
+
+static double bf16_to_f64(uint16_t b) {
+  uint32_t u = (uint32_t)b << 16;
+  float f;
+  memcpy(&f, &u, sizeof f);
+  return (double)f;
+}
+
+/* Element X(i, j) promoted to float64. */
+static double x_elem(const void* X, int dt, int lay, int64_t ld, int64_t i, int64_t j) {
+  int64_t idx = (lay == OR_COL) ? j * ld + i : i * ld + j;
+  if (dt == OR_F32) return (double)((const float*)X)[idx];
+  if (dt == OR_BF16) return bf16_to_f64(((const uint16_t*)X)[idx]);
+  return ((const double*)X)[idx];
+}
+
+/* Column X_j promoted to float64 into col[0..m-1]. */
+static void load_column(const void* X, int dt, int lay, int64_t ld, int64_t m, int64_t j,
+                        double* col) {
+  if (lay == OR_COL) {
+    const int64_t base = j * ld;
+    if (dt == OR_F32) {
+      const float* p = (const float*)X + base;
+      for (int64_t i = 0; i < m; ++i) col[i] = (double)p[i];
+    } else if (dt == OR_BF16) {
+      const uint16_t* p = (const uint16_t*)X + base;
+      for (int64_t i = 0; i < m; ++i) col[i] = bf16_to_f64(p[i]);
+    } else {
+      memcpy(col, (const double*)X + base, (size_t)m * sizeof(double));
+    }
+    return;
+  }
+  for (int64_t i = 0; i < m; ++i) col[i] = x_elem(X, dt, lay, ld, i, j);
+}
+
+static double norm2(const double* v, int64_t m) {
+  double s = 0.0;
+  for (int64_t i = 0; i < m; ++i) s += v[i] * v[i];
+  return sqrt(s);
+}
+
+static int valid_args(const void* X, int dt, int lay, int64_t m, int64_t n, int64_t ld) {
+  if (m < 0 || n < 0) return 0;
+  if (dt != OR_F32 && dt != OR_BF16 && dt != OR_F64) return 0;
+  if (lay != OR_COL && lay != OR_ROW) return 0;
+  if (lay == OR_COL && ld < (m > 1 ? m : 1)) return 0;
+  if (lay == OR_ROW && ld < (n > 1 ? n : 1)) return 0;
+  if (!X && m > 0 && n > 0) return 0;
+  return 1;
+}
+
+/*
+ * e = y - X·a in float64 (the residual definition of Algorithm 1 and Sec. 3).
+ * Writes e[0..m-1]; returns ||e||_2 through *enorm (may be NULL).
+ */
+int hpscd_oracle_residual(const void* X, int dt, int lay, int64_t m, int64_t n, int64_t ld,
+                          const double* y, const double* a, double* e, double* enorm) {
+  if (!valid_args(X, dt, lay, m, n, ld) || (!y && m > 0) || (!a && n > 0) || (!e && m > 0))
+    return OR_INVALID;
+  for (int64_t i = 0; i < m; ++i) e[i] = y[i];
+  if (lay == OR_COL) {
+    double* col = (double*)malloc((size_t)(m > 0 ? m : 1) * sizeof(double));
+    if (!col) return OR_NOMEM;
+    for (int64_t j = 0; j < n; ++j) {
+      load_column(X, dt, lay, ld, m, j, col);
+      for (int64_t i = 0; i < m; ++i) e[i] -= col[i] * a[j];
+    }
+    free(col);
+  } else {
+    for (int64_t i = 0; i < m; ++i) {
+      double s = 0.0;
+      for (int64_t j = 0; j < n; ++j) s += x_elem(X, dt, lay, ld, i, j) * a[j];
+      e[i] -= s;
+    }
+  }
+  if (enorm) *enorm = norm2(e, m);
+  return OR_OK;
+}
+
+/*
+ * Algorithm 1 (HPSCD), literally, in float64.
+ *
+ *   a <- a0 (0_n when a0 == NULL)                     initial guess
+ *   e <- y - X·a                                       initial residual
+ *   d_j <- <X_j, X_j>  for every j                     the denominator of the
+ *                                                      column step; X is
+ *                                                      constant, so it is
+ *                                                      formed once
+ *   for s = 1..max_sweeps:
+ *     for j = 1..n (in order):
+ *       da  <- <X_j, e> / d_j       (Eq. da2; skipped when d_j == 0)
+ *       e   <- e - X_j·da           (Eq. ek1-ek)
+ *       a_j <- a_j + da
+ *     hist[s] <- ||e|| / ||y||, then the stopping test
+ *
+ * Row-major X is first copied to column-major float64 storage so that each
+ * column is read contiguously; the arithmetic is unchanged.
+ *
+ * max_col_steps >= 0 stops after that many single-column steps in total
+ * (k = (s-1)·n + j counts them), even mid-sweep, to expose intermediate
+ * states for the invariant checks; -1 disables it.
+ *
+ * Outputs: a_out[n], e_out[m] (may be NULL), hist[max_sweeps+1] (may be NULL),
+ * *sweeps_done (number of completed sweeps; may be NULL).
+ * Returns OR_OK when the stopping rule was met (or for STOP_NONE / column-step
+ * limits), OR_NOT_CONVERGED when max_sweeps ran out first, OR_NONFINITE when a
+ * residual norm is not finite, OR_INVALID for bad arguments.
+ */
+int hpscd_oracle_solve(const void* X, int dt, int lay, int64_t m, int64_t n, int64_t ld,
+                       const double* y, const double* a0, double tol, int64_t max_sweeps,
+                       int stop_rule, int64_t max_col_steps, double* a_out, double* e_out,
+                       double* hist, int64_t* sweeps_done) {
+  if (!valid_args(X, dt, lay, m, n, ld) || (!y && m > 0) || (!a_out && n > 0) ||
+      max_sweeps < 0 || (stop_rule < 0 || stop_rule > 2) || !(tol >= 0.0))
+    return OR_INVALID;
+
+  const void* Xc = X;
+  int dtc = dt, layc = lay;
+  int64_t ldc = ld;
+  double* Xcopy = NULL;
+  if (lay == OR_ROW && m > 0 && n > 0) {
+    Xcopy = (double*)malloc((size_t)m * (size_t)n * sizeof(double));
+    if (!Xcopy) return OR_NOMEM;
+    for (int64_t i = 0; i < m; ++i)
+      for (int64_t j = 0; j < n; ++j) Xcopy[j * m + i] = x_elem(X, dt, lay, ld, i, j);
+    Xc = Xcopy;
+    dtc = OR_F64;
+    layc = OR_COL;
+    ldc = m;
+  }
+
+  double* e = (double*)malloc((size_t)(m > 0 ? m : 1) * sizeof(double));
+  double* col = (double*)malloc((size_t)(m > 0 ? m : 1) * sizeof(double));
+  double* d = (double*)malloc((size_t)(n > 0 ? n : 1) * sizeof(double));
+  if (!e || !col || !d) {
+    free(e); free(col); free(d); free(Xcopy);
+    return OR_NOMEM;
+  }
+
+  /* a <- a0 (or 0_n); e <- y - X·a. */
+  for (int64_t j = 0; j < n; ++j) a_out[j] = a0 ? a0[j] : 0.0;
+  for (int64_t i = 0; i < m; ++i) e[i] = y[i];
+  for (int64_t j = 0; j < n; ++j) {
+    if (a_out[j] == 0.0) continue;
+    load_column(Xc, dtc, layc, ldc, m, j, col);
+    for (int64_t i = 0; i < m; ++i) e[i] -= col[i] * a_out[j];
+  }
+  /* d_j = <X_j, X_j>. */
+  for (int64_t j = 0; j < n; ++j) {
+    load_column(Xc, dtc, layc, ldc, m, j, col);
+    double s = 0.0;
+    for (int64_t i = 0; i < m; ++i) s += col[i] * col[i];
+    d[j] = s;
+  }
+
+  const double ynorm = norm2(y, m);
+  const double scale = ynorm > 0.0 ? ynorm : 1.0;
+  double r_prev = norm2(e, m) / scale;
+  if (hist) hist[0] = r_prev;
+  int status = OR_NOT_CONVERGED;
+  int64_t s_done = 0;
+  int64_t steps = 0;
+  int stopped_mid = 0;
+
+  if (!isfinite(r_prev)) {
+    status = OR_NONFINITE;
+  } else if (stop_rule == OR_STOP_REL_RES && r_prev <= tol) {
+    status = OR_OK;
+  } else if (stop_rule == OR_STOP_NONE && max_sweeps == 0) {
+    status = OR_OK;
+  } else if (max_col_steps == 0) {
+    status = OR_OK;
+  } else {
+    for (int64_t s = 1; s <= max_sweeps; ++s) {
+      for (int64_t j = 0; j < n; ++j) {
+        load_column(Xc, dtc, layc, ldc, m, j, col);
+        double num = 0.0;
+        for (int64_t i = 0; i < m; ++i) num += col[i] * e[i];
+        const double da = d[j] > 0.0 ? num / d[j] : 0.0;
+        for (int64_t i = 0; i < m; ++i) e[i] -= col[i] * da;
+        a_out[j] += da;
+        ++steps;
+        if (max_col_steps > 0 && steps >= max_col_steps) {
+          stopped_mid = 1;
+          break;
+        }
+      }
+      if (stopped_mid && steps % (n > 0 ? n : 1) != 0) {
+        status = OR_OK;
+        break;
+      }
+      s_done = s;
+      const double r = norm2(e, m) / scale;
+      if (hist) hist[s] = r;
+      if (!isfinite(r)) {
+        status = OR_NONFINITE;
+        break;
+      }
+      if (stopped_mid) {
+        status = OR_OK;
+        break;
+      }
+      if (stop_rule == OR_STOP_REL_RES && r <= tol) {
+        status = OR_OK;
+        break;
+      }
+      if (stop_rule == OR_STOP_REL_CHANGE && (r_prev == 0.0 || fabs(r_prev - r) < tol * r_prev)) {
+        status = OR_OK;
+        break;
+      }
+      if (stop_rule == OR_STOP_NONE && s == max_sweeps) {
+        status = OR_OK;
+        break;
+      }
+      r_prev = r;
+    }
+  }
+  if (e_out)
+    for (int64_t i = 0; i < m; ++i) e_out[i] = e[i];
+  if (sweeps_done) *sweeps_done = s_done;
+  free(e);
+  free(col);
+  free(d);
+  free(Xcopy);
+  return status;
+}

@@ -1,0 +1,158 @@
+"""Seeded synthetic systems X·a = y shaped like the tall, wide and square
+workloads of the HPSCD paper (Sec. 2, the system statement; Sec. 9, the
+numerical experiments).
+
+This module is the ONLY code shared by the CPU oracle and the CUDA path.  It
+holds none of the method's arithmetic: it draws X, a_true and noise, forms the
+right-hand side y = X·a_true (+ noise) in float64, and converts storage
+formats.  Everything is reproducible from (shape, seed): the random stream is
+split into fixed-size chunks, each with its own child seed, so the values do
+not depend on how many threads fill them.
+
+Storage conventions (the C-ABI uses the same ones):
+  * column-major X (m×n, leading dimension m) is a numpy array of shape (n, m);
+    row j of that array is column X_j;
+  * row-major X (m×n, leading dimension n) is a numpy array of shape (m, n);
+  * BF16 values are kept as uint16 bit patterns.
+"""
+from __future__ import annotations
+
+import os
+from concurrent.futures import ThreadPoolExecutor
+from dataclasses import dataclass
+
+import numpy as np
+
+CHUNK = 1 << 22  # elements per independent random stream
+
+
+def _threads() -> int:
+    return max(1, min(32, os.cpu_count() or 1))
+
+
+def _fill_chunks(out_flat: np.ndarray, seed: int, tag: int, kind: str,
+                 lo: float = -1.0, hi: float = 1.0) -> None:
+    """Fill out_flat (float32 or float64) with iid draws, chunk by chunk."""
+    total = out_flat.size
+    nchunks = (total + CHUNK - 1) // CHUNK
+    seqs = np.random.SeedSequence([seed, tag]).spawn(max(nchunks, 1))
+
+    def work(c):
+        s, e = c * CHUNK, min(total, (c + 1) * CHUNK)
+        g = np.random.Generator(np.random.Philox(seqs[c]))
+        if kind == "normal":
+            out_flat[s:e] = g.standard_normal(e - s, dtype=out_flat.dtype)
+        else:
+            out_flat[s:e] = g.uniform(lo, hi, e - s).astype(out_flat.dtype)
+
+    if nchunks <= 1:
+        if total:
+            work(0)
+        return
+    with ThreadPoolExecutor(_threads()) as ex:
+        list(ex.map(work, range(nchunks)))
+
+
+def f32_to_bf16_bits(x: np.ndarray) -> np.ndarray:
+    """Round float32 to bfloat16 (round to nearest, ties to even); returns uint16 bits.
+    Inputs are finite."""
+    u = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32)
+    r = (u + np.uint32(0x7FFF) + ((u >> np.uint32(16)) & np.uint32(1))) >> np.uint32(16)
+    return r.astype(np.uint16)
+
+
+def bf16_bits_to_f32(b: np.ndarray) -> np.ndarray:
+    return (np.ascontiguousarray(b, dtype=np.uint16).astype(np.uint32) << np.uint32(16)).view(np.float32)
+
+
+@dataclass
+class System:
+    """One synthetic system.  X is stored as described in the module docstring."""
+    X: np.ndarray          # float32 / uint16(bf16) / float64 storage array
+    y: np.ndarray          # float32 (or float64 for the float64 tiny case), length m
+    a_true: np.ndarray     # float64, length n
+    m: int
+    n: int
+    layout: str            # "col" or "row"
+    dtype: str             # "f32", "bf16", "f64"
+
+    @property
+    def ld(self) -> int:
+        return self.m if self.layout == "col" else self.n
+
+    def x_values_f64_block(self, j0: int, j1: int) -> np.ndarray:
+        """Columns j0..j1-1 of X as float64, shape (m, j1-j0) (for forming y / tests)."""
+        if self.layout == "col":
+            blk = self.X[j0:j1]
+            if self.dtype == "bf16":
+                blk = bf16_bits_to_f32(blk)
+            return np.asarray(blk, dtype=np.float64).T
+        blk = self.X[:, j0:j1]
+        if self.dtype == "bf16":
+            blk = bf16_bits_to_f32(blk)
+        return np.asarray(blk, dtype=np.float64)
+
+    def dense_f64(self) -> np.ndarray:
+        """The whole X as a float64 (m, n) array.  Small systems only."""
+        return self.x_values_f64_block(0, self.n)
+
+
+def _matvec_f64(sysm: System, a: np.ndarray) -> np.ndarray:
+    """y = X·a in float64, streamed in column blocks so large X never exists in float64."""
+    y = np.zeros(sysm.m, dtype=np.float64)
+    step = max(1, (1 << 24) // max(sysm.m, 1))
+    for j0 in range(0, sysm.n, step):
+        j1 = min(sysm.n, j0 + step)
+        y += sysm.x_values_f64_block(j0, j1) @ a[j0:j1]
+    return y
+
+
+def make_system(m: int, n: int, seed: int = 0, *, layout: str = "col", dtype: str = "f32",
+                noise: float = 0.0, consistent_rhs_dtype: str = "f32") -> System:
+    """X iid N(0,1), a_true iid U(-1,1), y = X·a_true + noise·N(0,1).
+
+    The system solved is the STORED X (after rounding to the storage dtype);
+    y is formed from those stored values in float64 and then rounded to
+    float32 (or kept float64 when consistent_rhs_dtype == "f64")."""
+    if layout not in ("col", "row") or dtype not in ("f32", "bf16", "f64"):
+        raise ValueError("bad layout/dtype")
+    shape = (n, m) if layout == "col" else (m, n)
+    if dtype == "f64":
+        X = np.empty(shape, dtype=np.float64)
+        _fill_chunks(X.reshape(-1), seed, 1, "normal")
+    else:
+        Xf = np.empty(shape, dtype=np.float32)
+        _fill_chunks(Xf.reshape(-1), seed, 1, "normal")
+        X = f32_to_bf16_bits(Xf).reshape(shape) if dtype == "bf16" else Xf
+    a_true = np.empty(n, dtype=np.float64)
+    _fill_chunks(a_true, seed, 2, "uniform", -1.0, 1.0)
+    s = System(X=X, y=np.empty(0), a_true=a_true, m=m, n=n, layout=layout, dtype=dtype)
+    y = _matvec_f64(s, a_true)
+    if noise:
+        z = np.empty(m, dtype=np.float64)
+        _fill_chunks(z, seed, 3, "normal")
+        y += noise * z
+    s.y = y if consistent_rhs_dtype == "f64" else y.astype(np.float32)
+    return s
+
+
+# The paper's workload shapes (Sec. 2: tall, wide and square systems; Sec. 9:
+# Float32 storage).  Names state what each one is.
+WORKLOADS = {
+    # tall, consistent, float64: the small case the oracle finishes in seconds
+    "tall_200x50_f64": dict(m=200, n=50, layout="col", dtype="f64", noise=0.0,
+                            consistent_rhs_dtype="f64"),
+    # tall, noisy least squares, float32 column-major (1.02 GB of X)
+    "tall_1Mx256_f32": dict(m=1_000_000, n=256, layout="col", dtype="f32", noise=0.01),
+    # wide, consistent, float32 row-major (1.6 GB of X)
+    "wide_2000x200k_f32": dict(m=2000, n=200_000, layout="row", dtype="f32", noise=0.0),
+    # tall, consistent, bfloat16 storage (4.1 GB of X)
+    "tall_4Mx512_bf16": dict(m=4_000_000, n=512, layout="col", dtype="bf16", noise=0.0),
+}
+
+
+def workload(name: str, seed: int = 0, **override) -> System:
+    kw = dict(WORKLOADS[name])
+    kw.update(override)
+    m, n = kw.pop("m"), kw.pop("n")
+    return make_system(m, n, seed, **kw)
