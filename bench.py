@@ -1,0 +1,301 @@
+"""Benchmark of the HPSCD column sweep (Algorithm 1) on GB300.
+
+One step = one complete solve of the 1,000,000 x 256 float32 column-major
+noisy least-squares system (X iid N(0,1), a_true iid U(-1,1), noise 0.01):
+Gram/denominator set-up, then sweeps until the relative change of the
+residual norm falls below 1e-7, inputs already resident in HBM.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  value = algorithmic HBM bytes of a solve / time per
+solve (GB/s; X is 1.02 GB, larger than L2, so no flush is needed between
+steps).  Under torchrun every rank solves its own system (independent
+replicas, weak scaling); rank 0 prints.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "tall_1Mx256_f32"
+TOL, STOP, MAX_SWEEPS = 1e-7, "rel_change", 100
+METRIC = "time & HBM GB/s to rel. residual 1e-6; learned/BF16 vs plain FP32 on 1 GB300"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def algorithmic_bytes(m, n, esz, passes):
+    """Set-up reads X once; each streaming pass reads X once and reads+writes e."""
+    return esz * m * n * (passes + 1) + passes * 8 * m + 4 * m
+
+
+def sweep_kernel_bytes(m, n, esz, passes):
+    return passes * (esz * m * n + 8 * m)
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def traffic_from_profile(src_sha):
+    """Per-launch DRAM bytes of the sweep kernel from the committed ncu summary, if the
+    kernel source has not changed since it was captured (else None)."""
+    p = os.path.join(ROOT, "profiles", "tall_sweep_1Mx256_f32.md")
+    if not os.path.exists(p):
+        return None
+    rec = {}
+    for ln in open(p):
+        if ln.startswith("<!--") and "bench:" in ln:
+            for kv in ln.split("bench:")[1].replace("-->", "").split():
+                k, _, v = kv.partition("=")
+                rec[k] = v
+    if rec.get("kernel_sha") != src_sha or "traffic_bytes_per_launch" not in rec:
+        return None
+    return float(rec["traffic_bytes_per_launch"])
+
+
+def kernel_sha():
+    h = hashlib.sha256()
+    for f in ("tall_sweep.cu", "common.cuh", "kernels.h"):
+        h.update(open(os.path.join(ROOT, "paper_2104_12570_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(
+        os.environ.get("LOCAL_RANK", 0))
+
+
+def run_reference(args, rank, world):
+    """The oracle (float64 CPU Algorithm 1) on the same workload, on host cores."""
+    if rank != 0:
+        return
+    import oracle
+    from paper_2104_12570_gb300 import synth
+    s = synth.workload(WORKLOAD, seed=0)
+    times = []
+    res = None
+    for i in range(args.warmup + args.steps):
+        t = time.perf_counter()
+        res = oracle.solve_system(s, tol=TOL, max_sweeps=MAX_SWEEPS, stop=STOP)
+        dt = time.perf_counter() - t
+        if i >= args.warmup:
+            times.append(dt)
+    sec = sum(times) / len(times)
+    nbytes = algorithmic_bytes(s.m, s.n, 4, res.sweeps + 1)
+    val = nbytes / sec / 1e9
+    out = {"impl": "reference", "metric": METRIC, "value": val, "unit": "GB/s",
+           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "m": s.m, "n": s.n, "stop": f"{STOP}<{TOL}",
+                      "sweeps": res.sweeps},
+           "cpu_baseline": {"value": val, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                            "sample": f"full solve of {WORKLOAD} ({res.sweeps} sweeps) per step"},
+           "e2e": {"value": val, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def cpu_baseline_leg(s, budget_s=30.0):
+    import oracle
+    t = time.perf_counter()
+    r = oracle.solve_system(s, tol=TOL, max_sweeps=MAX_SWEEPS, stop=STOP)
+    dt = time.perf_counter() - t
+    nbytes = algorithmic_bytes(s.m, s.n, 4, r.sweeps + 1)
+    return {"value": nbytes / dt / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": f"one full solve of {WORKLOAD} ({r.sweeps} sweeps, {dt:.1f} s)",
+            "seconds": dt}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--rows", type=int, default=0,
+                    help="override m (smaller case for profiler captures; not a bench line)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    import torch.distributed as dist
+    import paper_2104_12570_gb300 as hp
+    from paper_2104_12570_gb300 import synth
+
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    s = synth.workload(WORKLOAD, seed=rank, **({"m": args.rows} if args.rows else {}))
+    esz = 4
+    X = torch.from_numpy(s.X).to(dev).T  # (m, n), column-major
+    y = torch.from_numpy(s.y).to(dev)
+    ctx = hp.Context(local)
+    a = torch.empty(s.n, dtype=torch.float32, device=dev)
+
+    def step():
+        return ctx.solve(X, y, tol=TOL, max_sweeps=MAX_SWEEPS, stop=STOP, out=a)
+
+    for _ in range(args.warmup):
+        r = step()
+    if r.status != "ok":
+        raise SystemExit(f"solve did not converge: {r.status}")
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    sweep_ms, passes = [], []
+    launches = 0
+    with ClockSampler(local) as clk:
+        barrier()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        for _ in range(args.steps):
+            r = step()
+            sweep_ms.append(r.timing["sweep_ms"])
+            passes.append(r.timing["passes"])
+            launches += r.timing["kernel_launches"]
+        ev1.record()
+        barrier()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    p_mean = float(np.mean(passes))
+    nbytes = algorithmic_bytes(s.m, s.n, esz, p_mean)
+    value = world * nbytes / (ms * 1e-3) / 1e9
+
+    # end to end through the C ABI from pinned host memory
+    e2e = None
+    if not args.skip_e2e:
+        Xh = torch.from_numpy(s.X).pin_memory().T
+        yh = torch.from_numpy(s.y).pin_memory()
+        ctx.solve_host(Xh, yh, tol=TOL, max_sweeps=MAX_SWEEPS, stop=STOP)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        e2e_steps = max(3, args.steps // 4)
+        for _ in range(e2e_steps):
+            rh = ctx.solve_host(Xh, yh, tol=TOL, max_sweeps=MAX_SWEEPS, stop=STOP)
+        e2e_s = (time.perf_counter() - t) / e2e_steps
+        e2e_val = world * algorithmic_bytes(s.m, s.n, esz, rh.timing["passes"]) / e2e_s / 1e9
+        e2e = {"value": e2e_val, "unit": "GB/s", "h2d_bytes_per_step": int(s.X.nbytes + s.y.nbytes),
+               "d2h_bytes_per_step": int(4 * s.n + 8 * (rh.sweeps + 1) + 48),
+               "ms_per_step": e2e_s * 1e3}
+
+    if rank == 0:
+        peak, peak_kind = peaks()
+        k_ms = float(np.mean(sweep_ms))
+        k_bytes = sweep_kernel_bytes(s.m, s.n, esz, p_mean)
+        achieved = k_bytes / (k_ms * 1e-3) / 1e9
+        tr = traffic_from_profile(kernel_sha())
+        out = {
+            "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "m": s.m, "n": s.n, "layout": "col-major",
+                       "stop": f"{STOP}<{TOL}", "sweeps": int(r.sweeps),
+                       "passes_per_solve": p_mean, "l2": "inputs larger than L2 (1.02 GB X)",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_kind": peak_kind,
+                         "kernel": "tall_sweep_kernel", "traffic": tr,
+                         "kernel_ms": k_ms, "algorithmic_bytes": k_bytes},
+            "setup_ms": float(r.timing["setup_ms"]),
+            "e2e": e2e,
+            "gpu_launches": int(launches),
+            "clocks": clk.summary(),
+        }
+        if not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline_leg(s)
+        print(json.dumps(out), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

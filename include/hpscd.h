@@ -1,0 +1,159 @@
+/*
+ * hpscd.h — C ABI of the GB300 (sm_103a) implementation of the HPSCD column
+ * sweep, Algorithm 1 of N. P. Bakas, "Algorithmic Solution for Systems of
+ * Linear Equations, in O(mn) time" (arXiv 2104.12570).
+ *
+ * Problem (Sec. 2, Eq. System): given X (m×n) and y (m), find a (n) with
+ * X·a ≈ y, for tall (least squares), wide (consistent, infinitely many
+ * solutions) and square systems.  Algorithm 1 sweeps the columns j = 1..n in
+ * order; for each it forms da = <X_j, e> / <X_j, X_j> (Eq. da2), applies the
+ * rank-1 correction e <- e - X_j·da (Eq. ek1-ek) and updates a_j <- a_j + da,
+ * sweep after sweep, until the residual meets a threshold (Sec. 2, "break if
+ * under a certain threshold").
+ *
+ * Conventions shared by every entry point:
+ *   - All pointers named X, y, a (and their batched forms) are DEVICE pointers
+ *     unless the function name ends in _host.  The caller owns them; X and y
+ *     are never written.  No call keeps a pointer after it returns.
+ *   - Column-major X: element (i, j) at X[j*ld + i], ld >= m.
+ *     Row-major X:    element (i, j) at X[i*ld + j], ld >= n.
+ *   - The residual is e = y - X·a (Algorithm 1, the initialisation of e).
+ *   - hist[s] = ||e_s||_2 / ||y||_2 after sweep s (hist[0] is the residual of
+ *     the initial guess); when y = 0 the absolute norm ||e_s||_2 is used.  The
+ *     norms are accumulated in float64 on the device.
+ *   - Stopping rules, tested once per sweep after column n:
+ *       HPSCD_STOP_REL_RES:    stop after sweep s >= 0 when hist[s] <= tol;
+ *       HPSCD_STOP_REL_CHANGE: stop after sweep s >= 1 when
+ *                              |hist[s-1] - hist[s]| < tol * hist[s-1]
+ *                              (or hist[s-1] == 0);
+ *       HPSCD_STOP_NONE:       run exactly max_sweeps sweeps.
+ *   - A column with <X_j, X_j> = 0 is skipped (da = 0).
+ *   - Every call is stream-ordered on the context's stream; the solve calls
+ *     return after the result (a, hist, status) is complete.
+ *   - Functions return an hpscd_status; nothing else crosses the ABI.  On
+ *     HPSCD_ERR_NOT_CONVERGED and HPSCD_ERR_NONFINITE the outputs still hold
+ *     the last iterate and its history.
+ */
+#ifndef HPSCD_H
+#define HPSCD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  HPSCD_OK = 0,
+  HPSCD_ERR_INVALID_ARG = 1,   /* bad pointer, size, stride, enum or option */
+  HPSCD_ERR_NOT_CONVERGED = 2, /* max_sweeps ran out before the stopping rule held */
+  HPSCD_ERR_NONFINITE = 3,     /* a residual norm became NaN or Inf */
+  HPSCD_ERR_TIMEOUT = 4,       /* a bounded device-side wait gave up */
+  HPSCD_ERR_CUDA = 5,          /* a CUDA runtime call failed */
+  HPSCD_ERR_UNSUPPORTED = 6,   /* shape/layout/dtype combination not provided */
+  HPSCD_ERR_NO_MEMORY = 7      /* workspace allocation failed or is too small */
+} hpscd_status;
+
+typedef enum { HPSCD_F32 = 0, HPSCD_BF16 = 1 } hpscd_dtype;
+typedef enum { HPSCD_COL_MAJOR = 0, HPSCD_ROW_MAJOR = 1 } hpscd_layout;
+typedef enum {
+  HPSCD_STOP_REL_RES = 0,
+  HPSCD_STOP_REL_CHANGE = 1,
+  HPSCD_STOP_NONE = 2
+} hpscd_stop_rule;
+
+/* Options of one solve.  Zero-initialise, then set the fields you need. */
+typedef struct {
+  double tol;            /* threshold of the stopping rule (>= 0) */
+  int64_t max_sweeps;    /* N of Algorithm 1 (>= 0) */
+  int32_t stop_rule;     /* hpscd_stop_rule */
+  int32_t refresh_every; /* k > 0: every k-th residual pass recomputes the true
+                            residual e = y - X·a with compensated (float64-grade)
+                            accumulation instead of updating e; 0: only the
+                            initial residual is recomputed */
+  int32_t debug_flags;   /* 0 in normal use.  Bit 0 (HPSCD_DEBUG_STALL_BARRIER):
+                            the first grid barrier waits for one arrival more
+                            than there are CTAs, so its bounded wait runs out
+                            and the solve returns HPSCD_ERR_TIMEOUT; it tests
+                            the timeout path without faulting or hanging */
+  int32_t reserved[5];   /* must be zero */
+} hpscd_opts;
+
+#define HPSCD_DEBUG_STALL_BARRIER 1
+
+/* Timings of the last solve on a context, from CUDA events on its stream. */
+typedef struct {
+  float setup_ms;        /* <X_j,X_j> and Gram set-up kernels */
+  float sweep_ms;        /* the persistent sweep kernel */
+  int64_t passes;        /* streaming passes over X made by the sweep kernel */
+  int64_t x_bytes;       /* bytes of X (m·n·element size) */
+  int32_t grid;          /* CTAs of the sweep kernel */
+  int32_t kernel_launches; /* kernels launched by the solve */
+} hpscd_timing;
+
+typedef struct hpscd_ctx hpscd_ctx;
+
+/* Create a context bound to CUDA device `device` and stream `stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  The context owns a
+ * device workspace that grows on demand (cudaMalloc) unless the caller installs
+ * one with hpscd_set_workspace.  Errors: INVALID_ARG, CUDA. */
+int hpscd_create(hpscd_ctx** out, int device, void* stream);
+
+/* Release the context and any workspace it allocated.  NULL is accepted. */
+int hpscd_destroy(hpscd_ctx* ctx);
+
+/* Rebind the context to another stream of the same device. */
+int hpscd_set_stream(hpscd_ctx* ctx, void* stream);
+
+/* Limit (seconds, > 0) of every device-side spin wait (grid barrier, copy
+ * completion).  When it runs out the kernel stops, the call returns
+ * HPSCD_ERR_TIMEOUT and the context stays usable.  Default 5 s. */
+int hpscd_set_timeout(hpscd_ctx* ctx, double seconds);
+
+/* Device workspace (bytes) a solve of this shape needs. */
+int hpscd_workspace_size(hpscd_ctx* ctx, int dtype, int layout, int64_t m, int64_t n,
+                         const hpscd_opts* opts, size_t* bytes);
+
+/* Install caller-owned device memory as the workspace (256-byte aligned).  The
+ * context never frees it; solves that need more return HPSCD_ERR_NO_MEMORY.
+ * ptr = NULL returns the context to allocating its own. */
+int hpscd_set_workspace(hpscd_ctx* ctx, void* ptr, size_t bytes);
+
+/*
+ * Solve X·a ≈ y by sweeps of Algorithm 1 (Sec. 2) on the GPU.
+ *   X      device, dtype HPSCD_F32 (float) or HPSCD_BF16 (bfloat16), layout/ld
+ *          as above.  Column-major: any m, n <= 512 (tall and square systems).
+ *          Row-major: any n, m <= 4096 (wide systems; the transposed path).
+ *          Other combinations return HPSCD_ERR_UNSUPPORTED.
+ *   y      device float[m].
+ *   a      device float[n]; in: the initial guess when a_is_guess != 0
+ *          (Algorithm 2's "or initial guess"), ignored otherwise (0_n);
+ *          out: the coefficients after the last sweep.
+ *   hist   HOST double[max_sweeps + 1] or NULL; entries past the last sweep
+ *          are left untouched.
+ *   sweeps_done, final_rel_res: HOST, may be NULL.
+ * Returns OK when the stopping rule held, NOT_CONVERGED, NONFINITE, TIMEOUT,
+ * INVALID_ARG, UNSUPPORTED, NO_MEMORY or CUDA.
+ */
+int hpscd_solve(hpscd_ctx* ctx, const void* X, int dtype, int layout, int64_t m, int64_t n,
+                int64_t ld, const float* y, float* a, int a_is_guess, const hpscd_opts* opts,
+                double* hist, int64_t* sweeps_done, double* final_rel_res);
+
+/* Same as hpscd_solve but X, y and a are HOST pointers: the call copies X and y
+ * to the device workspace, solves, and copies a back (an end-to-end call). */
+int hpscd_solve_host(hpscd_ctx* ctx, const void* X, int dtype, int layout, int64_t m,
+                     int64_t n, int64_t ld, const float* y, float* a, int a_is_guess,
+                     const hpscd_opts* opts, double* hist, int64_t* sweeps_done,
+                     double* final_rel_res);
+
+/* Timings of the last solve on this context. */
+int hpscd_last_timing(hpscd_ctx* ctx, hpscd_timing* out);
+
+/* Static description of a status code. */
+const char* hpscd_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HPSCD_H */

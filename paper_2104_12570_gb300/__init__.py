@@ -1,0 +1,307 @@
+"""Python binding of libhpscd.so, the GB300 (sm_103a) HPSCD column-sweep
+library (Algorithm 1 of arXiv 2104.12570).
+
+Argument marshalling only: every step of a solve runs in the library's CUDA
+kernels.  There is no CPU or eager-PyTorch fallback; when the library cannot
+be built or loaded, every call raises.
+
+X is a 2-D (m, n) array: a torch tensor on the GPU for solve(), a host array
+(numpy or CPU torch tensor) for solve_host().  Its strides pick the layout:
+stride (1, ld) is column-major, stride (ld, 1) is row-major.  dtypes: float32,
+bfloat16 (torch.bfloat16, or numpy uint16 bit patterns for solve_host).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import build as _build
+
+__all__ = ["Context", "solve", "solve_host", "HpscdError", "load", "STATUS"]
+
+STATUS = {0: "ok", 1: "invalid_arg", 2: "not_converged", 3: "nonfinite", 4: "timeout",
+          5: "cuda_error", 6: "unsupported", 7: "no_memory"}
+STOP = {"rel_res": 0, "rel_change": 1, "none": 2}
+F32, BF16 = 0, 1
+COL, ROW = 0, 1
+
+_lock = threading.Lock()
+_lib = None
+
+
+class HpscdError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        self.code = code
+        self.status = STATUS.get(code, str(code))
+        super().__init__(f"hpscd: {self.status}{(': ' + what) if what else ''}")
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("max_sweeps", ctypes.c_int64),
+                ("stop_rule", ctypes.c_int32), ("refresh_every", ctypes.c_int32),
+                ("debug_flags", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+
+
+class Timing(ctypes.Structure):
+    _fields_ = [("setup_ms", ctypes.c_float), ("sweep_ms", ctypes.c_float),
+                ("passes", ctypes.c_int64), ("x_bytes", ctypes.c_int64),
+                ("grid", ctypes.c_int32), ("kernel_launches", ctypes.c_int32)]
+
+
+SIGNATURES = {
+    "hpscd_create": ([ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_void_p], ctypes.c_int),
+    "hpscd_destroy": ([ctypes.c_void_p], ctypes.c_int),
+    "hpscd_set_stream": ([ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
+    "hpscd_set_timeout": ([ctypes.c_void_p, ctypes.c_double], ctypes.c_int),
+    "hpscd_workspace_size": ([ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int64,
+                              ctypes.c_int64, ctypes.POINTER(Opts),
+                              ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+    "hpscd_set_workspace": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t], ctypes.c_int),
+    "hpscd_solve": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int64,
+                     ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                     ctypes.POINTER(Opts), ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64),
+                     ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    "hpscd_solve_host": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                          ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p,
+                          ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(Opts), ctypes.c_void_p,
+                          ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)],
+                         ctypes.c_int),
+    "hpscd_last_timing": ([ctypes.c_void_p, ctypes.POINTER(Timing)], ctypes.c_int),
+    "hpscd_status_string": ([ctypes.c_int], ctypes.c_char_p),
+}
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_needed: bool = True):
+    """Load libhpscd.so (building it first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if build_if_needed:
+                _build.build()
+            if not os.path.exists(_build.LIB):
+                raise RuntimeError(f"libhpscd.so not found at {_build.LIB}; run build()")
+            lib = ctypes.CDLL(_build.LIB)
+            for name, (args, res) in SIGNATURES.items():
+                fn = getattr(lib, name)
+                fn.argtypes = args
+                fn.restype = res
+            _lib = lib
+    return _lib
+
+
+def make_opts(tol=1e-6, max_sweeps=1000, stop="rel_res", refresh_every=0, debug_flags=0) -> Opts:
+    o = Opts()
+    o.debug_flags = int(debug_flags)
+    o.tol = float(tol)
+    o.max_sweeps = int(max_sweeps)
+    o.stop_rule = STOP[stop] if isinstance(stop, str) else int(stop)
+    o.refresh_every = int(refresh_every)
+    return o
+
+
+def _describe(X):
+    """(ptr, dtype code, layout, m, n, ld) of a 2-D torch tensor or numpy array."""
+    try:
+        import torch
+        is_torch = isinstance(X, torch.Tensor)
+    except ImportError:  # pragma: no cover
+        is_torch = False
+    if is_torch:
+        if X.dim() != 2:
+            raise ValueError("X must be 2-D (m, n)")
+        import torch
+        if X.dtype == torch.float32:
+            dt = F32
+        elif X.dtype == torch.bfloat16:
+            dt = BF16
+        else:
+            raise TypeError("X dtype must be float32 or bfloat16")
+        m, n = X.shape
+        s0, s1 = X.stride()
+        ptr = X.data_ptr()
+    else:
+        X = np.asarray(X)
+        if X.ndim != 2:
+            raise ValueError("X must be 2-D (m, n)")
+        if X.dtype == np.float32:
+            dt = F32
+        elif X.dtype == np.uint16:
+            dt = BF16
+        else:
+            raise TypeError("X dtype must be float32 or uint16 (bfloat16 bits)")
+        m, n = X.shape
+        s0, s1 = (s // X.itemsize for s in X.strides)
+        ptr = X.ctypes.data
+    if m == 0 or n == 0:
+        return ptr, dt, COL, m, n, max(1, m)
+    if s0 == 1 and s1 >= max(1, m):
+        return ptr, dt, COL, m, n, s1
+    if n == 1 and s0 == 1:
+        return ptr, dt, COL, m, n, max(1, m)
+    if s1 == 1 and s0 >= max(1, n):
+        return ptr, dt, ROW, m, n, s0
+    raise ValueError("X must be column-major (stride (1, ld)) or row-major (stride (ld, 1))")
+
+
+@dataclass
+class SolveResult:
+    a: object
+    hist: np.ndarray
+    sweeps: int
+    rel_res: float
+    status: str
+    timing: dict = field(default_factory=dict)
+
+
+class Context:
+    """One library context: a device, a stream and a workspace."""
+
+    def __init__(self, device: int = 0, stream=None, timeout_s: float | None = None):
+        self._lib = load()
+        self.device = device
+        h = ctypes.c_void_p()
+        rc = self._lib.hpscd_create(ctypes.byref(h), int(device), self._stream_handle(stream))
+        if rc != 0:
+            raise HpscdError(rc, "hpscd_create")
+        self._h = h
+        if timeout_s is not None:
+            self.set_timeout(timeout_s)
+
+    @staticmethod
+    def _stream_handle(stream):
+        if stream is None:
+            return None
+        if isinstance(stream, int):
+            return ctypes.c_void_p(stream)
+        return ctypes.c_void_p(stream.cuda_stream)
+
+    def set_stream(self, stream):
+        rc = self._lib.hpscd_set_stream(self._h, self._stream_handle(stream))
+        if rc:
+            raise HpscdError(rc)
+
+    def set_timeout(self, seconds: float):
+        rc = self._lib.hpscd_set_timeout(self._h, float(seconds))
+        if rc:
+            raise HpscdError(rc)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.hpscd_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def timing(self) -> dict:
+        t = Timing()
+        self._lib.hpscd_last_timing(self._h, ctypes.byref(t))
+        return {"setup_ms": t.setup_ms, "sweep_ms": t.sweep_ms, "passes": t.passes,
+                "x_bytes": t.x_bytes, "grid": t.grid, "kernel_launches": t.kernel_launches}
+
+    def workspace_size(self, m, n, dtype="f32", layout="col", **opt_kw) -> int:
+        o = make_opts(**opt_kw)
+        b = ctypes.c_size_t(0)
+        rc = self._lib.hpscd_workspace_size(self._h, F32 if dtype == "f32" else BF16,
+                                            COL if layout == "col" else ROW, int(m), int(n),
+                                            ctypes.byref(o), ctypes.byref(b))
+        if rc:
+            raise HpscdError(rc)
+        return b.value
+
+    def _finish(self, rc, hist, sw, rr, a):
+        if rc in (1, 4, 5, 6, 7):
+            raise HpscdError(rc)
+        s = sw.value
+        return SolveResult(a=a, hist=hist[: s + 1].copy(), sweeps=s, rel_res=rr.value,
+                           status=STATUS[rc], timing=self.timing())
+
+    def solve(self, X, y, *, tol=1e-6, max_sweeps=1000, stop="rel_res", a0=None,
+              refresh_every=0, out=None, debug_flags=0) -> SolveResult:
+        """Solve X·a ≈ y on the GPU (X, y, a0, out: CUDA tensors on this device)."""
+        import torch
+        ptr, dt, lay, m, n, ld = _describe(X)
+        if not (isinstance(y, torch.Tensor) and y.is_cuda and y.dtype == torch.float32
+                and y.numel() == m and y.is_contiguous()):
+            raise TypeError("y must be a contiguous float32 CUDA tensor of length m")
+        if not X.is_cuda:
+            raise TypeError("X must be a CUDA tensor (use solve_host for host arrays)")
+        a = out if out is not None else torch.empty(n, dtype=torch.float32, device=X.device)
+        if a0 is not None:
+            a.copy_(a0)
+        o = make_opts(tol, max_sweeps, stop, refresh_every, debug_flags)
+        hist = np.full(int(max_sweeps) + 1, np.nan)
+        sw, rr = ctypes.c_int64(0), ctypes.c_double(0.0)
+        self.set_stream(torch.cuda.current_stream(X.device))
+        rc = self._lib.hpscd_solve(self._h, ctypes.c_void_p(ptr), dt, lay, m, n, ld,
+                                   ctypes.c_void_p(y.data_ptr()), ctypes.c_void_p(a.data_ptr()),
+                                   1 if a0 is not None else 0, ctypes.byref(o),
+                                   hist.ctypes.data_as(ctypes.c_void_p), ctypes.byref(sw),
+                                   ctypes.byref(rr))
+        return self._finish(rc, hist, sw, rr, a)
+
+    def solve_host(self, X, y, *, tol=1e-6, max_sweeps=1000, stop="rel_res", a0=None,
+                   refresh_every=0) -> SolveResult:
+        """End-to-end solve from host memory (numpy arrays or CPU tensors; pinned
+        memory makes the copies asynchronous).  Returns a as a numpy array."""
+        ptr, dt, lay, m, n, ld = _describe(X)
+        y_np = _host_f32(y, m)
+        a = np.zeros(n, dtype=np.float32) if a0 is None else np.array(a0, dtype=np.float32)
+        o = make_opts(tol, max_sweeps, stop, refresh_every)
+        hist = np.full(int(max_sweeps) + 1, np.nan)
+        sw, rr = ctypes.c_int64(0), ctypes.c_double(0.0)
+        rc = self._lib.hpscd_solve_host(self._h, ctypes.c_void_p(ptr), dt, lay, m, n, ld,
+                                        ctypes.c_void_p(y_np[0]), a.ctypes.data_as(ctypes.c_void_p),
+                                        1 if a0 is not None else 0, ctypes.byref(o),
+                                        hist.ctypes.data_as(ctypes.c_void_p), ctypes.byref(sw),
+                                        ctypes.byref(rr))
+        return self._finish(rc, hist, sw, rr, a)
+
+
+def _host_f32(y, m):
+    """(pointer, keep-alive) of a host float32 vector of length m."""
+    try:
+        import torch
+        if isinstance(y, torch.Tensor):
+            if y.is_cuda or y.dtype != torch.float32 or not y.is_contiguous() or y.numel() != m:
+                raise TypeError("y must be a contiguous float32 host vector of length m")
+            return (y.data_ptr(), y)
+    except ImportError:  # pragma: no cover
+        pass
+    yn = np.ascontiguousarray(y, dtype=np.float32)
+    if yn.size != m:
+        raise ValueError("y must have length m")
+    return (yn.ctypes.data, yn)
+
+
+_default = {}
+
+
+def _default_ctx(device):
+    with _lock:
+        c = _default.get(device)
+    if c is None:
+        c = Context(device)
+        with _lock:
+            _default[device] = c
+    return c
+
+
+def solve(X, y, **kw) -> SolveResult:
+    """Module-level solve on X's device with a shared default context."""
+    return _default_ctx(X.device.index or 0).solve(X, y, **kw)
+
+
+def solve_host(X, y, device: int = 0, **kw) -> SolveResult:
+    return _default_ctx(device).solve_host(X, y, **kw)

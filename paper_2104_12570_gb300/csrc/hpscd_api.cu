@@ -1,0 +1,417 @@
+// C ABI of the HPSCD GB300 library (declared in include/hpscd.h): argument
+// checks, workspace, tensor-map encoding and the launch sequence of a solve.
+#include <cudaTypedefs.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+
+#include "kernels.h"
+
+using namespace hpscd;
+
+struct hpscd_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int sms = 0;
+  int max_smem = 0;
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  bool ws_owned = true;
+  double timeout_s = 5.0;
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+  GridCtl* ctl_host = nullptr;  // pinned
+  hpscd_timing last{};
+  PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+};
+
+namespace {
+
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = false;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    ok = (prev == dev) || (cudaSetDevice(dev) == cudaSuccess);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+struct Layout {
+  size_t G = 0, partial = 0, e = 0, gpart = 0, npart = 0, ypart = 0, hist = 0, ctl = 0;
+  size_t xcopy = 0, ycopy = 0, acopy = 0, total = 0;
+};
+
+struct Plan {
+  TallConfig cfg;
+  GramPlan gp;
+  int64_t ntiles = 0;
+  int grid = 0;
+  Layout L;
+};
+
+int esize(int dtype) { return dtype == HPSCD_F32 ? 4 : 2; }
+
+int check_opts(const hpscd_opts* o) {
+  if (!o) return HPSCD_ERR_INVALID_ARG;
+  if (!(o->tol >= 0.0) || !isfinite(o->tol)) return HPSCD_ERR_INVALID_ARG;
+  if (o->max_sweeps < 0 || o->max_sweeps > (int64_t)1 << 40) return HPSCD_ERR_INVALID_ARG;
+  if (o->stop_rule < HPSCD_STOP_REL_RES || o->stop_rule > HPSCD_STOP_NONE) return HPSCD_ERR_INVALID_ARG;
+  if (o->refresh_every < 0) return HPSCD_ERR_INVALID_ARG;
+  if (o->debug_flags & ~HPSCD_DEBUG_STALL_BARRIER) return HPSCD_ERR_INVALID_ARG;
+  for (int i = 0; i < 5; ++i)
+    if (o->reserved[i] != 0) return HPSCD_ERR_INVALID_ARG;
+  return HPSCD_OK;
+}
+
+int check_shape(int dtype, int layout, int64_t m, int64_t n, int64_t ld) {
+  if (dtype != HPSCD_F32 && dtype != HPSCD_BF16) return HPSCD_ERR_INVALID_ARG;
+  if (layout != HPSCD_COL_MAJOR && layout != HPSCD_ROW_MAJOR) return HPSCD_ERR_INVALID_ARG;
+  if (m < 0 || n < 0) return HPSCD_ERR_INVALID_ARG;
+  if (m > ((int64_t)1 << 31) - 1024 || n > ((int64_t)1 << 31) - 1024) return HPSCD_ERR_INVALID_ARG;
+  const int64_t minld = layout == HPSCD_COL_MAJOR ? (m > 1 ? m : 1) : (n > 1 ? n : 1);
+  if (ld < minld) return HPSCD_ERR_INVALID_ARG;
+  return HPSCD_OK;
+}
+
+// Sizes the workspace of a solve.  Returns false for unsupported shapes.
+int make_plan(const hpscd_ctx* ctx, int dtype, int layout, int64_t m, int64_t n, int64_t ld,
+              const hpscd_opts* o, bool host_copies, Plan* P) {
+  if (layout != HPSCD_COL_MAJOR) return HPSCD_ERR_UNSUPPORTED;
+  if (n > 512) return HPSCD_ERR_UNSUPPORTED;
+  if (!tall_config(dtype, (int)n, ctx->max_smem, &P->cfg)) return HPSCD_ERR_UNSUPPORTED;
+  P->gp = gram_plan(m, P->cfg.npad, ctx->sms);
+  P->ntiles = (m + P->cfg.rows - 1) / P->cfg.rows;
+  int64_t grid = ctx->sms;
+  if (P->ntiles < grid) grid = P->ntiles;
+  if (grid < 1) grid = 1;
+  P->grid = (int)grid;
+  Layout& L = P->L;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = off;
+    off = align_up(off + bytes, 256);
+    return at;
+  };
+  L.G = take((size_t)P->gp.npad * P->gp.npad * sizeof(float));
+  L.partial = take(P->gp.partial_bytes);
+  L.e = take((size_t)(m > 0 ? m : 1) * sizeof(float));
+  L.gpart = take((size_t)2 * P->grid * P->cfg.npad * sizeof(float));
+  L.npart = take((size_t)2 * P->grid * sizeof(double));
+  L.ypart = take((size_t)P->grid * sizeof(double));
+  L.hist = take((size_t)(o->max_sweeps + 1) * sizeof(double));
+  L.ctl = take(sizeof(GridCtl));
+  if (host_copies) {
+    L.xcopy = take((size_t)(n > 0 ? n : 1) * (size_t)ld * esize(dtype));
+    L.ycopy = take((size_t)(m > 0 ? m : 1) * sizeof(float));
+    L.acopy = take((size_t)(n > 0 ? n : 1) * sizeof(float));
+  }
+  L.total = off;
+  return HPSCD_OK;
+}
+
+int ensure_ws(hpscd_ctx* ctx, size_t bytes) {
+  if (bytes <= ctx->ws_bytes) return HPSCD_OK;
+  if (!ctx->ws_owned) return HPSCD_ERR_NO_MEMORY;
+  if (ctx->ws) {
+    cudaStreamSynchronize(ctx->stream);
+    cudaFree(ctx->ws);
+    ctx->ws = nullptr;
+    ctx->ws_bytes = 0;
+  }
+  size_t want = bytes + bytes / 8;
+  if (cudaMalloc(&ctx->ws, want) != cudaSuccess) {
+    cudaGetLastError();
+    ctx->ws = nullptr;
+    return HPSCD_ERR_NO_MEMORY;
+  }
+  ctx->ws_bytes = want;
+  return HPSCD_OK;
+}
+
+int encode_tall_map(hpscd_ctx* ctx, const void* X, int dtype, int64_t m, int64_t n, int64_t ld,
+                    const TallConfig& cfg, CUtensorMap* map) {
+  if (!ctx->encode) return 0;
+  const int es = esize(dtype);
+  if ((reinterpret_cast<uintptr_t>(X) & 15) != 0) return 0;
+  if (((uint64_t)ld * es) % 16 != 0) return 0;
+  if (m < 1 || n < 1) return 0;
+  if ((uint64_t)ld * es >= ((uint64_t)1 << 40)) return 0;
+  cuuint64_t dims[2] = {(cuuint64_t)m, (cuuint64_t)n};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * es};
+  cuuint32_t box[2] = {(cuuint32_t)cfg.rows, (cuuint32_t)cfg.box_cols};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = ctx->encode(map, dtype == HPSCD_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                                   : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+                           2, const_cast<void*>(X), dims, strides, box, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? 1 : 0;
+}
+
+// m == 0: nothing to sweep; y = 0, so every recorded residual is the absolute norm 0.
+int solve_empty_rows(hpscd_ctx* ctx, int64_t n, float* a, int a_is_guess, const hpscd_opts* o,
+                     double* hist, int64_t* sweeps_done, double* final_rel_res) {
+  if (!a_is_guess && n > 0 && cudaMemsetAsync(a, 0, (size_t)n * sizeof(float), ctx->stream) != cudaSuccess)
+    return HPSCD_ERR_CUDA;
+  if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return HPSCD_ERR_CUDA;
+  int64_t s = 0;
+  if (o->stop_rule == HPSCD_STOP_REL_CHANGE) s = o->max_sweeps > 0 ? 1 : 0;
+  if (o->stop_rule == HPSCD_STOP_NONE) s = o->max_sweeps;
+  if (hist)
+    for (int64_t i = 0; i <= s; ++i) hist[i] = 0.0;
+  if (sweeps_done) *sweeps_done = s;
+  if (final_rel_res) *final_rel_res = 0.0;
+  ctx->last = hpscd_timing{};
+  if (o->stop_rule == HPSCD_STOP_REL_CHANGE && o->max_sweeps == 0) return HPSCD_ERR_NOT_CONVERGED;
+  return HPSCD_OK;
+}
+
+int solve_device(hpscd_ctx* ctx, const void* X, int dtype, int layout, int64_t m, int64_t n,
+                 int64_t ld, const float* y, float* a, int a_is_guess, const hpscd_opts* o,
+                 double* hist, int64_t* sweeps_done, double* final_rel_res, const Plan& P) {
+  if (m == 0) return solve_empty_rows(ctx, n, a, a_is_guess, o, hist, sweeps_done, final_rel_res);
+  char* ws = static_cast<char*>(ctx->ws);
+  const Layout& L = P.L;
+  float* G = reinterpret_cast<float*>(ws + L.G);
+  GridCtl* ctl = reinterpret_cast<GridCtl*>(ws + L.ctl);
+  cudaStream_t st = ctx->stream;
+
+  if (cudaEventRecord(ctx->ev[0], st) != cudaSuccess) return HPSCD_ERR_CUDA;
+  if (launch_gram(X, dtype, m, (int)n, ld, P.gp, reinterpret_cast<double*>(ws + L.partial), G,
+                  P.gp.npad, st) != cudaSuccess)
+    return HPSCD_ERR_CUDA;
+  if (cudaMemsetAsync(ctl, 0, sizeof(GridCtl), st) != cudaSuccess) return HPSCD_ERR_CUDA;
+  if (cudaEventRecord(ctx->ev[1], st) != cudaSuccess) return HPSCD_ERR_CUDA;
+
+  CUtensorMap map;
+  memset(&map, 0, sizeof(map));
+  const int use_tma = encode_tall_map(ctx, X, dtype, m, n, ld, P.cfg, &map);
+
+  TallParams p{};
+  p.X = X;
+  p.m = m;
+  p.n = (int)n;
+  p.ld = ld;
+  p.y = y;
+  p.e = reinterpret_cast<float*>(ws + L.e);
+  p.a_out = a;
+  p.a_in = a;
+  p.warm = a_is_guess ? 1 : 0;
+  p.G = G;
+  p.ldG = P.gp.npad;
+  p.gpart = reinterpret_cast<float*>(ws + L.gpart);
+  p.npart = reinterpret_cast<double*>(ws + L.npart);
+  p.ypart = reinterpret_cast<double*>(ws + L.ypart);
+  p.hist = reinterpret_cast<double*>(ws + L.hist);
+  p.ctl = ctl;
+  p.tol = o->tol;
+  p.max_sweeps = o->max_sweeps;
+  p.stop_rule = o->stop_rule;
+  p.refresh_every = o->refresh_every;
+  p.ntiles = P.ntiles;
+  p.nstages = P.cfg.nstages;
+  p.use_tma = use_tma;
+  p.timeout_ns = (uint64_t)(ctx->timeout_s * 1e9);
+  p.stall_barrier = (o->debug_flags & HPSCD_DEBUG_STALL_BARRIER) ? 1 : 0;
+  if (launch_tall_sweep(dtype, P.cfg, &map, p, P.grid, st) != cudaSuccess) {
+    cudaGetLastError();
+    return HPSCD_ERR_CUDA;
+  }
+  if (cudaEventRecord(ctx->ev[2], st) != cudaSuccess) return HPSCD_ERR_CUDA;
+  if (cudaMemcpyAsync(ctx->ctl_host, ctl, sizeof(GridCtl), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return HPSCD_ERR_CUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return HPSCD_ERR_CUDA;
+  const GridCtl c = *ctx->ctl_host;
+  if (hist && c.sweeps >= 0 && c.sweeps <= o->max_sweeps) {
+    if (cudaMemcpy(hist, p.hist, (size_t)(c.sweeps + 1) * sizeof(double), cudaMemcpyDeviceToHost) !=
+        cudaSuccess)
+      return HPSCD_ERR_CUDA;
+  }
+  if (sweeps_done) *sweeps_done = c.sweeps;
+  if (final_rel_res) *final_rel_res = c.final_res;
+  hpscd_timing t{};
+  cudaEventElapsedTime(&t.setup_ms, ctx->ev[0], ctx->ev[1]);
+  cudaEventElapsedTime(&t.sweep_ms, ctx->ev[1], ctx->ev[2]);
+  t.passes = c.passes;
+  t.x_bytes = m * n * esize(dtype);
+  t.grid = P.grid;
+  t.kernel_launches = 3;
+  ctx->last = t;
+  (void)layout;
+  if (c.err != DEV_OK) return HPSCD_ERR_TIMEOUT;
+  return c.status;
+}
+
+}  // namespace
+
+extern "C" {
+
+int hpscd_create(hpscd_ctx** out, int device, void* stream) {
+  if (!out) return HPSCD_ERR_INVALID_ARG;
+  *out = nullptr;
+  int count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess) { cudaGetLastError(); return HPSCD_ERR_CUDA; }
+  if (device < 0 || device >= count) return HPSCD_ERR_INVALID_ARG;
+  DeviceGuard g(device);
+  if (!g.ok) return HPSCD_ERR_CUDA;
+  hpscd_ctx* c = new (std::nothrow) hpscd_ctx();
+  if (!c) return HPSCD_ERR_NO_MEMORY;
+  c->device = device;
+  c->stream = static_cast<cudaStream_t>(stream);
+  if (cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&c->max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) !=
+          cudaSuccess) {
+    delete c;
+    return HPSCD_ERR_CUDA;
+  }
+  for (int i = 0; i < 3; ++i)
+    if (cudaEventCreate(&c->ev[i]) != cudaSuccess) { hpscd_destroy(c); return HPSCD_ERR_CUDA; }
+  if (cudaMallocHost(reinterpret_cast<void**>(&c->ctl_host), sizeof(GridCtl)) != cudaSuccess) {
+    c->ctl_host = nullptr;
+    hpscd_destroy(c);
+    return HPSCD_ERR_CUDA;
+  }
+  void* fn = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
+          cudaSuccess &&
+      q == cudaDriverEntryPointSuccess)
+    c->encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  else
+    cudaGetLastError();
+  *out = c;
+  return HPSCD_OK;
+}
+
+int hpscd_destroy(hpscd_ctx* ctx) {
+  if (!ctx) return HPSCD_OK;
+  DeviceGuard g(ctx->device);
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  else cudaDeviceSynchronize();
+  if (ctx->ws && ctx->ws_owned) cudaFree(ctx->ws);
+  for (int i = 0; i < 3; ++i)
+    if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
+  if (ctx->ctl_host) cudaFreeHost(ctx->ctl_host);
+  delete ctx;
+  return HPSCD_OK;
+}
+
+int hpscd_set_stream(hpscd_ctx* ctx, void* stream) {
+  if (!ctx) return HPSCD_ERR_INVALID_ARG;
+  ctx->stream = static_cast<cudaStream_t>(stream);
+  return HPSCD_OK;
+}
+
+int hpscd_set_timeout(hpscd_ctx* ctx, double seconds) {
+  if (!ctx || !(seconds > 0.0) || seconds > 3600.0) return HPSCD_ERR_INVALID_ARG;
+  ctx->timeout_s = seconds;
+  return HPSCD_OK;
+}
+
+int hpscd_workspace_size(hpscd_ctx* ctx, int dtype, int layout, int64_t m, int64_t n,
+                         const hpscd_opts* opts, size_t* bytes) {
+  if (!ctx || !bytes) return HPSCD_ERR_INVALID_ARG;
+  int rc = check_opts(opts);
+  if (rc) return rc;
+  const int64_t ld = layout == HPSCD_COL_MAJOR ? (m > 1 ? m : 1) : (n > 1 ? n : 1);
+  if ((rc = check_shape(dtype, layout, m, n, ld))) return rc;
+  Plan P;
+  if ((rc = make_plan(ctx, dtype, layout, m, n, ld, opts, false, &P))) return rc;
+  *bytes = P.L.total;
+  return HPSCD_OK;
+}
+
+int hpscd_set_workspace(hpscd_ctx* ctx, void* ptr, size_t bytes) {
+  if (!ctx) return HPSCD_ERR_INVALID_ARG;
+  if (ptr && (reinterpret_cast<uintptr_t>(ptr) & 255) != 0) return HPSCD_ERR_INVALID_ARG;
+  DeviceGuard g(ctx->device);
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  if (ctx->ws && ctx->ws_owned) cudaFree(ctx->ws);
+  ctx->ws = ptr;
+  ctx->ws_bytes = ptr ? bytes : 0;
+  ctx->ws_owned = (ptr == nullptr);
+  return HPSCD_OK;
+}
+
+int hpscd_solve(hpscd_ctx* ctx, const void* X, int dtype, int layout, int64_t m, int64_t n,
+                int64_t ld, const float* y, float* a, int a_is_guess, const hpscd_opts* opts,
+                double* hist, int64_t* sweeps_done, double* final_rel_res) {
+  if (!ctx) return HPSCD_ERR_INVALID_ARG;
+  int rc = check_opts(opts);
+  if (rc) return rc;
+  if ((rc = check_shape(dtype, layout, m, n, ld))) return rc;
+  if ((m > 0 && n > 0 && !X) || (m > 0 && !y) || (n > 0 && !a)) return HPSCD_ERR_INVALID_ARG;
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return HPSCD_ERR_CUDA;
+  Plan P;
+  if ((rc = make_plan(ctx, dtype, layout, m, n, ld, opts, false, &P))) return rc;
+  if ((rc = ensure_ws(ctx, P.L.total))) return rc;
+  return solve_device(ctx, X, dtype, layout, m, n, ld, y, a, a_is_guess, opts, hist, sweeps_done,
+                      final_rel_res, P);
+}
+
+int hpscd_solve_host(hpscd_ctx* ctx, const void* X, int dtype, int layout, int64_t m,
+                     int64_t n, int64_t ld, const float* y, float* a, int a_is_guess,
+                     const hpscd_opts* opts, double* hist, int64_t* sweeps_done,
+                     double* final_rel_res) {
+  if (!ctx) return HPSCD_ERR_INVALID_ARG;
+  int rc = check_opts(opts);
+  if (rc) return rc;
+  if ((rc = check_shape(dtype, layout, m, n, ld))) return rc;
+  if ((m > 0 && n > 0 && !X) || (m > 0 && !y) || (n > 0 && !a)) return HPSCD_ERR_INVALID_ARG;
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return HPSCD_ERR_CUDA;
+  Plan P;
+  if ((rc = make_plan(ctx, dtype, layout, m, n, ld, opts, true, &P))) return rc;
+  if ((rc = ensure_ws(ctx, P.L.total))) return rc;
+  char* ws = static_cast<char*>(ctx->ws);
+  void* Xd = ws + P.L.xcopy;
+  float* yd = reinterpret_cast<float*>(ws + P.L.ycopy);
+  float* ad = reinterpret_cast<float*>(ws + P.L.acopy);
+  cudaStream_t st = ctx->stream;
+  const size_t xbytes = layout == HPSCD_COL_MAJOR ? (size_t)n * ld * esize(dtype)
+                                                  : (size_t)m * ld * esize(dtype);
+  if (xbytes && cudaMemcpyAsync(Xd, X, xbytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
+    return HPSCD_ERR_CUDA;
+  if (m > 0 && cudaMemcpyAsync(yd, y, (size_t)m * sizeof(float), cudaMemcpyHostToDevice, st) != cudaSuccess)
+    return HPSCD_ERR_CUDA;
+  if (n > 0 && a_is_guess &&
+      cudaMemcpyAsync(ad, a, (size_t)n * sizeof(float), cudaMemcpyHostToDevice, st) != cudaSuccess)
+    return HPSCD_ERR_CUDA;
+  rc = solve_device(ctx, Xd, dtype, layout, m, n, ld, yd, ad, a_is_guess, opts, hist, sweeps_done,
+                    final_rel_res, P);
+  if (rc == HPSCD_ERR_CUDA || rc == HPSCD_ERR_INVALID_ARG || rc == HPSCD_ERR_UNSUPPORTED) return rc;
+  if (n > 0 && cudaMemcpyAsync(a, ad, (size_t)n * sizeof(float), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return HPSCD_ERR_CUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return HPSCD_ERR_CUDA;
+  return rc;
+}
+
+int hpscd_last_timing(hpscd_ctx* ctx, hpscd_timing* out) {
+  if (!ctx || !out) return HPSCD_ERR_INVALID_ARG;
+  *out = ctx->last;
+  return HPSCD_OK;
+}
+
+const char* hpscd_status_string(int status) {
+  switch (status) {
+    case HPSCD_OK: return "ok";
+    case HPSCD_ERR_INVALID_ARG: return "invalid argument";
+    case HPSCD_ERR_NOT_CONVERGED: return "not converged within max_sweeps";
+    case HPSCD_ERR_NONFINITE: return "non-finite residual";
+    case HPSCD_ERR_TIMEOUT: return "device-side wait timed out";
+    case HPSCD_ERR_CUDA: return "CUDA runtime error";
+    case HPSCD_ERR_UNSUPPORTED: return "unsupported shape/layout/dtype";
+    case HPSCD_ERR_NO_MEMORY: return "out of workspace memory";
+    default: return "unknown status";
+  }
+}
+
+}  // extern "C"

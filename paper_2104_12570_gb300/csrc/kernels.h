@@ -1,0 +1,61 @@
+// Internal launch interface between the C-ABI layer and the CUDA kernels.
+#pragma once
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace hpscd {
+
+// ---- Gram set-up: G = X^T X (lower triangle incl. diagonal), G_jj = <X_j, X_j> ----
+struct GramPlan {
+  int npad;         // padded column count (multiple of 64)
+  int ntile;        // lower-triangular 64x64 tiles
+  int ksplit;       // row splits
+  int64_t rows_per_split;
+  size_t partial_bytes;  // float64 partial tiles
+};
+GramPlan gram_plan(int64_t m, int npad, int sms);
+cudaError_t launch_gram(const void* X, int dtype, int64_t m, int n, int64_t ld, const GramPlan& gp,
+                        double* partial, float* G, int ldG, cudaStream_t stream);
+
+// ---- persistent tall sweep (column-major X, n <= 512) ----
+constexpr int MODE_COPY = 0, MODE_NORMAL = 1, MODE_REFRESH = 2;
+
+struct TallParams {
+  const void* X;
+  int64_t m;
+  int n;
+  int64_t ld;
+  const float* y;
+  float* e;
+  float* a_out;
+  const float* a_in;
+  int warm;
+  const float* G;  // row-major, leading dimension ldG, lower triangle used
+  int ldG;
+  float* gpart;    // [2][grid][npad]
+  double* npart;   // [2][grid]
+  double* ypart;   // [grid]
+  double* hist;    // [max_sweeps + 1]
+  GridCtl* ctl;
+  double tol;
+  int64_t max_sweeps;
+  int stop_rule;
+  int refresh_every;
+  int64_t ntiles;
+  int nstages;
+  int use_tma;
+  uint64_t timeout_ns;
+  int stall_barrier;  // test hook: first barrier waits for one arrival too many
+};
+
+struct TallConfig {
+  int cpw, rpl, npad, rows, stage_bytes, box_cols, nstages, smem_bytes, threads;
+};
+bool tall_config(int dtype, int n, int max_smem, TallConfig* cfg);
+cudaError_t launch_tall_sweep(int dtype, const TallConfig& cfg, const CUtensorMap* tmap,
+                              const TallParams& p, int grid, cudaStream_t stream);
+
+}  // namespace hpscd

@@ -1,0 +1,66 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every function
+that include/*.h declares (no GPU needed)."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+import paper_2104_12570_gb300 as hp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        for mt in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(hpscd_\w+)\s*\(", src, re.M):
+            names.add(mt.group(1))
+    return sorted(names)
+
+
+def test_header_declares_the_entry_points():
+    names = declared_functions()
+    for must in ("hpscd_create", "hpscd_destroy", "hpscd_solve", "hpscd_solve_host",
+                 "hpscd_status_string", "hpscd_workspace_size", "hpscd_set_workspace"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = hp.load()
+    for name in declared_functions():
+        assert hasattr(lib, name), f"{name} declared but not exported"
+        assert name in hp.SIGNATURES, f"{name} has no Python binding"
+
+
+def test_library_is_built_for_sm_103a_only():
+    path = hp.lib_path()
+    data = open(path, "rb").read()
+    assert b"sm_103a" in data or b"sm_103" in data
+
+
+def test_status_strings_and_null_context():
+    lib = hp.load()
+    assert lib.hpscd_status_string(0) == b"ok"
+    assert lib.hpscd_status_string(2).startswith(b"not converged")
+    assert lib.hpscd_status_string(99) == b"unknown status"
+    o = hp.make_opts()
+    rc = lib.hpscd_solve(None, None, 0, 0, 10, 10, 10, None, None, 0, ctypes.byref(o), None,
+                         None, None)
+    assert rc == 1
+    assert lib.hpscd_destroy(None) == 0
+
+
+def test_layout_detection():
+    import numpy as np
+    Xc = np.zeros((5, 7), dtype=np.float32).T  # (7, 5) logical, column-major
+    _, dt, lay, m, n, ld = hp._describe(Xc)
+    assert (dt, lay, m, n, ld) == (hp.F32, hp.COL, 7, 5, 7)
+    Xr = np.zeros((7, 5), dtype=np.uint16)
+    _, dt, lay, m, n, ld = hp._describe(Xr)
+    assert (dt, lay, m, n, ld) == (hp.BF16, hp.ROW, 7, 5, 5)
+    with pytest.raises(TypeError):
+        hp._describe(np.zeros((3, 3), dtype=np.float64))

@@ -1,0 +1,214 @@
+"""Parity of the CUDA tall sweep (column-major X, n <= 512) with the float64
+CPU oracle of Algorithm 1, through the C ABI.
+
+Tolerance (BASELINE): relative coefficient error <= 1e-5 for float32 arithmetic
+against the oracle at the same sweep count, and <= 1e-3 for bfloat16 storage
+(the oracle solves the same bfloat16-valued system, so storage rounding is not
+part of the error; the GPU's float32 accumulation is).
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2104_12570_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2104_12570_gb300 as hp  # noqa: E402
+
+RTOL_F32 = 1e-5
+RTOL_BF16 = 1e-3
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = hp.Context(0)
+    yield c
+    c.close()
+
+
+def to_gpu(s):
+    """synth.System -> (X logical (m, n) CUDA tensor with the system's layout, y)."""
+    if s.dtype == "bf16":
+        Xt = torch.from_numpy(s.X.view(np.int16)).view(torch.bfloat16)
+    else:
+        Xt = torch.from_numpy(np.ascontiguousarray(s.X, dtype=np.float32))
+    Xt = Xt.cuda()
+    X = Xt.T if s.layout == "col" else Xt
+    y = torch.from_numpy(np.asarray(s.y, dtype=np.float32)).cuda()
+    return X, y
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def oracle_same(s, sweeps, a0=None):
+    return oracle.solve_system(s, tol=0, max_sweeps=sweeps, stop="none", a0=a0)
+
+
+def test_hand_worked_example_exact(ctx):
+    g = json.load(open(os.path.join(GOLDEN, "hand_2x2.json")))
+    Xd = np.array(g["X_rows"], dtype=np.float32)
+    X = torch.from_numpy(np.ascontiguousarray(Xd.T)).cuda().T
+    y = torch.tensor(g["y"], dtype=torch.float32).cuda()
+    for rec in g["sweeps"]:
+        r = ctx.solve(X, y, tol=0, max_sweeps=rec["s"], stop="none")
+        assert r.status == "ok" and r.sweeps == rec["s"]
+        np.testing.assert_array_equal(r.a.cpu().numpy(), np.array(rec["a"], dtype=np.float32))
+        for s in range(rec["s"] + 1):
+            expect = 1.0 if s == 0 else np.sqrt(0.4) * 2.0 ** -s
+            assert r.hist[s] == pytest.approx(expect, rel=1e-14)
+
+
+@pytest.mark.parametrize("m,n", [(200, 50), (1000, 37), (777, 5), (64, 1), (3, 3), (5000, 300),
+                                 (4099, 512), (100_000, 64), (33, 129)])
+def test_equal_sweeps_matches_oracle(ctx, m, n):
+    s = synth.make_system(m, n, seed=m + n, noise=0.05)
+    X, y = to_gpu(s)
+    for sweeps in (1, 3, 8):
+        r = ctx.solve(X, y, tol=0, max_sweeps=sweeps, stop="none")
+        o = oracle_same(s, sweeps)
+        assert r.sweeps == sweeps
+        assert rel(r.a.cpu().numpy(), o.a) <= RTOL_F32, (sweeps, rel(r.a.cpu().numpy(), o.a))
+        np.testing.assert_allclose(r.hist, o.hist, rtol=1e-5)
+
+
+def test_converges_on_consistent_tall(ctx):
+    s = synth.make_system(200, 50, seed=0)
+    X, y = to_gpu(s)
+    r = ctx.solve(X, y, tol=1e-6, max_sweeps=200, stop="rel_res")
+    assert r.status == "ok" and r.rel_res <= 1e-6
+    o = oracle_same(s, r.sweeps)
+    assert rel(r.a.cpu().numpy(), o.a) <= RTOL_F32
+    # the true residual of the GPU's a, recomputed by the oracle, meets the tolerance
+    _, nrm = oracle.residual(s.X, s.y, r.a.cpu().numpy(), m=s.m, n=s.n)
+    assert nrm / np.linalg.norm(s.y.astype(np.float64)) <= 1.5e-6
+    assert rel(r.a.cpu().numpy(), s.a_true) <= 1e-5
+
+
+def test_bf16_storage_matches_oracle(ctx):
+    s = synth.make_system(20_000, 100, seed=3, dtype="bf16")
+    X, y = to_gpu(s)
+    r = ctx.solve(X, y, tol=1e-6, max_sweeps=100, stop="rel_res")
+    assert r.status == "ok"
+    o = oracle_same(s, r.sweeps)
+    assert rel(r.a.cpu().numpy(), o.a) <= RTOL_BF16
+    assert rel(r.a.cpu().numpy(), o.a) <= 1e-5  # the storage is exact: f32 arithmetic only
+
+
+def test_unaligned_leading_dimension_uses_plain_loads(ctx):
+    m, n = 1001, 17
+    s = synth.make_system(m, n, seed=4)
+    buf = np.zeros((n, m + 1), dtype=np.float32)
+    buf[:, :m] = s.X
+    Xt = torch.from_numpy(buf).cuda()
+    X = Xt[:, :m].T  # stride (1, m + 1): ld*4 not a multiple of 16
+    assert X.stride() == (1, m + 1)
+    y = torch.from_numpy(s.y).cuda()
+    r = ctx.solve(X, y, tol=0, max_sweeps=4, stop="none")
+    o = oracle_same(s, 4)
+    assert rel(r.a.cpu().numpy(), o.a) <= RTOL_F32
+
+
+def test_warm_start_matches_oracle(ctx):
+    s = synth.make_system(3000, 40, seed=5)
+    a0 = (s.a_true + 0.01 * np.random.default_rng(0).standard_normal(40)).astype(np.float32)
+    X, y = to_gpu(s)
+    r = ctx.solve(X, y, tol=0, max_sweeps=2, stop="none", a0=torch.from_numpy(a0).cuda())
+    o = oracle_same(s, 2, a0=a0.astype(np.float64))
+    assert rel(r.a.cpu().numpy(), o.a) <= RTOL_F32
+    np.testing.assert_allclose(r.hist, o.hist, rtol=1e-4)
+    cold = ctx.solve(X, y, tol=1e-6, max_sweeps=100, stop="rel_res")
+    warm = ctx.solve(X, y, tol=1e-6, max_sweeps=100, stop="rel_res", a0=torch.from_numpy(a0).cuda())
+    assert warm.sweeps < cold.sweeps
+
+
+def test_refresh_passes_match_oracle(ctx):
+    s = synth.make_system(50_000, 128, seed=6, dtype="bf16")
+    X, y = to_gpu(s)
+    r = ctx.solve(X, y, tol=1e-6, max_sweeps=50, stop="rel_res", refresh_every=2)
+    assert r.status == "ok"
+    o = oracle_same(s, r.sweeps)
+    assert rel(r.a.cpu().numpy(), o.a) <= 1e-5
+    _, nrm = oracle.residual(s.X, s.y, r.a.cpu().numpy(), m=s.m, n=s.n, dtype="bf16")
+    assert nrm / np.linalg.norm(s.y.astype(np.float64)) <= 1.1e-6
+
+
+def test_zero_column_is_skipped(ctx):
+    s = synth.make_system(500, 9, seed=7)
+    s.X[4, :] = 0.0
+    s.y = (s.dense_f64() @ s.a_true).astype(np.float32)
+    X, y = to_gpu(s)
+    r = ctx.solve(X, y, tol=0, max_sweeps=6, stop="none")
+    a = r.a.cpu().numpy()
+    assert a[4] == 0.0 and np.all(np.isfinite(a))
+    assert rel(a, oracle_same(s, 6).a) <= RTOL_F32
+
+
+def test_stopping_rules_follow_oracle(ctx):
+    s = synth.make_system(20_000, 64, seed=8, noise=0.01)
+    X, y = to_gpu(s)
+    r = ctx.solve(X, y, tol=1e-7, max_sweeps=100, stop="rel_change")
+    o = oracle.solve_system(s, tol=1e-7, max_sweeps=100, stop="rel_change")
+    assert r.status == "ok" and abs(r.sweeps - o.sweeps) <= 1
+    h = r.hist
+    assert abs(h[-2] - h[-1]) < 1e-7 * h[-2]
+    nc = ctx.solve(X, y, tol=1e-9, max_sweeps=2, stop="rel_res")
+    assert nc.status == "not_converged" and nc.sweeps == 2
+
+
+def test_degenerate_shapes(ctx):
+    y = torch.ones(10, device="cuda")
+    X = torch.zeros(10, 0, device="cuda")
+    r = ctx.solve(X, y, tol=1e-6, max_sweeps=3, stop="rel_res")
+    assert r.status == "not_converged" and np.allclose(r.hist, 1.0)
+    X = torch.zeros(0, 4, device="cuda")
+    r = ctx.solve(X, torch.zeros(0, device="cuda"), tol=1e-6, max_sweeps=3, stop="rel_res")
+    assert r.status == "ok" and r.sweeps == 0 and np.all(r.a.cpu().numpy() == 0)
+    s = synth.make_system(100, 10, seed=9)
+    Xs, ys = to_gpu(s)
+    r = ctx.solve(Xs, ys, tol=0, max_sweeps=0, stop="none")
+    assert r.sweeps == 0 and r.hist[0] == pytest.approx(1.0)
+    with pytest.raises(hp.HpscdError):
+        ctx.solve(torch.zeros(10, 600, device="cuda").T.contiguous().T[:, :600], y)
+
+
+def test_barrier_timeout_returns_status_and_context_survives(ctx):
+    s = synth.make_system(20_000, 32, seed=10)
+    X, y = to_gpu(s)
+    ctx.set_timeout(0.2)
+    with pytest.raises(hp.HpscdError) as ei:
+        ctx.solve(X, y, tol=1e-6, max_sweeps=10, stop="rel_res", debug_flags=1)
+    assert ei.value.status == "timeout"
+    ctx.set_timeout(5.0)
+    r = ctx.solve(X, y, tol=1e-6, max_sweeps=50, stop="rel_res")
+    assert r.status == "ok"
+
+
+def test_host_entry_point_end_to_end(ctx):
+    s = synth.make_system(4000, 48, seed=11)
+    r = ctx.solve_host(s.X.T, s.y, tol=0, max_sweeps=3, stop="none")
+    assert rel(r.a, oracle_same(s, 3).a) <= RTOL_F32
+
+
+@pytest.mark.slow
+def test_full_size_tall_1Mx256(ctx):
+    """The 1,000,000 x 256 float32 noisy least-squares workload, in the launch
+    configuration the benchmark times, against the oracle at equal sweeps."""
+    s = synth.workload("tall_1Mx256_f32")
+    X, y = to_gpu(s)
+    r = ctx.solve(X, y, tol=1e-7, max_sweeps=50, stop="rel_change")
+    assert r.status == "ok"
+    o = oracle_same(s, r.sweeps)
+    assert rel(r.a.cpu().numpy(), o.a) <= RTOL_F32
+    np.testing.assert_allclose(r.hist, o.hist, rtol=1e-5)
+    assert r.timing["grid"] >= 1
