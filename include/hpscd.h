@@ -150,6 +150,17 @@ int hpscd_solve_host(hpscd_ctx* ctx, const void* X, int dtype, int layout, int64
 /* Timings of the last solve on this context. */
 int hpscd_last_timing(hpscd_ctx* ctx, hpscd_timing* out);
 
+/* Device-side phase trace of the persistent sweep (tracing; off by default).
+ * max_passes > 0 enables it for the next solves (device memory is allocated
+ * here, not in the solve); 0 disables it.  After a solve, hpscd_get_trace
+ * copies to the host, for pass p < max_passes, six %globaltimer stamps (ns)
+ * taken by CTA 0: [6p+0] pass start, [6p+1] end of its streaming, [6p+2] grid
+ * barrier passed, [6p+3] partial sums reduced and g formed, [6p+5] forward
+ * substitution done ([6p+4] is unused; unused fields stay 0); then, at
+ * [6·max_passes + b], the time CTA b finished streaming in pass 1. */
+int hpscd_set_trace(hpscd_ctx* ctx, int max_passes);
+int hpscd_get_trace(hpscd_ctx* ctx, unsigned long long* out, int64_t words, int64_t* written);
+
 /* Static description of a status code. */
 const char* hpscd_status_string(int status);
 

@@ -71,6 +71,9 @@ SIGNATURES = {
                           ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)],
                          ctypes.c_int),
     "hpscd_last_timing": ([ctypes.c_void_p, ctypes.POINTER(Timing)], ctypes.c_int),
+    "hpscd_set_trace": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
+    "hpscd_get_trace": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_ulonglong), ctypes.c_int64,
+                         ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
     "hpscd_status_string": ([ctypes.c_int], ctypes.c_char_p),
 }
 
@@ -203,6 +206,38 @@ class Context:
             self.close()
         except Exception:
             pass
+
+    def set_trace(self, max_passes: int):
+        rc = self._lib.hpscd_set_trace(self._h, int(max_passes))
+        if rc:
+            raise HpscdError(rc)
+        self._trace_passes = int(max_passes)
+
+    def trace(self) -> dict:
+        """Phase durations (us) per pass of the last solve, and the spread of the
+        CTAs' end-of-streaming times in pass 1."""
+        P = getattr(self, "_trace_passes", 0)
+        if not P:
+            return {}
+        buf = (ctypes.c_ulonglong * (P * 6 + 4096))()
+        got = ctypes.c_int64(0)
+        rc = self._lib.hpscd_get_trace(self._h, buf, P * 6 + 4096, ctypes.byref(got))
+        if rc:
+            raise HpscdError(rc)
+        a = np.frombuffer(buf, dtype=np.uint64)[: got.value].astype(np.int64)
+        phases = a[: P * 6].reshape(P, 6)
+        rows = []
+        for r in phases:
+            if r[0] == 0:
+                break
+            def dt(a, b):
+                return (r[b] - r[a]) / 1e3 if r[a] and r[b] else None
+            rows.append({"stream_us": dt(0, 1), "barrier_us": dt(1, 2), "reduce_us": dt(2, 3),
+                         "subst_us": dt(3, 5)})
+        ends = a[P * 6:]
+        ends = ends[ends > 0]
+        spread = float((ends.max() - ends.min()) / 1e3) if ends.size else None
+        return {"passes": rows, "pass1_stream_end_spread_us": spread}
 
     def timing(self) -> dict:
         t = Timing()

@@ -142,6 +142,62 @@ __device__ __forceinline__ bool grid_barrier(GridCtl* ctl, unsigned expected, ui
   return ok;
 }
 
+// Named CTA barrier over the first `nthreads` threads (barrier id 1), for
+// kernels where a producer warp does not take part in the compute barriers.
+__device__ __forceinline__ void named_sync(int nthreads) {
+  asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
+}
+__device__ __forceinline__ int named_sync_or(int nthreads, int pred) {
+  int r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "setp.ne.s32 p, %1, 0;\n\t"
+      "bar.red.or.pred q, 1, %2, p;\n\t"
+      "selp.s32 %0, 1, 0, q;\n\t}"
+      : "=r"(r)
+      : "r"(pred), "r"(nthreads)
+      : "memory");
+  return r;
+}
+
+// grid_barrier for kernels whose compute threads are the first `nthreads`
+// of the CTA (named barrier 1 instead of __syncthreads).
+__device__ __forceinline__ bool grid_barrier_named(GridCtl* ctl, unsigned expected,
+                                                   uint64_t timeout_ns, int nthreads,
+                                                   int* s_fail) {
+  named_sync(nthreads);
+  if (threadIdx.x == 0) {
+    int fail = 0;
+    const unsigned g = ld_acquire_u32(&ctl->gen);
+    __threadfence();
+    const unsigned prev = atomicAdd(&ctl->arrive, 1u);
+    if (prev == expected - 1) {
+      atomicExch(&ctl->arrive, 0u);
+      __threadfence();
+      st_release_u32(&ctl->gen, g + 1);
+    } else {
+      const uint64_t t0 = global_timer_ns();
+      for (uint32_t it = 0;; ++it) {
+        if (ld_acquire_u32(&ctl->gen) != g) break;
+        if ((it & 15) == 15) {
+          if (*((volatile int*)&ctl->err) != DEV_OK) { fail = 1; break; }
+          if (global_timer_ns() - t0 > timeout_ns || it > (1u << 30)) {
+            atomicCAS(&ctl->err, DEV_OK, (int)DEV_TIMEOUT_BARRIER);
+            fail = 1;
+            break;
+          }
+          __nanosleep(32);
+        }
+      }
+    }
+    *s_fail = fail;
+  }
+  named_sync(nthreads);
+  const bool ok = (*((volatile int*)s_fail) == 0);
+  named_sync(nthreads);
+  return ok;
+}
+
 __device__ __forceinline__ float bf16_bits_to_float(uint16_t b) {
   return __uint_as_float(static_cast<uint32_t>(b) << 16);
 }

@@ -94,23 +94,20 @@ __global__ void __launch_bounds__(256) gram_partial_kernel(const T* __restrict__
     for (int j = 0; j < 4; ++j) out[(ty * 4 + i) * GT + tx * 4 + j] = acc64[i][j] + (double)acc[i][j];
 }
 
-// G[i][j] (i >= j) = sum over splits (fixed order) of the partial tiles; other entries 0.
+// G[i][j] = G[j][i] = sum over splits (fixed order) of the lower partial tiles.
 __global__ void gram_reduce_kernel(const double* __restrict__ partial, int ntile, int ksplit,
                                    int npad, float* __restrict__ G, int ldG) {
   const int64_t total = (int64_t)npad * npad;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
-    const int i = (int)(idx / npad), j = (int)(idx % npad);
-    float v = 0.f;
-    if (i >= j) {
-      const int I = i / GT, J = j / GT;
-      const int t = I * (I + 1) / 2 + J;
-      const int off = (i % GT) * GT + (j % GT);
-      double s = 0.0;
-      for (int k = 0; k < ksplit; ++k) s += partial[((size_t)k * ntile + t) * (GT * GT) + off];
-      v = (float)s;
-    }
-    G[(int64_t)i * ldG + j] = v;
+    const int i0 = (int)(idx / npad), j0 = (int)(idx % npad);
+    const int i = i0 >= j0 ? i0 : j0, j = i0 >= j0 ? j0 : i0;  // G is symmetric
+    const int I = i / GT, J = j / GT;
+    const int t = I * (I + 1) / 2 + J;
+    const int off = (i % GT) * GT + (j % GT);
+    double s = 0.0;
+    for (int k = 0; k < ksplit; ++k) s += partial[((size_t)k * ntile + t) * (GT * GT) + off];
+    G[(int64_t)i0 * ldG + j0] = (float)s;
   }
 }
 

@@ -23,6 +23,9 @@ struct hpscd_ctx {
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
   GridCtl* ctl_host = nullptr;  // pinned
   hpscd_timing last{};
+  int trace_passes = 0;                  // 0: tracing off
+  unsigned long long* trace_dev = nullptr;
+  int trace_grid = 0;
   PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
 };
 
@@ -44,7 +47,7 @@ struct DeviceGuard {
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 struct Layout {
-  size_t G = 0, partial = 0, e = 0, gpart = 0, npart = 0, ypart = 0, hist = 0, ctl = 0;
+  size_t G = 0, partial = 0, e = 0, gpart = 0, npart = 0, gw = 0, ypart = 0, hist = 0, ctl = 0;
   size_t xcopy = 0, ycopy = 0, acopy = 0, total = 0;
 };
 
@@ -53,6 +56,7 @@ struct Plan {
   GramPlan gp;
   int64_t ntiles = 0;
   int grid = 0;
+  int gstride = 0;
   Layout L;
 };
 
@@ -88,7 +92,7 @@ int make_plan(const hpscd_ctx* ctx, int dtype, int layout, int64_t m, int64_t n,
   if (!tall_config(dtype, (int)n, ctx->max_smem, &P->cfg)) return HPSCD_ERR_UNSUPPORTED;
   P->gp = gram_plan(m, P->cfg.npad, ctx->sms);
   P->ntiles = (m + P->cfg.rows - 1) / P->cfg.rows;
-  int64_t grid = ctx->sms;
+  int64_t grid = ctx->sms > 256 ? 256 : ctx->sms;  // the kernel's norm reduction covers 256 CTAs
   if (P->ntiles < grid) grid = P->ntiles;
   if (grid < 1) grid = 1;
   P->grid = (int)grid;
@@ -102,8 +106,10 @@ int make_plan(const hpscd_ctx* ctx, int dtype, int layout, int64_t m, int64_t n,
   L.G = take((size_t)P->gp.npad * P->gp.npad * sizeof(float));
   L.partial = take(P->gp.partial_bytes);
   L.e = take((size_t)(m > 0 ? m : 1) * sizeof(float));
-  L.gpart = take((size_t)2 * P->grid * P->cfg.npad * sizeof(float));
+  P->gstride = (P->grid + 3) / 4 * 4;
+  L.gpart = take((size_t)2 * P->gstride * P->cfg.npad * sizeof(float));
   L.npart = take((size_t)2 * P->grid * sizeof(double));
+  L.gw = take((size_t)2 * P->cfg.npad * sizeof(float));
   L.ypart = take((size_t)P->grid * sizeof(double));
   L.hist = take((size_t)(o->max_sweeps + 1) * sizeof(double));
   L.ctl = take(sizeof(GridCtl));
@@ -188,6 +194,9 @@ int solve_device(hpscd_ctx* ctx, const void* X, int dtype, int layout, int64_t m
                   P.gp.npad, st) != cudaSuccess)
     return HPSCD_ERR_CUDA;
   if (cudaMemsetAsync(ctl, 0, sizeof(GridCtl), st) != cudaSuccess) return HPSCD_ERR_CUDA;
+  if (cudaMemsetAsync(ws + L.gpart, 0, (size_t)2 * P.gstride * P.cfg.npad * sizeof(float), st) !=
+      cudaSuccess)
+    return HPSCD_ERR_CUDA;
   if (cudaEventRecord(ctx->ev[1], st) != cudaSuccess) return HPSCD_ERR_CUDA;
 
   CUtensorMap map;
@@ -207,7 +216,9 @@ int solve_device(hpscd_ctx* ctx, const void* X, int dtype, int layout, int64_t m
   p.G = G;
   p.ldG = P.gp.npad;
   p.gpart = reinterpret_cast<float*>(ws + L.gpart);
+  p.gstride = P.gstride;
   p.npart = reinterpret_cast<double*>(ws + L.npart);
+  p.gw = reinterpret_cast<float*>(ws + L.gw);
   p.ypart = reinterpret_cast<double*>(ws + L.ypart);
   p.hist = reinterpret_cast<double*>(ws + L.hist);
   p.ctl = ctl;
@@ -220,6 +231,16 @@ int solve_device(hpscd_ctx* ctx, const void* X, int dtype, int layout, int64_t m
   p.use_tma = use_tma;
   p.timeout_ns = (uint64_t)(ctx->timeout_s * 1e9);
   p.stall_barrier = (o->debug_flags & HPSCD_DEBUG_STALL_BARRIER) ? 1 : 0;
+  p.trace = nullptr;
+  p.trace_passes = 0;
+  if (ctx->trace_passes > 0 && ctx->trace_dev) {
+    const size_t words = (size_t)ctx->trace_passes * 6 + (size_t)P.grid;
+    if (cudaMemsetAsync(ctx->trace_dev, 0, words * sizeof(unsigned long long), st) != cudaSuccess)
+      return HPSCD_ERR_CUDA;
+    p.trace = ctx->trace_dev;
+    p.trace_passes = ctx->trace_passes;
+    ctx->trace_grid = P.grid;
+  }
   if (launch_tall_sweep(dtype, P.cfg, &map, p, P.grid, st) != cudaSuccess) {
     cudaGetLastError();
     return HPSCD_ERR_CUDA;
@@ -299,6 +320,7 @@ int hpscd_destroy(hpscd_ctx* ctx) {
   for (int i = 0; i < 3; ++i)
     if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
   if (ctx->ctl_host) cudaFreeHost(ctx->ctl_host);
+  if (ctx->trace_dev) cudaFree(ctx->trace_dev);
   delete ctx;
   return HPSCD_OK;
 }
@@ -392,6 +414,39 @@ int hpscd_solve_host(hpscd_ctx* ctx, const void* X, int dtype, int layout, int64
     return HPSCD_ERR_CUDA;
   if (cudaStreamSynchronize(st) != cudaSuccess) return HPSCD_ERR_CUDA;
   return rc;
+}
+
+int hpscd_set_trace(hpscd_ctx* ctx, int max_passes) {
+  if (!ctx || max_passes < 0 || max_passes > 65536) return HPSCD_ERR_INVALID_ARG;
+  DeviceGuard g(ctx->device);
+  if (ctx->trace_dev) {
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    cudaFree(ctx->trace_dev);
+    ctx->trace_dev = nullptr;
+  }
+  ctx->trace_passes = 0;
+  if (max_passes == 0) return HPSCD_OK;
+  const size_t words = (size_t)max_passes * 6 + 4096;
+  if (cudaMalloc(&ctx->trace_dev, words * sizeof(unsigned long long)) != cudaSuccess) {
+    cudaGetLastError();
+    ctx->trace_dev = nullptr;
+    return HPSCD_ERR_NO_MEMORY;
+  }
+  ctx->trace_passes = max_passes;
+  return HPSCD_OK;
+}
+
+int hpscd_get_trace(hpscd_ctx* ctx, unsigned long long* out, int64_t words, int64_t* written) {
+  if (!ctx || !out || words < 0) return HPSCD_ERR_INVALID_ARG;
+  if (!ctx->trace_dev) { if (written) *written = 0; return HPSCD_OK; }
+  DeviceGuard g(ctx->device);
+  int64_t avail = (int64_t)ctx->trace_passes * 6 + ctx->trace_grid;
+  if (words < avail) avail = words;
+  if (cudaMemcpy(out, ctx->trace_dev, (size_t)avail * sizeof(unsigned long long),
+                 cudaMemcpyDeviceToHost) != cudaSuccess)
+    return HPSCD_ERR_CUDA;
+  if (written) *written = avail;
+  return HPSCD_OK;
 }
 
 int hpscd_last_timing(hpscd_ctx* ctx, hpscd_timing* out) {

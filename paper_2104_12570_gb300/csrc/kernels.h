@@ -35,8 +35,10 @@ struct TallParams {
   int warm;
   const float* G;  // row-major, leading dimension ldG, lower triangle used
   int ldG;
-  float* gpart;    // [2][grid][npad]
+  float* gpart;    // [2][npad][gstride], zero-filled by the host
+  int gstride;     // grid rounded up to a multiple of 4
   double* npart;   // [2][grid]
+  float* gw;       // [2][npad]: G·w rows published by the CTAs
   double* ypart;   // [grid]
   double* hist;    // [max_sweeps + 1]
   GridCtl* ctl;
@@ -44,15 +46,19 @@ struct TallParams {
   int64_t max_sweeps;
   int stop_rule;
   int refresh_every;
-  int64_t ntiles;
+  int64_t ntiles;  // 128-row panels
   int nstages;
   int use_tma;
   uint64_t timeout_ns;
   int stall_barrier;  // test hook: first barrier waits for one arrival too many
+  unsigned long long* trace;  // optional: per-pass phase timestamps (see hpscd_trace)
+  int trace_passes;           // capacity of trace in passes
 };
 
 struct TallConfig {
-  int cpw, rpl, npad, rows, stage_bytes, box_cols, nstages, smem_bytes, threads;
+  int cpw;   // columns per warp per chunk (CW)
+  int rpl;   // chunks per 128-row panel (NCH)
+  int npad, rows, stage_bytes, box_cols, nstages, smem_bytes, threads;
 };
 bool tall_config(int dtype, int n, int max_smem, TallConfig* cfg);
 cudaError_t launch_tall_sweep(int dtype, const TallConfig& cfg, const CUtensorMap* tmap,

@@ -2,79 +2,47 @@
 // (column-major X, n <= 512), one CTA per SM, cooperative launch.
 //
 // Algorithm 1 makes column j's step depend on the residual left by column
-// j-1, through a reduction over all m rows.  Writing e_s for the residual at
-// the start of sweep s and g = X^T e_s, Eq. ek1-ek gives, just before column
-// j of sweep s,
-//     <X_j, e> = g_j - sum_{l<j} <X_j, X_l> da_l,
-// so the whole sweep's steps follow from g and the lower triangle of
+// j-1, through a reduction over all m rows.  Writing e_s for the residual
+// after sweep s and g_s = X^T e_s, Eq. ek1-ek gives, just before column j of
+// sweep s+1,
+//     <X_j, e> = g_{s,j} - sum_{l<j} <X_j, X_l> da_l,
+// so the whole sweep's steps follow from g_s and the lower triangle of
 // G = X^T X by forward substitution, in the paper's column order:
-//     da_j = (g_j - sum_{l<j} G_jl da_l) / G_jj        (Eq. da2, the ⊘ step)
-// and then e_{s+1} = e_s - X·da (the n rank-1 corrections of the sweep,
-// Eq. ek1-ek) and a <- a + da.  In exact arithmetic this is Algorithm 1 step
-// for step; it lets one streaming pass over X per sweep carry all of the
-// sweep's dot products and rank-1 corrections:
+//     da_j = (g_{s,j} - sum_{l<j} G_jl da_l) / G_jj      (Eq. da2, the ⊘ step)
+// followed by e_{s+1} = e_s - X·da (the sweep's n rank-1 corrections, Eq.
+// ek1-ek) and a <- a + da.  In exact arithmetic this is Algorithm 1 step for
+// step.  One streaming pass over X per sweep carries all of the sweep's dot
+// products and rank-1 corrections:
 //
-//   pass p (one read of X):  e <- e - X·da_p   (or e <- y - X·a on a
-//                            true-residual pass), then g <- X^T e and
-//                            ||e||^2 (float64), tile by tile;
-//   grid barrier;            every CTA sums the per-CTA partials of g and
-//                            ||e||^2 in a fixed order (bitwise identical in
-//                            every CTA), records hist[p] = ||e||/||y||, tests
-//                            the stopping rule, and runs the forward
-//                            substitution to get da_{p+1}.
+//   pass p reads X once and, row panel by row panel, forms
+//       e_out = e_in - X·v        (v = da_p; on a true-residual pass
+//                                  e_out = y - X·a_p instead)
+//       h     = X^T e_in          (against the residual the pass starts from)
+//       ||e_out||^2 in float64;
+//   grid barrier; every CTA sums the per-CTA partials of h and ||e||^2 in a
+//   fixed order (bitwise identical in every CTA), records
+//   hist[p] = ||e_p|| / ||y||, tests the stopping rule, forms
+//       g_p = h - G·da_p          (= X^T e_p by Eq. ek1-ek)
+//   and runs the forward substitution for da_{p+1}.
+// Pass 0 starts from e_in = y (h = X^T y) with v = a_0 (or nothing).
 //
-// X streams through shared memory by TMA (cp.async.bulk.tensor, zero fill
-// past m and n) in tiles of R rows × all columns, nstages deep; each warp owns
-// CPW columns, each lane RPL consecutive rows.  Phase A forms per-warp row
-// partials of X·v, a cross-warp reduction gives the new e of the tile; phase
-// B accumulates the lane's partial X^T e in registers for the whole pass.
+// Taking the dots against e_in rather than e_out makes the two halves of a
+// pass independent, so X streams through shared memory by TMA in chunks of
+// 128 rows × C columns (512 contiguous bytes per column for float32; TMA
+// zero-fills past m and n) with a full/empty mbarrier pair per stage and one
+// CTA barrier per 128-row panel.  Each warp owns C/16 columns of every chunk
+// and each lane 4 consecutive rows: the lane keeps its partial X^T e for its
+// columns in registers for the whole pass, and its partial row sums of X·v
+// for the panel, which a cross-warp reduction turns into the panel's e_out.
 #include "kernels.h"
 
 namespace hpscd {
 
 namespace {
 
-constexpr int NW = 16;
-constexpr int NT = NW * 32;
-
-template <typename T, int RPL>
-struct RowLoad;
-template <>
-struct RowLoad<float, 1> {
-  __device__ static void load(const float* p, float (&v)[1]) { v[0] = *p; }
-};
-template <>
-struct RowLoad<float, 2> {
-  __device__ static void load(const float* p, float (&v)[2]) {
-    const float2 t = *reinterpret_cast<const float2*>(p);
-    v[0] = t.x; v[1] = t.y;
-  }
-};
-template <>
-struct RowLoad<float, 4> {
-  __device__ static void load(const float* p, float (&v)[4]) {
-    const float4 t = *reinterpret_cast<const float4*>(p);
-    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
-  }
-};
-template <>
-struct RowLoad<uint16_t, 2> {
-  __device__ static void load(const uint16_t* p, float (&v)[2]) {
-    const uint32_t t = *reinterpret_cast<const uint32_t*>(p);
-    v[0] = __uint_as_float(t << 16);
-    v[1] = __uint_as_float(t & 0xffff0000u);
-  }
-};
-template <>
-struct RowLoad<uint16_t, 4> {
-  __device__ static void load(const uint16_t* p, float (&v)[4]) {
-    const uint2 t = *reinterpret_cast<const uint2*>(p);
-    v[0] = __uint_as_float(t.x << 16);
-    v[1] = __uint_as_float(t.x & 0xffff0000u);
-    v[2] = __uint_as_float(t.y << 16);
-    v[3] = __uint_as_float(t.y & 0xffff0000u);
-  }
-};
+constexpr int NW = 16;          // warps
+constexpr int NT = NW * 32;     // threads
+constexpr int DIAG_PACK = 32 * 31 / 2;  // strictly lower entries of a 32x32 block
 
 template <typename T>
 __device__ __forceinline__ T zero_elem();
@@ -83,26 +51,41 @@ __device__ __forceinline__ float zero_elem<float>() { return 0.f; }
 template <>
 __device__ __forceinline__ uint16_t zero_elem<uint16_t>() { return 0; }
 
+__device__ __forceinline__ void load_seg32(const float* __restrict__ src, float (&g)[32]) {
+  const float4* row = reinterpret_cast<const float4*>(src);
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const float4 t = __ldg(row + q);
+    g[4 * q] = t.x; g[4 * q + 1] = t.y; g[4 * q + 2] = t.z; g[4 * q + 3] = t.w;
+  }
+}
+
 // Forward substitution of one sweep (see the file comment):
 //   da_j = (r_j - sum_{l<j} G_jl da_l) / d_j, j = 0..n-1, da_j = 0 when d_j = 0.
-// Blocks of 32 columns: warp 0 solves the diagonal block with shuffles, then
-// every thread applies the block's contribution to one later row.
-// r (shared, in: g, overwritten), d and da are shared arrays of length npad.
+// Blocks of 32 columns.  Warp 0 solves each diagonal block with shuffles, one
+// IEEE division per column, reading the block's strictly lower triangle from
+// shared memory (diag_s, packed, staged once per launch); thread t >= 32 owns
+// row t and applies each finished block to it, loading its G segment for the
+// next block right after using the current one, so the load overlaps the
+// next block's solve.  r (in: g, overwritten), d and da are shared arrays of
+// length npad.
 __device__ void forward_substitution(const float* __restrict__ G, int ldG, int n, int npad,
-                                     float* r, const float* d, float* da) {
+                                     float* r, const float* d, float* da, const float* diag_s) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   for (int c = n + tid; c < npad; c += NT) da[c] = 0.f;
-  for (int b0 = 0; b0 < n; b0 += 32) {
+  if (n <= 0) { named_sync(NT); return; }
+  const int nb = (n + 31) / 32;
+  float seg[32];
+  if (tid >= 32 && tid < n) load_seg32(G + (int64_t)tid * ldG, seg);
+  named_sync(NT);  // r (written by the caller) is visible
+  for (int b = 0; b < nb; ++b) {
+    const int b0 = 32 * b;
     if (warp == 0) {
       const int i = b0 + lane;
-      float gl[32];
-      const float4* row = reinterpret_cast<const float4*>(G + (int64_t)i * ldG + b0);
+      // warp 0 never owns a trailing row: its seg holds the diagonal block's row
+      const float* dl = diag_s + b * DIAG_PACK + (lane * (lane - 1)) / 2;
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const float4 t = __ldg(row + q);
-        gl[4 * q] = t.x; gl[4 * q + 1] = t.y; gl[4 * q + 2] = t.z; gl[4 * q + 3] = t.w;
-      }
-      // lanes past n (and past npad when npad < 32) hold zeros and write nothing
+      for (int k = 0; k < 32; ++k) seg[k] = (k < lane) ? dl[k] : 0.f;
       float ri = (i < n) ? r[i] : 0.f;
       const float di = (i < n) ? d[i] : 0.f;
       float mine = 0.f;
@@ -112,25 +95,19 @@ __device__ void forward_substitution(const float* __restrict__ G, int ldG, int n
         if (lane == k) q = (di > 0.f) ? ri / di : 0.f;
         q = __shfl_sync(FULL_MASK, q, k);
         if (lane == k) mine = q;
-        if (lane > k) ri = fmaf(-gl[k], q, ri);
+        if (lane > k) ri = fmaf(-seg[k], q, ri);
       }
       if (i < npad) da[i] = mine;
     }
-    __syncthreads();
-    for (int i = b0 + 32 + tid; i < n; i += NT) {
-      const float4* row = reinterpret_cast<const float4*>(G + (int64_t)i * ldG + b0);
+    named_sync(NT);  // da of block b visible
+    if (tid >= 32 && tid < n && tid >= b0 + 32) {
       float acc = 0.f;
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const float4 t = __ldg(row + q);
-        acc = fmaf(t.x, da[b0 + 4 * q], acc);
-        acc = fmaf(t.y, da[b0 + 4 * q + 1], acc);
-        acc = fmaf(t.z, da[b0 + 4 * q + 2], acc);
-        acc = fmaf(t.w, da[b0 + 4 * q + 3], acc);
-      }
-      r[i] -= acc;
+      for (int k = 0; k < 32; ++k) acc = fmaf(seg[k], da[b0 + k], acc);
+      r[tid] -= acc;
+      if (tid >= b0 + 64) load_seg32(G + (int64_t)tid * ldG + b0 + 32, seg);
     }
-    __syncthreads();
+    named_sync(NT);  // r of block b+1 final
   }
 }
 
@@ -147,213 +124,374 @@ __device__ __forceinline__ void dot2_step(float x, float v, float& s, float& c) 
   c += err + pe;
 }
 
-template <typename T, int CPW, int RPL>
+template <typename T>
+struct Row4;
+template <>
+struct Row4<float> {
+  __device__ static void load(const float* p, float (&v)[4]) {
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+  }
+};
+template <>
+struct Row4<uint16_t> {
+  __device__ static void load(const uint16_t* p, float (&v)[4]) {
+    const uint2 t = *reinterpret_cast<const uint2*>(p);
+    v[0] = __uint_as_float(t.x << 16);
+    v[1] = __uint_as_float(t.x & 0xffff0000u);
+    v[2] = __uint_as_float(t.y << 16);
+    v[3] = __uint_as_float(t.y & 0xffff0000u);
+  }
+};
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+constexpr int PR = 128;  // rows per panel (and per chunk)
+constexpr int TRACE_FIELDS = 6;
+
+// Neumaier-compensated float32 accumulation: s + c carries the sum of the
+// added terms to about twice float32 precision, without float64 arithmetic
+// (float64 throughput is low on this part).
+__device__ __forceinline__ void comp_add(float x, float& s, float& c) {
+  const float t = s + x;
+  c += (fabsf(s) >= fabsf(x)) ? ((s - t) + x) : ((x - t) + s);
+  s = t;
+}
+
+// One chunk's work for one warp: lane partials of X^T e_in for the warp's
+// columns (phase B) and, unless the pass only copies y, the lane's partial row
+// sums of X·v (phase A; Dot2 pairs on a true-residual pass).
+template <int MODE, typename T, int CW, int CPW, bool VREG>
+__device__ __forceinline__ void chunk_compute(const T* __restrict__ st, int warp, int lane,
+                                              int ch, const float (&ein)[4],
+                                              float (&gacc)[CPW], const float (&vreg)[VREG ? CPW : 1],
+                                              const float* __restrict__ vsm, float (&ph)[4],
+                                              float (&pl)[4]) {
+  constexpr int C = NW * CW;
+#pragma unroll
+  for (int jj = 0; jj < CW; ++jj) {
+    const int j = ch * CW + jj;
+    float xv[4];
+    Row4<T>::load(st + (warp * CW + jj) * PR + 4 * lane, xv);
+#pragma unroll
+    for (int r = 0; r < 4; ++r) gacc[j] = fmaf(xv[r], ein[r], gacc[j]);
+    if constexpr (MODE != MODE_COPY) {
+      float vk;
+      if constexpr (VREG) vk = vreg[j];
+      else vk = vsm[ch * C + warp * CW + jj];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        if constexpr (MODE == MODE_NORMAL) ph[r] = fmaf(xv[r], vk, ph[r]);
+        else dot2_step(xv[r], vk, ph[r], pl[r]);
+      }
+    }
+  }
+}
+
+template <typename T, int CW, int NCH>
 __global__ void __launch_bounds__(NT, 1)
     tall_sweep_kernel(const __grid_constant__ CUtensorMap tmap, const TallParams p) {
-  constexpr int R = 32 * RPL;
-  constexpr int NPAD = NW * CPW;
-  constexpr int STAGE_ELEMS = R * NPAD;
-  constexpr int BOXC = NPAD < 256 ? NPAD : 256;
+  constexpr int C = NW * CW;          // columns per chunk
+  constexpr int NPAD = C * NCH;       // padded column count
+  constexpr int CPW = CW * NCH;       // columns per warp over a whole row
+  constexpr int CHUNK_ELEMS = PR * C;
+  constexpr bool V_IN_REGS = CPW <= 8;
 
   extern __shared__ unsigned char smem_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int nst = p.nstages;
   T* stages = reinterpret_cast<T*>(base);
-  float* red_hi = reinterpret_cast<float*>(base + (size_t)p.nstages * STAGE_ELEMS * sizeof(T));
-  float* red_lo = red_hi + NW * R;
-  float* etile = red_lo + NW * R;
-  float* rvec = etile + R;
+  float* red_hi = reinterpret_cast<float*>(base + (size_t)nst * CHUNK_ELEMS * sizeof(T));
+  float* red_lo = red_hi + 2 * NW * PR;  // [2][NW][PR] each
+  float* rvec = red_lo + 2 * NW * PR;
   float* da_s = rvec + NPAD;
   float* dd_s = da_s + NPAD;
-  double* a64_s = reinterpret_cast<double*>(dd_s + NPAD);
-  double* scal = a64_s + NPAD;  // [0]: ||e||^2 total, [1]: ||y||^2 total, [2..33]: scratch
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(scal + 40);
+  float* vsm = dd_s + NPAD;
+  double* a64_s = reinterpret_cast<double*>(vsm + NPAD);
+  double* scal = a64_s + NPAD;  // [0]: ||e||^2, [1]: ||y||^2, [2..33]: scratch
+  uint64_t* full = reinterpret_cast<uint64_t*>(scal + 40);
+  uint64_t* empty = full + 16;
+  int* flags = reinterpret_cast<int*>(empty + 16);  // [1]: grid barrier result
+  float* diag_s = reinterpret_cast<float*>(flags + 4);  // [max(1, NPAD/32)][DIAG_PACK]
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int grid = gridDim.x;
-  const int64_t t0 = p.ntiles * blockIdx.x / grid;
-  const int64_t t1 = p.ntiles * (blockIdx.x + 1) / grid;
-  const int64_t nt = t1 - t0;
-  const int nst = p.nstages;
+  const int gstride = p.gstride;
+  const int64_t npanels = p.ntiles;
+  const int64_t pn0 = npanels * blockIdx.x / grid;
+  const int64_t pn1 = npanels * (blockIdx.x + 1) / grid;
+  const int64_t npan = pn1 - pn0;
+  const uint64_t nchunk = (uint64_t)npan * NCH;  // chunks per pass
   const bool tma = p.use_tma != 0;
   const int64_t m = p.m;
   const int n = p.n;
 
-  if (tid == 0 && tma) {
-    for (int s = 0; s < nst; ++s) mbar_init(&mbar[s], 1);
-    fence_mbar_init();
+  if (tid == 0) {
+    if (tma) {
+      for (int s = 0; s < nst; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], NW); }
+      fence_mbar_init();
+    }
   }
   for (int c = tid; c < NPAD; c += NT) {
     a64_s[c] = (c < n && p.warm) ? (double)p.a_in[c] : 0.0;
     dd_s[c] = (c < n) ? p.G[(int64_t)c * p.ldG + c] : 0.f;
+    da_s[c] = 0.f;
+  }
+  for (int idx = tid; idx < ((n + 31) / 32) * DIAG_PACK; idx += NT) {
+    const int b = idx / DIAG_PACK, q = idx % DIAG_PACK;
+    int i = 1;
+    while ((i * (i + 1)) / 2 <= q) ++i;
+    const int k = q - (i * (i - 1)) / 2;
+    diag_s[idx] = p.G[(int64_t)(32 * b + i) * p.ldG + 32 * b + k];
   }
   __syncthreads();
 
-  uint64_t issued = 0, consumed = 0, waited = 0;
-  auto issue_next = [&]() {
-    const uint64_t seq = issued++;
-    const int s = (int)(seq % nst);
-    const int64_t tile = t0 + (int64_t)(seq % (uint64_t)nt);
-    T* dst = stages + (size_t)s * STAGE_ELEMS;
-    mbar_arrive_expect_tx(&mbar[s], STAGE_ELEMS * sizeof(T));
-#pragma unroll
-    for (int cb = 0; cb < NPAD; cb += BOXC)
-      tma_load_2d(dst + cb * R, &tmap, &mbar[s], (int32_t)(tile * R), cb);
+  // ---------------- TMA issue (thread 0) ----------------
+  // chunk sequence q = pass·nchunk + panel·NCH + ch, periodic over passes;
+  // stage q % nst.  The first nst chunks are issued up front; after the CTA
+  // barrier that ends chunk q, thread 0 issues chunk q + nst into its stage.
+  uint64_t issued = 0, waited = 0;
+  auto issue_chunk = [&](uint64_t k) {
+    const int s = (int)(k % nst);
+    const uint64_t kp = k % nchunk;
+    const int64_t panel = pn0 + (int64_t)(kp / NCH);
+    const int ch = (int)(kp % NCH);
+    fence_proxy_async_smem();
+    mbar_arrive_expect_tx(&full[s], CHUNK_ELEMS * sizeof(T));
+    tma_load_2d(stages + (size_t)s * CHUNK_ELEMS, &tmap, &full[s], (int32_t)(panel * PR), ch * C);
   };
-  if (tma && tid == 0)
-    for (int s = 0; s < nst; ++s) issue_next();
+  if (tma && tid == 0 && nchunk > 0)
+    while (issued < (uint64_t)nst) issue_chunk(issued++);
 
-  float v[CPW];
+  // ---------------- compute warps ----------------
+  for (int c = tid; c < NPAD; c += NT) vsm[c] = (float)a64_s[c];
+  named_sync(NT);
+  float v[V_IN_REGS ? CPW : 1];
+  if constexpr (V_IN_REGS) {
 #pragma unroll
-  for (int k = 0; k < CPW; ++k) v[k] = (float)a64_s[warp * CPW + k];
+    for (int j = 0; j < CPW; ++j) v[j] = vsm[(j / CW) * C + warp * CW + (j % CW)];
+  }
   float gacc[CPW];
 #pragma unroll
-  for (int k = 0; k < CPW; ++k) gacc[k] = 0.f;
+  for (int j = 0; j < CPW; ++j) gacc[j] = 0.f;
 
   int err = DEV_OK;
   int status = HPSCD_ERR_NOT_CONVERGED;
   double r_prev = 0.0, ynorm = 0.0;
   int64_t pass = 0, sweeps = 0;
+  uint64_t qbase = 0;
 
+  // optional trace: CTA 0 records, per pass, the global time at the start of
+  // the pass, end of streaming, end of the grid barrier, end of the partial-sum
+  // reduction, end of G·da and end of the forward substitution; every CTA
+  // records the end of its streaming in pass 1 (load balance).
+  unsigned long long* tr = (p.trace && blockIdx.x == 0 && tid == 0) ? p.trace : nullptr;
+  auto stamp = [&](int64_t ps, int k) {
+    if (tr && ps < p.trace_passes) tr[ps * TRACE_FIELDS + k] = global_timer_ns();
+  };
   for (pass = 0;; ++pass) {
+    stamp(pass, 0);
     const int mode = (pass == 0) ? (p.warm ? MODE_REFRESH : MODE_COPY)
                                  : ((p.refresh_every > 0 && pass % p.refresh_every == 0)
                                         ? MODE_REFRESH
                                         : MODE_NORMAL);
+    const float* __restrict__ ein_src = (pass == 0) ? p.y : p.e;
     double nrm = 0.0, ysq = 0.0;
-    for (int64_t it = 0; it < nt; ++it) {
-      const int64_t tile = t0 + it;
-      const uint64_t seq = consumed++;
-      const int s = (int)(seq % nst);
-      T* st = stages + (size_t)s * STAGE_ELEMS;
-      const int64_t row = tile * R + tid;
-      float e_old = 0.f, y_row = 0.f;
-      if (tid < R && row < m) {
-        if (mode == MODE_NORMAL) e_old = p.e[row];
-        else y_row = p.y[row];
+    bool ok = true;
+    float ein[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int64_t row = pn0 * PR + 4 * lane + r;
+      ein[r] = (npan > 0 && row < m) ? ein_src[row] : 0.f;
+    }
+    for (int64_t pi = 0; pi < npan; ++pi) {
+      const int64_t rbase = (pn0 + pi) * PR;
+      // reducer inputs of this panel and residual rows of the next, loaded early
+      const int rr = tid - (NT - PR);  // reducer rows are owned by the last PR/32 warps
+      const int64_t rrow = rbase + rr;
+      float red_ein = 0.f, red_y = 0.f;
+      if (rr >= 0 && rrow < m) {
+        if (mode != MODE_COPY) red_ein = ein_src[rrow];
+        if (mode != MODE_NORMAL) red_y = p.y[rrow];
       }
-      bool ok = true;
-      if (tma) {
-        ok = mbar_wait_bounded(&mbar[s], (uint32_t)((seq / nst) & 1), p.timeout_ns);
-      } else {
-        __syncthreads();
-        const T* X = reinterpret_cast<const T*>(p.X);
-        for (int idx = tid; idx < STAGE_ELEMS; idx += NT) {
-          const int c = idx / R, r = idx % R;
-          const int64_t gr = tile * R + r;
-          st[idx] = (gr < m && c < n) ? X[(int64_t)c * p.ld + gr] : zero_elem<T>();
+      float ein_next[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int64_t row = rbase + PR + 4 * lane + r;
+        ein_next[r] = (pi + 1 < npan && row < m) ? ein_src[row] : 0.f;
+      }
+      float ph[4] = {0.f, 0.f, 0.f, 0.f}, pl[4] = {0.f, 0.f, 0.f, 0.f};
+      const int rb = (int)(pi & 1);
+      bool fail = false;
+#pragma unroll
+      for (int ch = 0; ch < NCH; ++ch) {
+        const uint64_t q = qbase + (uint64_t)pi * NCH + ch;
+        const int s = (int)(q % nst);
+        T* st = stages + (size_t)s * CHUNK_ELEMS;
+        if (tma) {
+          if (ok && !mbar_wait_bounded(&full[s], (uint32_t)((q / nst) & 1), p.timeout_ns)) ok = false;
+        } else {
+          const T* X = reinterpret_cast<const T*>(p.X);
+          for (int idx = tid; idx < CHUNK_ELEMS; idx += NT) {
+            const int c = idx / PR, r = idx % PR;
+            const int64_t gr = rbase + r;
+            const int gc = ch * C + c;
+            st[idx] = (gr < m && gc < n) ? X[(int64_t)gc * p.ld + gr] : zero_elem<T>();
+          }
+          named_sync(NT);
         }
-        __syncthreads();
-      }
-      // phase A: per-warp partial of (X·v) for the tile's rows
-      if (ok && mode != MODE_COPY) {
-        float ph[RPL], pl[RPL];
-#pragma unroll
-        for (int r = 0; r < RPL; ++r) { ph[r] = 0.f; pl[r] = 0.f; }
-#pragma unroll
-        for (int k = 0; k < CPW; ++k) {
-          float xv[RPL];
-          RowLoad<T, RPL>::load(st + (warp * CPW + k) * R + lane * RPL, xv);
-#pragma unroll
-          for (int r = 0; r < RPL; ++r) {
-            if (mode == MODE_NORMAL) ph[r] = fmaf(xv[r], v[k], ph[r]);
-            else dot2_step(xv[r], v[k], ph[r], pl[r]);
+        if (ok) {
+          if (mode == MODE_NORMAL)
+            chunk_compute<MODE_NORMAL, T, CW, CPW, V_IN_REGS>(st, warp, lane, ch, ein, gacc, v, vsm, ph, pl);
+          else if (mode == MODE_REFRESH)
+            chunk_compute<MODE_REFRESH, T, CW, CPW, V_IN_REGS>(st, warp, lane, ch, ein, gacc, v, vsm, ph, pl);
+          else
+            chunk_compute<MODE_COPY, T, CW, CPW, V_IN_REGS>(st, warp, lane, ch, ein, gacc, v, vsm, ph, pl);
+        }
+        if (ch == NCH - 1) {
+          // the panel's row sums go to the cross-warp reduction buffer
+          float* rh = red_hi + (rb * NW + warp) * PR + 4 * lane;
+          *reinterpret_cast<float4*>(rh) = make_float4(ph[0], ph[1], ph[2], ph[3]);
+          if (mode == MODE_REFRESH) {
+            float* rl = red_lo + (rb * NW + warp) * PR + 4 * lane;
+            *reinterpret_cast<float4*>(rl) = make_float4(pl[0], pl[1], pl[2], pl[3]);
           }
         }
-#pragma unroll
-        for (int r = 0; r < RPL; ++r) {
-          red_hi[warp * R + lane * RPL + r] = ph[r];
-          red_lo[warp * R + lane * RPL + r] = pl[r];
+        // every warp is done with chunk q (and, after the last chunk, has written its row sums)
+        if (named_sync_or(NT, ok ? 0 : 1)) { fail = true; break; }
+        if (tma && tid == 0) {
+          ++waited;
+          issue_chunk(issued++);  // chunk q + nst into the stage just released
         }
       }
-      // S1: all warps are past phase B of the previous tile and phase A of this one
-      const int fail = __syncthreads_or(ok ? 0 : 1);
       if (fail) { err = DEV_TIMEOUT_COPY; break; }
-      ++waited;
-      if (tma && tid == 0 && seq >= 1) {
-        fence_proxy_async_smem();
-        issue_next();  // refills the previous tile's stage
-      }
-      if (tid < R) {
-        float e_new = 0.f;
-        if (row < m) {
-          if (mode == MODE_NORMAL) {
-            float sacc = 0.f;
+      if (rr >= 0 && rrow < m) {
+        float e_new;
+        if (mode == MODE_NORMAL) {
+          float sacc = 0.f;
 #pragma unroll
-            for (int w = 0; w < NW; ++w) sacc += red_hi[w * R + tid];
-            e_new = e_old - sacc;
-          } else if (mode == MODE_COPY) {
-            e_new = y_row;
-          } else {
-            double sacc = 0.0;
+          for (int w = 0; w < NW; ++w) sacc += red_hi[(rb * NW + w) * PR + rr];
+          e_new = red_ein - sacc;
+        } else if (mode == MODE_COPY) {
+          e_new = red_y;
+        } else {
+          // sum of the 16 (hi, lo) warp pairs, compensated; y - sum in float64
+          float sh = 0.f, sc = 0.f, sl = 0.f;
 #pragma unroll
-            for (int w = 0; w < NW; ++w)
-              sacc += (double)red_hi[w * R + tid] + (double)red_lo[w * R + tid];
-            e_new = (float)((double)y_row - sacc);
+          for (int w = 0; w < NW; ++w) {
+            comp_add(red_hi[(rb * NW + w) * PR + rr], sh, sc);
+            sl += red_lo[(rb * NW + w) * PR + rr];
           }
-          p.e[row] = e_new;
-          nrm = fma((double)e_new, (double)e_new, nrm);
-          if (pass == 0) ysq = fma((double)y_row, (double)y_row, ysq);
+          e_new = (float)(((double)red_y - (double)sh) - ((double)sc + (double)sl));
         }
-        etile[tid] = e_new;
+        p.e[rrow] = e_new;
+        nrm = fma((double)e_new, (double)e_new, nrm);
+        if (pass == 0) ysq = fma((double)red_y, (double)red_y, ysq);
       }
-      __syncthreads();  // S2
-      // phase B: lane partials of X^T e
-      float ev[RPL];
 #pragma unroll
-      for (int r = 0; r < RPL; ++r) ev[r] = etile[lane * RPL + r];
-#pragma unroll
-      for (int k = 0; k < CPW; ++k) {
-        float xv[RPL];
-        RowLoad<T, RPL>::load(st + (warp * CPW + k) * R + lane * RPL, xv);
-#pragma unroll
-        for (int r = 0; r < RPL; ++r) gacc[k] = fmaf(xv[r], ev[r], gacc[k]);
-      }
+      for (int r = 0; r < 4; ++r) ein[r] = ein_next[r];
     }
     if (err != DEV_OK) break;
+    qbase += nchunk;
+    stamp(pass, 1);
+    if (p.trace && pass == 1 && tid == 0)
+      p.trace[(int64_t)p.trace_passes * TRACE_FIELDS + blockIdx.x] = global_timer_ns();
 
-    // publish this CTA's partials
+    // publish this CTA's partials: gpart[buf][c][b]
     const int buf = (int)(pass & 1);
+    // this CTA's rows of G·w (w = da_p, or a_0 on a warm pass 0), one warp per
+    // row c = blockIdx.x + k·grid; the rows are spread over the CTAs and
+    // published with the partials, so after the barrier g_p = h - G·w costs n loads
+    if (pass > 0 || p.warm) {
+      const float* w = (pass == 0) ? vsm : da_s;
+      for (int c = blockIdx.x + warp * grid; c < n; c += NW * grid) {
+        const float* grow = p.G + (int64_t)c * p.ldG;
+        float acc = 0.f;
+        for (int l = lane; l < n; l += 32) acc = fmaf(__ldg(grow + l), w[l], acc);
 #pragma unroll
-    for (int k = 0; k < CPW; ++k) {
-      float sacc = gacc[k];
+        for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(FULL_MASK, acc, off);
+        if (lane == 0) p.gw[(size_t)buf * NPAD + c] = acc;
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < CPW; ++j) {
+      float sacc = gacc[j];
 #pragma unroll
       for (int off = 16; off > 0; off >>= 1) sacc += __shfl_xor_sync(FULL_MASK, sacc, off);
-      if (lane == 0) p.gpart[((size_t)buf * grid + blockIdx.x) * NPAD + warp * CPW + k] = sacc;
-      gacc[k] = 0.f;
+      const int c = (j / CW) * C + warp * CW + (j % CW);
+      if (lane == 0) p.gpart[((size_t)buf * NPAD + c) * gstride + blockIdx.x] = sacc;
+      gacc[j] = 0.f;
     }
-    if (warp < R / 32) {
+    if (warp >= NW - PR / 32) {
+      const int rw = warp - (NW - PR / 32);
 #pragma unroll
       for (int off = 16; off > 0; off >>= 1) {
         nrm += __shfl_xor_sync(FULL_MASK, nrm, off);
         ysq += __shfl_xor_sync(FULL_MASK, ysq, off);
       }
-      if (lane == 0) { scal[2 + warp] = nrm; scal[2 + 16 + warp] = ysq; }
+      if (lane == 0) { scal[2 + rw] = nrm; scal[2 + 16 + rw] = ysq; }
     }
-    __syncthreads();
+    named_sync(NT);
     if (tid == 0) {
       double a = 0.0, b = 0.0;
-      for (int w = 0; w < R / 32; ++w) { a += scal[2 + w]; b += scal[2 + 16 + w]; }
+      for (int w = 0; w < PR / 32; ++w) { a += scal[2 + w]; b += scal[2 + 16 + w]; }
       p.npart[(size_t)buf * grid + blockIdx.x] = a;
       if (pass == 0) p.ypart[blockIdx.x] = b;
     }
     const unsigned expected = (unsigned)grid + ((p.stall_barrier && pass == 0) ? 1u : 0u);
-    if (!grid_barrier(p.ctl, expected, p.timeout_ns)) { err = DEV_TIMEOUT_BARRIER; break; }
+    if (!grid_barrier_named(p.ctl, expected, p.timeout_ns, NT, &flags[1])) {
+      err = DEV_TIMEOUT_BARRIER;
+      break;
+    }
+    stamp(pass, 2);
 
-    // every CTA: g = sum of partials (fixed order), ||e||^2, ||y||^2
-    for (int c = tid; c < NPAD; c += NT) {
-      double sacc = 0.0;
-      const float* gp = p.gpart + (size_t)buf * grid * NPAD + c;
+    // every CTA: h = sum of partials (fixed order, compensated float32),
+    // TPC threads per column each summing a contiguous quarter/half of the CTAs
+    {
+      constexpr int TPC = NT / NPAD >= 4 ? 4 : (NT / NPAD >= 2 ? 2 : 1);
+      const int c = tid % NPAD, part = tid / NPAD;
+      const int q4 = gstride / 4;
+      const int per = (q4 + TPC - 1) / TPC;
+      float s0 = 0.f, c0 = 0.f;
+      if (part < TPC) {
+        const float4* gp4 =
+            reinterpret_cast<const float4*>(p.gpart + ((size_t)buf * NPAD + c) * gstride);
+        float s1 = 0.f, c1 = 0.f;
+        const int q0 = part * per, q1 = min(q4, q0 + per);
 #pragma unroll 8
-      for (int b = 0; b < grid; ++b) sacc += (double)__ldcg(gp + (size_t)b * NPAD);
-      rvec[c] = (float)sacc;
+        for (int q = q0; q < q1; ++q) {
+          const float4 t = __ldcg(gp4 + q);
+          comp_add(t.x, s0, c0); comp_add(t.y, s1, c1);
+          comp_add(t.z, s0, c0); comp_add(t.w, s1, c1);
+        }
+        comp_add(s1, s0, c0);
+        c0 += c1;
+      }
+      float* hs = red_hi;  // free between passes: [TPC][NPAD] sums, then compensations
+      if (part < TPC) { hs[part * NPAD + c] = s0; hs[(TPC + part) * NPAD + c] = c0; }
+      named_sync(NT);
+      if (tid < NPAD) {
+        float ss = 0.f, cc = 0.f;
+        for (int k = 0; k < TPC; ++k) { comp_add(hs[k * NPAD + tid], ss, cc); cc += hs[(TPC + k) * NPAD + tid]; }
+        const float gwc = (pass > 0 || p.warm) && tid < n ? __ldcg(p.gw + (size_t)buf * NPAD + tid) : 0.f;
+        rvec[tid] = (ss + cc) - gwc;
+      }
     }
     if (warp == 0) {
-      double a = 0.0, b = 0.0;
-      for (int blk = lane; blk < grid; blk += 32) {
-        a += __ldcg(p.npart + (size_t)buf * grid + blk);
-        if (pass == 0) b += __ldcg(p.ypart + blk);
+      // at most 8 CTAs per lane (grid <= 256); loads issued together
+      double av[8], bv[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const int blk = lane + 32 * k;
+        av[k] = blk < grid ? __ldcg(p.npart + (size_t)buf * grid + blk) : 0.0;
+        bv[k] = (pass == 0 && blk < grid) ? __ldcg(p.ypart + blk) : 0.0;
       }
+      double a = 0.0, b = 0.0;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) { a += av[k]; b += bv[k]; }
 #pragma unroll
       for (int off = 16; off > 0; off >>= 1) {
         a += __shfl_xor_sync(FULL_MASK, a, off);
@@ -361,7 +499,8 @@ __global__ void __launch_bounds__(NT, 1)
       }
       if (lane == 0) { scal[0] = a; scal[1] = b; }
     }
-    __syncthreads();
+    named_sync(NT);
+    stamp(pass, 3);
     if (pass == 0) ynorm = sqrt(scal[1]);
     const double enorm = sqrt(scal[0]);
     const double rel = ynorm > 0.0 ? enorm / ynorm : enorm;
@@ -382,27 +521,30 @@ __global__ void __launch_bounds__(NT, 1)
     r_prev = rel;
     if (stop) break;
 
-    forward_substitution(p.G, p.ldG, n, NPAD, rvec, dd_s, da_s);
-    for (int c = tid; c < NPAD; c += NT) a64_s[c] += (double)da_s[c];
-    __syncthreads();
+    forward_substitution(p.G, p.ldG, n, NPAD, rvec, dd_s, da_s, diag_s);
+    stamp(pass, 5);
     const int64_t nx = pass + 1;
     const bool next_refresh = p.refresh_every > 0 && nx % p.refresh_every == 0;
+    for (int c = tid; c < NPAD; c += NT) {
+      a64_s[c] += (double)da_s[c];
+      vsm[c] = next_refresh ? (float)a64_s[c] : da_s[c];
+    }
+    named_sync(NT);
+    if constexpr (V_IN_REGS) {
 #pragma unroll
-    for (int k = 0; k < CPW; ++k) {
-      const int c = warp * CPW + k;
-      v[k] = next_refresh ? (float)a64_s[c] : da_s[c];
+      for (int j = 0; j < CPW; ++j) v[j] = vsm[(j / CW) * C + warp * CW + (j % CW)];
     }
   }
 
   // drain copies still in flight before the CTA retires
   if (tma && tid == 0) {
-    for (uint64_t seq = waited; seq < issued; ++seq)
-      if (!mbar_wait_bounded(&mbar[seq % nst], (uint32_t)((seq / nst) & 1), p.timeout_ns)) {
+    for (uint64_t k = waited; k < issued; ++k)
+      if (!mbar_wait_bounded(&full[k % nst], (uint32_t)((k / nst) & 1), p.timeout_ns)) {
         if (err == DEV_OK) err = DEV_TIMEOUT_COPY;
         break;
       }
   }
-  __syncthreads();
+  named_sync(NT);
   if (err != DEV_OK && tid == 0) atomicCAS(&p.ctl->err, DEV_OK, err);
   if (blockIdx.x == 0) {
     for (int c = tid; c < n; c += NT) p.a_out[c] = (float)a64_s[c];
@@ -415,10 +557,10 @@ __global__ void __launch_bounds__(NT, 1)
   }
 }
 
-template <typename T, int CPW, int RPL>
+template <typename T, int CW, int NCH>
 cudaError_t launch_one(const TallConfig& cfg, const CUtensorMap* tmap, const TallParams& p,
                        int grid, cudaStream_t stream) {
-  auto kern = tall_sweep_kernel<T, CPW, RPL>;
+  auto kern = tall_sweep_kernel<T, CW, NCH>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        cfg.smem_bytes);
   if (e != cudaSuccess) return e;
@@ -431,28 +573,31 @@ cudaError_t launch_one(const TallConfig& cfg, const CUtensorMap* tmap, const Tal
 
 }  // namespace
 
-// Tile geometry: CPW = columns per warp (power of two, 16·CPW >= n), RPL = rows
-// per lane chosen so one stage (R × 16·CPW elements) stays near 64 KB.
+// Chunk geometry: 128 rows × C columns, C = 16·CW with CW = 4 (float32) or 8
+// (bfloat16) for wide enough n, so a chunk is 32 KB and each column segment
+// 512 or 256 contiguous bytes; NCH chunks (a power of two) cover n.
 bool tall_config(int dtype, int n, int max_smem, TallConfig* cfg) {
   if (n < 0 || n > 512) return false;
-  int cpw = 1;
-  while (NW * cpw < n) cpw *= 2;
   const int esz = (dtype == HPSCD_F32) ? 4 : 2;
-  const int rowbytes = NW * cpw * esz;
-  int rpl = rowbytes <= 256 ? 4 : (rowbytes <= 1024 ? 2 : 1);
-  if (dtype == HPSCD_BF16 && rpl == 1) rpl = 2;
-  cfg->cpw = cpw;
-  cfg->rpl = rpl;
-  cfg->npad = NW * cpw;
-  cfg->rows = 32 * rpl;
-  cfg->stage_bytes = cfg->rows * cfg->npad * esz;
-  cfg->box_cols = cfg->npad < 256 ? cfg->npad : 256;
+  const int cwmax = (dtype == HPSCD_F32) ? 4 : 8;
+  int cw = 1;
+  while (cw < cwmax && NW * cw < n) cw *= 2;
+  const int c = NW * cw;
+  int nch = 1;
+  while (c * nch < n) nch *= 2;
+  cfg->cpw = cw;      // columns per warp per chunk
+  cfg->rpl = nch;     // chunks per panel
+  cfg->npad = c * nch;
+  cfg->rows = PR;
+  cfg->stage_bytes = PR * c * esz;
+  cfg->box_cols = c;
   cfg->threads = NT;
-  const int fixed = 1024 /*align*/ + (2 * NW * cfg->rows + cfg->rows) * 4 + cfg->npad * (3 * 4 + 8) +
-                    40 * 8 + 8 * 8;
+  const int nblk = cfg->npad >= 32 ? cfg->npad / 32 : 1;
+  const int fixed = 1024 /*align*/ + 4 * NW * PR * 4 + cfg->npad * (4 * 4 + 8) + 40 * 8 +
+                    32 * 8 + 16 + nblk * DIAG_PACK * 4;
   int nst = (max_smem - 256 - fixed) / cfg->stage_bytes;
-  if (nst > 8) nst = 8;
-  if (nst < 2) return false;
+  if (nst > 12) nst = 12;
+  if (nst < 3) return false;
   cfg->nstages = nst;
   cfg->smem_bytes = fixed + nst * cfg->stage_bytes;
   return true;
@@ -460,22 +605,22 @@ bool tall_config(int dtype, int n, int max_smem, TallConfig* cfg) {
 
 cudaError_t launch_tall_sweep(int dtype, const TallConfig& cfg, const CUtensorMap* tmap,
                               const TallParams& p, int grid, cudaStream_t stream) {
-#define HPSCD_TALL_CASE(T, C, R)                                        \
-  if (cfg.cpw == C && cfg.rpl == R) return launch_one<T, C, R>(cfg, tmap, p, grid, stream);
+#define HPSCD_TALL_CASE(T, W, N)                                        \
+  if (cfg.cpw == W && cfg.rpl == N) return launch_one<T, W, N>(cfg, tmap, p, grid, stream);
   if (dtype == HPSCD_F32) {
-    HPSCD_TALL_CASE(float, 1, 4)
-    HPSCD_TALL_CASE(float, 2, 4)
+    HPSCD_TALL_CASE(float, 1, 1)
+    HPSCD_TALL_CASE(float, 2, 1)
+    HPSCD_TALL_CASE(float, 4, 1)
+    HPSCD_TALL_CASE(float, 4, 2)
     HPSCD_TALL_CASE(float, 4, 4)
-    HPSCD_TALL_CASE(float, 8, 2)
-    HPSCD_TALL_CASE(float, 16, 2)
-    HPSCD_TALL_CASE(float, 32, 1)
+    HPSCD_TALL_CASE(float, 4, 8)
   } else {
-    HPSCD_TALL_CASE(uint16_t, 1, 4)
-    HPSCD_TALL_CASE(uint16_t, 2, 4)
-    HPSCD_TALL_CASE(uint16_t, 4, 4)
+    HPSCD_TALL_CASE(uint16_t, 1, 1)
+    HPSCD_TALL_CASE(uint16_t, 2, 1)
+    HPSCD_TALL_CASE(uint16_t, 4, 1)
+    HPSCD_TALL_CASE(uint16_t, 8, 1)
+    HPSCD_TALL_CASE(uint16_t, 8, 2)
     HPSCD_TALL_CASE(uint16_t, 8, 4)
-    HPSCD_TALL_CASE(uint16_t, 16, 2)
-    HPSCD_TALL_CASE(uint16_t, 32, 2)
   }
 #undef HPSCD_TALL_CASE
   return cudaErrorInvalidConfiguration;

@@ -126,7 +126,8 @@ def test_warm_start_matches_oracle(ctx):
     r = ctx.solve(X, y, tol=0, max_sweeps=2, stop="none", a0=torch.from_numpy(a0).cuda())
     o = oracle_same(s, 2, a0=a0.astype(np.float64))
     assert rel(r.a.cpu().numpy(), o.a) <= RTOL_F32
-    np.testing.assert_allclose(r.hist, o.hist, rtol=1e-4)
+    # float32 residual arithmetic: hist carries ~1e-8·||y|| absolute error
+    np.testing.assert_allclose(r.hist, o.hist, rtol=1e-4, atol=1e-7)
     cold = ctx.solve(X, y, tol=1e-6, max_sweeps=100, stop="rel_res")
     warm = ctx.solve(X, y, tol=1e-6, max_sweeps=100, stop="rel_res", a0=torch.from_numpy(a0).cuda())
     assert warm.sweeps < cold.sweeps
