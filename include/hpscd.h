@@ -161,6 +161,30 @@ int hpscd_last_timing(hpscd_ctx* ctx, hpscd_timing* out);
 int hpscd_set_trace(hpscd_ctx* ctx, int max_passes);
 int hpscd_get_trace(hpscd_ctx* ctx, unsigned long long* out, int64_t words, int64_t* written);
 
+/*
+ * Allocation-free solve (no counterpart in the paper; an interface for callers
+ * that cannot allocate device memory when they solve: cudaMalloc/cudaFree can
+ * synchronize the device and stall other streams, and some callers run where a
+ * framework's caching allocator or a fixed memory budget owns device memory).
+ * Same arguments and results as hpscd_solve for a column-major X on the CURRENT
+ * device, on `stream` (a cudaStream_t, NULL = default stream), with no context:
+ * the call allocates nothing (no cudaMalloc, cudaFree or allocating library
+ * routine).  Its device scratch is one static 24 MiB array in the library,
+ * which every GPU that loads the library holds until the process exits.
+ * Limits: 1 <= m <= 1,048,576, 1 <= n <= 256, max_sweeps <= 4096 and
+ * opts->debug_flags == 0; larger problems return HPSCD_ERR_UNSUPPORTED.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before
+ * any stream capture.  Every call shares the array and clears what must start
+ * at zero, so calls that overlap on the GPU (other streams, other host
+ * threads) race and must be serialized by the caller.  Device-side waits are
+ * bounded at 5 s.  hist, sweeps_done and final_rel_res are HOST pointers (may
+ * be NULL); the call returns after the result is complete.
+ */
+int hpscd_solve_noalloc(void* stream, const void* X, int dtype, int64_t m, int64_t n, int64_t ld,
+                        const float* y, float* a, int a_is_guess, const hpscd_opts* opts,
+                        double* hist, int64_t* sweeps_done, double* final_rel_res);
+
 /* Static description of a status code. */
 const char* hpscd_status_string(int status);
 

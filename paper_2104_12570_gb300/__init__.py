@@ -71,6 +71,11 @@ SIGNATURES = {
                           ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)],
                          ctypes.c_int),
     "hpscd_last_timing": ([ctypes.c_void_p, ctypes.POINTER(Timing)], ctypes.c_int),
+    "hpscd_solve_noalloc": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int64,
+                             ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                             ctypes.c_int, ctypes.POINTER(Opts), ctypes.c_void_p,
+                             ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)],
+                            ctypes.c_int),
     "hpscd_set_trace": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
     "hpscd_get_trace": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_ulonglong), ctypes.c_int64,
                          ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
