@@ -81,6 +81,9 @@ typedef struct {
 } hpscd_opts;
 
 #define HPSCD_DEBUG_STALL_BARRIER 1
+/* Bit 1: form G = X^T X with the CUDA-core kernel even where the tensor-core
+ * (tcgen05) kernel applies (cross-checking the two). */
+#define HPSCD_DEBUG_SIMT_GRAM 2
 
 /* Timings of the last solve on a context, from CUDA events on its stream. */
 typedef struct {
@@ -146,6 +149,20 @@ int hpscd_solve_host(hpscd_ctx* ctx, const void* X, int dtype, int layout, int64
                      int64_t n, int64_t ld, const float* y, float* a, int a_is_guess,
                      const hpscd_opts* opts, double* hist, int64_t* sweeps_done,
                      double* final_rel_res);
+
+/*
+ * The Gram matrix G = X^T X of a column-major X (m×n, ld), the set-up of the
+ * sweep: G_jj = <X_j, X_j> are the denominators of the column step (Eq. da2)
+ * and G_jl (l < j) the couplings that Eq. ek1-ek introduces inside a sweep.
+ * G: device float[n × ldG], row-major, both triangles written; ldG >= n.
+ * Tensor cores (tcgen05) when X is TMA-aligned (16-byte base, ld·elem a
+ * multiple of 16) and n <= 512 (bfloat16) or n <= 256 (float32; a two-term
+ * tf32 split keeps float32-grade products); CUDA cores otherwise or with
+ * flags = HPSCD_DEBUG_SIMT_GRAM.  Accumulation is float32 within a row block
+ * and float64 across blocks.  Synchronous; timing in hpscd_last_timing.
+ */
+int hpscd_gram(hpscd_ctx* ctx, const void* X, int dtype, int64_t m, int64_t n, int64_t ld,
+               float* G, int64_t ldG, int flags);
 
 /* Timings of the last solve on this context. */
 int hpscd_last_timing(hpscd_ctx* ctx, hpscd_timing* out);

@@ -71,6 +71,8 @@ SIGNATURES = {
                           ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)],
                          ctypes.c_int),
     "hpscd_last_timing": ([ctypes.c_void_p, ctypes.POINTER(Timing)], ctypes.c_int),
+    "hpscd_gram": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_int64,
+                    ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int], ctypes.c_int),
     "hpscd_solve_noalloc": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int64,
                              ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
                              ctypes.c_int, ctypes.POINTER(Opts), ctypes.c_void_p,
@@ -290,6 +292,20 @@ class Context:
                                    hist.ctypes.data_as(ctypes.c_void_p), ctypes.byref(sw),
                                    ctypes.byref(rr))
         return self._finish(rc, hist, sw, rr, a)
+
+    def gram(self, X, simt: bool = False):
+        """G = X^T X (n×n float32 CUDA tensor) for a column-major CUDA X."""
+        import torch
+        ptr, dt, lay, m, n, ld = _describe(X)
+        if lay != COL:
+            raise ValueError("gram needs a column-major X")
+        G = torch.empty(n, n, dtype=torch.float32, device=X.device)
+        self.set_stream(torch.cuda.current_stream(X.device))
+        rc = self._lib.hpscd_gram(self._h, ctypes.c_void_p(ptr), dt, m, n, ld,
+                                  ctypes.c_void_p(G.data_ptr()), n, 2 if simt else 0)
+        if rc:
+            raise HpscdError(rc)
+        return G
 
     def solve_host(self, X, y, *, tol=1e-6, max_sweeps=1000, stop="rel_res", a0=None,
                    refresh_every=0) -> SolveResult:

@@ -1,0 +1,420 @@
+// Tensor-core set-up kernel: G = X^T X of a column-major X with tcgen05.
+//
+// The sweep needs <X_j, X_j> (the denominators of Eq. da2) and the lower
+// triangle of G (Eq. ek1-ek applied inside a sweep).  G is a dense contraction
+// over the m rows, the one part of the method that belongs on the tensor
+// cores.  Each CTA takes a range of rows (K) and a group of 128-column block
+// rows I of G, streams the needed 128-column blocks of X through shared memory
+// by TMA (128-byte swizzle: each column's K elements are the operand's
+// contiguous K-major rows), and accumulates D_I = X_I^T X_{0..I} in tensor
+// memory with tcgen05.mma issued by one thread.  bfloat16 X: kind::f16 (exact
+// products, float32 accumulation).  float32 X: kind::tf32 on a two-term split
+// x = hi + lo (hi = x truncated to tf32, written back in place; lo = x - hi),
+// accumulating hi·hi + hi·lo + lo·hi, which leaves ~2^-21 relative error per
+// product.  The tensor-core accumulation loses accuracy on long sums of
+// positive terms, so the diagonal <X_j, X_j> is summed on the CUDA cores from
+// the same shared-memory tiles (float32, float64 across blocks).  Per-split
+// float32 partials are summed in a fixed order by gram_tc_reduce_kernel into
+// the symmetric G.
+#include "kernels.h"
+
+namespace hpscd {
+
+namespace {
+
+constexpr int GT_THREADS = 128;
+constexpr int BLK = 128;                 // columns per block (MMA M)
+constexpr int ATOM_BYTES = BLK * 128;    // one 128-column block × 128 bytes of K = 16 KB
+constexpr int TMEM_COLS = 512;
+
+__device__ __forceinline__ uint64_t make_sw128_desc(uint32_t smem_addr) {
+  // tcgen05 shared-memory matrix descriptor, K-major operand, 128-byte swizzle:
+  // start address >> 4 [0,14), leading byte offset >> 4 [16,30) (unused for
+  // swizzled K-major; 1), stride byte offset >> 4 [32,46) = 1024 B between
+  // 8-row groups, version 1 [46,48), base offset 0, layout type 2 (SW128) [61,64).
+  uint64_t d = 0;
+  d |= (uint64_t)((smem_addr >> 4) & 0x3FFF);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(1024 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
+// Instruction descriptor, dense, D float32, A/B of format `fmt` (kind::f16:
+// 1 = bf16; kind::tf32: 2 = tf32), both K-major, M = 128, N.
+__host__ __device__ constexpr uint32_t make_idesc(uint32_t fmt, int N) {
+  return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(BLK >> 4) << 24);
+}
+
+template <bool TF32>
+__device__ __forceinline__ void mma_issue(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                          uint32_t idesc, uint32_t accumulate) {
+  if constexpr (TF32) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+  }
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+      "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+template <bool TF32>
+__global__ void __launch_bounds__(GT_THREADS, 1)
+    gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const GramTCParams p) {
+  constexpr int KB = TF32 ? 32 : 64;         // rows of X per 128-byte K block
+  constexpr uint32_t FMT = TF32 ? 2u : 1u;
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* base = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int g = blockIdx.y;
+  const int nload = p.group_nload[g];
+  const int nrows_g = p.group_count[g];
+  const int stage_raw = nload * ATOM_BYTES;
+  const int stage_bytes = stage_raw * (TF32 ? 2 : 1);
+  const int nst = p.nstages;
+  uint64_t* full = reinterpret_cast<uint64_t*>(base + (size_t)nst * stage_bytes);
+  uint64_t* empty = full + 8;
+  uint64_t* done = empty + 8;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  int* s_fail = reinterpret_cast<int*>(tmem_slot + 1);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t r0 = (int64_t)blockIdx.x * p.rows_per_split;
+  const int64_t r1 = min(p.m, r0 + p.rows_per_split);
+  const int64_t nkb = r1 > r0 ? (r1 - r0 + KB - 1) / KB : 0;
+
+  if (tid == 0) {
+    for (int s = 0; s < nst; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
+    mbar_init(done, 1);
+    *s_fail = 0;
+    fence_mbar_init();
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  int64_t issued = 0;  // thread 0: K blocks whose copies were issued
+  auto issue = [&](int64_t kb) {
+    const int s = (int)(kb % nst);
+    unsigned char* dst = base + (size_t)s * stage_bytes;
+    mbar_arrive_expect_tx(&full[s], (uint32_t)stage_raw);
+    for (int b = 0; b < nload; ++b)
+      tma_load_2d(dst + b * ATOM_BYTES, &tmap, &full[s], (int32_t)(r0 + kb * KB), b * BLK);
+  };
+  if (tid == 0)
+    while (issued < nst && issued < nkb) issue(issued++);
+
+  bool ok = true;
+  int64_t consumed = 0;  // K blocks whose copies every thread has seen land
+  // <X_j, X_j> on the CUDA cores: thread t sums the squares of the 16-byte
+  // chunks t + 128q of every stage, i.e. of column t/8 + 16q (the swizzle only
+  // permutes chunks within a column's 128 bytes); float32 per 64 K blocks,
+  // float64 across them.  The tensor-core accumulation drifts on long sums
+  // of positive terms, so these replace its diagonal.
+  constexpr int MAXQ = 32;  // 16-byte chunks per thread per stage (nload <= 4)
+  float dsq[MAXQ];
+  double dsq64[MAXQ];
+#pragma unroll
+  for (int q = 0; q < MAXQ; ++q) { dsq[q] = 0.f; dsq64[q] = 0.0; }
+  const int nq = 8 * nload;
+  for (int64_t kb = 0; kb < nkb; ++kb) {
+    const int s = (int)(kb % nst);
+    unsigned char* st = base + (size_t)s * stage_bytes;
+    if (ok && !mbar_wait_bounded(&full[s], (uint32_t)((kb / nst) & 1), p.timeout_ns)) ok = false;
+    if (ok) {
+      const uint4* raw4 = reinterpret_cast<const uint4*>(st);
+#pragma unroll
+      for (int q = 0; q < MAXQ; ++q) {
+        if (q < nq) {
+          const uint4 x = raw4[tid + GT_THREADS * q];
+          if constexpr (TF32) {
+            const float a0 = __uint_as_float(x.x), a1 = __uint_as_float(x.y);
+            const float a2 = __uint_as_float(x.z), a3 = __uint_as_float(x.w);
+            dsq[q] = fmaf(a0, a0, fmaf(a1, a1, fmaf(a2, a2, fmaf(a3, a3, dsq[q]))));
+          } else {
+            const uint32_t w[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+              const float lo16 = __uint_as_float(w[h] << 16), hi16 = __uint_as_float(w[h] & 0xffff0000u);
+              dsq[q] = fmaf(lo16, lo16, fmaf(hi16, hi16, dsq[q]));
+            }
+          }
+        }
+      }
+      if ((kb & 63) == 63) {
+#pragma unroll
+        for (int q = 0; q < MAXQ; ++q) { dsq64[q] += (double)dsq[q]; dsq[q] = 0.f; }
+      }
+    }
+    if constexpr (TF32) {
+      // split in place: hi (tf32-exact) over x, lo = x - hi in the second half
+      if (ok) {
+        uint4* raw = reinterpret_cast<uint4*>(st);
+        uint4* lo = reinterpret_cast<uint4*>(st + stage_raw);
+        for (int idx = tid; idx < stage_raw / 16; idx += GT_THREADS) {
+          const uint4 x = raw[idx];
+          uint4 h, l;
+          h.x = x.x & 0xFFFFE000u; h.y = x.y & 0xFFFFE000u;
+          h.z = x.z & 0xFFFFE000u; h.w = x.w & 0xFFFFE000u;
+          l.x = __float_as_uint(__uint_as_float(x.x) - __uint_as_float(h.x));
+          l.y = __float_as_uint(__uint_as_float(x.y) - __uint_as_float(h.y));
+          l.z = __float_as_uint(__uint_as_float(x.z) - __uint_as_float(h.z));
+          l.w = __float_as_uint(__uint_as_float(x.w) - __uint_as_float(h.w));
+          raw[idx] = h;
+          lo[idx] = l;
+        }
+      }
+      fence_proxy_async_smem();
+    }
+    if (__syncthreads_or(ok ? 0 : 1)) { ok = false; break; }
+    consumed = kb + 1;
+    if (tid == 32) {
+      tc_fence_after();
+      const uint32_t a_base = smem_u32(st);
+      uint32_t dcol = 0;
+      for (int gi = 0; gi < nrows_g; ++gi) {
+        const int I = p.group_rows[g][gi];
+        const int N_total = BLK * (I + 1);
+        for (int nb0 = 0; nb0 < N_total; nb0 += 256) {
+          const int N = min(256, N_total - nb0);
+          const uint32_t idesc = make_idesc(FMT, N);
+          const uint32_t d_tmem = tmem + dcol + nb0;
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const uint32_t koff = k * 32;
+            const uint64_t ah = make_sw128_desc(a_base + I * ATOM_BYTES + koff);
+            const uint64_t bh = make_sw128_desc(a_base + (nb0 / BLK) * ATOM_BYTES + koff);
+            const uint32_t acc = (kb > 0 || k > 0) ? 1u : 0u;
+            mma_issue<TF32>(d_tmem, ah, bh, idesc, acc);
+            if constexpr (TF32) {
+              const uint64_t al = make_sw128_desc(a_base + stage_raw + I * ATOM_BYTES + koff);
+              const uint64_t bl =
+                  make_sw128_desc(a_base + stage_raw + (nb0 / BLK) * ATOM_BYTES + koff);
+              mma_issue<TF32>(d_tmem, ah, bl, idesc, 1u);
+              mma_issue<TF32>(d_tmem, al, bh, idesc, 1u);
+            }
+          }
+        }
+        dcol += N_total;
+      }
+      mma_commit(&empty[s]);
+    }
+    if (tid == 0 && kb >= 1 && issued < nkb) {
+      // the previous K block's stage is free once the MMAs that read it have
+      // completed (issued one iteration ago); refill it
+      const int64_t pk = kb - 1;
+      if (!mbar_wait_bounded(&empty[pk % nst], (uint32_t)((pk / nst) & 1), p.timeout_ns)) ok = false;
+      else issue(issued++);
+    }
+  }
+  // every MMA issued so far completes on `done` (also after a failure, before TMEM is freed)
+  if (tid == 32) mma_commit(done);
+  if (!mbar_wait_bounded(done, 0, p.timeout_ns)) ok = false;
+  tc_fence_after();
+  const int fail = __syncthreads_or(ok ? 0 : 1);
+  if (!fail) {
+    // column sums of squares: the 8 lanes t = 8a..8a+7 share columns a + 16q
+#pragma unroll
+    for (int q = 0; q < MAXQ; ++q) {
+      double v = dsq64[q] + (double)dsq[q];
+      v += __shfl_xor_sync(FULL_MASK, v, 1);
+      v += __shfl_xor_sync(FULL_MASK, v, 2);
+      v += __shfl_xor_sync(FULL_MASK, v, 4);
+      const int col = tid / 8 + 16 * q;
+      if ((tid & 7) == 0 && q < nq) {
+        bool mine = false;
+        for (int gi = 0; gi < nrows_g; ++gi) mine |= (col / BLK == p.group_rows[g][gi]);
+        if (mine) p.dpart[(size_t)blockIdx.x * p.npad + col] = v;
+      }
+    }
+    float* out = p.partial + (size_t)blockIdx.x * p.npad * p.npad;
+    uint32_t dcol = 0;
+    for (int gi = 0; gi < nrows_g; ++gi) {
+      const int I = p.group_rows[g][gi];
+      const int N_total = BLK * (I + 1);
+      const int row = BLK * I + 32 * warp + lane;
+      float* orow = out + (size_t)row * p.npad;
+      for (int c0 = 0; c0 < N_total; c0 += 32) {
+        float v[32];
+        if (nkb > 0) {
+          tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + dcol + c0, v);
+        } else {
+#pragma unroll
+          for (int i = 0; i < 32; ++i) v[i] = 0.f;
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          *reinterpret_cast<float4*>(orow + c0 + 4 * q) =
+              make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+      }
+      dcol += N_total;
+    }
+  } else if (tid == 0) {
+    atomicExch(p.err, 1);
+    // copies issued but never consumed must land before the CTA retires
+    for (int64_t kb = consumed; kb < issued; ++kb)
+      if (!mbar_wait_bounded(&full[kb % nst], (uint32_t)((kb / nst) & 1), p.timeout_ns)) break;
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(TMEM_COLS)
+                 : "memory");
+}
+
+// G[i][j] = G[j][i] = sum over splits (fixed order) of the lower partials.
+// The diagonal comes from the CUDA-core sums of squares (dpart).
+__global__ void gram_tc_reduce_kernel(const float* __restrict__ partial,
+                                      const double* __restrict__ dpart, int ksplit, int npad,
+                                      float* __restrict__ G, int ldG) {
+  const int64_t total = (int64_t)npad * npad;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int i0 = (int)(idx / npad), j0 = (int)(idx % npad);
+    const int i = i0 >= j0 ? i0 : j0, j = i0 >= j0 ? j0 : i0;
+    double s = 0.0;
+    if (i == j)
+      for (int k = 0; k < ksplit; ++k) s += dpart[(size_t)k * npad + i];
+    else
+      for (int k = 0; k < ksplit; ++k) s += (double)partial[((size_t)k * npad + i) * npad + j];
+    G[(int64_t)i0 * ldG + j0] = (float)s;
+  }
+}
+
+}  // namespace
+
+bool gram_tc_plan(int dtype, int64_t m, int n, int sms, int max_smem, GramTCPlan* gp) {
+  if (m < 1 || n < 1 || n > 512) return false;
+  const int nb = (n + BLK - 1) / BLK;
+  if (dtype == HPSCD_F32 && nb > 2) return false;
+  gp->npad = nb * BLK;
+  // group the block rows so each group's accumulators fit 512 TMEM columns
+  int ng = 0;
+  for (int i = 0; i < 4; ++i) { gp->group_count[i] = 0; gp->group_nload[i] = 0; }
+  if (nb == 1) { gp->group_rows[0][0] = 0; gp->group_count[0] = 1; ng = 1; }
+  else if (nb == 2) {
+    gp->group_rows[0][0] = 0; gp->group_rows[0][1] = 1; gp->group_count[0] = 2; ng = 1;
+  } else if (nb == 3) {
+    gp->group_rows[0][0] = 2; gp->group_count[0] = 1;
+    gp->group_rows[1][0] = 0; gp->group_rows[1][1] = 1; gp->group_count[1] = 2; ng = 2;
+  } else {
+    gp->group_rows[0][0] = 3; gp->group_count[0] = 1;
+    gp->group_rows[1][0] = 2; gp->group_count[1] = 1;
+    gp->group_rows[2][0] = 0; gp->group_rows[2][1] = 1; gp->group_count[2] = 2; ng = 3;
+  }
+  gp->ngroups = ng;
+  int maxload = 0;
+  for (int i = 0; i < ng; ++i) {
+    int mx = 0;
+    for (int k = 0; k < gp->group_count[i]; ++k) mx = gp->group_rows[i][k] > mx ? gp->group_rows[i][k] : mx;
+    gp->group_nload[i] = mx + 1;
+    maxload = gp->group_nload[i] > maxload ? gp->group_nload[i] : maxload;
+  }
+  const int kb_rows = dtype == HPSCD_F32 ? 32 : 64;
+  const int stage = maxload * ATOM_BYTES * (dtype == HPSCD_F32 ? 2 : 1);
+  int nst = (max_smem - 2048) / stage;
+  if (nst > 6) nst = 6;
+  if (nst < 2) return false;
+  gp->nstages = nst;
+  gp->smem_bytes = nst * stage + 1024 + 256;
+  // one CTA per SM: each CTA allocates all 512 tensor-memory columns
+  if (gp->smem_bytes < max_smem / 2 + 4096) gp->smem_bytes = max_smem / 2 + 4096;
+  int ksplit = sms / ng;
+  if (ksplit < 1) ksplit = 1;
+  int64_t rps = (m + ksplit - 1) / ksplit;
+  rps = (rps + kb_rows - 1) / kb_rows * kb_rows;
+  gp->rows_per_split = rps;
+  gp->ksplit = (int)((m + rps - 1) / rps);
+  gp->partial_bytes = (size_t)gp->ksplit * gp->npad * gp->npad * sizeof(float) +
+                      (size_t)gp->ksplit * gp->npad * sizeof(double);
+  return true;
+}
+
+cudaError_t launch_gram_tc(const CUtensorMap* tmap, int dtype, int64_t m, const GramTCPlan& gp,
+                           float* partial, int* err, uint64_t timeout_ns, float* G, int ldG,
+                           cudaStream_t stream) {
+  GramTCParams p{};
+  p.m = m;
+  p.npad = gp.npad;
+  for (int i = 0; i < 4; ++i) {
+    p.group_count[i] = gp.group_count[i];
+    p.group_nload[i] = gp.group_nload[i];
+    for (int k = 0; k < 4; ++k) p.group_rows[i][k] = gp.group_rows[i][k];
+  }
+  p.rows_per_split = gp.rows_per_split;
+  p.partial = partial;
+  p.dpart = reinterpret_cast<double*>(reinterpret_cast<char*>(partial) +
+                                      (size_t)gp.ksplit * gp.npad * gp.npad * sizeof(float));
+  p.err = err;
+  p.timeout_ns = timeout_ns;
+  p.nstages = gp.nstages;
+  dim3 grid(gp.ksplit, gp.ngroups);
+  cudaError_t e;
+  if (dtype == HPSCD_F32) {
+    e = cudaFuncSetAttribute(gram_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             gp.smem_bytes);
+    if (e != cudaSuccess) return e;
+    gram_tc_kernel<true><<<grid, GT_THREADS, gp.smem_bytes, stream>>>(*tmap, p);
+  } else {
+    e = cudaFuncSetAttribute(gram_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             gp.smem_bytes);
+    if (e != cudaSuccess) return e;
+    gram_tc_kernel<false><<<grid, GT_THREADS, gp.smem_bytes, stream>>>(*tmap, p);
+  }
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int64_t total = (int64_t)gp.npad * gp.npad;
+  int blocks = (int)((total + 255) / 256);
+  if (blocks > 4096) blocks = 4096;
+  gram_tc_reduce_kernel<<<blocks, 256, 0, stream>>>(partial, p.dpart, gp.ksplit, gp.npad, G, ldG);
+  return cudaGetLastError();
+}
+
+}  // namespace hpscd

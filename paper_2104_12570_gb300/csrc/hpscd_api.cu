@@ -54,6 +54,9 @@ struct Layout {
 struct Plan {
   TallConfig cfg;
   GramPlan gp;
+  GramTCPlan gtc;
+  bool tc_ok = false;  // the tensor-core Gram applies to this shape
+  int ldG = 0;
   int64_t ntiles = 0;
   int grid = 0;
   int gstride = 0;
@@ -68,7 +71,7 @@ int check_opts(const hpscd_opts* o) {
   if (o->max_sweeps < 0 || o->max_sweeps > (int64_t)1 << 40) return HPSCD_ERR_INVALID_ARG;
   if (o->stop_rule < HPSCD_STOP_REL_RES || o->stop_rule > HPSCD_STOP_NONE) return HPSCD_ERR_INVALID_ARG;
   if (o->refresh_every < 0) return HPSCD_ERR_INVALID_ARG;
-  if (o->debug_flags & ~HPSCD_DEBUG_STALL_BARRIER) return HPSCD_ERR_INVALID_ARG;
+  if (o->debug_flags & ~(HPSCD_DEBUG_STALL_BARRIER | HPSCD_DEBUG_SIMT_GRAM)) return HPSCD_ERR_INVALID_ARG;
   for (int i = 0; i < 5; ++i)
     if (o->reserved[i] != 0) return HPSCD_ERR_INVALID_ARG;
   return HPSCD_OK;
@@ -91,6 +94,8 @@ int make_plan(const hpscd_ctx* ctx, int dtype, int layout, int64_t m, int64_t n,
   if (n > 512) return HPSCD_ERR_UNSUPPORTED;
   if (!tall_config(dtype, (int)n, ctx->max_smem, &P->cfg)) return HPSCD_ERR_UNSUPPORTED;
   P->gp = gram_plan(m, P->cfg.npad, ctx->sms);
+  P->tc_ok = gram_tc_plan(dtype, m, (int)n, ctx->sms, ctx->max_smem, &P->gtc);
+  P->ldG = P->tc_ok && P->gtc.npad > P->gp.npad ? P->gtc.npad : P->gp.npad;
   P->ntiles = (m + P->cfg.rows - 1) / P->cfg.rows;
   int64_t grid = ctx->sms > 256 ? 256 : ctx->sms;  // the kernel's norm reduction covers 256 CTAs
   if (P->ntiles < grid) grid = P->ntiles;
@@ -103,8 +108,9 @@ int make_plan(const hpscd_ctx* ctx, int dtype, int layout, int64_t m, int64_t n,
     off = align_up(off + bytes, 256);
     return at;
   };
-  L.G = take((size_t)P->gp.npad * P->gp.npad * sizeof(float));
-  L.partial = take(P->gp.partial_bytes);
+  L.G = take((size_t)P->ldG * P->ldG * sizeof(float));
+  L.partial = take(P->tc_ok && P->gtc.partial_bytes > P->gp.partial_bytes ? P->gtc.partial_bytes
+                                                                          : P->gp.partial_bytes);
   L.e = take((size_t)(m > 0 ? m : 1) * sizeof(float));
   P->gstride = (P->grid + 3) / 4 * 4;
   L.gpart = take((size_t)2 * P->gstride * P->cfg.npad * sizeof(float));
@@ -161,6 +167,51 @@ int encode_tall_map(hpscd_ctx* ctx, const void* X, int dtype, int64_t m, int64_t
   return r == CUDA_SUCCESS ? 1 : 0;
 }
 
+// 128-byte-swizzled map for the tensor-core Gram: boxes of one 128-byte K
+// block (32 float32 / 64 bfloat16 rows) × 128 columns.
+int encode_gram_map(hpscd_ctx* ctx, const void* X, int dtype, int64_t m, int64_t n, int64_t ld,
+                    CUtensorMap* map) {
+  if (!ctx->encode) return 0;
+  const int es = esize(dtype);
+  if ((reinterpret_cast<uintptr_t>(X) & 15) != 0 || ((uint64_t)ld * es) % 16 != 0) return 0;
+  if (m < 1 || n < 1 || (uint64_t)ld * es >= ((uint64_t)1 << 40)) return 0;
+  cuuint64_t dims[2] = {(cuuint64_t)m, (cuuint64_t)n};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * es};
+  cuuint32_t box[2] = {(cuuint32_t)(128 / es), 128};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = ctx->encode(map, dtype == HPSCD_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                                   : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+                           2, const_cast<void*>(X), dims, strides, box, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? 1 : 0;
+}
+
+// G = X^T X into G (ldG), by the tensor-core kernel when it applies, else the
+// CUDA-core kernel.  `err` receives a device-side failure flag.
+int run_gram(hpscd_ctx* ctx, const void* X, int dtype, int64_t m, int64_t n, int64_t ld,
+             const Plan& P, void* partial, float* G, int ldG, int* err, bool force_simt,
+             int* launches) {
+  CUtensorMap gmap;
+  memset(&gmap, 0, sizeof(gmap));
+  if (!force_simt && P.tc_ok && encode_gram_map(ctx, X, dtype, m, n, ld, &gmap)) {
+    if (launch_gram_tc(&gmap, dtype, m, P.gtc, static_cast<float*>(partial), err,
+                       (uint64_t)(ctx->timeout_s * 1e9), G, ldG, ctx->stream) != cudaSuccess) {
+      cudaGetLastError();
+      return HPSCD_ERR_CUDA;
+    }
+    *launches = 2;
+    return HPSCD_OK;
+  }
+  if (launch_gram(X, dtype, m, (int)n, ld, P.gp, static_cast<double*>(partial), G, ldG,
+                  ctx->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return HPSCD_ERR_CUDA;
+  }
+  *launches = 2;
+  return HPSCD_OK;
+}
+
 // m == 0: nothing to sweep; y = 0, so every recorded residual is the absolute norm 0.
 int solve_empty_rows(hpscd_ctx* ctx, int64_t n, float* a, int a_is_guess, const hpscd_opts* o,
                      double* hist, int64_t* sweeps_done, double* final_rel_res) {
@@ -189,11 +240,12 @@ int solve_device(hpscd_ctx* ctx, const void* X, int dtype, int layout, int64_t m
   GridCtl* ctl = reinterpret_cast<GridCtl*>(ws + L.ctl);
   cudaStream_t st = ctx->stream;
 
-  if (cudaEventRecord(ctx->ev[0], st) != cudaSuccess) return HPSCD_ERR_CUDA;
-  if (launch_gram(X, dtype, m, (int)n, ld, P.gp, reinterpret_cast<double*>(ws + L.partial), G,
-                  P.gp.npad, st) != cudaSuccess)
-    return HPSCD_ERR_CUDA;
   if (cudaMemsetAsync(ctl, 0, sizeof(GridCtl), st) != cudaSuccess) return HPSCD_ERR_CUDA;
+  if (cudaEventRecord(ctx->ev[0], st) != cudaSuccess) return HPSCD_ERR_CUDA;
+  int gram_launches = 0;
+  int rcg = run_gram(ctx, X, dtype, m, n, ld, P, ws + L.partial, G, P.ldG, &ctl->err,
+                     (o->debug_flags & HPSCD_DEBUG_SIMT_GRAM) != 0, &gram_launches);
+  if (rcg != HPSCD_OK) return rcg;
   if (cudaMemsetAsync(ws + L.gpart, 0, (size_t)2 * P.gstride * P.cfg.npad * sizeof(float), st) !=
       cudaSuccess)
     return HPSCD_ERR_CUDA;
@@ -214,7 +266,7 @@ int solve_device(hpscd_ctx* ctx, const void* X, int dtype, int layout, int64_t m
   p.a_in = a;
   p.warm = a_is_guess ? 1 : 0;
   p.G = G;
-  p.ldG = P.gp.npad;
+  p.ldG = P.ldG;
   p.gpart = reinterpret_cast<float*>(ws + L.gpart);
   p.gstride = P.gstride;
   p.npart = reinterpret_cast<double*>(ws + L.npart);
@@ -263,7 +315,7 @@ int solve_device(hpscd_ctx* ctx, const void* X, int dtype, int layout, int64_t m
   t.passes = c.passes;
   t.x_bytes = m * n * esize(dtype);
   t.grid = P.grid;
-  t.kernel_launches = 3;
+  t.kernel_launches = gram_launches + 1;
   ctx->last = t;
   (void)layout;
   if (c.err != DEV_OK) return HPSCD_ERR_TIMEOUT;
@@ -447,6 +499,46 @@ int hpscd_get_trace(hpscd_ctx* ctx, unsigned long long* out, int64_t words, int6
     return HPSCD_ERR_CUDA;
   if (written) *written = avail;
   return HPSCD_OK;
+}
+
+int hpscd_gram(hpscd_ctx* ctx, const void* X, int dtype, int64_t m, int64_t n, int64_t ld,
+               float* G, int64_t ldG, int flags) {
+  if (!ctx) return HPSCD_ERR_INVALID_ARG;
+  int rc = check_shape(dtype, HPSCD_COL_MAJOR, m, n, ld);
+  if (rc) return rc;
+  if (m < 1 || n < 1 || !X || !G || ldG < n || (flags & ~HPSCD_DEBUG_SIMT_GRAM))
+    return HPSCD_ERR_INVALID_ARG;
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return HPSCD_ERR_CUDA;
+  hpscd_opts o{};
+  o.max_sweeps = 0;
+  Plan P;
+  if ((rc = make_plan(ctx, dtype, HPSCD_COL_MAJOR, m, n, ld, &o, false, &P))) return rc;
+  if ((rc = ensure_ws(ctx, P.L.total))) return rc;
+  char* ws = static_cast<char*>(ctx->ws);
+  float* Gw = reinterpret_cast<float*>(ws + P.L.G);
+  GridCtl* ctl = reinterpret_cast<GridCtl*>(ws + P.L.ctl);
+  cudaStream_t st = ctx->stream;
+  if (cudaMemsetAsync(ctl, 0, sizeof(GridCtl), st) != cudaSuccess) return HPSCD_ERR_CUDA;
+  if (cudaEventRecord(ctx->ev[0], st) != cudaSuccess) return HPSCD_ERR_CUDA;
+  int launches = 0;
+  rc = run_gram(ctx, X, dtype, m, n, ld, P, ws + P.L.partial, Gw, P.ldG, &ctl->err,
+                (flags & HPSCD_DEBUG_SIMT_GRAM) != 0, &launches);
+  if (rc) return rc;
+  if (cudaEventRecord(ctx->ev[1], st) != cudaSuccess) return HPSCD_ERR_CUDA;
+  if (cudaMemcpy2DAsync(G, (size_t)ldG * sizeof(float), Gw, (size_t)P.ldG * sizeof(float),
+                        (size_t)n * sizeof(float), (size_t)n, cudaMemcpyDeviceToDevice, st) !=
+      cudaSuccess)
+    return HPSCD_ERR_CUDA;
+  if (cudaMemcpyAsync(ctx->ctl_host, ctl, sizeof(GridCtl), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return HPSCD_ERR_CUDA;
+  hpscd_timing t{};
+  cudaEventElapsedTime(&t.setup_ms, ctx->ev[0], ctx->ev[1]);
+  t.x_bytes = m * n * esize(dtype);
+  t.kernel_launches = launches;
+  ctx->last = t;
+  return ctx->ctl_host->err ? HPSCD_ERR_TIMEOUT : HPSCD_OK;
 }
 
 int hpscd_last_timing(hpscd_ctx* ctx, hpscd_timing* out) {

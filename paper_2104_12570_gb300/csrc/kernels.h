@@ -20,6 +20,37 @@ GramPlan gram_plan(int64_t m, int npad, int sms);
 cudaError_t launch_gram(const void* X, int dtype, int64_t m, int n, int64_t ld, const GramPlan& gp,
                         double* partial, float* G, int ldG, cudaStream_t stream);
 
+// ---- tensor-core Gram set-up (tcgen05), G = X^T X ----
+struct GramTCPlan {
+  int npad;                 // multiple of 128
+  int ngroups;              // groups of 128-column block rows (TMEM capacity)
+  int group_rows[4][4];     // block rows of each group
+  int group_count[4];
+  int group_nload[4];       // column blocks a group streams (0..max row)
+  int ksplit;
+  int64_t rows_per_split;
+  int nstages;
+  int smem_bytes;
+  size_t partial_bytes;     // float32 partials [ksplit][npad][npad] + float64 [ksplit][npad]
+};
+struct GramTCParams {
+  int64_t m;
+  int npad;
+  int group_rows[4][4];
+  int group_count[4];
+  int group_nload[4];
+  int64_t rows_per_split;
+  float* partial;
+  double* dpart;   // [ksplit][npad] CUDA-core sums of squares (the diagonal)
+  int* err;
+  uint64_t timeout_ns;
+  int nstages;
+};
+bool gram_tc_plan(int dtype, int64_t m, int n, int sms, int max_smem, GramTCPlan* gp);
+cudaError_t launch_gram_tc(const CUtensorMap* tmap, int dtype, int64_t m, const GramTCPlan& gp,
+                           float* partial, int* err, uint64_t timeout_ns, float* G, int ldG,
+                           cudaStream_t stream);
+
 // ---- persistent tall sweep (column-major X, n <= 512) ----
 constexpr int MODE_COPY = 0, MODE_NORMAL = 1, MODE_REFRESH = 2;
 

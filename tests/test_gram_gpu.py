@@ -1,0 +1,67 @@
+"""The Gram set-up G = X^T X (the denominators <X_j, X_j> of Eq. da2 and the
+couplings <X_j, X_l> of Eq. ek1-ek inside a sweep) on the GPU, through the C
+ABI, against float64 X^T X computed on the host.
+
+Bound: each entry within 4e-6·sqrt(G_ii G_jj) (float32-grade: float32
+accumulation of products that are exact for bfloat16 X and carry ~2^-21
+relative error for float32 X split into two tf32 terms)."""
+import numpy as np
+import pytest
+
+from paper_2104_12570_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2104_12570_gb300 as hp  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = hp.Context(0)
+    yield c
+    c.close()
+
+
+def gpu_X(s):
+    if s.dtype == "bf16":
+        return torch.from_numpy(s.X.view(np.int16)).view(torch.bfloat16).cuda().T
+    return torch.from_numpy(s.X).cuda().T
+
+
+def check(G, s, tol=4e-6):
+    Xd = s.dense_f64()
+    G64 = Xd.T @ Xd
+    d = np.sqrt(np.clip(np.diag(G64), 1e-300, None))
+    err = np.abs(G.cpu().numpy().astype(np.float64) - G64) / np.outer(d, d)
+    assert err.max() <= tol, err.max()
+    np.testing.assert_array_equal(G.cpu().numpy(), G.cpu().numpy().T)  # symmetric
+
+
+@pytest.mark.parametrize("m,n,dtype", [(64, 1, "f32"), (200, 50, "f32"), (1000, 37, "f32"),
+                                       (5000, 256, "f32"), (4099, 129, "f32"),
+                                       (777, 300, "bf16"), (3333, 100, "bf16"),
+                                       (20000, 512, "bf16"), (130, 256, "bf16")])
+def test_gram_matches_float64(ctx, m, n, dtype):
+    s = synth.make_system(m, n, seed=m + n, dtype=dtype)
+    X = gpu_X(s)
+    check(ctx.gram(X), s)
+    check(ctx.gram(X, simt=True), s)
+
+
+def test_gram_tensor_core_vs_cuda_core(ctx):
+    s = synth.make_system(100_000, 256, seed=3)
+    X = gpu_X(s)
+    Gt = ctx.gram(X).cpu().numpy().astype(np.float64)
+    Gs = ctx.gram(X, simt=True).cpu().numpy().astype(np.float64)
+    d = np.sqrt(np.diag(Gs))
+    assert (np.abs(Gt - Gs) / np.outer(d, d)).max() <= 2e-6
+
+
+def test_solve_same_with_either_gram(ctx):
+    s = synth.make_system(30_000, 200, seed=4, noise=0.01)
+    X = gpu_X(s)
+    y = torch.from_numpy(s.y).cuda()
+    a = ctx.solve(X, y, tol=0, max_sweeps=5, stop="none").a.cpu().numpy()
+    b = ctx.solve(X, y, tol=0, max_sweeps=5, stop="none", debug_flags=2).a.cpu().numpy()
+    assert np.linalg.norm(a - b) / np.linalg.norm(b) <= 2e-6
