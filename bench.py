@@ -179,6 +179,43 @@ def cpu_baseline_leg(s, budget_s=30.0):
             "seconds": dt}
 
 
+def precision_comparison(hp, synth, ctx, dev, steps=5, warmup=3):
+    """Time to relative residual 1e-6 on the 4,000,000 x 512 consistent system: X
+    stored bfloat16 (float32 accumulation, true-residual refresh every 4 passes)
+    against the same values stored float32 (plain float32 sweep)."""
+    import torch
+    s = synth.workload("tall_4Mx512_bf16", seed=0)
+    Xb = torch.from_numpy(s.X.view(np.int16)).view(torch.bfloat16).to(dev).T
+    y = torch.from_numpy(s.y).to(dev)
+    out = {"workload": "tall_4Mx512 (X iid N(0,1) rounded to bfloat16, consistent)",
+           "stop": "rel_res<=1e-6"}
+    for name, X, kw in (("bf16_refresh4", Xb, dict(refresh_every=4)),
+                        ("f32_plain", None, {})):
+        if X is None:
+            X = Xb.T.float().contiguous().T
+            del Xb
+        for _ in range(warmup):
+            r = ctx.solve(X, y, tol=1e-6, max_sweeps=100, stop="rel_res", **kw)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            r = ctx.solve(X, y, tol=1e-6, max_sweeps=100, stop="rel_res", **kw)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        esz = 2 if X.dtype == torch.bfloat16 else 4
+        nbytes = algorithmic_bytes(s.m, s.n, esz, r.timing["passes"])
+        out[name] = {"ms_to_tol": ms, "GBps": nbytes / (ms * 1e-3) / 1e9, "sweeps": int(r.sweeps),
+                     "rel_res": float(r.rel_res), "setup_ms": float(r.timing["setup_ms"]),
+                     "sweep_kernel_ms": float(r.timing["sweep_ms"]),
+                     "sweep_kernel_GBps": sweep_kernel_bytes(s.m, s.n, esz, r.timing["passes"])
+                     / (r.timing["sweep_ms"] * 1e-3) / 1e9}
+        del X
+    out["bf16_speedup_time_to_tol"] = out["f32_plain"]["ms_to_tol"] / out["bf16_refresh4"]["ms_to_tol"]
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -187,6 +224,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--no-compare", action="store_true",
+                    help="skip the bfloat16-vs-float32 comparison on the 4,000,000 x 512 system")
     ap.add_argument("--rows", type=int, default=0,
                     help="override m (smaller case for profiler captures; not a bench line)")
     args = ap.parse_args()
@@ -291,6 +330,10 @@ def main():
         }
         if not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline_leg(s)
+        if not args.no_compare and not args.rows:
+            del X
+            torch.cuda.empty_cache()
+            out["precision_mode"] = precision_comparison(hp, synth, ctx, dev)
         print(json.dumps(out), flush=True)
     ctx.close()
     if world > 1:
