@@ -126,9 +126,12 @@ int hpscd_set_workspace(hpscd_ctx* ctx, void* ptr, size_t bytes);
 /*
  * Solve X·a ≈ y by sweeps of Algorithm 1 (Sec. 2) on the GPU.
  *   X      device, dtype HPSCD_F32 (float) or HPSCD_BF16 (bfloat16), layout/ld
- *          as above.  Column-major: any m, n <= 512 (tall and square systems).
- *          Row-major: any n, m <= 4096 (wide systems; the transposed path).
- *          Other combinations return HPSCD_ERR_UNSUPPORTED.
+ *          as above.  Column-major: any m, n <= 512 (tall and square systems;
+ *          float32 or bfloat16).  Row-major: float32, any n, m <= 4096 (wide
+ *          systems; TMA tiles when X is 16-byte aligned and ld a multiple
+ *          of 4, plain loads otherwise): one
+ *          thread-block cluster walks the column chain with TMA-re-tiled
+ *          row-major blocks).  Other combinations return HPSCD_ERR_UNSUPPORTED.
  *   y      device float[m].
  *   a      device float[n]; in: the initial guess when a_is_guess != 0
  *          (Algorithm 2's "or initial guess"), ignored otherwise (0_n);

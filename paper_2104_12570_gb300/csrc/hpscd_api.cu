@@ -212,6 +212,116 @@ int run_gram(hpscd_ctx* ctx, const void* X, int dtype, int64_t m, int64_t n, int
   return HPSCD_OK;
 }
 
+// ---- wide systems: row-major X, m <= 4096 (the cluster sweep) ----
+struct WideLayout {
+  size_t Gb = 0, e = 0, a64 = 0, dsw = 0, atmp = 0, ysq = 0, hist = 0, ctl = 0, xcopy = 0, ycopy = 0,
+         acopy = 0, total = 0;
+};
+
+int make_wide_plan(const hpscd_ctx* ctx, int dtype, int64_t m, int64_t n, int64_t ld,
+                   const hpscd_opts* o, bool host_copies, WideConfig* cfg, WideLayout* L) {
+  if (dtype != HPSCD_F32) return HPSCD_ERR_UNSUPPORTED;
+  if (!wide_config(m, ctx->max_smem, cfg)) return HPSCD_ERR_UNSUPPORTED;
+  const int64_t nblk = (n + 63) / 64;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = off;
+    off = align_up(off + bytes, 256);
+    return at;
+  };
+  L->Gb = take((size_t)nblk * 64 * 64 * sizeof(float));
+  L->e = take((size_t)m * sizeof(float));
+  L->a64 = take((size_t)n * sizeof(double));
+  L->dsw = take((size_t)n * sizeof(float));
+  L->atmp = take((size_t)n * sizeof(float));
+  L->ysq = take(sizeof(double));
+  L->hist = take((size_t)(o->max_sweeps + 1) * sizeof(double));
+  L->ctl = take(sizeof(GridCtl));
+  if (host_copies) {
+    L->xcopy = take((size_t)m * ld * sizeof(float));
+    L->ycopy = take((size_t)m * sizeof(float));
+    L->acopy = take((size_t)n * sizeof(float));
+  }
+  L->total = off;
+  return HPSCD_OK;
+}
+
+int solve_wide(hpscd_ctx* ctx, const void* X, int64_t m, int64_t n, int64_t ld, const float* y,
+               float* a, int a_is_guess, const hpscd_opts* o, double* hist, int64_t* sweeps_done,
+               double* final_rel_res, const WideConfig& cfg, const WideLayout& L) {
+  const bool aligned = ctx->encode && (reinterpret_cast<uintptr_t>(X) & 15) == 0 && (ld * 4) % 16 == 0;
+  char* ws = static_cast<char*>(ctx->ws);
+  GridCtl* ctl = reinterpret_cast<GridCtl*>(ws + L.ctl);
+  cudaStream_t st = ctx->stream;
+  CUtensorMap map;
+  memset(&map, 0, sizeof(map));
+  cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)m};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * 4};
+  cuuint32_t box[2] = {64, (cuuint32_t)cfg.rows_box};
+  cuuint32_t estr[2] = {1, 1};
+  const int use_tma =
+      aligned && ctx->encode(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(X), dims,
+                             strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+  if (cudaMemsetAsync(ctl, 0, sizeof(GridCtl), st) != cudaSuccess) return HPSCD_ERR_CUDA;
+  if (cudaEventRecord(ctx->ev[0], st) != cudaSuccess) return HPSCD_ERR_CUDA;
+  WideParams p{};
+  p.X = static_cast<const float*>(X);
+  p.use_tma = use_tma;
+  p.m = m;
+  p.n = n;
+  p.ld = ld;
+  p.Gb = reinterpret_cast<float*>(ws + L.Gb);
+  p.e = reinterpret_cast<float*>(ws + L.e);
+  p.a64 = reinterpret_cast<double*>(ws + L.a64);
+  p.dsw = reinterpret_cast<float*>(ws + L.dsw);
+  p.a_out = a;
+  p.ysq = reinterpret_cast<double*>(ws + L.ysq);
+  p.hist = reinterpret_cast<double*>(ws + L.hist);
+  p.ctl = ctl;
+  p.tol = o->tol;
+  p.max_sweeps = o->max_sweeps;
+  p.stop_rule = o->stop_rule;
+  p.timeout_ns = (uint64_t)(ctx->timeout_s * 1e9);
+  p.trace = nullptr;
+  p.trace_passes = 0;
+  if (ctx->trace_passes > 0 && ctx->trace_dev) {
+    if (cudaMemsetAsync(ctx->trace_dev, 0, (size_t)ctx->trace_passes * 6 * sizeof(unsigned long long),
+                        st) != cudaSuccess)
+      return HPSCD_ERR_CUDA;
+    p.trace = ctx->trace_dev;
+    p.trace_passes = ctx->trace_passes;
+    ctx->trace_grid = 0;
+  }
+  if (launch_wide(static_cast<const float*>(X), m, n, ld, cfg, &map, p, y, a, a_is_guess,
+                  reinterpret_cast<float*>(ws + L.atmp), st) != cudaSuccess) {
+    cudaGetLastError();
+    return HPSCD_ERR_CUDA;
+  }
+  if (cudaEventRecord(ctx->ev[2], st) != cudaSuccess) return HPSCD_ERR_CUDA;
+  if (cudaMemcpyAsync(ctx->ctl_host, ctl, sizeof(GridCtl), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return HPSCD_ERR_CUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return HPSCD_ERR_CUDA;
+  const GridCtl c = *ctx->ctl_host;
+  if (hist && c.sweeps >= 0 && c.sweeps <= o->max_sweeps) {
+    if (cudaMemcpy(hist, p.hist, (size_t)(c.sweeps + 1) * sizeof(double), cudaMemcpyDeviceToHost) !=
+        cudaSuccess)
+      return HPSCD_ERR_CUDA;
+  }
+  if (sweeps_done) *sweeps_done = c.sweeps;
+  if (final_rel_res) *final_rel_res = c.final_res;
+  hpscd_timing t{};
+  cudaEventElapsedTime(&t.sweep_ms, ctx->ev[0], ctx->ev[2]);
+  t.passes = c.passes;
+  t.x_bytes = m * n * 4;
+  t.grid = cfg.csize;
+  t.kernel_launches = 6;
+  ctx->last = t;
+  if (c.err != DEV_OK) return HPSCD_ERR_TIMEOUT;
+  return c.status;
+}
+
 // m == 0: nothing to sweep; y = 0, so every recorded residual is the absolute norm 0.
 int solve_empty_rows(hpscd_ctx* ctx, int64_t n, float* a, int a_is_guess, const hpscd_opts* o,
                      double* hist, int64_t* sweeps_done, double* final_rel_res) {
@@ -396,8 +506,15 @@ int hpscd_workspace_size(hpscd_ctx* ctx, int dtype, int layout, int64_t m, int64
   if (rc) return rc;
   const int64_t ld = layout == HPSCD_COL_MAJOR ? (m > 1 ? m : 1) : (n > 1 ? n : 1);
   if ((rc = check_shape(dtype, layout, m, n, ld))) return rc;
+  if (layout == HPSCD_ROW_MAJOR && m > 0 && n > 0) {
+    WideConfig wc;
+    WideLayout wl;
+    if ((rc = make_wide_plan(ctx, dtype, m, n, ld, opts, false, &wc, &wl))) return rc;
+    *bytes = wl.total;
+    return HPSCD_OK;
+  }
   Plan P;
-  if ((rc = make_plan(ctx, dtype, layout, m, n, ld, opts, false, &P))) return rc;
+  if ((rc = make_plan(ctx, dtype, HPSCD_COL_MAJOR, m, n, m > 1 ? m : 1, opts, false, &P))) return rc;
   *bytes = P.L.total;
   return HPSCD_OK;
 }
@@ -424,6 +541,15 @@ int hpscd_solve(hpscd_ctx* ctx, const void* X, int dtype, int layout, int64_t m,
   if ((m > 0 && n > 0 && !X) || (m > 0 && !y) || (n > 0 && !a)) return HPSCD_ERR_INVALID_ARG;
   DeviceGuard g(ctx->device);
   if (!g.ok) return HPSCD_ERR_CUDA;
+  if (layout == HPSCD_ROW_MAJOR && m > 0 && n > 0) {
+    WideConfig wc;
+    WideLayout wl;
+    if ((rc = make_wide_plan(ctx, dtype, m, n, ld, opts, false, &wc, &wl))) return rc;
+    if ((rc = ensure_ws(ctx, wl.total))) return rc;
+    return solve_wide(ctx, X, m, n, ld, y, a, a_is_guess, opts, hist, sweeps_done, final_rel_res,
+                      wc, wl);
+  }
+  if (layout == HPSCD_ROW_MAJOR) { layout = HPSCD_COL_MAJOR; ld = m > 1 ? m : 1; }
   Plan P;
   if ((rc = make_plan(ctx, dtype, layout, m, n, ld, opts, false, &P))) return rc;
   if ((rc = ensure_ws(ctx, P.L.total))) return rc;
@@ -442,13 +568,22 @@ int hpscd_solve_host(hpscd_ctx* ctx, const void* X, int dtype, int layout, int64
   if ((m > 0 && n > 0 && !X) || (m > 0 && !y) || (n > 0 && !a)) return HPSCD_ERR_INVALID_ARG;
   DeviceGuard g(ctx->device);
   if (!g.ok) return HPSCD_ERR_CUDA;
+  const bool wide = layout == HPSCD_ROW_MAJOR && m > 0 && n > 0;
+  if (layout == HPSCD_ROW_MAJOR && !wide) { layout = HPSCD_COL_MAJOR; ld = m > 1 ? m : 1; }
   Plan P;
-  if ((rc = make_plan(ctx, dtype, layout, m, n, ld, opts, true, &P))) return rc;
-  if ((rc = ensure_ws(ctx, P.L.total))) return rc;
+  WideConfig wc;
+  WideLayout wl;
+  if (wide) {
+    if ((rc = make_wide_plan(ctx, dtype, m, n, ld, opts, true, &wc, &wl))) return rc;
+    if ((rc = ensure_ws(ctx, wl.total))) return rc;
+  } else {
+    if ((rc = make_plan(ctx, dtype, layout, m, n, ld, opts, true, &P))) return rc;
+    if ((rc = ensure_ws(ctx, P.L.total))) return rc;
+  }
   char* ws = static_cast<char*>(ctx->ws);
-  void* Xd = ws + P.L.xcopy;
-  float* yd = reinterpret_cast<float*>(ws + P.L.ycopy);
-  float* ad = reinterpret_cast<float*>(ws + P.L.acopy);
+  void* Xd = ws + (wide ? wl.xcopy : P.L.xcopy);
+  float* yd = reinterpret_cast<float*>(ws + (wide ? wl.ycopy : P.L.ycopy));
+  float* ad = reinterpret_cast<float*>(ws + (wide ? wl.acopy : P.L.acopy));
   cudaStream_t st = ctx->stream;
   const size_t xbytes = layout == HPSCD_COL_MAJOR ? (size_t)n * ld * esize(dtype)
                                                   : (size_t)m * ld * esize(dtype);
@@ -459,8 +594,10 @@ int hpscd_solve_host(hpscd_ctx* ctx, const void* X, int dtype, int layout, int64
   if (n > 0 && a_is_guess &&
       cudaMemcpyAsync(ad, a, (size_t)n * sizeof(float), cudaMemcpyHostToDevice, st) != cudaSuccess)
     return HPSCD_ERR_CUDA;
-  rc = solve_device(ctx, Xd, dtype, layout, m, n, ld, yd, ad, a_is_guess, opts, hist, sweeps_done,
-                    final_rel_res, P);
+  rc = wide ? solve_wide(ctx, Xd, m, n, ld, yd, ad, a_is_guess, opts, hist, sweeps_done,
+                         final_rel_res, wc, wl)
+            : solve_device(ctx, Xd, dtype, layout, m, n, ld, yd, ad, a_is_guess, opts, hist,
+                           sweeps_done, final_rel_res, P);
   if (rc == HPSCD_ERR_CUDA || rc == HPSCD_ERR_INVALID_ARG || rc == HPSCD_ERR_UNSUPPORTED) return rc;
   if (n > 0 && cudaMemcpyAsync(a, ad, (size_t)n * sizeof(float), cudaMemcpyDeviceToHost, st) != cudaSuccess)
     return HPSCD_ERR_CUDA;

@@ -95,4 +95,33 @@ bool tall_config(int dtype, int n, int max_smem, TallConfig* cfg);
 cudaError_t launch_tall_sweep(int dtype, const TallConfig& cfg, const CUtensorMap* tmap,
                               const TallParams& p, int grid, cudaStream_t stream);
 
+// ---- wide sweep (row-major X, m <= 4096): one thread-block cluster ----
+struct WideParams {
+  const float* X;    // row-major X (plain-load path)
+  int use_tma;
+  int64_t m, n, ld;
+  float* Gb;         // [nblk][64][64] Gram blocks (set-up)
+  float* e;          // [m] residual (in: initial; out: final)
+  double* a64;       // [n] coefficients
+  float* dsw;        // [n] da of the current sweep
+  float* a_out;      // [n]
+  double* ysq;       // ||y||^2 (device)
+  double* hist;
+  GridCtl* ctl;
+  double tol;
+  int64_t max_sweeps;
+  int stop_rule;
+  int csize, rows_box, nstages;
+  uint64_t timeout_ns;
+  unsigned long long* trace;  // optional: per-block phase stamps of the first blocks
+  int trace_passes;
+};
+struct WideConfig {
+  int csize, rows_box, nstages, smem_bytes;
+};
+bool wide_config(int64_t m, int max_smem, WideConfig* cfg);
+cudaError_t launch_wide(const float* X, int64_t m, int64_t n, int64_t ld, const WideConfig& cfg,
+                        const CUtensorMap* tmap, WideParams p, const float* y, const float* a_in,
+                        int warm, float* a_tmp, cudaStream_t stream);
+
 }  // namespace hpscd
