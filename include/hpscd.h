@@ -205,6 +205,84 @@ int hpscd_solve_noalloc(void* stream, const void* X, int dtype, int64_t m, int64
                         const float* y, float* a, int a_is_guess, const hpscd_opts* opts,
                         double* hist, int64_t* sweeps_done, double* final_rel_res);
 
+/* ---- batched solves (many independent systems, one persistent launch) ----
+ *
+ * The paper notes that solving many similar systems repeatedly is where the
+ * method pays (Sec. 9); a batch sweeps every system of a list with Algorithm 1
+ * (the same restated sweep and stopping rules as hpscd_solve) in ONE
+ * persistent kernel launch, replayed from a CUDA graph captured once. */
+
+/* One system of a batch.  All pointers are DEVICE pointers owned by the
+ * caller; X column-major (element (i, j) at X[j*ld + i]). */
+typedef struct {
+  const void* X;       /* float32, m×n, ld >= max(m, 1) */
+  const float* y;      /* float[m] */
+  float* a;            /* float[n]: in: guess when a_is_guess != 0; out: coefficients */
+  double* hist;        /* double[max_sweeps + 1] or NULL: residual history */
+  int64_t m;           /* 0 <= m <= max rows of the batch (see hpscd_batch_create) */
+  int64_t n;           /* 0 <= n <= 256 */
+  int64_t ld;
+  int32_t a_is_guess;
+  int32_t reserved;    /* must be zero */
+} hpscd_sys;
+
+/* Result of one system of a batch. */
+typedef struct {
+  int64_t sweeps;      /* sweeps made */
+  double rel_res;      /* hist[sweeps] */
+  int32_t status;      /* hpscd_status of this system */
+  int32_t passes;      /* streaming passes over its X (sweeps + 1) */
+} hpscd_sys_result;
+
+/* Launch shape of a batch.  cluster = CTAs that share one system (1, 2, 4 or
+ * 8; each CTA owns a slice of its rows and of its residual); 0 = let the
+ * library pick.  hpscd_autotune_batch fills this by timing candidates. */
+typedef struct {
+  int32_t cluster;
+  int32_t reserved[7]; /* must be zero */
+} hpscd_tuning;
+
+typedef struct hpscd_batch hpscd_batch;
+
+/*
+ * Plan a batch of `count` systems (sys: HOST array of descriptors, copied;
+ * the device buffers they point to must stay valid while the batch is used).
+ * dtype must be HPSCD_F32.  Every system: 0 <= n <= 256 and m small enough
+ * for its residual slice to stay in shared memory (m <= 16384 per CTA of a
+ * cluster, i.e. m <= 16384·cluster); opts->refresh_every and debug_flags
+ * must be 0.  The call allocates the batch's device workspace (descriptors,
+ * queue order by decreasing m·n, per-cluster Gram slots, results) and captures
+ * the launch sequence (queue reset, persistent kernel) in a CUDA graph on the
+ * context's device.  Errors: INVALID_ARG, UNSUPPORTED, NO_MEMORY, CUDA.
+ */
+int hpscd_batch_create(hpscd_ctx* ctx, const hpscd_sys* sys, int64_t count, int dtype,
+                       const hpscd_opts* opts, const hpscd_tuning* tuning, hpscd_batch** out);
+
+/* Replay the batch's graph on the context's stream (asynchronous; the
+ * systems' a and hist and the results are complete when the stream reaches
+ * this point).  CUDA-event timing goes to hpscd_last_timing (sweep_ms). */
+int hpscd_batch_launch(hpscd_batch* b);
+
+/* Wait for the last launch and copy the per-system results to the HOST array
+ * out[count].  Returns OK, or the first non-OK status among the systems. */
+int hpscd_batch_results(hpscd_batch* b, hpscd_sys_result* out);
+
+/* The tuning the batch was planned with. */
+int hpscd_batch_tuning(hpscd_batch* b, hpscd_tuning* out);
+
+/* Release the batch (waits for its last launch).  NULL is accepted. */
+int hpscd_batch_destroy(hpscd_batch* b);
+
+/*
+ * Autotuner: plans the batch with each candidate cluster size that fits,
+ * times `trial_sweeps` sweeps of every system (stop rule NONE, systems' a and
+ * hist written as by a solve) with CUDA events, and returns the fastest in
+ * *out (ms_per_candidate: HOST double[4] or NULL, the time of clusters 1, 2,
+ * 4, 8; a candidate that does not fit reads as a negative number).
+ */
+int hpscd_autotune_batch(hpscd_ctx* ctx, const hpscd_sys* sys, int64_t count, int dtype,
+                         int64_t trial_sweeps, hpscd_tuning* out, double* ms_per_candidate);
+
 /* Static description of a status code. */
 const char* hpscd_status_string(int status);
 

@@ -21,7 +21,7 @@ import numpy as np
 
 from . import build as _build
 
-__all__ = ["Context", "solve", "solve_host", "HpscdError", "load", "STATUS"]
+__all__ = ["Context", "Batch", "solve", "solve_host", "HpscdError", "load", "STATUS"]
 
 STATUS = {0: "ok", 1: "invalid_arg", 2: "not_converged", 3: "nonfinite", 4: "timeout",
           5: "cuda_error", 6: "unsupported", 7: "no_memory"}
@@ -50,6 +50,21 @@ class Timing(ctypes.Structure):
     _fields_ = [("setup_ms", ctypes.c_float), ("sweep_ms", ctypes.c_float),
                 ("passes", ctypes.c_int64), ("x_bytes", ctypes.c_int64),
                 ("grid", ctypes.c_int32), ("kernel_launches", ctypes.c_int32)]
+
+
+class Sys(ctypes.Structure):
+    _fields_ = [("X", ctypes.c_void_p), ("y", ctypes.c_void_p), ("a", ctypes.c_void_p),
+                ("hist", ctypes.c_void_p), ("m", ctypes.c_int64), ("n", ctypes.c_int64),
+                ("ld", ctypes.c_int64), ("a_is_guess", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class SysResult(ctypes.Structure):
+    _fields_ = [("sweeps", ctypes.c_int64), ("rel_res", ctypes.c_double),
+                ("status", ctypes.c_int32), ("passes", ctypes.c_int32)]
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("cluster", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
 
 
 SIGNATURES = {
@@ -81,6 +96,16 @@ SIGNATURES = {
     "hpscd_set_trace": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
     "hpscd_get_trace": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_ulonglong), ctypes.c_int64,
                          ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
+    "hpscd_batch_create": ([ctypes.c_void_p, ctypes.POINTER(Sys), ctypes.c_int64, ctypes.c_int,
+                            ctypes.POINTER(Opts), ctypes.POINTER(Tuning),
+                            ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
+    "hpscd_batch_launch": ([ctypes.c_void_p], ctypes.c_int),
+    "hpscd_batch_results": ([ctypes.c_void_p, ctypes.POINTER(SysResult)], ctypes.c_int),
+    "hpscd_batch_tuning": ([ctypes.c_void_p, ctypes.POINTER(Tuning)], ctypes.c_int),
+    "hpscd_batch_destroy": ([ctypes.c_void_p], ctypes.c_int),
+    "hpscd_autotune_batch": ([ctypes.c_void_p, ctypes.POINTER(Sys), ctypes.c_int64, ctypes.c_int,
+                              ctypes.c_int64, ctypes.POINTER(Tuning),
+                              ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "hpscd_status_string": ([ctypes.c_int], ctypes.c_char_p),
 }
 
@@ -323,6 +348,109 @@ class Context:
                                         hist.ctypes.data_as(ctypes.c_void_p), ctypes.byref(sw),
                                         ctypes.byref(rr))
         return self._finish(rc, hist, sw, rr, a)
+
+
+def _sys_array(systems, hist_len=0):
+    """ctypes array of hpscd_sys from (X, y, a, a_is_guess[, hist]) CUDA tensors."""
+    import torch
+    arr = (Sys * max(1, len(systems)))()
+    for i, t in enumerate(systems):
+        X, y, a, guess = t[:4]
+        hist = t[4] if len(t) > 4 else None
+        ptr, dt, lay, m, n, ld = _describe(X)
+        if dt != F32 or lay != COL:
+            raise TypeError("batched systems need a float32 column-major X")
+        for v, ln in ((y, m), (a, n)):
+            if not (isinstance(v, torch.Tensor) and v.is_cuda and v.dtype == torch.float32
+                    and v.is_contiguous() and v.numel() == ln):
+                raise TypeError("y and a must be contiguous float32 CUDA vectors of length m, n")
+        arr[i].X, arr[i].y, arr[i].a = ptr, y.data_ptr(), a.data_ptr()
+        arr[i].hist = hist.data_ptr() if hist is not None else None
+        arr[i].m, arr[i].n, arr[i].ld = m, n, ld
+        arr[i].a_is_guess = 1 if guess else 0
+    return arr
+
+
+class Batch:
+    """Many independent column-major float32 systems solved in one persistent,
+    graph-captured launch (hpscd_batch_*).  `systems` is a list of tuples
+    (X, y, a, a_is_guess) or (X, y, a, a_is_guess, hist) of CUDA tensors: X (m, n)
+    column-major, y (m,), a (n,) in/out, hist (max_sweeps + 1,) float64 or None.
+    The tensors must stay alive while the batch is used (the batch keeps them)."""
+
+    def __init__(self, ctx: "Context", systems, *, tol=1e-6, max_sweeps=1000, stop="rel_res",
+                 cluster: int = 0):
+        import torch
+        self._lib = ctx._lib
+        self.ctx = ctx
+        self.systems = list(systems)
+        self.count = len(self.systems)
+        self._sys = _sys_array(self.systems)
+        o = make_opts(tol, max_sweeps, stop)
+        t = Tuning()
+        t.cluster = int(cluster)
+        dev = self.systems[0][0].device if self.systems else torch.device("cuda", ctx.device)
+        ctx.set_stream(torch.cuda.current_stream(dev))
+        h = ctypes.c_void_p()
+        rc = self._lib.hpscd_batch_create(ctx._h, self._sys, self.count, F32, ctypes.byref(o),
+                                          ctypes.byref(t), ctypes.byref(h))
+        if rc:
+            raise HpscdError(rc, "hpscd_batch_create")
+        self._h = h
+        self._res = (SysResult * max(1, self.count))()
+
+    @property
+    def cluster(self) -> int:
+        t = Tuning()
+        self._lib.hpscd_batch_tuning(self._h, ctypes.byref(t))
+        return t.cluster
+
+    def launch(self):
+        rc = self._lib.hpscd_batch_launch(self._h)
+        if rc:
+            raise HpscdError(rc, "hpscd_batch_launch")
+
+    def results(self) -> dict:
+        """Wait for the last launch; per-system sweeps, rel_res, status, passes."""
+        rc = self._lib.hpscd_batch_results(self._h, self._res)
+        if rc in (1, 5):
+            raise HpscdError(rc, "hpscd_batch_results")
+        n = self.count
+        return {"sweeps": np.array([self._res[i].sweeps for i in range(n)], dtype=np.int64),
+                "rel_res": np.array([self._res[i].rel_res for i in range(n)]),
+                "status": [STATUS.get(self._res[i].status, str(self._res[i].status))
+                           for i in range(n)],
+                "passes": np.array([self._res[i].passes for i in range(n)], dtype=np.int64),
+                "timing": self.ctx.timing()}
+
+    def run(self) -> dict:
+        self.launch()
+        return self.results()
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.hpscd_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def autotune_batch(ctx: "Context", systems, trial_sweeps: int = 4):
+    """(best cluster size, {cluster: ms of trial_sweeps sweeps of every system})."""
+    import torch
+    arr = _sys_array(systems)
+    t = Tuning()
+    ms = (ctypes.c_double * 4)()
+    ctx.set_stream(torch.cuda.current_stream(systems[0][0].device))
+    rc = ctx._lib.hpscd_autotune_batch(ctx._h, arr, len(systems), F32, int(trial_sweeps),
+                                       ctypes.byref(t), ms)
+    if rc:
+        raise HpscdError(rc, "hpscd_autotune_batch")
+    return t.cluster, {k: ms[i] for i, k in enumerate((1, 2, 4, 8)) if ms[i] >= 0}
 
 
 def _host_f32(y, m):

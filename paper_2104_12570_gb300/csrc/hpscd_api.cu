@@ -7,27 +7,9 @@
 
 #include <new>
 
-#include "kernels.h"
+#include "ctx.h"
 
 using namespace hpscd;
-
-struct hpscd_ctx {
-  int device = 0;
-  cudaStream_t stream = nullptr;
-  int sms = 0;
-  int max_smem = 0;
-  void* ws = nullptr;
-  size_t ws_bytes = 0;
-  bool ws_owned = true;
-  double timeout_s = 5.0;
-  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
-  GridCtl* ctl_host = nullptr;  // pinned
-  hpscd_timing last{};
-  int trace_passes = 0;                  // 0: tracing off
-  unsigned long long* trace_dev = nullptr;
-  int trace_grid = 0;
-  PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
-};
 
 namespace {
 

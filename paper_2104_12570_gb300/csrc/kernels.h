@@ -124,4 +124,24 @@ cudaError_t launch_wide(const float* X, int64_t m, int64_t n, int64_t ld, const 
                         const CUtensorMap* tmap, WideParams p, const float* y, const float* a_in,
                         int warm, float* a_tmp, cudaStream_t stream);
 
+// ---- batched sweep: many column-major systems, one persistent launch ----
+struct BatchParams {
+  const hpscd_sys* sys;     // device [count]
+  const int* order;         // device [count]: queue order (decreasing m·n)
+  int count;
+  int* queue;               // device counter, zeroed before every launch
+  hpscd_sys_result* res;    // device [count]
+  float* gpart;             // [grid][256*256] partial Gram of each CTA
+  float* gfinal;            // [clusters][256*256] G~ = D^{-1} G of each cluster's system
+  float* dfinal;            // [clusters][256] d = diag(G)
+  int ecap;                 // residual rows held in shared memory per CTA
+  double tol;
+  int64_t max_sweeps;
+  int stop_rule;
+};
+int batched_smem_bytes(int64_t mmax, int K);
+int batched_ecap(int64_t mmax, int K);
+int batched_max_clusters(int K, int smem, int max_smem);
+cudaError_t launch_batched(const BatchParams& p, int K, int clusters, int smem, cudaStream_t stream);
+
 }  // namespace hpscd

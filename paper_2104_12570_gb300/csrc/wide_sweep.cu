@@ -31,11 +31,6 @@ constexpr int WW = 64;        // columns per block
 constexpr int WNT = 512;      // threads per CTA
 constexpr int WNW = WNT / 32;
 
-__device__ __forceinline__ uint32_t mapa_u32(uint32_t addr, uint32_t rank) {
-  uint32_t r;
-  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
-  return r;
-}
 __device__ __forceinline__ void st_cluster_f32(uint32_t addr, float v) {
   asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
 }
@@ -67,15 +62,6 @@ __device__ __forceinline__ bool wait_cluster_bounded(uint64_t* bar, uint32_t par
     if ((it & 63) == 0 && global_timer_ns() - t0 > timeout_ns) return false;
   }
   return false;
-}
-__device__ __forceinline__ uint32_t cluster_ctarank() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-  return r;
-}
-__device__ __forceinline__ void cluster_sync_all() {
-  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::
-                   : "memory");
 }
 
 }  // namespace

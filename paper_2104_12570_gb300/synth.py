@@ -156,3 +156,95 @@ def workload(name: str, seed: int = 0, **override) -> System:
     kw.update(override)
     m, n = kw.pop("m"), kw.pop("n")
     return make_system(m, n, seed, **kw)
+
+
+# ---- the batched family: many similar RBF systems (Sec. 9 notes the method
+# pays when similar systems are solved many times) ----
+#
+# Every system of the family takes the first n of 256 fixed centres c_k and the
+# first m of 16384 fixed inputs x_i, all iid U[0,1]^4 (drawn once, seed-fixed),
+# so a system is determined by (m, n, theta):
+#     X_ik = exp(-||x_i - c_k||^2 / (2 * 0.3^2))            (RBF features)
+#     y_i  = f_theta(x_i) = sum_k theta_k cos(omega_k . x_i + b_k) / 4
+# with omega_k ~ N(0, I_4) and b_k ~ U[0, 2 pi) drawn once, theta ~ N(0, I_16)
+# per system, m log-uniform in [256, 16384] and n uniform in [8, 256].
+RBF_MAX_M, RBF_MAX_N, RBF_DIM, RBF_THETA = 16384, 256, 4, 16
+RBF_WIDTH = 0.3
+
+
+@dataclass
+class RBFFamily:
+    C: np.ndarray      # (256, 4) centres
+    P: np.ndarray      # (16384, 4) inputs
+    omega: np.ndarray  # (16, 4)
+    b: np.ndarray      # (16,)
+    M: np.ndarray      # (256, 16384) float32: row k = feature column k over all inputs
+    F: np.ndarray      # (16384, 16) float64: cos(omega_k . x_i + b_k) / 4
+
+
+def rbf_family(seed: int = 0) -> RBFFamily:
+    g = np.random.Generator(np.random.Philox(np.random.SeedSequence([seed, 101])))
+    C = g.uniform(0.0, 1.0, (RBF_MAX_N, RBF_DIM))
+    P = g.uniform(0.0, 1.0, (RBF_MAX_M, RBF_DIM))
+    omega = g.standard_normal((RBF_THETA, RBF_DIM))
+    b = g.uniform(0.0, 2.0 * np.pi, RBF_THETA)
+    d2 = ((C[:, None, :] - P[None, :, :]) ** 2).sum(axis=-1)
+    M = np.exp(-d2 / (2.0 * RBF_WIDTH ** 2)).astype(np.float32)
+    F = np.cos(P @ omega.T + b) / 4.0
+    return RBFFamily(C=C, P=P, omega=omega, b=b, M=M, F=F)
+
+
+def rbf_params(count: int, seed: int):
+    """(m, n, theta) of `count` systems: m log-uniform [256, 16384], n uniform
+    [8, 256], theta ~ N(0, I_16)."""
+    g = np.random.Generator(np.random.Philox(np.random.SeedSequence([seed, 102])))
+    m = np.rint(np.exp(g.uniform(np.log(256.0), np.log(float(RBF_MAX_M)), count))).astype(np.int64)
+    m = np.clip(m, 256, RBF_MAX_M)
+    n = g.integers(8, RBF_MAX_N + 1, count).astype(np.int64)
+    theta = g.standard_normal((count, RBF_THETA))
+    return m, n, theta
+
+
+def rbf_rhs(fam: RBFFamily, m: int, theta: np.ndarray) -> np.ndarray:
+    """y = f_theta(x_1..x_m), formed in float64 and rounded to float32."""
+    return (fam.F[:m] @ np.asarray(theta, dtype=np.float64)).astype(np.float32)
+
+
+def rbf_system(fam: RBFFamily, m: int, n: int, theta: np.ndarray) -> System:
+    """One member of the family as a column-major float32 System (a_true unknown: zeros)."""
+    X = np.ascontiguousarray(fam.M[:n, :m])
+    return System(X=X, y=rbf_rhs(fam, m, theta), a_true=np.zeros(n), m=int(m), n=int(n),
+                  layout="col", dtype="f32")
+
+
+def device_rbf_batch(fam: RBFFamily, m, n, theta, device, share_master: bool = False):
+    """The systems (m[i], n[i], theta[i]) of the family as CUDA tensors.
+
+    Returns (keep, systems): systems[i] = (X, y) with X an (m, n) column-major
+    float32 view and y (m,) float32 (the values rbf_system/rbf_rhs give).  By
+    default every system owns its copy of X (leading dimension m rounded up to
+    a multiple of 4, so columns start on 16-byte boundaries); share_master
+    makes every X a view of the one 16384-row master matrix (ld = 16384).
+    `keep` holds the backing buffers."""
+    import torch
+    count = len(m)
+    Md = torch.from_numpy(fam.M).to(device)
+    ys = [rbf_rhs(fam, int(m[i]), theta[i]) for i in range(count)]
+    yoff = np.concatenate([[0], np.cumsum([len(v) for v in ys])]).astype(np.int64)
+    yflat = torch.from_numpy(np.concatenate(ys) if count else np.zeros(0, np.float32)).to(device)
+    systems = []
+    if share_master:
+        for i in range(count):
+            X = Md[: int(n[i]), : int(m[i])].T
+            systems.append((X, yflat[yoff[i]: yoff[i + 1]]))
+        return (Md, yflat), systems
+    lds = [((int(mi) + 3) // 4) * 4 for mi in m]
+    offs = np.concatenate([[0], np.cumsum([int(n[i]) * lds[i] for i in range(count)])]).astype(np.int64)
+    flat = torch.empty(int(offs[-1]) + 4, dtype=torch.float32, device=device)
+    for i in range(count):
+        mi, ni, ld = int(m[i]), int(n[i]), lds[i]
+        blk = flat[offs[i]: offs[i] + ni * ld].view(ni, ld)
+        blk[:, :mi].copy_(Md[:ni, :mi])
+        systems.append((blk[:, :mi].T, yflat[yoff[i]: yoff[i + 1]]))
+    del Md
+    return (flat, yflat), systems
