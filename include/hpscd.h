@@ -283,6 +283,57 @@ int hpscd_batch_destroy(hpscd_batch* b);
 int hpscd_autotune_batch(hpscd_ctx* ctx, const hpscd_sys* sys, int64_t count, int dtype,
                          int64_t trial_sweeps, hpscd_tuning* out, double* ms_per_candidate);
 
+/* ---- learned warm start (an initial guess, as Algorithm 2 allows, for
+ * families of similar systems) ----
+ *
+ * A 3-layer MLP maps the features phi = [theta_1..16, n/256, log(m)/log(16384)]
+ * of a system of a parametric family to a predicted a (256 outputs, of which
+ * the first n are used): Linear(18, 256), ReLU, Linear(256, 256), ReLU,
+ * Linear(256, 256).  Matrix operands are bfloat16 (weights and activations),
+ * accumulation float32 on the tensor cores; master weights and Adam moments are
+ * float32.  It is trained on solutions the sweep itself produces. */
+typedef struct hpscd_mlp hpscd_mlp;
+
+/* Create an MLP on the context's device for batches of up to max_batch rows.
+ * Parameters start at zero: set them with hpscd_mlp_set_params.
+ * Errors: INVALID_ARG, UNSUPPORTED (no tensor-map support), NO_MEMORY, CUDA. */
+int hpscd_mlp_create(hpscd_ctx* ctx, int64_t max_batch, hpscd_mlp** out);
+int hpscd_mlp_destroy(hpscd_mlp* mlp);
+
+/* Number of float32 parameters: W1 [256][18], b1 [256], W2 [256][256], b2,
+ * W3 [256][256], b3, in this order, row-major (W[out][in]). */
+int64_t hpscd_mlp_param_count(void);
+
+/* Copy all parameters from / to a HOST float array of hpscd_mlp_param_count()
+ * entries.  set_params also resets the Adam moments and step count. */
+int hpscd_mlp_set_params(hpscd_mlp* mlp, const float* host_params);
+int hpscd_mlp_get_params(hpscd_mlp* mlp, float* host_params);
+
+/* Predictions out[b][0..255] (DEVICE float[B][256]) for theta (DEVICE
+ * float[B][16]) and the HOST int64 arrays m[B], n[B] (0 <= n <= 256). */
+int hpscd_mlp_predict(hpscd_mlp* mlp, const float* theta, const int64_t* m, const int64_t* n,
+                      int64_t B, float* out);
+
+/* Loss L = mean over b < B, j < n_b of (out[b][j] - target[b][j])^2 (target:
+ * DEVICE float[B][256]) and its gradient with respect to every parameter,
+ * copied to the HOST array host_grads (layout of the parameters); no update. */
+int hpscd_mlp_gradients(hpscd_mlp* mlp, const float* theta, const int64_t* m, const int64_t* n,
+                        const float* target, int64_t B, double* loss, float* host_grads);
+
+/* One Adam step (Kingma and Ba 2015: learning rate lr, beta1, beta2, eps, bias
+ * correction) on the loss of hpscd_mlp_gradients; *loss (HOST, may be NULL)
+ * receives the loss before the step.  Synchronous. */
+int hpscd_mlp_train_step(hpscd_mlp* mlp, const float* theta, const int64_t* m, const int64_t* n,
+                         const float* target, int64_t B, float lr, float beta1, float beta2,
+                         float eps, double* loss);
+
+/* Make every launch of the batch start each system from the MLP's prediction:
+ * the batch's graph is re-captured as [MLP forward on theta (DEVICE
+ * float[count][16], row i = system i) -> a_i of each system -> the sweep].
+ * mlp = NULL restores the descriptors' own a_is_guess.  The MLP and theta must
+ * stay valid while the batch is launched. */
+int hpscd_batch_set_warm_start(hpscd_batch* b, hpscd_mlp* mlp, const float* theta);
+
 /* Static description of a status code. */
 const char* hpscd_status_string(int status);
 

@@ -21,7 +21,7 @@ import numpy as np
 
 from . import build as _build
 
-__all__ = ["Context", "Batch", "solve", "solve_host", "HpscdError", "load", "STATUS"]
+__all__ = ["Context", "Batch", "MLP", "solve", "solve_host", "HpscdError", "load", "STATUS"]
 
 STATUS = {0: "ok", 1: "invalid_arg", 2: "not_converged", 3: "nonfinite", 4: "timeout",
           5: "cuda_error", 6: "unsupported", 7: "no_memory"}
@@ -106,6 +106,22 @@ SIGNATURES = {
     "hpscd_autotune_batch": ([ctypes.c_void_p, ctypes.POINTER(Sys), ctypes.c_int64, ctypes.c_int,
                               ctypes.c_int64, ctypes.POINTER(Tuning),
                               ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    "hpscd_mlp_create": ([ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(ctypes.c_void_p)],
+                         ctypes.c_int),
+    "hpscd_mlp_destroy": ([ctypes.c_void_p], ctypes.c_int),
+    "hpscd_mlp_param_count": ([], ctypes.c_int64),
+    "hpscd_mlp_set_params": ([ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
+    "hpscd_mlp_get_params": ([ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
+    "hpscd_mlp_predict": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                          ctypes.c_int64, ctypes.c_void_p], ctypes.c_int),
+    "hpscd_mlp_gradients": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                            ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(ctypes.c_double),
+                            ctypes.c_void_p], ctypes.c_int),
+    "hpscd_mlp_train_step": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                             ctypes.c_void_p, ctypes.c_int64, ctypes.c_float, ctypes.c_float,
+                             ctypes.c_float, ctypes.c_float, ctypes.POINTER(ctypes.c_double)],
+                            ctypes.c_int),
+    "hpscd_batch_set_warm_start": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
     "hpscd_status_string": ([ctypes.c_int], ctypes.c_char_p),
 }
 
@@ -427,9 +443,144 @@ class Batch:
         self.launch()
         return self.results()
 
+    def set_warm_start(self, mlp: "MLP | None", theta=None):
+        """Start every system from mlp's prediction for theta (CUDA float32
+        (count, 16), row i = system i); None restores the cold start."""
+        if mlp is None:
+            rc = self._lib.hpscd_batch_set_warm_start(self._h, None, None)
+            self._theta = None
+        else:
+            if not (theta.is_cuda and theta.dtype.is_floating_point and theta.is_contiguous()
+                    and tuple(theta.shape) == (self.count, 16)):
+                raise TypeError("theta must be a contiguous float32 CUDA tensor (count, 16)")
+            self._theta = theta
+            self._mlp = mlp
+            rc = self._lib.hpscd_batch_set_warm_start(self._h, mlp._h, ctypes.c_void_p(theta.data_ptr()))
+        if rc:
+            raise HpscdError(rc, "hpscd_batch_set_warm_start")
+
     def close(self):
         if getattr(self, "_h", None):
             self._lib.hpscd_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+MLP_IN, MLP_HID, MLP_OUT, MLP_THETA = 18, 256, 256, 16
+MLP_SHAPES = [(MLP_HID, MLP_IN), (MLP_HID,), (MLP_HID, MLP_HID), (MLP_HID,), (MLP_OUT, MLP_HID),
+              (MLP_OUT,)]
+
+
+def mlp_init(seed: int = 0) -> np.ndarray:
+    """He-uniform weights, zero biases, as one flat float32 parameter vector."""
+    g = np.random.default_rng(seed)
+    parts = []
+    for shp in MLP_SHAPES:
+        if len(shp) == 2:
+            lim = np.sqrt(6.0 / shp[1])
+            parts.append(g.uniform(-lim, lim, shp).ravel())
+        else:
+            parts.append(np.zeros(shp))
+    return np.concatenate(parts).astype(np.float32)
+
+
+def mlp_split(flat: np.ndarray):
+    """Flat parameter vector -> [W1, b1, W2, b2, W3, b3] views."""
+    out, off = [], 0
+    for shp in MLP_SHAPES:
+        k = int(np.prod(shp))
+        out.append(flat[off: off + k].reshape(shp))
+        off += k
+    return out
+
+
+class MLP:
+    """Warm-start network phi(theta, m, n) -> a on the GPU (hpscd_mlp_*)."""
+
+    def __init__(self, ctx: "Context", max_batch: int = 4096, params=None, seed: int = 0):
+        import torch
+        self._lib = ctx._lib
+        self.ctx = ctx
+        self.max_batch = int(max_batch)
+        ctx.set_stream(torch.cuda.current_stream(torch.device("cuda", ctx.device)))
+        h = ctypes.c_void_p()
+        rc = self._lib.hpscd_mlp_create(ctx._h, self.max_batch, ctypes.byref(h))
+        if rc:
+            raise HpscdError(rc, "hpscd_mlp_create")
+        self._h = h
+        self.n_params = int(self._lib.hpscd_mlp_param_count())
+        self.set_params(mlp_init(seed) if params is None else params)
+
+    def set_params(self, flat):
+        flat = np.ascontiguousarray(flat, dtype=np.float32)
+        if flat.size != self.n_params:
+            raise ValueError(f"expected {self.n_params} parameters")
+        rc = self._lib.hpscd_mlp_set_params(self._h, flat.ctypes.data_as(ctypes.c_void_p))
+        if rc:
+            raise HpscdError(rc, "hpscd_mlp_set_params")
+
+    def params(self) -> np.ndarray:
+        out = np.empty(self.n_params, dtype=np.float32)
+        rc = self._lib.hpscd_mlp_get_params(self._h, out.ctypes.data_as(ctypes.c_void_p))
+        if rc:
+            raise HpscdError(rc, "hpscd_mlp_get_params")
+        return out
+
+    @staticmethod
+    def _shapes(m, n):
+        m = np.ascontiguousarray(m, dtype=np.int64)
+        n = np.ascontiguousarray(n, dtype=np.int64)
+        return m, n
+
+    def predict(self, theta, m, n):
+        """(B, 256) float32 CUDA predictions for theta (B, 16) CUDA, m, n host ints."""
+        import torch
+        m, n = self._shapes(m, n)
+        B = len(m)
+        out = torch.empty(B, MLP_OUT, dtype=torch.float32, device=theta.device)
+        rc = self._lib.hpscd_mlp_predict(self._h, ctypes.c_void_p(theta.data_ptr()),
+                                         m.ctypes.data_as(ctypes.c_void_p),
+                                         n.ctypes.data_as(ctypes.c_void_p), B,
+                                         ctypes.c_void_p(out.data_ptr()))
+        if rc:
+            raise HpscdError(rc, "hpscd_mlp_predict")
+        return out
+
+    def gradients(self, theta, m, n, target):
+        """(loss, flat float32 gradient) of the masked mean-squared error."""
+        m, n = self._shapes(m, n)
+        g = np.empty(self.n_params, dtype=np.float32)
+        loss = ctypes.c_double(0.0)
+        rc = self._lib.hpscd_mlp_gradients(self._h, ctypes.c_void_p(theta.data_ptr()),
+                                           m.ctypes.data_as(ctypes.c_void_p),
+                                           n.ctypes.data_as(ctypes.c_void_p),
+                                           ctypes.c_void_p(target.data_ptr()), len(m),
+                                           ctypes.byref(loss), g.ctypes.data_as(ctypes.c_void_p))
+        if rc:
+            raise HpscdError(rc, "hpscd_mlp_gradients")
+        return loss.value, g
+
+    def train_step(self, theta, m, n, target, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8) -> float:
+        m, n = self._shapes(m, n)
+        loss = ctypes.c_double(0.0)
+        rc = self._lib.hpscd_mlp_train_step(self._h, ctypes.c_void_p(theta.data_ptr()),
+                                            m.ctypes.data_as(ctypes.c_void_p),
+                                            n.ctypes.data_as(ctypes.c_void_p),
+                                            ctypes.c_void_p(target.data_ptr()), len(m),
+                                            float(lr), float(beta1), float(beta2), float(eps),
+                                            ctypes.byref(loss))
+        if rc:
+            raise HpscdError(rc, "hpscd_mlp_train_step")
+        return loss.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.hpscd_mlp_destroy(self._h)
             self._h = None
 
     def __del__(self):

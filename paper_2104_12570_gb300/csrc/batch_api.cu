@@ -29,6 +29,11 @@ struct hpscd_batch {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   bool launched = false;
+  BatchParams params{};
+  std::vector<hpscd_sys> sys_host;   // descriptors as given
+  int64_t* mn_d = nullptr;           // device int64 m[count], n[count]
+  hpscd_mlp* mlp = nullptr;          // learned warm start (optional)
+  const float* theta = nullptr;      // device float[count][16]
 };
 
 namespace {
@@ -88,6 +93,26 @@ void release(hpscd_batch* b) {
   b->dev = nullptr;
 }
 
+// The launch sequence, captured once per configuration: reset the queue,
+// [learned warm start: MLP forward + scatter into every system's a], run the
+// persistent kernel.
+int capture(hpscd_batch* b) {
+  if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
+  if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
+  if (cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return HPSCD_ERR_CUDA;
+  bool body = cudaMemsetAsync(b->queue_d, 0, sizeof(int), b->cap) == cudaSuccess;
+  if (body && b->mlp && b->count > 0)
+    body = mlp_enqueue_warm_start(b->mlp, b->cap, b->theta, b->mn_d, b->mn_d + b->count, b->sys_d,
+                                  b->count) == HPSCD_OK;
+  body = body && launch_batched(b->params, b->K, b->clusters, b->smem, b->cap) == cudaSuccess;
+  const bool ended = cudaStreamEndCapture(b->cap, &b->graph) == cudaSuccess;
+  if (!(body && ended && cudaGraphInstantiate(&b->exec, b->graph, 0) == cudaSuccess)) {
+    cudaGetLastError();
+    return HPSCD_ERR_CUDA;
+  }
+  return HPSCD_OK;
+}
+
 // Fit check and cluster count of a candidate number of CTAs per system.
 bool candidate(const hpscd_ctx* ctx, int64_t mmax, int K, int* smem, int* clusters) {
   *smem = batched_smem_bytes(mmax, K);
@@ -137,6 +162,7 @@ int create(hpscd_ctx* ctx, const hpscd_sys* sys, int64_t count, const hpscd_opts
   const size_t o_gpart = off; off = align256(off + (size_t)grid * 256 * 256 * sizeof(float));
   const size_t o_gfinal = off; off = align256(off + (size_t)clusters * 256 * 256 * sizeof(float));
   const size_t o_dfinal = off; off = align256(off + (size_t)clusters * 256 * sizeof(float));
+  const size_t o_mn = off; off = align256(off + 2 * n_sys * sizeof(int64_t));
   if (cudaMalloc(&b->dev, off) != cudaSuccess) {
     cudaGetLastError();
     delete b;
@@ -150,6 +176,9 @@ int create(hpscd_ctx* ctx, const hpscd_sys* sys, int64_t count, const hpscd_opts
   b->gpart = reinterpret_cast<float*>(base + o_gpart);
   b->gfinal = reinterpret_cast<float*>(base + o_gfinal);
   b->dfinal = reinterpret_cast<float*>(base + o_dfinal);
+  b->mn_d = reinterpret_cast<int64_t*>(base + o_mn);
+  std::vector<int64_t> mn((size_t)2 * n_sys, 0);
+  for (int64_t i = 0; i < count; ++i) { mn[(size_t)i] = sys[i].m; mn[(size_t)(count + i)] = sys[i].n; }
 
   // queue order: decreasing m·n (longest first), ties by index
   std::vector<int> order((size_t)count);
@@ -163,6 +192,8 @@ int create(hpscd_ctx* ctx, const hpscd_sys* sys, int64_t count, const hpscd_opts
                      cudaMemcpyAsync(b->order_d, order.data(), (size_t)count * sizeof(int),
                                      cudaMemcpyHostToDevice, st) != cudaSuccess)) ||
       cudaMemsetAsync(b->res_d, 0, n_sys * sizeof(hpscd_sys_result), st) != cudaSuccess ||
+      cudaMemcpyAsync(b->mn_d, mn.data(), mn.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st) !=
+          cudaSuccess ||
       cudaStreamSynchronize(st) != cudaSuccess) {
     cudaGetLastError();
     release(b);
@@ -184,15 +215,10 @@ int create(hpscd_ctx* ctx, const hpscd_sys* sys, int64_t count, const hpscd_opts
   p.max_sweeps = opts->max_sweeps;
   p.stop_rule = opts->stop_rule;
 
-  // the launch sequence, captured once: reset the queue, run the persistent kernel
+  b->params = p;
+  b->sys_host.assign(sys, sys + count);
   bool ok = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) == cudaSuccess &&
-            cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
-  if (ok) {
-    const bool body = cudaMemsetAsync(b->queue_d, 0, sizeof(int), b->cap) == cudaSuccess &&
-                      launch_batched(p, K, clusters, smem, b->cap) == cudaSuccess;
-    const bool ended = cudaStreamEndCapture(b->cap, &b->graph) == cudaSuccess;
-    ok = body && ended && cudaGraphInstantiate(&b->exec, b->graph, 0) == cudaSuccess;
-  }
+            capture(b) == HPSCD_OK;
   if (!ok) {
     cudaGetLastError();
     release(b);
@@ -255,9 +281,8 @@ int hpscd_batch_results(hpscd_batch* b, hpscd_sys_result* out) {
   if (b->launched) {
     hpscd_timing t{};
     cudaEventElapsedTime(&t.sweep_ms, b->ctx->ev[1], b->ctx->ev[2]);
-    int64_t passes = 0, bytes = 0;
+    int64_t passes = 0;
     for (int64_t i = 0; i < b->count; ++i) passes += out[i].passes;
-    (void)bytes;
     t.passes = passes;
     t.grid = b->clusters * b->K;
     t.kernel_launches = 1;
@@ -266,6 +291,26 @@ int hpscd_batch_results(hpscd_batch* b, hpscd_sys_result* out) {
   for (int64_t i = 0; i < b->count; ++i)
     if (out[i].status != HPSCD_OK) return out[i].status;
   return HPSCD_OK;
+}
+
+int hpscd_batch_set_warm_start(hpscd_batch* b, hpscd_mlp* mlp, const float* theta) {
+  if (!b || (mlp && !theta && b->count > 0)) return HPSCD_ERR_INVALID_ARG;
+  if (mlp && mlp_device(mlp) != b->ctx->device) return HPSCD_ERR_INVALID_ARG;
+  DevGuard g(b->ctx->device);
+  if (!g.ok) return HPSCD_ERR_CUDA;
+  if (cudaStreamSynchronize(b->ctx->stream) != cudaSuccess) { cudaGetLastError(); return HPSCD_ERR_CUDA; }
+  // the kernel starts every system from its a when a warm start is configured
+  std::vector<hpscd_sys> d(b->sys_host);
+  if (mlp)
+    for (auto& s : d) s.a_is_guess = 1;
+  if (b->count > 0 &&
+      cudaMemcpy(b->sys_d, d.data(), d.size() * sizeof(hpscd_sys), cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaGetLastError();
+    return HPSCD_ERR_CUDA;
+  }
+  b->mlp = mlp;
+  b->theta = mlp ? theta : nullptr;
+  return capture(b);
 }
 
 int hpscd_batch_tuning(hpscd_batch* b, hpscd_tuning* out) {

@@ -22,3 +22,13 @@ struct hpscd_ctx {
   int trace_grid = 0;
   PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
 };
+
+// Learned warm start inside a batch's graph (mlp.cu): enqueue on `st` the MLP
+// forward pass for systems [0, count) of `sys` (theta: device float[count][16];
+// m, n: device int64[count]) and write each prediction into the system's a.
+struct hpscd_mlp;
+namespace hpscd {
+int mlp_enqueue_warm_start(hpscd_mlp* p, cudaStream_t st, const float* theta, const int64_t* m,
+                           const int64_t* n, const hpscd_sys* sys, int64_t count);
+int mlp_device(const hpscd_mlp* p);
+}  // namespace hpscd
