@@ -216,6 +216,34 @@ def precision_comparison(hp, synth, ctx, dev, steps=5, warmup=3):
     return out
 
 
+def batched_comparison(hp, synth, ctx):
+    """The batched + learned-warm-start workload: 4096 RBF systems (m log-uniform
+    in [256, 16384], n uniform in [8, 256]) swept to a relative change of ||e||
+    below 1e-6 (at most 10^4 sweeps) in one persistent graph-captured launch,
+    cold start against the MLP's warm start (weights trained on 50,000
+    method-generated solutions of the family, seed 1)."""
+    from paper_2104_12570_gb300 import warm_start as ws
+    fam = synth.rbf_family(0)
+    m, n, th = synth.rbf_params(4096, seed=0)
+    keep, a, b = ws.build_batch(ctx, fam, m, n, th, max_sweeps=4)
+    systems = b.systems
+    best, tms = hp.autotune_batch(ctx, systems, trial_sweeps=3)
+    b.close()
+    del keep, a, systems
+    out = {"workload": "rbf_batch_4096 (RBF features of U[0,1]^4 inputs, width 0.3; "
+                       "y = f_theta(x))",
+           "stop": f"{ws.STOP}<{ws.TOL}, max_sweeps {ws.MAX_SWEEPS}",
+           "x_bytes": int((m * n * 4).sum()), "autotune_ms_per_3_sweeps": tms, "cluster": best}
+    if not os.path.exists(ws.WEIGHTS):
+        out["warm"] = "no trained weights"
+        return out
+    mlp = ws.load(ctx)
+    ev = ws.evaluate(ctx, fam, mlp, m, n, th, reps=1, cluster=best)
+    mlp.close()
+    out.update(ev)
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -226,6 +254,8 @@ def main():
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the bfloat16-vs-float32 comparison on the 4,000,000 x 512 system")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the batched cold-vs-learned-warm-start comparison (4096 RBF systems)")
     ap.add_argument("--rows", type=int, default=0,
                     help="override m (smaller case for profiler captures; not a bench line)")
     args = ap.parse_args()
@@ -334,6 +364,9 @@ def main():
             del X
             torch.cuda.empty_cache()
             out["precision_mode"] = precision_comparison(hp, synth, ctx, dev)
+        if not args.no_batched and not args.rows:
+            torch.cuda.empty_cache()
+            out["batched"] = batched_comparison(hp, synth, ctx)
         print(json.dumps(out), flush=True)
     ctx.close()
     if world > 1:

@@ -3,11 +3,12 @@
 // The sweep needs <X_j, X_j> (the denominators of Eq. da2) and the lower
 // triangle of G (Eq. ek1-ek applied inside a sweep).  G is a dense contraction
 // over the m rows, the one part of the method that belongs on the tensor
-// cores.  Each CTA takes a range of rows (K) and a group of 128-column block
-// rows I of G, streams the needed 128-column blocks of X through shared memory
-// by TMA (128-byte swizzle: each column's K elements are the operand's
-// contiguous K-major rows), and accumulates D_I = X_I^T X_{0..I} in tensor
-// memory with tcgen05.mma issued by one thread.  bfloat16 X: kind::f16 (exact
+// cores.  Each CTA takes a range of rows (K) and a group of at most four lower
+// 128×128 tiles (I, J) of G, streams the 128-column blocks of X those tiles
+// need (at most four; two for float32, whose split doubles a stage) through
+// shared memory by TMA (128-byte swizzle: each column's K elements are the
+// operand's contiguous K-major rows), and accumulates D_IJ = X_I^T X_J in
+// tensor memory (128 columns per tile) with tcgen05.mma issued by one thread.  bfloat16 X: kind::f16 (exact
 // products, float32 accumulation).  float32 X: kind::tf32 on a two-term split
 // x = hi + lo (hi = x truncated to tf32, written back in place; lo = x - hi),
 // accumulating hi·hi + hi·lo + lo·hi, which leaves ~2^-21 relative error per
@@ -16,6 +17,8 @@
 // the same shared-memory tiles (float32, float64 across blocks).  Per-split
 // float32 partials are summed in a fixed order by gram_tc_reduce_kernel into
 // the symmetric G.
+#include <string.h>
+
 #include "kernels.h"
 
 namespace hpscd {
@@ -105,8 +108,8 @@ __global__ void __launch_bounds__(GT_THREADS, 1)
   unsigned char* base = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int g = blockIdx.y;
-  const int nload = p.group_nload[g];
-  const int nrows_g = p.group_count[g];
+  const int nload = p.grp.nload[g];
+  const int ntile = p.grp.ntile[g];
   const int stage_raw = nload * ATOM_BYTES;
   const int stage_bytes = stage_raw * (TF32 ? 2 : 1);
   const int nst = p.nstages;
@@ -145,7 +148,8 @@ __global__ void __launch_bounds__(GT_THREADS, 1)
     unsigned char* dst = base + (size_t)s * stage_bytes;
     mbar_arrive_expect_tx(&full[s], (uint32_t)stage_raw);
     for (int b = 0; b < nload; ++b)
-      tma_load_2d(dst + b * ATOM_BYTES, &tmap, &full[s], (int32_t)(r0 + kb * KB), b * BLK);
+      tma_load_2d(dst + b * ATOM_BYTES, &tmap, &full[s], (int32_t)(r0 + kb * KB),
+                  p.grp.load_blk[g][b] * BLK);
   };
   if (tid == 0)
     while (issued < nst && issued < nkb) issue(issued++);
@@ -217,31 +221,24 @@ __global__ void __launch_bounds__(GT_THREADS, 1)
     if (tid == 32) {
       tc_fence_after();
       const uint32_t a_base = smem_u32(st);
-      uint32_t dcol = 0;
-      for (int gi = 0; gi < nrows_g; ++gi) {
-        const int I = p.group_rows[g][gi];
-        const int N_total = BLK * (I + 1);
-        for (int nb0 = 0; nb0 < N_total; nb0 += 256) {
-          const int N = min(256, N_total - nb0);
-          const uint32_t idesc = make_idesc(FMT, N);
-          const uint32_t d_tmem = tmem + dcol + nb0;
+      const uint32_t idesc = make_idesc(FMT, BLK);
+      for (int t = 0; t < ntile; ++t) {
+        const uint32_t d_tmem = tmem + (uint32_t)(BLK * t);
+        const int si = p.grp.tile_si[g][t], sj = p.grp.tile_sj[g][t];
 #pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            const uint32_t koff = k * 32;
-            const uint64_t ah = make_sw128_desc(a_base + I * ATOM_BYTES + koff);
-            const uint64_t bh = make_sw128_desc(a_base + (nb0 / BLK) * ATOM_BYTES + koff);
-            const uint32_t acc = (kb > 0 || k > 0) ? 1u : 0u;
-            mma_issue<TF32>(d_tmem, ah, bh, idesc, acc);
-            if constexpr (TF32) {
-              const uint64_t al = make_sw128_desc(a_base + stage_raw + I * ATOM_BYTES + koff);
-              const uint64_t bl =
-                  make_sw128_desc(a_base + stage_raw + (nb0 / BLK) * ATOM_BYTES + koff);
-              mma_issue<TF32>(d_tmem, ah, bl, idesc, 1u);
-              mma_issue<TF32>(d_tmem, al, bh, idesc, 1u);
-            }
+        for (int k = 0; k < 4; ++k) {
+          const uint32_t koff = k * 32;
+          const uint64_t ah = make_sw128_desc(a_base + si * ATOM_BYTES + koff);
+          const uint64_t bh = make_sw128_desc(a_base + sj * ATOM_BYTES + koff);
+          const uint32_t acc = (kb > 0 || k > 0) ? 1u : 0u;
+          mma_issue<TF32>(d_tmem, ah, bh, idesc, acc);
+          if constexpr (TF32) {
+            const uint64_t al = make_sw128_desc(a_base + stage_raw + si * ATOM_BYTES + koff);
+            const uint64_t bl = make_sw128_desc(a_base + stage_raw + sj * ATOM_BYTES + koff);
+            mma_issue<TF32>(d_tmem, ah, bl, idesc, 1u);
+            mma_issue<TF32>(d_tmem, al, bh, idesc, 1u);
           }
         }
-        dcol += N_total;
       }
       mma_commit(&empty[s]);
     }
@@ -266,24 +263,18 @@ __global__ void __launch_bounds__(GT_THREADS, 1)
       v += __shfl_xor_sync(FULL_MASK, v, 1);
       v += __shfl_xor_sync(FULL_MASK, v, 2);
       v += __shfl_xor_sync(FULL_MASK, v, 4);
-      const int col = tid / 8 + 16 * q;
-      if ((tid & 7) == 0 && q < nq) {
-        bool mine = false;
-        for (int gi = 0; gi < nrows_g; ++gi) mine |= (col / BLK == p.group_rows[g][gi]);
-        if (mine) p.dpart[(size_t)blockIdx.x * p.npad + col] = v;
-      }
+      const int lcol = tid / 8 + 16 * q;  // column within the streamed slots
+      if ((tid & 7) == 0 && q < nq && p.grp.diag_slot[g][lcol / BLK])
+        p.dpart[(size_t)blockIdx.x * p.npad + p.grp.load_blk[g][lcol / BLK] * BLK + lcol % BLK] = v;
     }
     float* out = p.partial + (size_t)blockIdx.x * p.npad * p.npad;
-    uint32_t dcol = 0;
-    for (int gi = 0; gi < nrows_g; ++gi) {
-      const int I = p.group_rows[g][gi];
-      const int N_total = BLK * (I + 1);
-      const int row = BLK * I + 32 * warp + lane;
-      float* orow = out + (size_t)row * p.npad;
-      for (int c0 = 0; c0 < N_total; c0 += 32) {
+    for (int t = 0; t < ntile; ++t) {
+      const int row = BLK * p.grp.tile_i[g][t] + 32 * warp + lane;
+      float* orow = out + (size_t)row * p.npad + BLK * p.grp.tile_j[g][t];
+      for (int c0 = 0; c0 < BLK; c0 += 32) {
         float v[32];
         if (nkb > 0) {
-          tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + dcol + c0, v);
+          tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + BLK * t + c0, v);
         } else {
 #pragma unroll
           for (int i = 0; i < 32; ++i) v[i] = 0.f;
@@ -293,7 +284,6 @@ __global__ void __launch_bounds__(GT_THREADS, 1)
           *reinterpret_cast<float4*>(orow + c0 + 4 * q) =
               make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
       }
-      dcol += N_total;
     }
   } else if (tid == 0) {
     atomicExch(p.err, 1);
@@ -330,35 +320,57 @@ __global__ void gram_tc_reduce_kernel(const float* __restrict__ partial,
 
 }  // namespace
 
+// Adds tile (I, J) to group g, streaming blocks I and J into slots.
+static void add_tile(GramTCGroups& G, int g, int I, int J) {
+  auto slot = [&](int blk) {
+    for (int s = 0; s < G.nload[g]; ++s)
+      if (G.load_blk[g][s] == blk) return s;
+    G.load_blk[g][G.nload[g]] = blk;
+    G.diag_slot[g][G.nload[g]] = 0;
+    return G.nload[g]++;
+  };
+  const int t = G.ntile[g]++;
+  G.tile_i[g][t] = I;
+  G.tile_j[g][t] = J;
+  G.tile_si[g][t] = slot(I);
+  G.tile_sj[g][t] = slot(J);
+  if (I == J) G.diag_slot[g][G.tile_si[g][t]] = 1;
+}
+
 bool gram_tc_plan(int dtype, int64_t m, int n, int sms, int max_smem, GramTCPlan* gp) {
   if (m < 1 || n < 1 || n > 512) return false;
   const int nb = (n + BLK - 1) / BLK;
-  if (dtype == HPSCD_F32 && nb > 2) return false;
   gp->npad = nb * BLK;
-  // group the block rows so each group's accumulators fit 512 TMEM columns
-  int ng = 0;
-  for (int i = 0; i < 4; ++i) { gp->group_count[i] = 0; gp->group_nload[i] = 0; }
-  if (nb == 1) { gp->group_rows[0][0] = 0; gp->group_count[0] = 1; ng = 1; }
-  else if (nb == 2) {
-    gp->group_rows[0][0] = 0; gp->group_rows[0][1] = 1; gp->group_count[0] = 2; ng = 1;
-  } else if (nb == 3) {
-    gp->group_rows[0][0] = 2; gp->group_count[0] = 1;
-    gp->group_rows[1][0] = 0; gp->group_rows[1][1] = 1; gp->group_count[1] = 2; ng = 2;
-  } else {
-    gp->group_rows[0][0] = 3; gp->group_count[0] = 1;
-    gp->group_rows[1][0] = 2; gp->group_count[1] = 1;
-    gp->group_rows[2][0] = 0; gp->group_rows[2][1] = 1; gp->group_count[2] = 2; ng = 3;
+  GramTCGroups& G = gp->grp;
+  memset(&G, 0, sizeof(G));
+  // Groups of lower tiles: at most 4 tiles (512 TMEM columns); bfloat16 streams
+  // up to 4 column blocks per stage, float32 (whose hi/lo split doubles a
+  // stage) at most 2.
+  static const int f32_groups[4][6][4][2] = {
+      {{{0, 0}, {-1, -1}}},
+      {{{0, 0}, {1, 0}, {1, 1}, {-1, -1}}},
+      {{{0, 0}, {1, 0}, {1, 1}, {-1, -1}}, {{2, 0}, {2, 2}, {-1, -1}}, {{2, 1}, {-1, -1}}},
+      {{{0, 0}, {1, 0}, {1, 1}, {-1, -1}}, {{2, 2}, {3, 2}, {3, 3}, {-1, -1}},
+       {{2, 0}, {-1, -1}}, {{3, 0}, {-1, -1}}, {{2, 1}, {-1, -1}}, {{3, 1}, {-1, -1}}}};
+  static const int bf16_groups[4][3][4][2] = {
+      {{{0, 0}, {-1, -1}}},
+      {{{0, 0}, {1, 0}, {1, 1}, {-1, -1}}},
+      {{{2, 0}, {2, 1}, {2, 2}, {-1, -1}}, {{0, 0}, {1, 0}, {1, 1}, {-1, -1}}},
+      {{{3, 0}, {3, 1}, {3, 2}, {3, 3}}, {{2, 0}, {2, 1}, {2, 2}, {-1, -1}},
+       {{0, 0}, {1, 0}, {1, 1}, {-1, -1}}}};
+  static const int f32_ngroups[4] = {1, 1, 3, 6}, bf16_ngroups[4] = {1, 1, 2, 3};
+  const bool f32 = dtype == HPSCD_F32;
+  const int ng = f32 ? f32_ngroups[nb - 1] : bf16_ngroups[nb - 1];
+  for (int gi = 0; gi < ng; ++gi) {
+    const int(*tiles)[2] = f32 ? f32_groups[nb - 1][gi] : bf16_groups[nb - 1][gi];
+    const int g = G.ngroups++;
+    for (int t = 0; t < 4 && tiles[t][0] >= 0; ++t) add_tile(G, g, tiles[t][0], tiles[t][1]);
   }
-  gp->ngroups = ng;
   int maxload = 0;
-  for (int i = 0; i < ng; ++i) {
-    int mx = 0;
-    for (int k = 0; k < gp->group_count[i]; ++k) mx = gp->group_rows[i][k] > mx ? gp->group_rows[i][k] : mx;
-    gp->group_nload[i] = mx + 1;
-    maxload = gp->group_nload[i] > maxload ? gp->group_nload[i] : maxload;
-  }
-  const int kb_rows = dtype == HPSCD_F32 ? 32 : 64;
-  const int stage = maxload * ATOM_BYTES * (dtype == HPSCD_F32 ? 2 : 1);
+  for (int g = 0; g < G.ngroups; ++g) maxload = G.nload[g] > maxload ? G.nload[g] : maxload;
+  gp->maxload = maxload;
+  const int kb_rows = f32 ? 32 : 64;
+  const int stage = maxload * ATOM_BYTES * (f32 ? 2 : 1);
   int nst = (max_smem - 2048) / stage;
   if (nst > 6) nst = 6;
   if (nst < 2) return false;
@@ -366,7 +378,7 @@ bool gram_tc_plan(int dtype, int64_t m, int n, int sms, int max_smem, GramTCPlan
   gp->smem_bytes = nst * stage + 1024 + 256;
   // one CTA per SM: each CTA allocates all 512 tensor-memory columns
   if (gp->smem_bytes < max_smem / 2 + 4096) gp->smem_bytes = max_smem / 2 + 4096;
-  int ksplit = sms / ng;
+  int ksplit = sms / G.ngroups;
   if (ksplit < 1) ksplit = 1;
   int64_t rps = (m + ksplit - 1) / ksplit;
   rps = (rps + kb_rows - 1) / kb_rows * kb_rows;
@@ -383,11 +395,7 @@ cudaError_t launch_gram_tc(const CUtensorMap* tmap, int dtype, int64_t m, const 
   GramTCParams p{};
   p.m = m;
   p.npad = gp.npad;
-  for (int i = 0; i < 4; ++i) {
-    p.group_count[i] = gp.group_count[i];
-    p.group_nload[i] = gp.group_nload[i];
-    for (int k = 0; k < 4; ++k) p.group_rows[i][k] = gp.group_rows[i][k];
-  }
+  p.grp = gp.grp;
   p.rows_per_split = gp.rows_per_split;
   p.partial = partial;
   p.dpart = reinterpret_cast<double*>(reinterpret_cast<char*>(partial) +
@@ -395,7 +403,7 @@ cudaError_t launch_gram_tc(const CUtensorMap* tmap, int dtype, int64_t m, const 
   p.err = err;
   p.timeout_ns = timeout_ns;
   p.nstages = gp.nstages;
-  dim3 grid(gp.ksplit, gp.ngroups);
+  dim3 grid(gp.ksplit, gp.grp.ngroups);
   cudaError_t e;
   if (dtype == HPSCD_F32) {
     e = cudaFuncSetAttribute(gram_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -29,7 +29,8 @@ struct DeviceGuard {
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 struct Layout {
-  size_t G = 0, partial = 0, e = 0, gpart = 0, npart = 0, gw = 0, ypart = 0, hist = 0, ctl = 0;
+  size_t G = 0, Gt = 0, dvec = 0, partial = 0, e = 0, hacc = 0, npart = 0, gw = 0, ypart = 0, hist = 0,
+         ctl = 0;
   size_t xcopy = 0, ycopy = 0, acopy = 0, total = 0;
 };
 
@@ -41,7 +42,6 @@ struct Plan {
   int ldG = 0;
   int64_t ntiles = 0;
   int grid = 0;
-  int gstride = 0;
   Layout L;
 };
 
@@ -91,11 +91,12 @@ int make_plan(const hpscd_ctx* ctx, int dtype, int layout, int64_t m, int64_t n,
     return at;
   };
   L.G = take((size_t)P->ldG * P->ldG * sizeof(float));
+  L.Gt = take((size_t)P->ldG * P->ldG * sizeof(float));
+  L.dvec = take((size_t)P->ldG * sizeof(float));
   L.partial = take(P->tc_ok && P->gtc.partial_bytes > P->gp.partial_bytes ? P->gtc.partial_bytes
                                                                           : P->gp.partial_bytes);
   L.e = take((size_t)(m > 0 ? m : 1) * sizeof(float));
-  P->gstride = (P->grid + 3) / 4 * 4;
-  L.gpart = take((size_t)2 * P->gstride * P->cfg.npad * sizeof(float));
+  L.hacc = take((size_t)3 * P->cfg.npad * sizeof(double));
   L.npart = take((size_t)2 * P->grid * sizeof(double));
   L.gw = take((size_t)2 * P->cfg.npad * sizeof(float));
   L.ypart = take((size_t)P->grid * sizeof(double));
@@ -338,8 +339,13 @@ int solve_device(hpscd_ctx* ctx, const void* X, int dtype, int layout, int64_t m
   int rcg = run_gram(ctx, X, dtype, m, n, ld, P, ws + L.partial, G, P.ldG, &ctl->err,
                      (o->debug_flags & HPSCD_DEBUG_SIMT_GRAM) != 0, &gram_launches);
   if (rcg != HPSCD_OK) return rcg;
-  if (cudaMemsetAsync(ws + L.gpart, 0, (size_t)2 * P.gstride * P.cfg.npad * sizeof(float), st) !=
-      cudaSuccess)
+  float* Gt = reinterpret_cast<float*>(ws + L.Gt);
+  float* dvec = reinterpret_cast<float*>(ws + L.dvec);
+  if (launch_scale_rows(G, P.ldG, (int)n, Gt, dvec, st) != cudaSuccess) {
+    cudaGetLastError();
+    return HPSCD_ERR_CUDA;
+  }
+  if (cudaMemsetAsync(ws + L.hacc, 0, (size_t)3 * P.cfg.npad * sizeof(double), st) != cudaSuccess)
     return HPSCD_ERR_CUDA;
   if (cudaEventRecord(ctx->ev[1], st) != cudaSuccess) return HPSCD_ERR_CUDA;
 
@@ -357,10 +363,10 @@ int solve_device(hpscd_ctx* ctx, const void* X, int dtype, int layout, int64_t m
   p.a_out = a;
   p.a_in = a;
   p.warm = a_is_guess ? 1 : 0;
-  p.G = G;
+  p.Gt = Gt;
+  p.dvec = dvec;
   p.ldG = P.ldG;
-  p.gpart = reinterpret_cast<float*>(ws + L.gpart);
-  p.gstride = P.gstride;
+  p.hacc = reinterpret_cast<double*>(ws + L.hacc);
   p.npart = reinterpret_cast<double*>(ws + L.npart);
   p.gw = reinterpret_cast<float*>(ws + L.gw);
   p.ypart = reinterpret_cast<double*>(ws + L.ypart);
@@ -407,7 +413,7 @@ int solve_device(hpscd_ctx* ctx, const void* X, int dtype, int layout, int64_t m
   t.passes = c.passes;
   t.x_bytes = m * n * esize(dtype);
   t.grid = P.grid;
-  t.kernel_launches = gram_launches + 1;
+  t.kernel_launches = gram_launches + 2;
   ctx->last = t;
   (void)layout;
   if (c.err != DEV_OK) return HPSCD_ERR_TIMEOUT;

@@ -21,12 +21,25 @@ cudaError_t launch_gram(const void* X, int dtype, int64_t m, int n, int64_t ld, 
                         double* partial, float* G, int ldG, cudaStream_t stream);
 
 // ---- tensor-core Gram set-up (tcgen05), G = X^T X ----
+// A group is a set of at most 4 lower 128×128 tiles (I, J) of G (one TMEM
+// accumulator of 128 columns each) computed by one CTA from the column blocks
+// it streams (slots of a stage, at most 4).
+constexpr int GTC_MAX_GROUPS = 8;
+struct GramTCGroups {
+  int ngroups;
+  int ntile[GTC_MAX_GROUPS];
+  int tile_si[GTC_MAX_GROUPS][4];   // slot of block I of each tile
+  int tile_sj[GTC_MAX_GROUPS][4];   // slot of block J
+  int tile_i[GTC_MAX_GROUPS][4];    // block I (rows of G)
+  int tile_j[GTC_MAX_GROUPS][4];    // block J (columns of G)
+  int nload[GTC_MAX_GROUPS];
+  int load_blk[GTC_MAX_GROUPS][4];  // column block streamed into each slot
+  int diag_slot[GTC_MAX_GROUPS][4]; // 1 when the group holds tile (b, b) of the block in that slot
+};
 struct GramTCPlan {
   int npad;                 // multiple of 128
-  int ngroups;              // groups of 128-column block rows (TMEM capacity)
-  int group_rows[4][4];     // block rows of each group
-  int group_count[4];
-  int group_nload[4];       // column blocks a group streams (0..max row)
+  GramTCGroups grp;
+  int maxload;
   int ksplit;
   int64_t rows_per_split;
   int nstages;
@@ -36,9 +49,7 @@ struct GramTCPlan {
 struct GramTCParams {
   int64_t m;
   int npad;
-  int group_rows[4][4];
-  int group_count[4];
-  int group_nload[4];
+  GramTCGroups grp;
   int64_t rows_per_split;
   float* partial;
   double* dpart;   // [ksplit][npad] CUDA-core sums of squares (the diagonal)
@@ -64,12 +75,14 @@ struct TallParams {
   float* a_out;
   const float* a_in;
   int warm;
-  const float* G;  // row-major, leading dimension ldG, lower triangle used
+  const float* Gt;     // G~ = D^{-1} G: row j of G divided by G_jj (0 for a zero
+                       // column), row-major, leading dimension ldG, columns n..ldG-1 zero
+  const float* dvec;   // d = diag(G) [n]
   int ldG;
-  float* gpart;    // [2][npad][gstride], zero-filled by the host
-  int gstride;     // grid rounded up to a multiple of 4
-  double* npart;   // [2][grid]
-  float* gw;       // [2][npad]: G·w rows published by the CTAs
+  double* hacc;        // [3][npad]: X^T e_in of a pass, accumulated over the CTAs
+                       // (float64 atomics); zero-filled by the host
+  double* npart;       // [2][grid]
+  float* gw;           // [2][npad]: G~·w rows published by the CTAs
   double* ypart;   // [grid]
   double* hist;    // [max_sweeps + 1]
   GridCtl* ctl;
@@ -92,6 +105,8 @@ struct TallConfig {
   int npad, rows, stage_bytes, box_cols, nstages, smem_bytes, threads;
 };
 bool tall_config(int dtype, int n, int max_smem, TallConfig* cfg);
+// G~ = D^{-1} G and d = diag(G) from the Gram matrix G (n×n, ldG), columns n..ldG-1 of G~ zeroed.
+cudaError_t launch_scale_rows(const float* G, int ldG, int n, float* Gt, float* d, cudaStream_t stream);
 cudaError_t launch_tall_sweep(int dtype, const TallConfig& cfg, const CUtensorMap* tmap,
                               const TallParams& p, int grid, cudaStream_t stream);
 

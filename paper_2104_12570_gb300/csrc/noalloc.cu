@@ -122,14 +122,15 @@ extern "C" int hpscd_solve_noalloc(void* stream, const void* X, int dtype, int64
   int64_t grid64 = d->sms > 256 ? 256 : d->sms;
   if (ntiles < grid64) grid64 = ntiles;
   const int grid = (int)grid64;
-  const int gstride = (grid + 3) / 4 * 4;
 
   size_t off = 0;
   auto take = [&](size_t bytes) { const size_t at = off; off = up256(off + bytes); return at; };
   const size_t oG = take((size_t)gp.npad * gp.npad * sizeof(float));
+  const size_t oGt = take((size_t)gp.npad * gp.npad * sizeof(float));
+  const size_t oD = take((size_t)gp.npad * sizeof(float));
   const size_t oPartial = take(gp.partial_bytes);
   const size_t oE = take((size_t)m * sizeof(float));
-  const size_t oGpart = take((size_t)2 * cfg.npad * gstride * sizeof(float));
+  const size_t oHacc = take((size_t)3 * cfg.npad * sizeof(double));
   const size_t oNpart = take((size_t)2 * grid * sizeof(double));
   const size_t oGw = take((size_t)2 * cfg.npad * sizeof(float));
   const size_t oYpart = take((size_t)grid * sizeof(double));
@@ -142,11 +143,13 @@ extern "C" int hpscd_solve_noalloc(void* stream, const void* X, int dtype, int64
 
   // ---- the scratch keeps the previous call's contents: clear what must start at zero ----
   if (cudaMemsetAsync(ctl, 0, sizeof(GridCtl), st) != cudaSuccess ||
-      cudaMemsetAsync(ws + oGpart, 0, (size_t)2 * cfg.npad * gstride * sizeof(float), st) !=
-          cudaSuccess)
+      cudaMemsetAsync(ws + oHacc, 0, (size_t)3 * cfg.npad * sizeof(double), st) != cudaSuccess)
     return HPSCD_ERR_CUDA;
+  float* Gt = reinterpret_cast<float*>(ws + oGt);
+  float* dvec = reinterpret_cast<float*>(ws + oD);
   if (launch_gram(X, dtype, m, (int)n, ld, gp, reinterpret_cast<double*>(ws + oPartial), G,
-                  gp.npad, st) != cudaSuccess) {
+                  gp.npad, st) != cudaSuccess ||
+      launch_scale_rows(G, gp.npad, (int)n, Gt, dvec, st) != cudaSuccess) {
     cudaGetLastError();
     return HPSCD_ERR_CUDA;
   }
@@ -179,10 +182,10 @@ extern "C" int hpscd_solve_noalloc(void* stream, const void* X, int dtype, int64
   p.a_out = a;
   p.a_in = a;
   p.warm = a_is_guess ? 1 : 0;
-  p.G = G;
+  p.Gt = Gt;
+  p.dvec = dvec;
   p.ldG = gp.npad;
-  p.gpart = reinterpret_cast<float*>(ws + oGpart);
-  p.gstride = gstride;
+  p.hacc = reinterpret_cast<double*>(ws + oHacc);
   p.npart = reinterpret_cast<double*>(ws + oNpart);
   p.gw = reinterpret_cast<float*>(ws + oGw);
   p.ypart = reinterpret_cast<double*>(ws + oYpart);

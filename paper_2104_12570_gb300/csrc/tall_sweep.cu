@@ -19,11 +19,15 @@
 //                                  e_out = y - X·a_p instead)
 //       h     = X^T e_in          (against the residual the pass starts from)
 //       ||e_out||^2 in float64;
-//   grid barrier; every CTA sums the per-CTA partials of h and ||e||^2 in a
-//   fixed order (bitwise identical in every CTA), records
-//   hist[p] = ||e_p|| / ||y||, tests the stopping rule, forms
-//       g_p = h - G·da_p          (= X^T e_p by Eq. ek1-ek)
-//   and runs the forward substitution for da_{p+1}.
+//   the CTAs add their partials of h into one float64 vector (atomics) and
+//   publish their ||e||^2 partials; grid barrier; every CTA reads the same h
+//   and sums the norm partials in a fixed order (bitwise identical in every
+//   CTA), records hist[p] = ||e_p|| / ||y||, tests the stopping rule, forms
+//       r = h ⊘ d - G~·da_p       (= (X^T e_p) ⊘ d by Eq. ek1-ek; d = diag(G),
+//                                  G~ = D^{-1} G, the ⊘ step applied once to
+//                                  the couplings in set-up)
+//   and runs the forward substitution da_j = r_j - sum_{l<j} G~_jl da_l for
+//   da_{p+1}, which has no division on its dependency chain.
 // Pass 0 starts from e_in = y (h = X^T y) with v = a_0 (or nothing).
 //
 // Taking the dots against e_in rather than e_out makes the two halves of a
@@ -61,22 +65,22 @@ __device__ __forceinline__ void load_seg32(const float* __restrict__ src, float 
 }
 
 // Forward substitution of one sweep (see the file comment):
-//   da_j = (r_j - sum_{l<j} G_jl da_l) / d_j, j = 0..n-1, da_j = 0 when d_j = 0.
-// Blocks of 32 columns.  Warp 0 solves each diagonal block with shuffles, one
-// IEEE division per column, reading the block's strictly lower triangle from
-// shared memory (diag_s, packed, staged once per launch); thread t >= 32 owns
-// row t and applies each finished block to it, loading its G segment for the
-// next block right after using the current one, so the load overlaps the
-// next block's solve.  r (in: g, overwritten), d and da are shared arrays of
-// length npad.
-__device__ void forward_substitution(const float* __restrict__ G, int ldG, int n, int npad,
-                                     float* r, const float* d, float* da, const float* diag_s) {
+//   da_j = r_j - sum_{l<j} G~_jl da_l, j = 0..n-1 (r = g ⊘ d; da_j = 0 when d_j = 0,
+//   where row j of G~ is zero).
+// Blocks of 32 columns.  Warp 0 walks each diagonal block with shuffles,
+// reading the block's strictly lower triangle from shared memory (diag_s,
+// packed, staged once per launch); thread t >= 32 owns row t and applies each
+// finished block to it, loading its G~ segment for the next block right after
+// using the current one, so the load overlaps the next block's walk.  r (in:
+// g ⊘ d, overwritten) and da are shared arrays of length npad.
+__device__ void forward_substitution(const float* __restrict__ Gt, int ldG, int n, int npad,
+                                     float* r, float* da, const float* diag_s) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   for (int c = n + tid; c < npad; c += NT) da[c] = 0.f;
   if (n <= 0) { named_sync(NT); return; }
   const int nb = (n + 31) / 32;
   float seg[32];
-  if (tid >= 32 && tid < n) load_seg32(G + (int64_t)tid * ldG, seg);
+  if (tid >= 32 && tid < n) load_seg32(Gt + (int64_t)tid * ldG, seg);
   named_sync(NT);  // r (written by the caller) is visible
   for (int b = 0; b < nb; ++b) {
     const int b0 = 32 * b;
@@ -87,17 +91,12 @@ __device__ void forward_substitution(const float* __restrict__ G, int ldG, int n
 #pragma unroll
       for (int k = 0; k < 32; ++k) seg[k] = (k < lane) ? dl[k] : 0.f;
       float ri = (i < n) ? r[i] : 0.f;
-      const float di = (i < n) ? d[i] : 0.f;
-      float mine = 0.f;
 #pragma unroll
       for (int k = 0; k < 32; ++k) {
-        float q = 0.f;
-        if (lane == k) q = (di > 0.f) ? ri / di : 0.f;
-        q = __shfl_sync(FULL_MASK, q, k);
-        if (lane == k) mine = q;
+        const float q = __shfl_sync(FULL_MASK, ri, k);  // lane k's value is final
         if (lane > k) ri = fmaf(-seg[k], q, ri);
       }
-      if (i < npad) da[i] = mine;
+      if (i < npad) da[i] = (i < n) ? ri : 0.f;
     }
     named_sync(NT);  // da of block b visible
     if (tid >= 32 && tid < n && tid >= b0 + 32) {
@@ -105,7 +104,7 @@ __device__ void forward_substitution(const float* __restrict__ G, int ldG, int n
 #pragma unroll
       for (int k = 0; k < 32; ++k) acc = fmaf(seg[k], da[b0 + k], acc);
       r[tid] -= acc;
-      if (tid >= b0 + 64) load_seg32(G + (int64_t)tid * ldG + b0 + 32, seg);
+      if (tid >= b0 + 64) load_seg32(Gt + (int64_t)tid * ldG + b0 + 32, seg);
     }
     named_sync(NT);  // r of block b+1 final
   }
@@ -219,7 +218,6 @@ __global__ void __launch_bounds__(NT, 1)
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int grid = gridDim.x;
-  const int gstride = p.gstride;
   const int64_t npanels = p.ntiles;
   const int64_t pn0 = npanels * blockIdx.x / grid;
   const int64_t pn1 = npanels * (blockIdx.x + 1) / grid;
@@ -237,7 +235,7 @@ __global__ void __launch_bounds__(NT, 1)
   }
   for (int c = tid; c < NPAD; c += NT) {
     a64_s[c] = (c < n && p.warm) ? (double)p.a_in[c] : 0.0;
-    dd_s[c] = (c < n) ? p.G[(int64_t)c * p.ldG + c] : 0.f;
+    dd_s[c] = (c < n) ? p.dvec[c] : 0.f;
     da_s[c] = 0.f;
   }
   for (int idx = tid; idx < ((n + 31) / 32) * DIAG_PACK; idx += NT) {
@@ -245,7 +243,7 @@ __global__ void __launch_bounds__(NT, 1)
     int i = 1;
     while ((i * (i + 1)) / 2 <= q) ++i;
     const int k = q - (i * (i - 1)) / 2;
-    diag_s[idx] = p.G[(int64_t)(32 * b + i) * p.ldG + 32 * b + k];
+    diag_s[idx] = (32 * b + i < n) ? p.Gt[(int64_t)(32 * b + i) * p.ldG + 32 * b + k] : 0.f;
   }
   __syncthreads();
 
@@ -400,15 +398,17 @@ __global__ void __launch_bounds__(NT, 1)
     if (p.trace && pass == 1 && tid == 0)
       p.trace[(int64_t)p.trace_passes * TRACE_FIELDS + blockIdx.x] = global_timer_ns();
 
-    // publish this CTA's partials: gpart[buf][c][b]
+    // publish this CTA's partials: h into hacc[pass % 3] (float64 atomics),
+    // G~·w rows into gw[pass % 2], ||e||^2 into npart[pass % 2]
     const int buf = (int)(pass & 1);
-    // this CTA's rows of G·w (w = da_p, or a_0 on a warm pass 0), one warp per
+    const int hb = (int)(pass % 3);
+    // this CTA's rows of G~·w (w = da_p, or a_0 on a warm pass 0), one warp per
     // row c = blockIdx.x + k·grid; the rows are spread over the CTAs and
-    // published with the partials, so after the barrier g_p = h - G·w costs n loads
+    // published with the partials, so after the barrier r costs n loads
     if (pass > 0 || p.warm) {
       const float* w = (pass == 0) ? vsm : da_s;
       for (int c = blockIdx.x + warp * grid; c < n; c += NW * grid) {
-        const float* grow = p.G + (int64_t)c * p.ldG;
+        const float* grow = p.Gt + (int64_t)c * p.ldG;
         float acc = 0.f;
         for (int l = lane; l < n; l += 32) acc = fmaf(__ldg(grow + l), w[l], acc);
 #pragma unroll
@@ -422,7 +422,7 @@ __global__ void __launch_bounds__(NT, 1)
 #pragma unroll
       for (int off = 16; off > 0; off >>= 1) sacc += __shfl_xor_sync(FULL_MASK, sacc, off);
       const int c = (j / CW) * C + warp * CW + (j % CW);
-      if (lane == 0) p.gpart[((size_t)buf * NPAD + c) * gstride + blockIdx.x] = sacc;
+      if (lane == 0 && c < n) atomicAdd(p.hacc + (size_t)hb * NPAD + c, (double)sacc);
       gacc[j] = 0.f;
     }
     if (warp >= NW - PR / 32) {
@@ -448,37 +448,19 @@ __global__ void __launch_bounds__(NT, 1)
     }
     stamp(pass, 2);
 
-    // every CTA: h = sum of partials (fixed order, compensated float32),
-    // TPC threads per column each summing a contiguous quarter/half of the CTAs
-    {
-      constexpr int TPC = NT / NPAD >= 4 ? 4 : (NT / NPAD >= 2 ? 2 : 1);
-      const int c = tid % NPAD, part = tid / NPAD;
-      const int q4 = gstride / 4;
-      const int per = (q4 + TPC - 1) / TPC;
-      float s0 = 0.f, c0 = 0.f;
-      if (part < TPC) {
-        const float4* gp4 =
-            reinterpret_cast<const float4*>(p.gpart + ((size_t)buf * NPAD + c) * gstride);
-        float s1 = 0.f, c1 = 0.f;
-        const int q0 = part * per, q1 = min(q4, q0 + per);
-#pragma unroll 8
-        for (int q = q0; q < q1; ++q) {
-          const float4 t = __ldcg(gp4 + q);
-          comp_add(t.x, s0, c0); comp_add(t.y, s1, c1);
-          comp_add(t.z, s0, c0); comp_add(t.w, s1, c1);
-        }
-        comp_add(s1, s0, c0);
-        c0 += c1;
+    // every CTA: r = h ⊘ d - G~·w from the accumulated h (the same values in
+    // every CTA); CTA 0 clears the h buffer of pass + 2, which no CTA reads any
+    // more (its readers passed this barrier) and none adds to before the next one
+    if (blockIdx.x == 0)
+      for (int c = tid; c < NPAD; c += NT) p.hacc[(size_t)((pass + 2) % 3) * NPAD + c] = 0.0;
+    if (tid < NPAD) {
+      float rv = 0.f;
+      if (tid < n && dd_s[tid] > 0.f) {
+        const double hd = __ldcg(p.hacc + (size_t)hb * NPAD + tid);
+        const double gwc = (pass > 0 || p.warm) ? (double)__ldcg(p.gw + (size_t)buf * NPAD + tid) : 0.0;
+        rv = (float)(hd / (double)dd_s[tid] - gwc);
       }
-      float* hs = red_hi;  // free between passes: [TPC][NPAD] sums, then compensations
-      if (part < TPC) { hs[part * NPAD + c] = s0; hs[(TPC + part) * NPAD + c] = c0; }
-      named_sync(NT);
-      if (tid < NPAD) {
-        float ss = 0.f, cc = 0.f;
-        for (int k = 0; k < TPC; ++k) { comp_add(hs[k * NPAD + tid], ss, cc); cc += hs[(TPC + k) * NPAD + tid]; }
-        const float gwc = (pass > 0 || p.warm) && tid < n ? __ldcg(p.gw + (size_t)buf * NPAD + tid) : 0.f;
-        rvec[tid] = (ss + cc) - gwc;
-      }
+      rvec[tid] = rv;
     }
     if (warp == 0) {
       // at most 8 CTAs per lane (grid <= 256); loads issued together
@@ -521,7 +503,7 @@ __global__ void __launch_bounds__(NT, 1)
     r_prev = rel;
     if (stop) break;
 
-    forward_substitution(p.G, p.ldG, n, NPAD, rvec, dd_s, da_s, diag_s);
+    forward_substitution(p.Gt, p.ldG, n, NPAD, rvec, da_s, diag_s);
     stamp(pass, 5);
     const int64_t nx = pass + 1;
     const bool next_refresh = p.refresh_every > 0 && nx % p.refresh_every == 0;
@@ -571,7 +553,28 @@ cudaError_t launch_one(const TallConfig& cfg, const CUtensorMap* tmap, const Tal
                                      (size_t)cfg.smem_bytes, stream);
 }
 
+// G~ = D^{-1} G (row i divided by G_ii; a zero row for G_ii <= 0), d = diag(G),
+// columns n..ldG-1 of G~ zeroed.  One CTA per row.
+__global__ void scale_rows_kernel(const float* __restrict__ G, int ldG, int n, float* __restrict__ Gt,
+                                  float* __restrict__ d) {
+  const int i = blockIdx.x;
+  const float gi = G[(int64_t)i * ldG + i];
+  const bool live = gi > 0.f;
+  for (int j = threadIdx.x; j < ldG; j += blockDim.x) {
+    float v = 0.f;
+    if (live && j < n) v = (j == i) ? 1.f : G[(int64_t)i * ldG + j] / gi;
+    Gt[(int64_t)i * ldG + j] = v;
+  }
+  if (threadIdx.x == 0) d[i] = live ? gi : 0.f;
+}
+
 }  // namespace
+
+cudaError_t launch_scale_rows(const float* G, int ldG, int n, float* Gt, float* d, cudaStream_t stream) {
+  if (n <= 0) return cudaSuccess;
+  scale_rows_kernel<<<n, 256, 0, stream>>>(G, ldG, n, Gt, d);
+  return cudaGetLastError();
+}
 
 // Chunk geometry: 128 rows × C columns, C = 16·CW with CW = 4 (float32) or 8
 // (bfloat16) for wide enough n, so a chunk is 32 KB and each column segment

@@ -71,7 +71,7 @@ def solve_family(ctx, fam, m, n, th, chunk=4096, **kw):
     return labels, sweeps, res
 
 
-def train(ctx, theta, m, n, labels, *, epochs=200, batch=1024, lr=1e-3, lr_min=1e-5, seed=0,
+def train(ctx, theta, m, n, labels, *, epochs=400, batch=512, lr=1e-3, lr_min=1e-5, seed=0,
           val_frac=0.1, log=None):
     """Train a fresh MLP; returns (MLP, history)."""
     import torch
@@ -174,8 +174,8 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--train", type=int, default=50_000, help="training systems (seed 1)")
     ap.add_argument("--eval", type=int, default=4096, help="evaluation systems (seed 0)")
-    ap.add_argument("--epochs", type=int, default=200)
-    ap.add_argument("--batch", type=int, default=1024)
+    ap.add_argument("--epochs", type=int, default=400)
+    ap.add_argument("--batch", type=int, default=512)
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--out", default=WEIGHTS)
     ap.add_argument("--labels", default="", help="cache file of the training labels (.npz)")
