@@ -244,6 +244,31 @@ def batched_comparison(hp, synth, ctx):
     return out
 
 
+def profile_small(hp, synth):
+    """A small case for profiler captures (not a bench line): a 512-system batch
+    of the RBF family (seed 5), stop rule none, 5 sweeps, cluster 1, launched
+    twice; then one training step and one prediction of the warm-start MLP at
+    batch 1024."""
+    import torch
+    from paper_2104_12570_gb300 import warm_start as ws
+    ctx = hp.Context(0)
+    fam = synth.rbf_family(0)
+    m, n, th = synth.rbf_params(512, seed=5)
+    keep, a, b = ws.build_batch(ctx, fam, m, n, th, tol=0, stop="none", max_sweeps=5, cluster=1)
+    b.run()
+    r = b.run()
+    mlp = hp.MLP(ctx, max_batch=1024, seed=0)
+    g = torch.Generator(device="cuda").manual_seed(0)
+    theta = torch.randn(1024, 16, device="cuda", generator=g)
+    tgt = torch.randn(1024, 256, device="cuda", generator=g)
+    mm, nn = np.full(1024, 4000), np.full(1024, 200)
+    mlp.train_step(theta, mm, nn, tgt, lr=1e-4)
+    mlp.predict(theta, mm, nn)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_small": True, "batch_ms": r["timing"]["sweep_ms"],
+                      "x_bytes": int((m * n * 4).sum())}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -258,7 +283,14 @@ def main():
                     help="skip the batched cold-vs-learned-warm-start comparison (4096 RBF systems)")
     ap.add_argument("--rows", type=int, default=0,
                     help="override m (smaller case for profiler captures; not a bench line)")
+    ap.add_argument("--profile-small", action="store_true",
+                    help="run only the small batched + MLP case used for profiler captures")
     args = ap.parse_args()
+    if args.profile_small:
+        import paper_2104_12570_gb300 as hp
+        from paper_2104_12570_gb300 import synth
+        profile_small(hp, synth)
+        return
     if args.warmup < 3:
         args.warmup = 3
     rank, world, local = dist_env()
