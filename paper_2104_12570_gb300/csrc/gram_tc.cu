@@ -299,22 +299,42 @@ __global__ void __launch_bounds__(GT_THREADS, 1)
                  : "memory");
 }
 
-// G[i][j] = G[j][i] = sum over splits (fixed order) of the lower partials.
+// G[i][j] = G[j][i] = sum over splits (fixed order) of the lower partials,
+// one CTA per row i: lanes take columns j <= i (coalesced), the 8 warps take
+// contiguous slices of the splits, and the slices are added in warp order.
 // The diagonal comes from the CUDA-core sums of squares (dpart).
-__global__ void gram_tc_reduce_kernel(const float* __restrict__ partial,
-                                      const double* __restrict__ dpart, int ksplit, int npad,
-                                      float* __restrict__ G, int ldG) {
-  const int64_t total = (int64_t)npad * npad;
-  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
-       idx += (int64_t)gridDim.x * blockDim.x) {
-    const int i0 = (int)(idx / npad), j0 = (int)(idx % npad);
-    const int i = i0 >= j0 ? i0 : j0, j = i0 >= j0 ? j0 : i0;
+constexpr int RED_WARPS = 8;
+constexpr int RED_MAXC = 16;  // column chunks of 32 (npad <= 512)
+__global__ void __launch_bounds__(RED_WARPS * 32)
+    gram_tc_reduce_kernel(const float* __restrict__ partial, const double* __restrict__ dpart,
+                          int ksplit, int npad, float* __restrict__ G, int ldG) {
+  __shared__ double acc_s[RED_WARPS][RED_MAXC * 32];
+  const int i = blockIdx.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nc = (i + 32) / 32;  // chunks covering j = 0..i
+  const int k0 = ksplit * warp / RED_WARPS, k1 = ksplit * (warp + 1) / RED_WARPS;
+  double acc[RED_MAXC];
+#pragma unroll
+  for (int c = 0; c < RED_MAXC; ++c) acc[c] = 0.0;
+  for (int k = k0; k < k1; ++k) {
+    const float* row = partial + ((size_t)k * npad + i) * npad + lane;
+#pragma unroll
+    for (int c = 0; c < RED_MAXC; ++c)
+      if (c < nc) acc[c] += (double)__ldg(row + 32 * c);
+  }
+#pragma unroll
+  for (int c = 0; c < RED_MAXC; ++c)
+    if (c < nc) acc_s[warp][32 * c + lane] = acc[c];
+  __syncthreads();
+  for (int j = threadIdx.x; j <= i; j += RED_WARPS * 32) {
     double s = 0.0;
-    if (i == j)
+    if (j == i) {
       for (int k = 0; k < ksplit; ++k) s += dpart[(size_t)k * npad + i];
-    else
-      for (int k = 0; k < ksplit; ++k) s += (double)partial[((size_t)k * npad + i) * npad + j];
-    G[(int64_t)i0 * ldG + j0] = (float)s;
+    } else {
+      for (int w = 0; w < RED_WARPS; ++w) s += acc_s[w][j];
+    }
+    G[(int64_t)i * ldG + j] = (float)s;
+    G[(int64_t)j * ldG + i] = (float)s;
   }
 }
 
@@ -418,10 +438,8 @@ cudaError_t launch_gram_tc(const CUtensorMap* tmap, int dtype, int64_t m, const 
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const int64_t total = (int64_t)gp.npad * gp.npad;
-  int blocks = (int)((total + 255) / 256);
-  if (blocks > 4096) blocks = 4096;
-  gram_tc_reduce_kernel<<<blocks, 256, 0, stream>>>(partial, p.dpart, gp.ksplit, gp.npad, G, ldG);
+  gram_tc_reduce_kernel<<<gp.npad, RED_WARPS * 32, 0, stream>>>(partial, p.dpart, gp.ksplit, gp.npad,
+                                                               G, ldG);
   return cudaGetLastError();
 }
 
