@@ -22,12 +22,12 @@
 //   set-up:  the cluster forms G (CUDA cores, X staged through shared memory,
 //            each CTA over its rows; partials summed in rank order), d and G~;
 //   pass p:  one read of X forms e_out = e_in - X·v (v = da_p; a warm start's
-//            a_0 on pass 0) and, from the same registers, h = X^T e_out, plus
-//            ||e_out||^2 in float64; the CTAs of the cluster exchange their
-//            partial h and norms through distributed shared memory (one
-//            cluster barrier) and sum them in rank order, so every CTA holds
-//            bitwise identical values; hist[p] = ||e_p|| / ||y||, the stopping
-//            test, then r = h ⊘ d (= (X^T e_p) ⊘ d) and the forward substitution.
+//            a_0 on pass 0) and h = X^T e_in, plus ||e_out||^2 in float64;
+//            the CTAs of the cluster exchange their partial h and norms
+//            through distributed shared memory (one cluster barrier) and sum
+//            them in rank order, so every CTA holds bitwise identical values;
+//            hist[p] = ||e_p|| / ||y||, the stopping test, then
+//            r = h ⊘ d - G~·v (= (X^T e_p) ⊘ d) and the forward substitution.
 // There are no spin waits: the only waits are CTA and cluster barriers, which
 // every CTA of a cluster reaches in the same order (the stopping decision is
 // taken on identical values in all of them).
@@ -191,12 +191,7 @@ __device__ void gram_partial(const float* __restrict__ X, int64_t ld, int64_t r0
 // ---- one streaming pass over this CTA's rows --------------------------------
 // CPW columns per warp; RPL = 16 / CPW row blocks of 128 rows per lane step,
 // so every lane has 16 independent 16-byte loads in flight.  NWC warps split
-// the columns, NWR = 16 / NWC warps split the rows of a panel.  The panel's X
-// values stay in registers while the panel's new residual is formed:
-//   phase A: row sums of X·v -> e_out = e_in - X·v (cross-warp, shared memory)
-//   phase B: h += X^T e_out from the same registers,
-// so h is X^T e against the residual the sweep's corrections produced, and
-// the sweep's next step needs no G·v correction.
+// the columns, NWR = 16 / NWC warps split the rows of a panel.
 template <int CPW>
 __device__ void stream_pass(const float* __restrict__ X, int64_t ld, int64_t r0, int mloc, int n,
                             int nwc, int vec, float* e_s, const float* vsm, float* red,
@@ -215,9 +210,12 @@ __device__ void stream_pass(const float* __restrict__ X, int64_t ld, int64_t r0,
   for (int pbase = 0; pbase < mloc; pbase += ph, ++pi) {
     float* rb_buf = red + (pi & 1) * REDF;
     float xv[RPL][CPW][4];
+    float ein[RPL][4];
 #pragma unroll
     for (int rb = 0; rb < RPL; ++rb) {
       const int lrow = pbase + (wr * RPL + rb) * 128 + 4 * lane;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) ein[rb][q] = (lrow + q < mloc) ? e_s[lrow + q] : 0.f;
 #pragma unroll
       for (int j = 0; j < CPW; ++j) {
         const int col = wc * CPW + j;
@@ -232,7 +230,6 @@ __device__ void stream_pass(const float* __restrict__ X, int64_t ld, int64_t r0,
         }
       }
     }
-    // phase A: this warp's partial row sums of X·v
 #pragma unroll
     for (int rb = 0; rb < RPL; ++rb) {
       float acc[4] = {0.f, 0.f, 0.f, 0.f};
@@ -240,7 +237,10 @@ __device__ void stream_pass(const float* __restrict__ X, int64_t ld, int64_t r0,
       for (int j = 0; j < CPW; ++j) {
         const float vj = vw[j];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) acc[q] = fmaf(xv[rb][j][q], vj, acc[q]);
+        for (int q = 0; q < 4; ++q) {
+          h[j] = fmaf(xv[rb][j][q], ein[rb][q], h[j]);
+          acc[q] = fmaf(xv[rb][j][q], vj, acc[q]);
+        }
       }
       float* dst = rb_buf + wc * ph + (wr * RPL + rb) * 128 + 4 * lane;
       *reinterpret_cast<float4*>(dst) = make_float4(acc[0], acc[1], acc[2], acc[3]);
@@ -255,19 +255,6 @@ __device__ void stream_pass(const float* __restrict__ X, int64_t ld, int64_t r0,
         e_s[lrow] = e_new;
         nrm = fma((double)e_new, (double)e_new, nrm);
       }
-    }
-    __syncthreads();
-    // phase B: h += X^T e_out for this warp's columns
-#pragma unroll
-    for (int rb = 0; rb < RPL; ++rb) {
-      const int lrow = pbase + (wr * RPL + rb) * 128 + 4 * lane;
-      float eo[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) eo[q] = (lrow + q < mloc) ? e_s[lrow + q] : 0.f;
-#pragma unroll
-      for (int j = 0; j < CPW; ++j)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) h[j] = fmaf(xv[rb][j][q], eo[q], h[j]);
     }
   }
   // lane partials of h -> one value per (row group, column)
@@ -513,10 +500,17 @@ __global__ void __launch_bounds__(BNT, 1) batched_sweep_kernel(const BatchParams
       r_prev = rel;
       if (stop) break;
       __syncthreads();  // rvec (h) complete
-      // r = h ⊘ d: h was formed against the pass's own e_out = e_p (the ⊘ step of Eq. da2)
-      for (int c = tid; c < n; c += BNT) {
-        const float dc = dd_s[c];
-        rvec[c] = dc > 0.f ? rvec[c] / dc : 0.f;
+      // r = h ⊘ d - G~·v, one warp per row
+      for (int c = warp; c < n; c += BNW) {
+        const float* grow = Gt + (size_t)c * BLDG;
+        float acc = 0.f;
+        for (int l = lane; l < n; l += 32) acc = fmaf(__ldcg(grow + l), vsm[l], acc);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(FULL_MASK, acc, off);
+        if (lane == 0) {
+          const float dc = dd_s[c];
+          rvec[c] = (dc > 0.f ? rvec[c] / dc : 0.f) - acc;
+        }
       }
       __syncthreads();
       forward_sub_scaled(Gt, n, rvec, da_s, diag_s);

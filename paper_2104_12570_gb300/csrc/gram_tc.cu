@@ -299,42 +299,73 @@ __global__ void __launch_bounds__(GT_THREADS, 1)
                  : "memory");
 }
 
-// G[i][j] = G[j][i] = sum over splits (fixed order) of the lower partials,
-// one CTA per row i: lanes take columns j <= i (coalesced), the 8 warps take
-// contiguous slices of the splits, and the slices are added in warp order.
-// The diagonal comes from the CUDA-core sums of squares (dpart).
-constexpr int RED_WARPS = 8;
-constexpr int RED_MAXC = 16;  // column chunks of 32 (npad <= 512)
-__global__ void __launch_bounds__(RED_WARPS * 32)
-    gram_tc_reduce_kernel(const float* __restrict__ partial, const double* __restrict__ dpart,
-                          int ksplit, int npad, float* __restrict__ G, int ldG) {
-  __shared__ double acc_s[RED_WARPS][RED_MAXC * 32];
-  const int i = blockIdx.x;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nc = (i + 32) / 32;  // chunks covering j = 0..i
-  const int k0 = ksplit * warp / RED_WARPS, k1 = ksplit * (warp + 1) / RED_WARPS;
-  double acc[RED_MAXC];
-#pragma unroll
-  for (int c = 0; c < RED_MAXC; ++c) acc[c] = 0.0;
-  for (int k = k0; k < k1; ++k) {
-    const float* row = partial + ((size_t)k * npad + i) * npad + lane;
-#pragma unroll
-    for (int c = 0; c < RED_MAXC; ++c)
-      if (c < nc) acc[c] += (double)__ldg(row + 32 * c);
-  }
-#pragma unroll
-  for (int c = 0; c < RED_MAXC; ++c)
-    if (c < nc) acc_s[warp][32 * c + lane] = acc[c];
-  __syncthreads();
-  for (int j = threadIdx.x; j <= i; j += RED_WARPS * 32) {
-    double s = 0.0;
-    if (j == i) {
-      for (int k = 0; k < ksplit; ++k) s += dpart[(size_t)k * npad + i];
-    } else {
-      for (int w = 0; w < RED_WARPS; ++w) s += acc_s[w][j];
+// Sum of the per-split partials in two stages (fixed order, so every run
+// gives the same G):
+//   stage 1: tmp[s][i][j..j+3] = sum over the splits of slice s of the lower
+//            partials (float4 loads, independent across threads; one thread
+//            per slice, row and 4 columns), and d_i = sum_k dpart[k][i] (the
+//            CUDA-core diagonal, float64);
+//   stage 2: G_ij = G_ji = sum_s tmp[s][i][j], G_ii = d_i; optionally
+//            G~ = D^{-1} G in both triangles and d as float32.
+constexpr int RED_SLICES = 16;
+__global__ void gram_tc_reduce1_kernel(const float* __restrict__ partial,
+                                       const double* __restrict__ dpart, int ksplit, int npad,
+                                       float* __restrict__ tmp, double* __restrict__ d64) {
+  const int n4 = npad / 4;
+  const int64_t total = (int64_t)RED_SLICES * npad * n4;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int j4 = (int)(idx % n4);
+    const int i = (int)((idx / n4) % npad);
+    const int sl = (int)(idx / ((int64_t)n4 * npad));
+    if (4 * j4 > i) continue;
+    const int k0 = ksplit * sl / RED_SLICES, k1 = ksplit * (sl + 1) / RED_SLICES;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+#pragma unroll 4
+    for (int k = k0; k < k1; ++k) {
+      const float4 v = __ldg(reinterpret_cast<const float4*>(partial + ((size_t)k * npad + i) * npad) + j4);
+      a0 += v.x; a1 += v.y; a2 += v.z; a3 += v.w;
     }
-    G[(int64_t)i * ldG + j] = (float)s;
-    G[(int64_t)j * ldG + i] = (float)s;
+    *reinterpret_cast<float4*>(tmp + ((size_t)sl * npad + i) * npad + 4 * j4) =
+        make_float4((float)a0, (float)a1, (float)a2, (float)a3);
+    if (sl == 0 && j4 == 0) {
+      double dd = 0.0;
+      for (int k = 0; k < ksplit; ++k) dd += dpart[(size_t)k * npad + i];
+      d64[i] = dd;
+    }
+  }
+}
+
+__global__ void gram_tc_reduce2_kernel(const float* __restrict__ tmp, const double* __restrict__ d64,
+                                       int npad, int n, float* __restrict__ G, int ldG,
+                                       float* __restrict__ Gt, float* __restrict__ dvec) {
+  const int64_t total = (int64_t)npad * npad;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(idx / npad), j = (int)(idx % npad);
+    if (j > i) continue;
+    float g;
+    if (j == i) {
+      g = (float)d64[i];
+    } else {
+      double sacc = 0.0;
+#pragma unroll
+      for (int sl = 0; sl < RED_SLICES; ++sl) sacc += tmp[((size_t)sl * npad + i) * npad + j];
+      g = (float)sacc;
+    }
+    G[(int64_t)i * ldG + j] = g;
+    G[(int64_t)j * ldG + i] = g;
+    if (Gt) {
+      const float di = (float)d64[i], dj = (float)d64[j];
+      const bool live_i = i < n && di > 0.f, live_j = j < n && dj > 0.f;
+      if (j == i) {
+        Gt[(int64_t)i * ldG + i] = live_i ? 1.f : 0.f;
+        if (dvec) dvec[i] = live_i ? di : 0.f;
+      } else {
+        Gt[(int64_t)i * ldG + j] = (live_i && j < n) ? g / di : 0.f;
+        Gt[(int64_t)j * ldG + i] = (live_j && i < n) ? g / dj : 0.f;
+      }
+    }
   }
 }
 
@@ -405,13 +436,15 @@ bool gram_tc_plan(int dtype, int64_t m, int n, int sms, int max_smem, GramTCPlan
   gp->rows_per_split = rps;
   gp->ksplit = (int)((m + rps - 1) / rps);
   gp->partial_bytes = (size_t)gp->ksplit * gp->npad * gp->npad * sizeof(float) +
-                      (size_t)gp->ksplit * gp->npad * sizeof(double);
+                      (size_t)gp->ksplit * gp->npad * sizeof(double) +
+                      (size_t)RED_SLICES * gp->npad * gp->npad * sizeof(float) +
+                      (size_t)gp->npad * sizeof(double);
   return true;
 }
 
 cudaError_t launch_gram_tc(const CUtensorMap* tmap, int dtype, int64_t m, const GramTCPlan& gp,
                            float* partial, int* err, uint64_t timeout_ns, float* G, int ldG,
-                           cudaStream_t stream) {
+                           cudaStream_t stream, int n, float* Gt, float* dvec) {
   GramTCParams p{};
   p.m = m;
   p.npad = gp.npad;
@@ -438,8 +471,15 @@ cudaError_t launch_gram_tc(const CUtensorMap* tmap, int dtype, int64_t m, const 
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  gram_tc_reduce_kernel<<<gp.npad, RED_WARPS * 32, 0, stream>>>(partial, p.dpart, gp.ksplit, gp.npad,
-                                                               G, ldG);
+  float* tmp = reinterpret_cast<float*>(reinterpret_cast<char*>(p.dpart) +
+                                        (size_t)gp.ksplit * gp.npad * sizeof(double));
+  double* d64 = reinterpret_cast<double*>(tmp + (size_t)RED_SLICES * gp.npad * gp.npad);
+  const int64_t t1 = (int64_t)RED_SLICES * gp.npad * (gp.npad / 4);
+  gram_tc_reduce1_kernel<<<(unsigned)((t1 + 255) / 256), 256, 0, stream>>>(partial, p.dpart, gp.ksplit,
+                                                                          gp.npad, tmp, d64);
+  const int64_t t2 = (int64_t)gp.npad * gp.npad;
+  gram_tc_reduce2_kernel<<<(unsigned)((t2 + 255) / 256), 256, 0, stream>>>(tmp, d64, gp.npad, n, G, ldG,
+                                                                          Gt, dvec);
   return cudaGetLastError();
 }
 

@@ -172,26 +172,30 @@ int encode_gram_map(hpscd_ctx* ctx, const void* X, int dtype, int64_t m, int64_t
 
 // G = X^T X into G (ldG), by the tensor-core kernel when it applies, else the
 // CUDA-core kernel.  `err` receives a device-side failure flag.
+// When Gt is given, also G~ = D^{-1} G and d (fused into the tensor-core
+// path's reduction; one extra kernel after the CUDA-core path).
 int run_gram(hpscd_ctx* ctx, const void* X, int dtype, int64_t m, int64_t n, int64_t ld,
              const Plan& P, void* partial, float* G, int ldG, int* err, bool force_simt,
-             int* launches) {
+             int* launches, float* Gt = nullptr, float* dvec = nullptr) {
   CUtensorMap gmap;
   memset(&gmap, 0, sizeof(gmap));
   if (!force_simt && P.tc_ok && encode_gram_map(ctx, X, dtype, m, n, ld, &gmap)) {
     if (launch_gram_tc(&gmap, dtype, m, P.gtc, static_cast<float*>(partial), err,
-                       (uint64_t)(ctx->timeout_s * 1e9), G, ldG, ctx->stream) != cudaSuccess) {
+                       (uint64_t)(ctx->timeout_s * 1e9), G, ldG, ctx->stream, (int)n, Gt,
+                       dvec) != cudaSuccess) {
       cudaGetLastError();
       return HPSCD_ERR_CUDA;
     }
-    *launches = 2;
+    *launches = 3;
     return HPSCD_OK;
   }
   if (launch_gram(X, dtype, m, (int)n, ld, P.gp, static_cast<double*>(partial), G, ldG,
-                  ctx->stream) != cudaSuccess) {
+                  ctx->stream) != cudaSuccess ||
+      (Gt && launch_scale_rows(G, ldG, (int)n, Gt, dvec, ctx->stream) != cudaSuccess)) {
     cudaGetLastError();
     return HPSCD_ERR_CUDA;
   }
-  *launches = 2;
+  *launches = Gt ? 3 : 2;
   return HPSCD_OK;
 }
 
@@ -336,15 +340,11 @@ int solve_device(hpscd_ctx* ctx, const void* X, int dtype, int layout, int64_t m
   if (cudaMemsetAsync(ctl, 0, sizeof(GridCtl), st) != cudaSuccess) return HPSCD_ERR_CUDA;
   if (cudaEventRecord(ctx->ev[0], st) != cudaSuccess) return HPSCD_ERR_CUDA;
   int gram_launches = 0;
-  int rcg = run_gram(ctx, X, dtype, m, n, ld, P, ws + L.partial, G, P.ldG, &ctl->err,
-                     (o->debug_flags & HPSCD_DEBUG_SIMT_GRAM) != 0, &gram_launches);
-  if (rcg != HPSCD_OK) return rcg;
   float* Gt = reinterpret_cast<float*>(ws + L.Gt);
   float* dvec = reinterpret_cast<float*>(ws + L.dvec);
-  if (launch_scale_rows(G, P.ldG, (int)n, Gt, dvec, st) != cudaSuccess) {
-    cudaGetLastError();
-    return HPSCD_ERR_CUDA;
-  }
+  int rcg = run_gram(ctx, X, dtype, m, n, ld, P, ws + L.partial, G, P.ldG, &ctl->err,
+                     (o->debug_flags & HPSCD_DEBUG_SIMT_GRAM) != 0, &gram_launches, Gt, dvec);
+  if (rcg != HPSCD_OK) return rcg;
   if (cudaMemsetAsync(ws + L.hacc, 0, (size_t)3 * P.cfg.npad * sizeof(double), st) != cudaSuccess)
     return HPSCD_ERR_CUDA;
   if (cudaEventRecord(ctx->ev[1], st) != cudaSuccess) return HPSCD_ERR_CUDA;
@@ -413,7 +413,7 @@ int solve_device(hpscd_ctx* ctx, const void* X, int dtype, int layout, int64_t m
   t.passes = c.passes;
   t.x_bytes = m * n * esize(dtype);
   t.grid = P.grid;
-  t.kernel_launches = gram_launches + 2;
+  t.kernel_launches = gram_launches + 1;
   ctx->last = t;
   (void)layout;
   if (c.err != DEV_OK) return HPSCD_ERR_TIMEOUT;

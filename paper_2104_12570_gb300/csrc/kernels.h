@@ -58,9 +58,11 @@ struct GramTCParams {
   int nstages;
 };
 bool gram_tc_plan(int dtype, int64_t m, int n, int sms, int max_smem, GramTCPlan* gp);
+// G = X^T X into G (ldG); when Gt is given, also G~ = D^{-1} G (ldG, rows and
+// columns >= n zero) and d = diag(G) (float32, dvec).
 cudaError_t launch_gram_tc(const CUtensorMap* tmap, int dtype, int64_t m, const GramTCPlan& gp,
                            float* partial, int* err, uint64_t timeout_ns, float* G, int ldG,
-                           cudaStream_t stream);
+                           cudaStream_t stream, int n, float* Gt, float* dvec);
 
 // ---- persistent tall sweep (column-major X, n <= 512) ----
 constexpr int MODE_COPY = 0, MODE_NORMAL = 1, MODE_REFRESH = 2;
