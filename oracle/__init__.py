@@ -47,6 +47,13 @@ def load_library(path: str):
     lib.hpscd_oracle_residual.argtypes = [vp, ctypes.c_int, ctypes.c_int, i64, i64, i64,
                                           dp, dp, dp, ctypes.POINTER(ctypes.c_double)]
     lib.hpscd_oracle_residual.restype = ctypes.c_int
+    lib.hpscd_oracle_solve_blocks.argtypes = [vp, ctypes.c_int, ctypes.c_int, i64, i64, i64,
+                                              dp, dp, i64, ctypes.c_double, i64, ctypes.c_int,
+                                              dp, dp, dp, ctypes.POINTER(i64)]
+    lib.hpscd_oracle_solve_blocks.restype = ctypes.c_int
+    lib.hpscd_oracle_select.argtypes = [vp, ctypes.c_int, ctypes.c_int, i64, i64, i64, dp, i64,
+                                        vp, dp, dp]
+    lib.hpscd_oracle_select.restype = ctypes.c_int
     return lib
 
 
@@ -100,6 +107,42 @@ def solve(X, y, *, m, n, layout="col", dtype="f32", a0=None, tol=1e-6, max_sweep
     if st in (1, 4):
         raise ValueError(f"oracle: {STATUS[st]}")
     return OracleResult(a, e, hist[: sw.value + 1], sw.value, STATUS[st])
+
+
+def solve_blocks(X, y, *, m, n, thr, layout="col", dtype="f32", a0=None, tol=1e-6,
+                 max_sweeps=1000, stop="rel_res", want_e=False) -> OracleResult:
+    """Algorithm 2 (blocks of thr columns updated from one residual) in float64."""
+    _check_x(X, m, n, layout, dtype)
+    lib = _load()
+    y64 = np.ascontiguousarray(y, dtype=np.float64)
+    a064 = None if a0 is None else np.ascontiguousarray(a0, dtype=np.float64)
+    a = np.zeros(n, dtype=np.float64)
+    e = np.zeros(m, dtype=np.float64) if want_e else None
+    hist = np.full(max_sweeps + 1, np.nan, dtype=np.float64)
+    sw = ctypes.c_int64(0)
+    ld = max(1, m if layout == "col" else n)
+    st = lib.hpscd_oracle_solve_blocks(_ptr(X), DTYPES[dtype], LAYOUTS[layout], m, n, ld, _ptr(y64),
+                                       _ptr(a064), int(thr), float(tol), int(max_sweeps),
+                                       STOP[stop], _ptr(a), _ptr(e), _ptr(hist), ctypes.byref(sw))
+    if st in (1, 4):
+        raise ValueError(f"oracle: {STATUS[st]}")
+    return OracleResult(a, e, hist[: sw.value + 1], sw.value, STATUS[st])
+
+
+def select(X, y, *, m, n, F, layout="col", dtype="f32"):
+    """Algorithm 3: (selected index per step, a, hist) in float64."""
+    _check_x(X, m, n, layout, dtype)
+    lib = _load()
+    y64 = np.ascontiguousarray(y, dtype=np.float64)
+    sel = np.zeros(max(F, 1), dtype=np.int64)
+    a = np.zeros(n, dtype=np.float64)
+    hist = np.zeros(F + 1, dtype=np.float64)
+    ld = max(1, m if layout == "col" else n)
+    st = lib.hpscd_oracle_select(_ptr(X), DTYPES[dtype], LAYOUTS[layout], m, n, ld, _ptr(y64),
+                                 int(F), _ptr(sel), _ptr(a), _ptr(hist))
+    if st != 0:
+        raise ValueError(f"oracle select: {STATUS[st]}")
+    return sel[:F], a, hist
 
 
 def residual(X, y, a, *, m, n, layout="col", dtype="f32"):

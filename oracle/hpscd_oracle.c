@@ -271,3 +271,160 @@ int hpscd_oracle_solve(const void* X, int dt, int lay, int64_t m, int64_t n, int
   free(Xcopy);
   return status;
 }
+
+/*
+ * Algorithm 2 (HPSCDP, Sec. 7), literally, in float64.
+ *
+ *   a <- a0 (or 0_n); e <- y - X·a
+ *   for s = 1..max_sweeps:
+ *     aprev <- a
+ *     for each block jj = {k, ..., k+thr-1} of thr consecutive columns
+ *         (the last block holds the n mod thr remaining columns):
+ *       for every k in jj, against the SAME e:  a_k <- a_k + <X_k, e> / <X_k, X_k>
+ *       e <- e - X_jj·(a_jj - aprev_jj)
+ *     hist[s] <- ||e|| / ||y||, then the stopping test (as in Algorithm 1)
+ * thr = 1 is Algorithm 1; thr >= n updates every column from one residual.
+ * Zero columns are skipped (da = 0).  Returns like hpscd_oracle_solve.
+ */
+int hpscd_oracle_solve_blocks(const void* X, int dt, int lay, int64_t m, int64_t n, int64_t ld,
+                              const double* y, const double* a0, int64_t thr, double tol,
+                              int64_t max_sweeps, int stop_rule, double* a_out, double* e_out,
+                              double* hist, int64_t* sweeps_done) {
+  if (!valid_args(X, dt, lay, m, n, ld) || (!y && m > 0) || (!a_out && n > 0) ||
+      max_sweeps < 0 || (stop_rule < 0 || stop_rule > 2) || !(tol >= 0.0) || thr < 1)
+    return OR_INVALID;
+  double* e = (double*)malloc((size_t)(m > 0 ? m : 1) * sizeof(double));
+  double* col = (double*)malloc((size_t)(m > 0 ? m : 1) * sizeof(double));
+  double* d = (double*)malloc((size_t)(n > 0 ? n : 1) * sizeof(double));
+  double* aprev = (double*)malloc((size_t)(n > 0 ? n : 1) * sizeof(double));
+  if (!e || !col || !d || !aprev) {
+    free(e); free(col); free(d); free(aprev);
+    return OR_NOMEM;
+  }
+  for (int64_t j = 0; j < n; ++j) a_out[j] = a0 ? a0[j] : 0.0;
+  for (int64_t i = 0; i < m; ++i) e[i] = y[i];
+  for (int64_t c = 0; c < n; ++c) {
+    load_column(X, dt, lay, ld, m, c, col);
+    double sq = 0.0;
+    for (int64_t i = 0; i < m; ++i) {
+      e[i] -= col[i] * a_out[c];
+      sq += col[i] * col[i];
+    }
+    d[c] = sq;
+  }
+  const double ynorm = norm2(y, m);
+  const double scale = ynorm > 0.0 ? ynorm : 1.0;
+  double r_prev = norm2(e, m) / scale;
+  if (hist) hist[0] = r_prev;
+  int status = OR_NOT_CONVERGED;
+  int64_t s_done = 0;
+  if (!isfinite(r_prev)) {
+    status = OR_NONFINITE;
+  } else if ((stop_rule == OR_STOP_REL_RES && r_prev <= tol) ||
+             (stop_rule == OR_STOP_NONE && max_sweeps == 0)) {
+    status = OR_OK;
+  } else {
+    for (int64_t s = 1; s <= max_sweeps; ++s) {
+      for (int64_t j = 0; j < n; ++j) aprev[j] = a_out[j];
+      for (int64_t k0 = 0; k0 < n; k0 += thr) {
+        const int64_t k1 = k0 + thr < n ? k0 + thr : n;
+        /* every column of the block against the same e */
+        for (int64_t k = k0; k < k1; ++k) {
+          load_column(X, dt, lay, ld, m, k, col);
+          double dot = 0.0;
+          for (int64_t i = 0; i < m; ++i) dot += col[i] * e[i];
+          a_out[k] += d[k] > 0.0 ? dot / d[k] : 0.0;
+        }
+        /* e <- e - X_jj (a_jj - aprev_jj) */
+        for (int64_t k = k0; k < k1; ++k) {
+          const double delta = a_out[k] - aprev[k];
+          if (delta == 0.0) continue;
+          load_column(X, dt, lay, ld, m, k, col);
+          for (int64_t i = 0; i < m; ++i) e[i] -= col[i] * delta;
+        }
+      }
+      s_done = s;
+      const double r = norm2(e, m) / scale;
+      if (hist) hist[s] = r;
+      if (!isfinite(r)) { status = OR_NONFINITE; break; }
+      if (stop_rule == OR_STOP_REL_RES && r <= tol) { status = OR_OK; break; }
+      if (stop_rule == OR_STOP_REL_CHANGE && (r_prev == 0.0 || fabs(r_prev - r) < tol * r_prev)) {
+        status = OR_OK;
+        break;
+      }
+      if (stop_rule == OR_STOP_NONE && s == max_sweeps) { status = OR_OK; break; }
+      r_prev = r;
+    }
+  }
+  if (e_out)
+    for (int64_t i = 0; i < m; ++i) e_out[i] = e[i];
+  if (sweeps_done) *sweeps_done = s_done;
+  free(e); free(col); free(d); free(aprev);
+  return status;
+}
+
+/*
+ * Algorithm 3 (HPSCDF, Sec. 8), literally, in float64, for F steps.
+ *
+ *   a <- 0_n; e <- y; J <- (); d_j <- <X_j, X_j>  (the diagonal of X^T X)
+ *   for f = 1..F:
+ *     da   <- (X^T e) ⊘ d                       (elementwise; 0 where d_j = 0)
+ *     E_j  <- sum_i (e_i - X_ij·da_j)^2         for every j
+ *     jhat <- argmin_j E_j                      (lowest j among equal values)
+ *     J    <- (J, jhat)  when jhat is not in J yet
+ *     a_jhat <- a_jhat + da_jhat;  e <- e - X_jhat·da_jhat
+ *     hist[f] <- ||e|| / ||y||
+ * Outputs: sel[f-1] = jhat of step f (F entries), a_out[n], hist[F+1] (may
+ * be NULL).  Returns OR_OK or OR_INVALID / OR_NOMEM.
+ */
+int hpscd_oracle_select(const void* X, int dt, int lay, int64_t m, int64_t n, int64_t ld,
+                        const double* y, int64_t F, int64_t* sel, double* a_out, double* hist) {
+  if (!valid_args(X, dt, lay, m, n, ld) || (!y && m > 0) || (!a_out && n > 0) || F < 0 ||
+      (!sel && F > 0) || n < 1)
+    return OR_INVALID;
+  double* e = (double*)malloc((size_t)(m > 0 ? m : 1) * sizeof(double));
+  double* col = (double*)malloc((size_t)(m > 0 ? m : 1) * sizeof(double));
+  double* d = (double*)malloc((size_t)n * sizeof(double));
+  double* da = (double*)malloc((size_t)n * sizeof(double));
+  if (!e || !col || !d || !da) {
+    free(e); free(col); free(d); free(da);
+    return OR_NOMEM;
+  }
+  for (int64_t j = 0; j < n; ++j) a_out[j] = 0.0;
+  for (int64_t i = 0; i < m; ++i) e[i] = y[i];
+  for (int64_t c = 0; c < n; ++c) {
+    load_column(X, dt, lay, ld, m, c, col);
+    double sq = 0.0;
+    for (int64_t i = 0; i < m; ++i) sq += col[i] * col[i];
+    d[c] = sq;
+  }
+  const double ynorm = norm2(y, m);
+  const double scale = ynorm > 0.0 ? ynorm : 1.0;
+  if (hist) hist[0] = norm2(e, m) / scale;
+  for (int64_t f = 1; f <= F; ++f) {
+    for (int64_t c = 0; c < n; ++c) {
+      load_column(X, dt, lay, ld, m, c, col);
+      double corr = 0.0;
+      for (int64_t i = 0; i < m; ++i) corr += col[i] * e[i];
+      da[c] = d[c] > 0.0 ? corr / d[c] : 0.0;
+    }
+    int64_t jhat = 0;
+    double best = 0.0;
+    for (int64_t j = 0; j < n; ++j) {
+      load_column(X, dt, lay, ld, m, j, col);
+      double E = 0.0;
+      for (int64_t i = 0; i < m; ++i) {
+        const double r = e[i] - col[i] * da[j];
+        E += r * r;
+      }
+      if (j == 0 || E < best) { best = E; jhat = j; }
+    }
+    sel[f - 1] = jhat;
+    a_out[jhat] += da[jhat];
+    load_column(X, dt, lay, ld, m, jhat, col);
+    for (int64_t i = 0; i < m; ++i) e[i] -= col[i] * da[jhat];
+    if (hist) hist[f] = norm2(e, m) / scale;
+  }
+  free(e); free(col); free(d); free(da);
+  return OR_OK;
+}

@@ -25,6 +25,20 @@ MUTANTS = {
     "norm_without_sqrt": ("  return sqrt(s);", "  return s;"),
     "row_major_transposed": ("Xcopy[j * m + i] = x_elem(X, dt, lay, ld, i, j)",
                              "Xcopy[j * m + i] = x_elem(X, dt, lay, ld, i % n, j % m)"),
+    # Algorithm 2 (blocks): the correction uses a instead of a - aprev; a block
+    # column sees the residual already updated by its block neighbours
+    "blocks_correction_not_delta": ("const double delta = a_out[k] - aprev[k];",
+                                    "const double delta = a_out[k];"),
+    "blocks_gauss_seidel_inside": ("a_out[k] += d[k] > 0.0 ? dot / d[k] : 0.0;",
+                                   "a_out[k] += d[k] > 0.0 ? dot / d[k] : 0.0;"
+                                   " { const double dd = d[k] > 0.0 ? dot / d[k] : 0.0;"
+                                   " for (int64_t i = 0; i < m; ++i) e[i] -= col[i] * dd;"
+                                   " aprev[k] += dd; }"),
+    # Algorithm 3 (selection): argmax instead of argmin; the printed assignment
+    # instead of the accumulated update; an unsquared error sum
+    "select_argmax": ("if (j == 0 || E < best)", "if (j == 0 || E > best)"),
+    "select_assign": ("a_out[jhat] += da[jhat];", "a_out[jhat] = da[jhat];"),
+    "select_unsquared": ("E += r * r;", "E += r;"),
 }
 
 
@@ -76,7 +90,63 @@ def battery(lib):
                          tol=0, max_sweeps=2, stop="none", lib=lib)
     if not np.allclose(r_row.a, r.a, rtol=1e-13, atol=1e-13):
         failed.append("layout")
+
+    # Algorithm 2: one sweep is the block splitting (D + L_B)^{-1} X^T (y - X a)
+    thr = 3
+    blk = np.arange(8) // thr
+    M = np.diag(np.diag(G)) + np.where(blk[:, None] > blk[None, :], G, 0.0)
+    a_b = np.linalg.solve(M, Xd.T @ y)
+    a_b = a_b + np.linalg.solve(M, Xd.T @ (y - Xd @ a_b))  # two sweeps
+    rb = _blocks(lib, Xd, y, thr, sweeps=2)
+    if not (np.allclose(rb[0], a_b, rtol=1e-10, atol=1e-12) and
+            np.allclose(rb[1], y - Xd @ rb[0], atol=1e-10)):
+        failed.append("blocks_splitting")
+
+    # Algorithm 3: argmax of <X_j,e>^2/<X_j,X_j> each step, e = y - X·a (correlated columns
+    # make the selection return to a chosen column)
+    base = rng.standard_normal(30)
+    Xc = np.stack([base + 0.3 * rng.standard_normal(30) for _ in range(5)], axis=1)
+    yc = Xc @ np.array([1.0, 1.0, -0.5, 0.7, 0.2])
+    sel, a_s, hist_s = _select(lib, Xc, yc, 12)
+    e = yc.copy()
+    d = (Xc * Xc).sum(axis=0)
+    ok = True
+    for f in range(12):
+        c = Xc.T @ e
+        j = int(np.argmax(c * c / d))
+        ok &= sel[f] == j
+        e = e - Xc[:, j] * (c[j] / d[j])
+    ok &= np.allclose(yc - Xc @ a_s, e, atol=1e-10)
+    if not ok:
+        failed.append("selection")
     return failed
+
+
+def _blocks(lib, Xd, y, thr, sweeps):
+    import ctypes
+    m, n = Xd.shape
+    Xs = np.ascontiguousarray(Xd.T)
+    a = np.zeros(n)
+    e = np.zeros(m)
+    hist = np.zeros(sweeps + 1)
+    sw = ctypes.c_int64(0)
+    p = lambda v: v.ctypes.data_as(ctypes.c_void_p)
+    lib.hpscd_oracle_solve_blocks(p(Xs), 2, 0, m, n, m, p(np.ascontiguousarray(y)), None, thr,
+                                  0.0, sweeps, 2, p(a), p(e), p(hist), ctypes.byref(sw))
+    return a, e
+
+
+def _select(lib, Xd, y, F):
+    import ctypes
+    m, n = Xd.shape
+    Xs = np.ascontiguousarray(Xd.T)
+    sel = np.zeros(F, dtype=np.int64)
+    a = np.zeros(n)
+    hist = np.zeros(F + 1)
+    p = lambda v: v.ctypes.data_as(ctypes.c_void_p)
+    lib.hpscd_oracle_select(p(Xs), 2, 0, m, n, m, p(np.ascontiguousarray(y)), F, p(sel), p(a),
+                            p(hist))
+    return sel, a, hist
 
 
 def test_real_oracle_passes_battery():

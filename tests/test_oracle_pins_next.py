@@ -1,0 +1,143 @@
+"""Pins of the oracle's Algorithm 2 (HPSCDP, blocks of thr columns updated from
+one residual, Sec. 7) and Algorithm 3 (HPSCDF, greedy feature selection,
+Sec. 8), each against something other than itself (no GPU)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2104_12570_gb300 import synth
+
+
+def sys64(m, n, seed, noise=0.05):
+    return synth.make_system(m, n, seed=seed, noise=noise, dtype="f64", consistent_rhs_dtype="f64")
+
+
+def blocks(s, thr, sweeps, **kw):
+    return oracle.solve_blocks(s.X, s.y, m=s.m, n=s.n, thr=thr, dtype=s.dtype, tol=0,
+                               max_sweeps=sweeps, stop="none", **kw)
+
+
+# ---------------- Algorithm 2 ----------------
+
+def test_thr_one_is_algorithm_1():
+    s = sys64(300, 40, 1)
+    o1 = oracle.solve_system(s, tol=0, max_sweeps=6, stop="none")
+    o2 = blocks(s, 1, 6)
+    np.testing.assert_allclose(o2.a, o1.a, rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(o2.hist, o1.hist, rtol=1e-12)
+
+
+@pytest.mark.parametrize("thr", [3, 7, 16, 40, 100])
+def test_one_sweep_is_the_block_splitting(thr):
+    """One sweep of Algorithm 2 is a <- a + (D + L_B)^{-1} X^T (y - X a), where
+    L_B holds the couplings G_jl of columns l in EARLIER blocks than j (within a
+    block every column sees the same residual); thr >= n is the Jacobi iteration."""
+    s = sys64(120, 40, 2)
+    X = s.dense_f64()
+    G = X.T @ X
+    n = s.n
+    blk = np.arange(n) // thr
+    M = np.diag(np.diag(G)) + np.where(blk[:, None] > blk[None, :], G, 0.0)
+    a = np.zeros(n)
+    for k in range(1, 5):
+        a = a + np.linalg.solve(M, X.T @ (s.y - X @ a))
+        o = blocks(s, thr, k)
+        np.testing.assert_allclose(o.a, a, rtol=1e-9, atol=1e-12)
+
+
+def test_jacobi_limit_thr_ge_n():
+    s = sys64(200, 12, 3)
+    X = s.dense_f64()
+    d = (X * X).sum(axis=0)
+    a = np.zeros(s.n)
+    for _ in range(3):
+        a = a + (X.T @ (s.y - X @ a)) / d
+    np.testing.assert_allclose(blocks(s, 12, 3).a, a, rtol=1e-10)
+    np.testing.assert_allclose(blocks(s, 1000, 3).a, a, rtol=1e-10)
+
+
+def test_blocks_bookkeeping_and_orthogonal_columns():
+    s = sys64(150, 30, 4)
+    o = blocks(s, 7, 5, want_e=True)
+    X = s.dense_f64()
+    np.testing.assert_allclose(o.e, s.y - X @ o.a, rtol=0, atol=1e-11 * np.linalg.norm(s.y))
+    # orthogonal columns: every block step is exact, one sweep reaches X^T y ⊘ d for any thr
+    g = np.random.default_rng(5)
+    Q, _ = np.linalg.qr(g.standard_normal((80, 10)))
+    Q = Q * np.linspace(1, 3, 10)
+    y = g.standard_normal(80)
+    Xs = np.ascontiguousarray(Q.T)
+    for thr in (1, 3, 10):
+        r = oracle.solve_blocks(Xs, y, m=80, n=10, thr=thr, dtype="f64", tol=0, max_sweeps=1,
+                                stop="none")
+        np.testing.assert_allclose(r.a, (Q.T @ y) / (Q * Q).sum(axis=0), rtol=1e-12)
+
+
+# ---------------- Algorithm 3 ----------------
+
+def test_selection_minimises_E_by_its_closed_form():
+    """E_j = ||e - X_j da_j||^2 = ||e||^2 - <X_j,e>^2 / <X_j,X_j>: the oracle's
+    literal argmin over E must be the argmax of the closed form at every step,
+    the chosen column is orthogonal to the new residual, and ||e|| never grows."""
+    s = sys64(90, 25, 6)
+    X = s.dense_f64()
+    F = 12
+    sel, a, hist = oracle.select(s.X, s.y, m=s.m, n=s.n, F=F, dtype="f64")
+    e = s.y.copy()
+    d = (X * X).sum(axis=0)
+    aa = np.zeros(s.n)
+    for f in range(F):
+        c = X.T @ e
+        score = c * c / d
+        j = int(np.argmax(score))
+        assert sel[f] == j
+        aa[j] += c[j] / d[j]
+        e = e - X[:, j] * (c[j] / d[j])
+        assert abs(X[:, j] @ e) <= 1e-10 * np.linalg.norm(X[:, j]) * np.linalg.norm(e) + 1e-14
+        assert hist[f + 1] <= hist[f] + 1e-15
+    np.testing.assert_allclose(a, aa, rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(s.y - X @ a, e, atol=1e-12)
+
+
+def test_orthogonal_features_are_selected_by_correlation():
+    g = np.random.default_rng(7)
+    Q, _ = np.linalg.qr(g.standard_normal((60, 12)))
+    Q = Q * g.uniform(0.5, 2.0, 12)
+    y = g.standard_normal(60)
+    Xs = np.ascontiguousarray(Q.T)
+    sel, a, hist = oracle.select(Xs, y, m=60, n=12, F=12, dtype="f64")
+    c = Q.T @ y
+    d = (Q * Q).sum(axis=0)
+    np.testing.assert_array_equal(sel, np.argsort(-(c * c / d), kind="stable"))
+    np.testing.assert_allclose(a, c / d, rtol=1e-12)
+    # all features selected: the residual is y's component outside the span
+    P = Q @ np.linalg.solve(Q.T @ Q, Q.T @ y)
+    assert hist[-1] == pytest.approx(np.linalg.norm(y - P) / np.linalg.norm(y), rel=1e-10)
+
+
+def test_planted_support_is_found_first():
+    g = np.random.default_rng(8)
+    m, n = 400, 60
+    X = g.standard_normal((m, n))
+    S = [5, 17, 33, 48]
+    y = X[:, S] @ np.array([3.0, -2.5, 2.0, -1.5])
+    Xs = np.ascontiguousarray(X.T)
+    sel, a, hist = oracle.select(Xs, y, m=m, n=n, F=4, dtype="f64")
+    assert sorted(sel.tolist()) == S
+    assert hist[-1] < 0.2
+
+
+def test_reselection_accumulates_and_keeps_the_bookkeeping():
+    """Correlated columns make the greedy step come back to a chosen column; the
+    update a_j <- a_j + da_j keeps e = y - X·a (the printed assignment agrees with
+    it for a column chosen the first time, where a_j = 0)."""
+    g = np.random.default_rng(9)
+    base = g.standard_normal(50)
+    X = np.stack([base + 0.3 * g.standard_normal(50) for _ in range(4)], axis=1)
+    y = X @ np.array([1.0, 1.0, -0.5, 0.7])
+    Xs = np.ascontiguousarray(X.T)
+    sel, a, hist = oracle.select(Xs, y, m=50, n=4, F=20, dtype="f64")
+    assert len(set(sel.tolist())) < len(sel)  # some column was chosen more than once
+    e = y - X @ a
+    assert np.linalg.norm(e) / np.linalg.norm(y) == pytest.approx(hist[-1], rel=1e-9)
+    assert np.all(np.diff(hist) <= 1e-15)
