@@ -146,6 +146,40 @@ int hpscd_solve(hpscd_ctx* ctx, const void* X, int dtype, int layout, int64_t m,
                 int64_t ld, const float* y, float* a, int a_is_guess, const hpscd_opts* opts,
                 double* hist, int64_t* sweeps_done, double* final_rel_res);
 
+/*
+ * Algorithm 2 (HPSCDP, Sec. 7): the sweep of hpscd_solve with the columns taken
+ * in blocks of thr consecutive columns (the last block holds the n mod thr
+ * remaining ones); every column of a block takes its step
+ * da_k = <X_k, e> / <X_k, X_k> against the SAME residual, then
+ * e <- e - X_block·da_block.  thr = 1 is Algorithm 1, thr >= n a Jacobi
+ * iteration; the paper finds convergence for thr around n/10, which is not
+ * guaranteed in general.  Column-major X only (n <= 512); other arguments,
+ * results and errors as hpscd_solve (INVALID_ARG for thr < 1).
+ */
+int hpscd_solve_blocks(hpscd_ctx* ctx, const void* X, int dtype, int64_t m, int64_t n, int64_t ld,
+                       const float* y, float* a, int a_is_guess, int64_t thr,
+                       const hpscd_opts* opts, double* hist, int64_t* sweeps_done,
+                       double* final_rel_res);
+
+/*
+ * Algorithm 3 (HPSCDF, Sec. 8): greedy feature selection.  From a = 0, e = y,
+ * each step forms da = (X^T e) ⊘ diag(X^T X) for every column, takes the column
+ * jhat of least error E_j = sum_i (e_i - X_ij·da_j)^2 (lowest j on ties), and
+ * adds it: a_jhat <- a_jhat + da_jhat, e <- e - X_jhat·da_jhat.  One step costs
+ * one streaming pass over X.  opts->max_sweeps is the number of steps F; the
+ * stopping rules apply per step on hist (REL_CHANGE stops once the errors stop
+ * decreasing, the paper's while-loop variant); refresh_every must be 0.
+ *   sel        HOST int64[max_sweeps]: the column chosen at each step (a column
+ *              may be chosen again; the selected set is the distinct entries).
+ *   a          DEVICE float[n], out: the coefficients (0 for unselected columns).
+ *   hist       HOST double[max_sweeps + 1] or NULL: ||e|| / ||y|| after each step.
+ *   steps_done, final_rel_res: HOST, may be NULL.
+ * Column-major X (m >= 1, 1 <= n <= 512).  Errors as hpscd_solve.
+ */
+int hpscd_select(hpscd_ctx* ctx, const void* X, int dtype, int64_t m, int64_t n, int64_t ld,
+                 const float* y, float* a, const hpscd_opts* opts, int64_t* sel, double* hist,
+                 int64_t* steps_done, double* final_rel_res);
+
 /* Same as hpscd_solve but X, y and a are HOST pointers: the call copies X and y
  * to the device workspace, solves, and copies a back (an end-to-end call). */
 int hpscd_solve_host(hpscd_ctx* ctx, const void* X, int dtype, int layout, int64_t m,

@@ -85,6 +85,16 @@ SIGNATURES = {
                           ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(Opts), ctypes.c_void_p,
                           ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)],
                          ctypes.c_int),
+    "hpscd_solve_blocks": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int64,
+                            ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                            ctypes.c_int, ctypes.c_int64, ctypes.POINTER(Opts), ctypes.c_void_p,
+                            ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)],
+                           ctypes.c_int),
+    "hpscd_select": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int64,
+                      ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                      ctypes.POINTER(Opts), ctypes.c_void_p, ctypes.c_void_p,
+                      ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)],
+                     ctypes.c_int),
     "hpscd_last_timing": ([ctypes.c_void_p, ctypes.POINTER(Timing)], ctypes.c_int),
     "hpscd_gram": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_int64,
                     ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int], ctypes.c_int),
@@ -333,6 +343,47 @@ class Context:
                                    hist.ctypes.data_as(ctypes.c_void_p), ctypes.byref(sw),
                                    ctypes.byref(rr))
         return self._finish(rc, hist, sw, rr, a)
+
+    def solve_blocks(self, X, y, thr: int, *, tol=1e-6, max_sweeps=1000, stop="rel_res",
+                     a0=None, out=None) -> SolveResult:
+        """Algorithm 2: blocks of thr columns take their steps from one residual."""
+        import torch
+        ptr, dt, lay, m, n, ld = _describe(X)
+        if lay != COL or not X.is_cuda:
+            raise ValueError("solve_blocks needs a column-major CUDA X")
+        a = out if out is not None else torch.empty(n, dtype=torch.float32, device=X.device)
+        if a0 is not None:
+            a.copy_(a0)
+        o = make_opts(tol, max_sweeps, stop)
+        hist = np.full(int(max_sweeps) + 1, np.nan)
+        sw, rr = ctypes.c_int64(0), ctypes.c_double(0.0)
+        self.set_stream(torch.cuda.current_stream(X.device))
+        rc = self._lib.hpscd_solve_blocks(self._h, ctypes.c_void_p(ptr), dt, m, n, ld,
+                                          ctypes.c_void_p(y.data_ptr()), ctypes.c_void_p(a.data_ptr()),
+                                          1 if a0 is not None else 0, int(thr), ctypes.byref(o),
+                                          hist.ctypes.data_as(ctypes.c_void_p), ctypes.byref(sw),
+                                          ctypes.byref(rr))
+        return self._finish(rc, hist, sw, rr, a)
+
+    def select(self, X, y, F: int, *, tol=0.0, stop="none"):
+        """Algorithm 3: F greedy selection steps; returns (SolveResult, chosen column per step)."""
+        import torch
+        ptr, dt, lay, m, n, ld = _describe(X)
+        if lay != COL or not X.is_cuda:
+            raise ValueError("select needs a column-major CUDA X")
+        a = torch.empty(n, dtype=torch.float32, device=X.device)
+        o = make_opts(tol, F, stop)
+        hist = np.full(int(F) + 1, np.nan)
+        sel = np.full(max(int(F), 1), -1, dtype=np.int64)
+        sw, rr = ctypes.c_int64(0), ctypes.c_double(0.0)
+        self.set_stream(torch.cuda.current_stream(X.device))
+        rc = self._lib.hpscd_select(self._h, ctypes.c_void_p(ptr), dt, m, n, ld,
+                                    ctypes.c_void_p(y.data_ptr()), ctypes.c_void_p(a.data_ptr()),
+                                    ctypes.byref(o), sel.ctypes.data_as(ctypes.c_void_p),
+                                    hist.ctypes.data_as(ctypes.c_void_p), ctypes.byref(sw),
+                                    ctypes.byref(rr))
+        res = self._finish(rc, hist, sw, rr, a)
+        return res, sel[: res.sweeps]
 
     def gram(self, X, simt: bool = False):
         """G = X^T X (n×n float32 CUDA tensor) for a column-major CUDA X."""

@@ -30,7 +30,7 @@ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 struct Layout {
   size_t G = 0, Gt = 0, dvec = 0, partial = 0, e = 0, hacc = 0, npart = 0, gw = 0, ypart = 0, hist = 0,
-         ctl = 0;
+         ctl = 0, sel = 0;
   size_t xcopy = 0, ycopy = 0, acopy = 0, total = 0;
 };
 
@@ -102,6 +102,7 @@ int make_plan(const hpscd_ctx* ctx, int dtype, int layout, int64_t m, int64_t n,
   L.ypart = take((size_t)P->grid * sizeof(double));
   L.hist = take((size_t)(o->max_sweeps + 1) * sizeof(double));
   L.ctl = take(sizeof(GridCtl));
+  L.sel = take((size_t)(o->max_sweeps + 1) * sizeof(int64_t));
   if (host_copies) {
     L.xcopy = take((size_t)(n > 0 ? n : 1) * (size_t)ld * esize(dtype));
     L.ycopy = take((size_t)(m > 0 ? m : 1) * sizeof(float));
@@ -327,9 +328,13 @@ int solve_empty_rows(hpscd_ctx* ctx, int64_t n, float* a, int a_is_guess, const 
   return HPSCD_OK;
 }
 
+// The variants of the sweep: Algorithm 1 (thr <= 1, select = 0), Algorithm 2
+// (blocks of thr columns from one residual) and Algorithm 3 (select = 1: one
+// greedily chosen column per pass; sel receives the choices, HOST int64[max_sweeps]).
 int solve_device(hpscd_ctx* ctx, const void* X, int dtype, int layout, int64_t m, int64_t n,
                  int64_t ld, const float* y, float* a, int a_is_guess, const hpscd_opts* o,
-                 double* hist, int64_t* sweeps_done, double* final_rel_res, const Plan& P) {
+                 double* hist, int64_t* sweeps_done, double* final_rel_res, const Plan& P,
+                 int thr = 0, int select = 0, int64_t* sel = nullptr) {
   if (m == 0) return solve_empty_rows(ctx, n, a, a_is_guess, o, hist, sweeps_done, final_rel_res);
   char* ws = static_cast<char*>(ctx->ws);
   const Layout& L = P.L;
@@ -381,6 +386,9 @@ int solve_device(hpscd_ctx* ctx, const void* X, int dtype, int layout, int64_t m
   p.use_tma = use_tma;
   p.timeout_ns = (uint64_t)(ctx->timeout_s * 1e9);
   p.stall_barrier = (o->debug_flags & HPSCD_DEBUG_STALL_BARRIER) ? 1 : 0;
+  p.thr = thr;
+  p.select = select;
+  p.sel_out = select ? reinterpret_cast<int64_t*>(ws + L.sel) : nullptr;
   p.trace = nullptr;
   p.trace_passes = 0;
   if (ctx->trace_passes > 0 && ctx->trace_dev) {
@@ -402,6 +410,11 @@ int solve_device(hpscd_ctx* ctx, const void* X, int dtype, int layout, int64_t m
   const GridCtl c = *ctx->ctl_host;
   if (hist && c.sweeps >= 0 && c.sweeps <= o->max_sweeps) {
     if (cudaMemcpy(hist, p.hist, (size_t)(c.sweeps + 1) * sizeof(double), cudaMemcpyDeviceToHost) !=
+        cudaSuccess)
+      return HPSCD_ERR_CUDA;
+  }
+  if (sel && select && c.sweeps > 0 && c.sweeps <= o->max_sweeps) {
+    if (cudaMemcpy(sel, p.sel_out, (size_t)c.sweeps * sizeof(int64_t), cudaMemcpyDeviceToHost) !=
         cudaSuccess)
       return HPSCD_ERR_CUDA;
   }
@@ -543,6 +556,43 @@ int hpscd_solve(hpscd_ctx* ctx, const void* X, int dtype, int layout, int64_t m,
   if ((rc = ensure_ws(ctx, P.L.total))) return rc;
   return solve_device(ctx, X, dtype, layout, m, n, ld, y, a, a_is_guess, opts, hist, sweeps_done,
                       final_rel_res, P);
+}
+
+int hpscd_solve_blocks(hpscd_ctx* ctx, const void* X, int dtype, int64_t m, int64_t n, int64_t ld,
+                       const float* y, float* a, int a_is_guess, int64_t thr,
+                       const hpscd_opts* opts, double* hist, int64_t* sweeps_done,
+                       double* final_rel_res) {
+  if (!ctx || thr < 1) return HPSCD_ERR_INVALID_ARG;
+  int rc = check_opts(opts);
+  if (rc) return rc;
+  if ((rc = check_shape(dtype, HPSCD_COL_MAJOR, m, n, ld))) return rc;
+  if ((m > 0 && n > 0 && !X) || (m > 0 && !y) || (n > 0 && !a)) return HPSCD_ERR_INVALID_ARG;
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return HPSCD_ERR_CUDA;
+  Plan P;
+  if ((rc = make_plan(ctx, dtype, HPSCD_COL_MAJOR, m, n, ld, opts, false, &P))) return rc;
+  if ((rc = ensure_ws(ctx, P.L.total))) return rc;
+  const int t = thr > n ? (int)(n > 0 ? n : 1) : (int)thr;
+  return solve_device(ctx, X, dtype, HPSCD_COL_MAJOR, m, n, ld, y, a, a_is_guess, opts, hist,
+                      sweeps_done, final_rel_res, P, t, 0, nullptr);
+}
+
+int hpscd_select(hpscd_ctx* ctx, const void* X, int dtype, int64_t m, int64_t n, int64_t ld,
+                 const float* y, float* a, const hpscd_opts* opts, int64_t* sel, double* hist,
+                 int64_t* steps_done, double* final_rel_res) {
+  if (!ctx) return HPSCD_ERR_INVALID_ARG;
+  int rc = check_opts(opts);
+  if (rc) return rc;
+  if ((rc = check_shape(dtype, HPSCD_COL_MAJOR, m, n, ld))) return rc;
+  if (m < 1 || n < 1 || !X || !y || !a || (!sel && opts->max_sweeps > 0)) return HPSCD_ERR_INVALID_ARG;
+  if (opts->refresh_every != 0) return HPSCD_ERR_UNSUPPORTED;
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return HPSCD_ERR_CUDA;
+  Plan P;
+  if ((rc = make_plan(ctx, dtype, HPSCD_COL_MAJOR, m, n, ld, opts, false, &P))) return rc;
+  if ((rc = ensure_ws(ctx, P.L.total))) return rc;
+  return solve_device(ctx, X, dtype, HPSCD_COL_MAJOR, m, n, ld, y, a, 0, opts, hist, steps_done,
+                      final_rel_res, P, 0, 1, sel);
 }
 
 int hpscd_solve_host(hpscd_ctx* ctx, const void* X, int dtype, int layout, int64_t m,

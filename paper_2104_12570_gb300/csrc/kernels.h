@@ -97,6 +97,11 @@ struct TallParams {
   int use_tma;
   uint64_t timeout_ns;
   int stall_barrier;  // test hook: first barrier waits for one arrival too many
+  int thr;            // > 1: Algorithm 2 — columns in blocks of thr take their steps from
+                      // the same residual (no couplings inside a block); <= 1: Algorithm 1
+  int select;         // 1: Algorithm 3 — each pass adds the one column with the largest
+                      // <X_j,e>^2 / <X_j,X_j> (greedy selection) instead of a sweep
+  int64_t* sel_out;   // Algorithm 3: column chosen after pass p, [max_sweeps]
   unsigned long long* trace;  // optional: per-pass phase timestamps (see hpscd_trace)
   int trace_passes;           // capacity of trace in passes
 };

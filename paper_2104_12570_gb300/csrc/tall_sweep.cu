@@ -73,14 +73,26 @@ __device__ __forceinline__ void load_seg32(const float* __restrict__ src, float 
 // finished block to it, loading its G~ segment for the next block right after
 // using the current one, so the load overlaps the next block's walk.  r (in:
 // g ⊘ d, overwritten) and da are shared arrays of length npad.
+// With thr > 1 (Algorithm 2) the couplings of a row to the columns of its own
+// block of thr columns are dropped: row t keeps columns l < (t / thr)·thr.
+__device__ __forceinline__ void mask_seg32(float (&g)[32], int t, int b0, int thr) {
+  if (thr <= 1) return;
+  const int lim = (t / thr) * thr - b0;
+#pragma unroll
+  for (int k = 0; k < 32; ++k) g[k] = (k < lim) ? g[k] : 0.f;
+}
+
 __device__ void forward_substitution(const float* __restrict__ Gt, int ldG, int n, int npad,
-                                     float* r, float* da, const float* diag_s) {
+                                     float* r, float* da, const float* diag_s, int thr) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   for (int c = n + tid; c < npad; c += NT) da[c] = 0.f;
   if (n <= 0) { named_sync(NT); return; }
   const int nb = (n + 31) / 32;
   float seg[32];
-  if (tid >= 32 && tid < n) load_seg32(Gt + (int64_t)tid * ldG, seg);
+  if (tid >= 32 && tid < n) {
+    load_seg32(Gt + (int64_t)tid * ldG, seg);
+    mask_seg32(seg, tid, 0, thr);
+  }
   named_sync(NT);  // r (written by the caller) is visible
   for (int b = 0; b < nb; ++b) {
     const int b0 = 32 * b;
@@ -104,10 +116,44 @@ __device__ void forward_substitution(const float* __restrict__ Gt, int ldG, int 
 #pragma unroll
       for (int k = 0; k < 32; ++k) acc = fmaf(seg[k], da[b0 + k], acc);
       r[tid] -= acc;
-      if (tid >= b0 + 64) load_seg32(Gt + (int64_t)tid * ldG + b0 + 32, seg);
+      if (tid >= b0 + 64) {
+        load_seg32(Gt + (int64_t)tid * ldG + b0 + 32, seg);
+        mask_seg32(seg, tid, b0 + 32, thr);
+      }
     }
     named_sync(NT);  // r of block b+1 final
   }
+}
+
+// Algorithm 3's step (Sec. 8): with r = (X^T e) ⊘ d (every column's da against
+// the same residual), E_j = ||e - X_j da_j||^2 = ||e||^2 - r_j^2 d_j, so the
+// column of least error is the one of largest r_j^2 d_j (ties: lowest j).  The
+// step adds only that column: da = r_jhat at jhat, 0 elsewhere.  Returns jhat.
+__device__ int select_step(int n, int npad, const float* r, const float* d, float* da,
+                           float* fscr, int* iscr) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  float best = -1.f;
+  int bj = 0x7fffffff;
+  for (int c = tid; c < n; c += NT) {
+    const float sc = d[c] > 0.f ? r[c] * r[c] * d[c] : 0.f;
+    if (sc > best || (sc == best && c < bj)) { best = sc; bj = c; }
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const float ob = __shfl_xor_sync(FULL_MASK, best, off);
+    const int oj = __shfl_xor_sync(FULL_MASK, bj, off);
+    if (ob > best || (ob == best && oj < bj)) { best = ob; bj = oj; }
+  }
+  if (lane == 0) { fscr[warp] = best; iscr[warp] = bj; }
+  named_sync(NT);
+  best = fscr[0];
+  bj = iscr[0];
+  for (int w = 1; w < NW; ++w)
+    if (fscr[w] > best || (fscr[w] == best && iscr[w] < bj)) { best = fscr[w]; bj = iscr[w]; }
+  if (bj >= n) bj = 0;
+  for (int c = tid; c < npad; c += NT) da[c] = (c == bj && n > 0) ? r[c] : 0.f;
+  named_sync(NT);
+  return bj;
 }
 
 // Error-free product and sum (Ogita, Rump, Oishi, "Accurate sum and dot
@@ -243,7 +289,9 @@ __global__ void __launch_bounds__(NT, 1)
     int i = 1;
     while ((i * (i + 1)) / 2 <= q) ++i;
     const int k = q - (i * (i - 1)) / 2;
-    diag_s[idx] = (32 * b + i < n) ? p.Gt[(int64_t)(32 * b + i) * p.ldG + 32 * b + k] : 0.f;
+    // Algorithm 2 drops the couplings inside a block of thr columns
+    const bool keep = p.thr <= 1 || 32 * b + k < ((32 * b + i) / p.thr) * p.thr;
+    diag_s[idx] = (32 * b + i < n && keep) ? p.Gt[(int64_t)(32 * b + i) * p.ldG + 32 * b + k] : 0.f;
   }
   __syncthreads();
 
@@ -503,7 +551,13 @@ __global__ void __launch_bounds__(NT, 1)
     r_prev = rel;
     if (stop) break;
 
-    forward_substitution(p.Gt, p.ldG, n, NPAD, rvec, da_s, diag_s);
+    if (p.select) {
+      // scratch for the argmax: the row-sum buffer is free between passes
+      const int jhat = select_step(n, NPAD, rvec, dd_s, da_s, red_hi, reinterpret_cast<int*>(red_lo));
+      if (blockIdx.x == 0 && tid == 0 && p.sel_out) p.sel_out[pass] = jhat;
+    } else {
+      forward_substitution(p.Gt, p.ldG, n, NPAD, rvec, da_s, diag_s, p.thr);
+    }
     stamp(pass, 5);
     const int64_t nx = pass + 1;
     const bool next_refresh = p.refresh_every > 0 && nx % p.refresh_every == 0;
