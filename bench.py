@@ -269,6 +269,45 @@ def profile_small(hp, synth):
                       "x_bytes": int((m * n * 4).sum())}), flush=True)
 
 
+def next_algorithms(hp, synth, ctx, X, y, s, reps=3):
+    """Algorithm 2 (blocks of thr = n/10 columns from one residual, the paper's
+    setting) against Algorithm 1 on the benchmark system, both to the relative
+    change of ||e|| < 1e-7; and Algorithm 3 (greedy selection) for 32 steps."""
+    import torch
+    out = {}
+    esz = 4
+    for name, fn in (("alg1_sweep", lambda: ctx.solve(X, y, tol=TOL, max_sweeps=MAX_SWEEPS, stop=STOP)),
+                     ("alg2_blocks_thr25", lambda: ctx.solve_blocks(X, y, max(1, s.n // 10), tol=TOL,
+                                                                    max_sweeps=MAX_SWEEPS, stop=STOP))):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            r = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        out[name] = {"ms_to_tol": ms, "sweeps": int(r.sweeps), "rel_res": float(r.rel_res),
+                     "sweep_kernel_GBps": sweep_kernel_bytes(s.m, s.n, esz, r.timing["passes"])
+                     / (r.timing["sweep_ms"] * 1e-3) / 1e9}
+    F = 32
+    ctx.select(X, y, F)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        r, sel = ctx.select(X, y, F)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    out["alg3_select_32"] = {"ms": ms, "ms_per_step": r.timing["sweep_ms"] / (F + 1),
+                             "sweep_kernel_GBps": sweep_kernel_bytes(s.m, s.n, esz, r.timing["passes"])
+                             / (r.timing["sweep_ms"] * 1e-3) / 1e9,
+                             "rel_res_after": float(r.rel_res), "first_selected": sel[:8].tolist()}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -279,6 +318,8 @@ def main():
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the bfloat16-vs-float32 comparison on the 4,000,000 x 512 system")
+    ap.add_argument("--no-next", action="store_true",
+                    help="skip Algorithm 2 / Algorithm 3 on the benchmark system")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the batched cold-vs-learned-warm-start comparison (4096 RBF systems)")
     ap.add_argument("--rows", type=int, default=0,
@@ -392,6 +433,8 @@ def main():
         }
         if not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline_leg(s)
+        if not args.no_next and not args.rows:
+            out["next_algorithms"] = next_algorithms(hp, synth, ctx, X, y, s)
         if not args.no_compare and not args.rows:
             del X
             torch.cuda.empty_cache()
