@@ -82,23 +82,60 @@ __device__ __forceinline__ void mask_seg32(float (&g)[32], int t, int b0, int th
   for (int k = 0; k < 32; ++k) g[k] = (k < lim) ? g[k] : 0.f;
 }
 
-__device__ void forward_substitution(const float* __restrict__ Gt, int ldG, int n, int npad,
-                                     float* r, float* da, const float* diag_s, int thr) {
+__device__ __forceinline__ int ld_acquire_cta(const int* p) {
+  int v;
+  asm volatile("ld.acquire.cta.shared::cta.s32 %0, [%1];" : "=r"(v) : "r"(smem_u32(p)) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_cta(int* p, int v) {
+  asm volatile("st.release.cta.shared::cta.s32 [%0], %1;" ::"r"(smem_u32(p)), "r"(v) : "memory");
+}
+// Lane 0 waits (bounded) until *flag >= want, then the warp proceeds together.
+// Returns false when the wait gave up.
+__device__ __forceinline__ bool warp_wait_flag(const int* flag, int want, uint64_t timeout_ns) {
+  int ok = 1;
+  if ((threadIdx.x & 31) == 0) {
+    if (ld_acquire_cta(flag) < want) {
+      const uint64_t t0 = global_timer_ns();
+      for (uint32_t it = 0;; ++it) {
+        if (ld_acquire_cta(flag) >= want) break;
+        if ((it & 63) == 63 && global_timer_ns() - t0 > timeout_ns) { ok = 0; break; }
+      }
+    }
+  }
+  ok = __shfl_sync(FULL_MASK, ok, 0);
+  __syncwarp();
+  return ok != 0;
+}
+
+// Forward substitution of one sweep (see the file comment):
+//   da_j = r_j - sum_{l<j} G~_jl da_l, j = 0..n-1 (r = g ⊘ d; da_j = 0 when d_j = 0,
+//   where row j of G~ is zero).
+// Dataflow over blocks of 32 columns, no CTA barrier between blocks: warp w
+// owns rows 32w..32w+31.  Warp 0 solves block c (shuffles along the block's
+// strictly lower triangle, staged in diag_s) as soon as warp c has applied
+// blocks 0..c-1 to its rows, then publishes da of the block; every warp w
+// applies each published block b < w to its rows (its G~ segment of block b+1
+// loaded while it waits) and, after block w-1, signals warp 0.  The critical
+// path is one block's walk plus one hand-off per block.  With thr > 1
+// (Algorithm 2) the couplings inside a block of thr columns are masked.
+// flags: [0] blocks solved, [1 + w] warp w's rows ready; r (in: g ⊘ d) and da
+// are shared arrays of length npad.  Returns false when a wait gave up.
+__device__ bool forward_substitution(const float* __restrict__ Gt, int ldG, int n, int npad,
+                                     float* r, float* da, const float* diag_s, int thr,
+                                     int* flags, uint64_t timeout_ns) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   for (int c = n + tid; c < npad; c += NT) da[c] = 0.f;
-  if (n <= 0) { named_sync(NT); return; }
+  if (tid <= NW) flags[tid] = 0;
+  named_sync(NT);  // r (written by the caller) and the cleared flags are visible
+  if (n <= 0) return true;
   const int nb = (n + 31) / 32;
-  float seg[32];
-  if (tid >= 32 && tid < n) {
-    load_seg32(Gt + (int64_t)tid * ldG, seg);
-    mask_seg32(seg, tid, 0, thr);
-  }
-  named_sync(NT);  // r (written by the caller) is visible
-  for (int b = 0; b < nb; ++b) {
-    const int b0 = 32 * b;
-    if (warp == 0) {
-      const int i = b0 + lane;
-      // warp 0 never owns a trailing row: its seg holds the diagonal block's row
+  bool ok = true;
+  if (warp == 0) {
+    for (int b = 0; b < nb && ok; ++b) {
+      if (b > 0 && !warp_wait_flag(&flags[1 + b], 1, timeout_ns)) { ok = false; break; }
+      const int i = 32 * b + lane;
+      float seg[32];
       const float* dl = diag_s + b * DIAG_PACK + (lane * (lane - 1)) / 2;
 #pragma unroll
       for (int k = 0; k < 32; ++k) seg[k] = (k < lane) ? dl[k] : 0.f;
@@ -109,20 +146,37 @@ __device__ void forward_substitution(const float* __restrict__ Gt, int ldG, int 
         if (lane > k) ri = fmaf(-seg[k], q, ri);
       }
       if (i < npad) da[i] = (i < n) ? ri : 0.f;
+      __syncwarp();
+      if (lane == 0) st_release_cta(&flags[0], b + 1);
     }
-    named_sync(NT);  // da of block b visible
-    if (tid >= 32 && tid < n && tid >= b0 + 32) {
-      float acc = 0.f;
+  } else if (warp < nb) {
+    const int t = tid;
+    float rt = (t < n) ? r[t] : 0.f;
+    float seg[32];
+    load_seg32(Gt + (int64_t)(t < n ? t : 0) * ldG, seg);
+    mask_seg32(seg, t, 0, thr);
+    for (int b = 0; b < warp; ++b) {
+      if (!warp_wait_flag(&flags[0], b + 1, timeout_ns)) { ok = false; break; }
+      const float* dab = da + 32 * b;
+      float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
 #pragma unroll
-      for (int k = 0; k < 32; ++k) acc = fmaf(seg[k], da[b0 + k], acc);
-      r[tid] -= acc;
-      if (tid >= b0 + 64) {
-        load_seg32(Gt + (int64_t)tid * ldG + b0 + 32, seg);
-        mask_seg32(seg, tid, b0 + 32, thr);
+      for (int k = 0; k < 32; k += 4) {
+        a0 = fmaf(seg[k], dab[k], a0);
+        a1 = fmaf(seg[k + 1], dab[k + 1], a1);
+        a2 = fmaf(seg[k + 2], dab[k + 2], a2);
+        a3 = fmaf(seg[k + 3], dab[k + 3], a3);
+      }
+      rt -= (a0 + a1) + (a2 + a3);
+      if (b + 1 < warp) {
+        load_seg32(Gt + (int64_t)(t < n ? t : 0) * ldG + 32 * (b + 1), seg);
+        mask_seg32(seg, t, 32 * (b + 1), thr);
       }
     }
-    named_sync(NT);  // r of block b+1 final
+    if (t < npad) r[t] = rt;
+    __syncwarp();
+    if (lane == 0) st_release_cta(&flags[1 + warp], 1);
   }
+  return named_sync_or(NT, ok ? 0 : 1) == 0;  // da complete (or a wait gave up)
 }
 
 // Algorithm 3's step (Sec. 8): with r = (X^T e) ⊘ d (every column's da against
@@ -556,7 +610,12 @@ __global__ void __launch_bounds__(NT, 1)
       const int jhat = select_step(n, NPAD, rvec, dd_s, da_s, red_hi, reinterpret_cast<int*>(red_lo));
       if (blockIdx.x == 0 && tid == 0 && p.sel_out) p.sel_out[pass] = jhat;
     } else {
-      forward_substitution(p.Gt, p.ldG, n, NPAD, rvec, da_s, diag_s, p.thr);
+      // the row-sum buffers are free between passes: flags of the substitution
+      if (!forward_substitution(p.Gt, p.ldG, n, NPAD, rvec, da_s, diag_s, p.thr,
+                                reinterpret_cast<int*>(red_lo), p.timeout_ns)) {
+        err = DEV_TIMEOUT_BARRIER;
+        break;
+      }
     }
     stamp(pass, 5);
     const int64_t nx = pass + 1;

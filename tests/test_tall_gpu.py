@@ -79,7 +79,9 @@ def test_equal_sweeps_matches_oracle(ctx, m, n):
         o = oracle_same(s, sweeps)
         assert r.sweeps == sweeps
         assert rel(r.a.cpu().numpy(), o.a) <= RTOL_F32, (sweeps, rel(r.a.cpu().numpy(), o.a))
-        np.testing.assert_allclose(r.hist, o.hist, rtol=1e-5)
+        # ||e||/||y|| from a float32 residual carries ~1e-7 absolute error: wide
+        # (consistent) systems decay to that floor, where only an absolute bound holds
+        np.testing.assert_allclose(r.hist, o.hist, rtol=1e-5, atol=1e-6)
 
 
 def test_converges_on_consistent_tall(ctx):
