@@ -25,7 +25,7 @@ namespace hpscd {
 
 namespace {
 
-constexpr int GT_THREADS = 128;
+constexpr int GT_THREADS = 192;  // 6 warps: producer, MMA issuer, 4 workers
 constexpr int BLK = 128;                 // columns per block (MMA M)
 constexpr int ATOM_BYTES = BLK * 128;    // one 128-column block × 128 bytes of K = 16 KB
 constexpr int TMEM_COLS = 512;
@@ -69,6 +69,10 @@ __device__ __forceinline__ void mma_issue(uint32_t d_tmem, uint64_t adesc, uint6
   }
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
   asm volatile(
       "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -99,6 +103,19 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// Warp roles: warp 0 lane 0 feeds the stages by TMA; warp 1 lane 0 issues
+// the MMAs; warps 2..5 (the workers, one per tensor-memory lane quarter) sum
+// the squares of every column (the diagonal), split float32 tiles into tf32
+// hi/lo, and run the epilogue.  Per stage s and K block kb:
+//   full[s]  : TMA bytes landed                 (producer -> workers, MMA for bf16)
+//   ready[s] : the workers are done with the tile (workers -> MMA issuer)
+//   empty[s] : the MMAs that read the tile completed (tcgen05.commit -> producer)
+// so the split of block kb+1 and the copies of later blocks overlap the MMAs
+// of block kb.  Every wait is bounded; a wait that gives up raises s_fail, which
+// every role polls, and the CTA drains its copies and frees tensor memory.
+constexpr int GT_WORK_WARP0 = 2;
+constexpr int GT_WORKERS = 128;
+
 template <bool TF32>
 __global__ void __launch_bounds__(GT_THREADS, 1)
     gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const GramTCParams p) {
@@ -114,7 +131,8 @@ __global__ void __launch_bounds__(GT_THREADS, 1)
   const int stage_bytes = stage_raw * (TF32 ? 2 : 1);
   const int nst = p.nstages;
   uint64_t* full = reinterpret_cast<uint64_t*>(base + (size_t)nst * stage_bytes);
-  uint64_t* empty = full + 8;
+  uint64_t* ready = full + 8;
+  uint64_t* empty = ready + 8;
   uint64_t* done = empty + 8;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
   int* s_fail = reinterpret_cast<int*>(tmem_slot + 1);
@@ -125,7 +143,13 @@ __global__ void __launch_bounds__(GT_THREADS, 1)
   const int64_t nkb = r1 > r0 ? (r1 - r0 + KB - 1) / KB : 0;
 
   if (tid == 0) {
-    for (int s = 0; s < nst; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
+    for (int s = 0; s < nst; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&ready[s], GT_WORKERS / 32);
+      // float32: the split is done before the MMAs read the tile, so only the
+      // MMA commit frees it; bfloat16: the workers read it alongside the MMAs
+      mbar_init(&empty[s], TF32 ? 1 : 1 + GT_WORKERS / 32);
+    }
     mbar_init(done, 1);
     *s_fail = 0;
     fence_mbar_init();
@@ -141,51 +165,129 @@ __global__ void __launch_bounds__(GT_THREADS, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-
-  int64_t issued = 0;  // thread 0: K blocks whose copies were issued
-  auto issue = [&](int64_t kb) {
-    const int s = (int)(kb % nst);
-    unsigned char* dst = base + (size_t)s * stage_bytes;
-    mbar_arrive_expect_tx(&full[s], (uint32_t)stage_raw);
-    for (int b = 0; b < nload; ++b)
-      tma_load_2d(dst + b * ATOM_BYTES, &tmap, &full[s], (int32_t)(r0 + kb * KB),
-                  p.grp.load_blk[g][b] * BLK);
+  volatile int* vfail = s_fail;
+  auto fail_now = [&]() {
+    *vfail = 1;
+    atomicExch(p.err, 1);
   };
-  if (tid == 0)
-    while (issued < nst && issued < nkb) issue(issued++);
+  auto wait = [&](uint64_t* bar, uint32_t parity) -> bool {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_timer_ns();
+    for (uint32_t it = 1;; ++it) {
+      if (mbar_try_wait(bar, parity)) return true;
+      if ((it & 63) == 0) {
+        if (*vfail) return false;
+        if (global_timer_ns() - t0 > p.timeout_ns) { fail_now(); return false; }
+      }
+    }
+  };
 
-  bool ok = true;
-  int64_t consumed = 0;  // K blocks whose copies every thread has seen land
-  // <X_j, X_j> on the CUDA cores: thread t sums the squares of the 16-byte
-  // chunks t + 128q of every stage, i.e. of column t/8 + 16q (the swizzle only
-  // permutes chunks within a column's 128 bytes); float32 per 64 K blocks,
-  // float64 across them.  The tensor-core accumulation drifts on long sums
-  // of positive terms, so these replace its diagonal.
-  constexpr int MAXQ = 32;  // 16-byte chunks per thread per stage (nload <= 4)
-  float dsq[MAXQ];
-  double dsq64[MAXQ];
+  // ---------------- producer: warp 0, lane 0 ----------------
+  if (warp == 0) {
+    if (lane == 0) {
+      int64_t kb = 0;
+      for (; kb < nkb; ++kb) {
+        const int s = (int)(kb % nst);
+        if (kb >= nst && !wait(&empty[s], (uint32_t)(((kb / nst) - 1) & 1))) break;
+        unsigned char* dst = base + (size_t)s * stage_bytes;
+        mbar_arrive_expect_tx(&full[s], (uint32_t)stage_raw);
+        for (int b = 0; b < nload; ++b)
+          tma_load_2d(dst + b * ATOM_BYTES, &tmap, &full[s], (int32_t)(r0 + kb * KB),
+                      p.grp.load_blk[g][b] * BLK);
+      }
+      // the copies issued land before the CTA may retire
+      for (int64_t k = kb - nst > 0 ? kb - nst : 0; k < kb; ++k) {
+        const int s = (int)(k % nst);
+        for (uint32_t it = 0; !mbar_try_wait(&full[s], (uint32_t)((k / nst) & 1)); ++it)
+          if (it > (1u << 26)) break;
+      }
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    // ---------------- MMA issuer: warp 1, lane 0 ----------------
+    if (lane == 0) {
+      const uint32_t idesc = make_idesc(FMT, BLK);
+      for (int64_t kb = 0; kb < nkb; ++kb) {
+        const int s = (int)(kb % nst);
+        const uint32_t par = (uint32_t)((kb / nst) & 1);
+        if (TF32 ? !wait(&ready[s], par) : !wait(&full[s], par)) break;
+        tc_fence_after();
+        const uint32_t a_base = smem_u32(base + (size_t)s * stage_bytes);
+        for (int t = 0; t < ntile; ++t) {
+          const uint32_t d_tmem = tmem + (uint32_t)(BLK * t);
+          const int si = p.grp.tile_si[g][t], sj = p.grp.tile_sj[g][t];
 #pragma unroll
-  for (int q = 0; q < MAXQ; ++q) { dsq[q] = 0.f; dsq64[q] = 0.0; }
-  const int nq = 8 * nload;
-  for (int64_t kb = 0; kb < nkb; ++kb) {
-    const int s = (int)(kb % nst);
-    unsigned char* st = base + (size_t)s * stage_bytes;
-    if (ok && !mbar_wait_bounded(&full[s], (uint32_t)((kb / nst) & 1), p.timeout_ns)) ok = false;
-    if (ok) {
-      const uint4* raw4 = reinterpret_cast<const uint4*>(st);
+          for (int k = 0; k < 4; ++k) {
+            const uint32_t koff = k * 32;
+            const uint64_t ah = make_sw128_desc(a_base + si * ATOM_BYTES + koff);
+            const uint64_t bh = make_sw128_desc(a_base + sj * ATOM_BYTES + koff);
+            const uint32_t acc = (kb > 0 || k > 0) ? 1u : 0u;
+            mma_issue<TF32>(d_tmem, ah, bh, idesc, acc);
+            if constexpr (TF32) {
+              const uint64_t al = make_sw128_desc(a_base + stage_raw + si * ATOM_BYTES + koff);
+              const uint64_t bl = make_sw128_desc(a_base + stage_raw + sj * ATOM_BYTES + koff);
+              mma_issue<TF32>(d_tmem, ah, bl, idesc, 1u);
+              mma_issue<TF32>(d_tmem, al, bh, idesc, 1u);
+            }
+          }
+        }
+        mma_commit(&empty[s]);
+      }
+      // every MMA issued completes on `done` (also after a failure, before TMEM is freed)
+      mma_commit(done);
+    }
+    __syncwarp();
+  }
+
+  // ---------------- workers: warps 2..5 ----------------
+  // <X_j, X_j> on the CUDA cores: worker w sums the squares of the 16-byte
+  // chunks w + 128q of every stage, i.e. of column w/8 + 16q (the swizzle only
+  // permutes chunks within a column's 128 bytes); float32 per 64 K blocks,
+  // float64 across them.  The tensor-core accumulation drifts on long sums of
+  // positive terms, so these replace its diagonal.
+  constexpr int MAXQ = 32;  // 16-byte chunks per worker per stage (nload <= 4)
+  const int wt = tid - GT_WORK_WARP0 * 32;
+  const bool worker = warp >= GT_WORK_WARP0 && warp < GT_WORK_WARP0 + GT_WORKERS / 32;
+  double dsq64[MAXQ];
+  if (worker) {
+    float dsq[MAXQ];
+#pragma unroll
+    for (int q = 0; q < MAXQ; ++q) { dsq[q] = 0.f; dsq64[q] = 0.0; }
+    const int nq = 8 * nload;
+    for (int64_t kb = 0; kb < nkb; ++kb) {
+      const int s = (int)(kb % nst);
+      const uint32_t par = (uint32_t)((kb / nst) & 1);
+      int ok = 1;
+      if (lane == 0) ok = wait(&full[s], par) ? 1 : 0;
+      ok = __shfl_sync(FULL_MASK, ok, 0);
+      __syncwarp();
+      if (!ok) break;
+      unsigned char* st = base + (size_t)s * stage_bytes;
+      uint4* raw4 = reinterpret_cast<uint4*>(st);
+      uint4* lo4 = reinterpret_cast<uint4*>(st + stage_raw);
 #pragma unroll
       for (int q = 0; q < MAXQ; ++q) {
         if (q < nq) {
-          const uint4 x = raw4[tid + GT_THREADS * q];
+          const uint4 x = raw4[wt + GT_WORKERS * q];
           if constexpr (TF32) {
             const float a0 = __uint_as_float(x.x), a1 = __uint_as_float(x.y);
             const float a2 = __uint_as_float(x.z), a3 = __uint_as_float(x.w);
             dsq[q] = fmaf(a0, a0, fmaf(a1, a1, fmaf(a2, a2, fmaf(a3, a3, dsq[q]))));
+            // split in place: hi (tf32-exact) over x, lo = x - hi in the second half
+            uint4 h, l;
+            h.x = x.x & 0xFFFFE000u; h.y = x.y & 0xFFFFE000u;
+            h.z = x.z & 0xFFFFE000u; h.w = x.w & 0xFFFFE000u;
+            l.x = __float_as_uint(a0 - __uint_as_float(h.x));
+            l.y = __float_as_uint(a1 - __uint_as_float(h.y));
+            l.z = __float_as_uint(a2 - __uint_as_float(h.z));
+            l.w = __float_as_uint(a3 - __uint_as_float(h.w));
+            raw4[wt + GT_WORKERS * q] = h;
+            lo4[wt + GT_WORKERS * q] = l;
           } else {
-            const uint32_t w[4] = {x.x, x.y, x.z, x.w};
+            const uint32_t w4[4] = {x.x, x.y, x.z, x.w};
 #pragma unroll
             for (int h = 0; h < 4; ++h) {
-              const float lo16 = __uint_as_float(w[h] << 16), hi16 = __uint_as_float(w[h] & 0xffff0000u);
+              const float lo16 = __uint_as_float(w4[h] << 16), hi16 = __uint_as_float(w4[h] & 0xffff0000u);
               dsq[q] = fmaf(lo16, lo16, fmaf(hi16, hi16, dsq[q]));
             }
           }
@@ -195,86 +297,50 @@ __global__ void __launch_bounds__(GT_THREADS, 1)
 #pragma unroll
         for (int q = 0; q < MAXQ; ++q) { dsq64[q] += (double)dsq[q]; dsq[q] = 0.f; }
       }
-    }
-    if constexpr (TF32) {
-      // split in place: hi (tf32-exact) over x, lo = x - hi in the second half
-      if (ok) {
-        uint4* raw = reinterpret_cast<uint4*>(st);
-        uint4* lo = reinterpret_cast<uint4*>(st + stage_raw);
-        for (int idx = tid; idx < stage_raw / 16; idx += GT_THREADS) {
-          const uint4 x = raw[idx];
-          uint4 h, l;
-          h.x = x.x & 0xFFFFE000u; h.y = x.y & 0xFFFFE000u;
-          h.z = x.z & 0xFFFFE000u; h.w = x.w & 0xFFFFE000u;
-          l.x = __float_as_uint(__uint_as_float(x.x) - __uint_as_float(h.x));
-          l.y = __float_as_uint(__uint_as_float(x.y) - __uint_as_float(h.y));
-          l.z = __float_as_uint(__uint_as_float(x.z) - __uint_as_float(h.z));
-          l.w = __float_as_uint(__uint_as_float(x.w) - __uint_as_float(h.w));
-          raw[idx] = h;
-          lo[idx] = l;
-        }
+      if constexpr (TF32) fence_proxy_async_smem();  // the split is visible to the MMAs
+      __syncwarp();
+      if (lane == 0) {
+        if constexpr (TF32) mbar_arrive(&ready[s]);
+        else mbar_arrive(&empty[s]);
       }
-      fence_proxy_async_smem();
     }
-    if (__syncthreads_or(ok ? 0 : 1)) { ok = false; break; }
-    consumed = kb + 1;
-    if (tid == 32) {
-      tc_fence_after();
-      const uint32_t a_base = smem_u32(st);
-      const uint32_t idesc = make_idesc(FMT, BLK);
-      for (int t = 0; t < ntile; ++t) {
-        const uint32_t d_tmem = tmem + (uint32_t)(BLK * t);
-        const int si = p.grp.tile_si[g][t], sj = p.grp.tile_sj[g][t];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const uint32_t koff = k * 32;
-          const uint64_t ah = make_sw128_desc(a_base + si * ATOM_BYTES + koff);
-          const uint64_t bh = make_sw128_desc(a_base + sj * ATOM_BYTES + koff);
-          const uint32_t acc = (kb > 0 || k > 0) ? 1u : 0u;
-          mma_issue<TF32>(d_tmem, ah, bh, idesc, acc);
-          if constexpr (TF32) {
-            const uint64_t al = make_sw128_desc(a_base + stage_raw + si * ATOM_BYTES + koff);
-            const uint64_t bl = make_sw128_desc(a_base + stage_raw + sj * ATOM_BYTES + koff);
-            mma_issue<TF32>(d_tmem, ah, bl, idesc, 1u);
-            mma_issue<TF32>(d_tmem, al, bh, idesc, 1u);
-          }
-        }
-      }
-      mma_commit(&empty[s]);
-    }
-    if (tid == 0 && kb >= 1 && issued < nkb) {
-      // the previous K block's stage is free once the MMAs that read it have
-      // completed (issued one iteration ago); refill it
-      const int64_t pk = kb - 1;
-      if (!mbar_wait_bounded(&empty[pk % nst], (uint32_t)((pk / nst) & 1), p.timeout_ns)) ok = false;
-      else issue(issued++);
-    }
+    for (int q = 0; q < MAXQ; ++q) dsq64[q] += (double)dsq[q];
   }
-  // every MMA issued so far completes on `done` (also after a failure, before TMEM is freed)
-  if (tid == 32) mma_commit(done);
-  if (!mbar_wait_bounded(done, 0, p.timeout_ns)) ok = false;
+
+  // ---------------- epilogue ----------------
+  bool ok = true;
+  if (worker) {
+    int w = 1;
+    if (lane == 0) w = wait(done, 0) ? 1 : 0;
+    w = __shfl_sync(FULL_MASK, w, 0);
+    __syncwarp();
+    ok = w != 0;
+  }
   tc_fence_after();
-  const int fail = __syncthreads_or(ok ? 0 : 1);
-  if (!fail) {
-    // column sums of squares: the 8 lanes t = 8a..8a+7 share columns a + 16q
+  const int fail = __syncthreads_or((!ok || *vfail) ? 1 : 0);
+  if (!fail && worker) {
+    // column sums of squares: the 8 workers 8a..8a+7 share columns a + 16q
 #pragma unroll
     for (int q = 0; q < MAXQ; ++q) {
-      double v = dsq64[q] + (double)dsq[q];
+      double v = dsq64[q];
       v += __shfl_xor_sync(FULL_MASK, v, 1);
       v += __shfl_xor_sync(FULL_MASK, v, 2);
       v += __shfl_xor_sync(FULL_MASK, v, 4);
-      const int lcol = tid / 8 + 16 * q;  // column within the streamed slots
-      if ((tid & 7) == 0 && q < nq && p.grp.diag_slot[g][lcol / BLK])
+      const int lcol = wt / 8 + 16 * q;  // column within the streamed slots
+      if ((wt & 7) == 0 && q < 8 * nload && p.grp.diag_slot[g][lcol / BLK])
         p.dpart[(size_t)blockIdx.x * p.npad + p.grp.load_blk[g][lcol / BLK] * BLK + lcol % BLK] = v;
     }
+    // tensor memory: worker warp w reads lane quarter w % 4 (rows 32·(w%4)..+31)
+    const int quarter = warp & 3;
     float* out = p.partial + (size_t)blockIdx.x * p.npad * p.npad;
     for (int t = 0; t < ntile; ++t) {
-      const int row = BLK * p.grp.tile_i[g][t] + 32 * warp + lane;
+      const int row = BLK * p.grp.tile_i[g][t] + 32 * quarter + lane;
       float* orow = out + (size_t)row * p.npad + BLK * p.grp.tile_j[g][t];
       for (int c0 = 0; c0 < BLK; c0 += 32) {
         float v[32];
         if (nkb > 0) {
-          tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + BLK * t + c0, v);
+          tmem_ld32(tmem + ((uint32_t)(32 * quarter) << 16) + BLK * t + c0, v);
         } else {
 #pragma unroll
           for (int i = 0; i < 32; ++i) v[i] = 0.f;
@@ -285,11 +351,6 @@ __global__ void __launch_bounds__(GT_THREADS, 1)
               make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
       }
     }
-  } else if (tid == 0) {
-    atomicExch(p.err, 1);
-    // copies issued but never consumed must land before the CTA retires
-    for (int64_t kb = consumed; kb < issued; ++kb)
-      if (!mbar_wait_bounded(&full[kb % nst], (uint32_t)((kb / nst) & 1), p.timeout_ns)) break;
   }
   tc_fence_before();
   __syncthreads();
