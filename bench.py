@@ -308,6 +308,31 @@ def next_algorithms(hp, synth, ctx, X, y, s, reps=3):
     return out
 
 
+def wide_comparison(hp, synth, ctx, dev, reps=2):
+    """The wide workload: 2,000 x 200,000 float32 row-major consistent system
+    (infinitely many solutions) swept to relative residual 1e-6 by the cluster
+    kernel (the transposed path)."""
+    import torch
+    s = synth.workload("wide_2000x200k_f32", seed=0)
+    X = torch.from_numpy(s.X).to(dev)  # (m, n) row-major
+    y = torch.from_numpy(s.y).to(dev)
+    r = ctx.solve(X, y, tol=1e-6, max_sweeps=200, stop="rel_res")
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        r = ctx.solve(X, y, tol=1e-6, max_sweeps=200, stop="rel_res")
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    xb = 4 * s.m * s.n
+    return {"workload": "wide_2000x200k_f32 (row-major, consistent)", "stop": "rel_res<=1e-6",
+            "status": r.status, "sweeps": int(r.sweeps), "rel_res": float(r.rel_res), "ms_to_tol": ms,
+            "sweep_kernel_ms": float(r.timing["sweep_ms"]),
+            "GBps": xb * (r.timing["passes"] + 1) / (ms * 1e-3) / 1e9,
+            "ms_per_sweep": float(r.timing["sweep_ms"]) / max(1, r.timing["passes"])}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -318,6 +343,8 @@ def main():
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the bfloat16-vs-float32 comparison on the 4,000,000 x 512 system")
+    ap.add_argument("--no-wide", action="store_true",
+                    help="skip the wide 2,000 x 200,000 row-major system")
     ap.add_argument("--no-next", action="store_true",
                     help="skip Algorithm 2 / Algorithm 3 on the benchmark system")
     ap.add_argument("--no-batched", action="store_true",
@@ -435,6 +462,8 @@ def main():
             out["cpu_baseline"] = cpu_baseline_leg(s)
         if not args.no_next and not args.rows:
             out["next_algorithms"] = next_algorithms(hp, synth, ctx, X, y, s)
+        if not args.no_wide and not args.rows:
+            out["wide"] = wide_comparison(hp, synth, ctx, dev)
         if not args.no_compare and not args.rows:
             del X
             torch.cuda.empty_cache()

@@ -51,9 +51,11 @@ def build_batch(ctx, fam, m, n, th, device="cuda", tol=TOL, stop=STOP, max_sweep
     return (keep, sysd), a, b
 
 
-def solve_family(ctx, fam, m, n, th, chunk=4096, **kw):
-    """Cold-start solutions as a zero-padded (count, 256) float32 array, plus
-    the sweeps and final residuals."""
+def solve_family(ctx, fam, m, n, th, chunk=4096, mlp=None, **kw):
+    """Solutions as a zero-padded (count, 256) float32 array, plus the sweeps
+    and final residuals: from a cold start, or from mlp's prediction when given
+    (the solve then continues from where the network puts each system)."""
+    import torch
     count = len(m)
     labels = np.zeros((count, 256), dtype=np.float32)
     sweeps = np.zeros(count, dtype=np.int64)
@@ -61,6 +63,9 @@ def solve_family(ctx, fam, m, n, th, chunk=4096, **kw):
     for c0 in range(0, count, chunk):
         c1 = min(count, c0 + chunk)
         keep, a, b = build_batch(ctx, fam, m[c0:c1], n[c0:c1], th[c0:c1], **kw)
+        if mlp is not None:
+            theta = torch.from_numpy(np.ascontiguousarray(th[c0:c1], dtype=np.float32)).cuda()
+            b.set_warm_start(mlp, theta)
         r = b.run()
         for i, ai in enumerate(a):
             labels[c0 + i, : ai.numel()] = ai.cpu().numpy()
@@ -179,6 +184,10 @@ def main():
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--out", default=WEIGHTS)
     ap.add_argument("--labels", default="", help="cache file of the training labels (.npz)")
+    ap.add_argument("--rounds", type=int, default=1,
+                    help="self-training rounds: after each, the training systems are solved again "
+                         "from the network's prediction (same rule and cap) and the network is "
+                         "retrained on those further-converged solutions")
     args = ap.parse_args()
     import torch
     ctx = hp.Context(0)
@@ -197,10 +206,18 @@ def main():
                       "label_hit_cap": int((sw >= MAX_SWEEPS).sum())}), flush=True)
     mlp, hist = train(ctx, th, m, n, labels, epochs=args.epochs, batch=args.batch, lr=args.lr,
                       log=lambda h: print(json.dumps(h), flush=True))
+    for rnd in range(1, args.rounds):
+        labels, sw, res = solve_family(ctx, fam, m, n, th, mlp=mlp)
+        print(json.dumps({"round": rnd, "label_sweeps_mean": float(sw.mean()),
+                          "label_hit_cap": int((sw >= MAX_SWEEPS).sum())}), flush=True)
+        mlp.close()
+        mlp, hist = train(ctx, th, m, n, labels, epochs=args.epochs, batch=args.batch, lr=args.lr,
+                          log=lambda h: print(json.dumps(h), flush=True))
     t2 = time.time()
     me, ne, te = synth.rbf_params(args.eval, seed=0)
     ev = evaluate(ctx, fam, mlp, me, ne, te)
     meta = {"train_systems": args.train, "epochs": args.epochs, "batch": args.batch, "lr": args.lr,
+            "rounds": args.rounds,
             "train_s": t2 - t1, "labels_s": t1 - t0, "final": hist[-1], "eval": ev,
             "stop": f"{STOP}<{TOL}, max_sweeps {MAX_SWEEPS}"}
     save(mlp, args.out, meta)
