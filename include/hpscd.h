@@ -103,7 +103,10 @@ typedef struct hpscd_ctx hpscd_ctx;
  * one with hpscd_set_workspace.  Errors: INVALID_ARG, CUDA. */
 int hpscd_create(hpscd_ctx** out, int device, void* stream);
 
-/* Release the context and any workspace it allocated.  NULL is accepted. */
+/* Release the context and any workspace it allocated.  NULL is accepted.
+ * Batches and networks made on the context keep it: destroyed while any of
+ * them is alive, the context is only marked closed (no further calls on it)
+ * and is freed when the last of them is destroyed. */
 int hpscd_destroy(hpscd_ctx* ctx);
 
 /* Rebind the context to another stream of the same device. */
@@ -304,7 +307,8 @@ int hpscd_batch_results(hpscd_batch* b, hpscd_sys_result* out);
 /* The tuning the batch was planned with. */
 int hpscd_batch_tuning(hpscd_batch* b, hpscd_tuning* out);
 
-/* Release the batch (waits for its last launch).  NULL is accepted. */
+/* Release the batch (waits for its last launch) and its hold on the warm-start
+ * network and the context.  NULL is accepted. */
 int hpscd_batch_destroy(hpscd_batch* b);
 
 /*
@@ -332,6 +336,8 @@ typedef struct hpscd_mlp hpscd_mlp;
  * Parameters start at zero: set them with hpscd_mlp_set_params.
  * Errors: INVALID_ARG, UNSUPPORTED (no tensor-map support), NO_MEMORY, CUDA. */
 int hpscd_mlp_create(hpscd_ctx* ctx, int64_t max_batch, hpscd_mlp** out);
+/* A network that batches start from (hpscd_batch_set_warm_start) is freed
+ * when the last such batch lets go of it; until then only no further calls. */
 int hpscd_mlp_destroy(hpscd_mlp* mlp);
 
 /* Number of float32 parameters: W1 [256][18], b1 [256], W2 [256][256], b2,

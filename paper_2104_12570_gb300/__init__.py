@@ -15,6 +15,7 @@ from __future__ import annotations
 import ctypes
 import os
 import threading
+import weakref
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -233,6 +234,7 @@ class Context:
         if rc != 0:
             raise HpscdError(rc, "hpscd_create")
         self._h = h
+        self._children = weakref.WeakSet()  # batches and networks made on this context
         if timeout_s is not None:
             self.set_timeout(timeout_s)
 
@@ -255,7 +257,12 @@ class Context:
             raise HpscdError(rc)
 
     def close(self):
+        """Destroy the context, after the batches and networks made on it (their
+        handles point into it)."""
         if getattr(self, "_h", None):
+            kids = list(getattr(self, "_children", ()))
+            for k in sorted(kids, key=lambda k: isinstance(k, MLP)):  # batches first
+                k.close()
             self._lib.hpscd_destroy(self._h)
             self._h = None
 
@@ -465,6 +472,7 @@ class Batch:
             raise HpscdError(rc, "hpscd_batch_create")
         self._h = h
         self._res = (SysResult * max(1, self.count))()
+        ctx._children.add(self)
 
     @property
     def cluster(self) -> int:
@@ -506,6 +514,7 @@ class Batch:
                 raise TypeError("theta must be a contiguous float32 CUDA tensor (count, 16)")
             self._theta = theta
             self._mlp = mlp
+            mlp._users.add(self)
             rc = self._lib.hpscd_batch_set_warm_start(self._h, mlp._h, ctypes.c_void_p(theta.data_ptr()))
         if rc:
             raise HpscdError(rc, "hpscd_batch_set_warm_start")
@@ -514,6 +523,9 @@ class Batch:
         if getattr(self, "_h", None):
             self._lib.hpscd_batch_destroy(self._h)
             self._h = None
+            mlp = getattr(self, "_mlp", None)
+            if mlp is not None:
+                mlp._users.discard(self)
 
     def __del__(self):
         try:
@@ -564,6 +576,8 @@ class MLP:
         if rc:
             raise HpscdError(rc, "hpscd_mlp_create")
         self._h = h
+        self._users = weakref.WeakSet()  # batches that start from this network
+        ctx._children.add(self)
         self.n_params = int(self._lib.hpscd_mlp_param_count())
         self.set_params(mlp_init(seed) if params is None else params)
 
@@ -630,7 +644,11 @@ class MLP:
         return loss.value
 
     def close(self):
+        """Destroy the network; batches that start from it go back to the cold start."""
         if getattr(self, "_h", None):
+            for b in list(getattr(self, "_users", ())):
+                if getattr(b, "_h", None):
+                    b.set_warm_start(None)
             self._lib.hpscd_mlp_destroy(self._h)
             self._h = None
 

@@ -34,14 +34,6 @@ struct hpscd_batch {
   int64_t* mn_d = nullptr;           // device int64 m[count], n[count]
   hpscd_mlp* mlp = nullptr;          // learned warm start (optional)
   const float* theta = nullptr;      // device float[count][16]
-  // tensor-core Gram of the TMA-addressable systems (a graph node before the sweep)
-  CUtensorMap* maps_d = nullptr;     // [count] per-system tensor maps
-  int64_t* gt_off_d = nullptr;       // [count] slot offsets (-1: formed in the sweep kernel)
-  float* gt_d = nullptr;             // slots: G~ [ldg][ldg] then d [ldg], ldg = 32·ceil(n/32)
-  int* gq_d = nullptr;               // queue of the Gram kernel
-  int* gerr_d = nullptr;             // its failure flag
-  int64_t n_pre = 0;                 // systems on the tensor-core path
-  int gsmem = 0, gnst = 0;
 };
 
 namespace {
@@ -108,13 +100,7 @@ int capture(hpscd_batch* b) {
   if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
   if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
   if (cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return HPSCD_ERR_CUDA;
-  bool body = cudaMemsetAsync(b->queue_d, 0, sizeof(int), b->cap) == cudaSuccess &&
-              cudaMemsetAsync(b->gq_d, 0, 2 * sizeof(int), b->cap) == cudaSuccess;
-  // set-up of the TMA-addressable systems on the tensor cores, one persistent launch
-  if (body && b->n_pre > 0)
-    body = launch_batched_gram_tc(b->maps_d, b->sys_d, b->order_d, (int)b->count, b->gq_d, b->gt_off_d,
-                                  b->gt_d, b->gerr_d, (uint64_t)(b->ctx->timeout_s * 1e9), b->ctx->sms,
-                                  b->gsmem, b->gnst, b->cap) == cudaSuccess;
+  bool body = cudaMemsetAsync(b->queue_d, 0, sizeof(int), b->cap) == cudaSuccess;
   if (body && b->mlp && b->count > 0)
     body = mlp_enqueue_warm_start(b->mlp, b->cap, b->theta, b->mn_d, b->mn_d + b->count, b->sys_d,
                                   b->count) == HPSCD_OK;
@@ -177,34 +163,6 @@ int create(hpscd_ctx* ctx, const hpscd_sys* sys, int64_t count, const hpscd_opts
   const size_t o_gfinal = off; off = align256(off + (size_t)clusters * 256 * 256 * sizeof(float));
   const size_t o_dfinal = off; off = align256(off + (size_t)clusters * 256 * sizeof(float));
   const size_t o_mn = off; off = align256(off + 2 * n_sys * sizeof(int64_t));
-  // per-system tensor maps and Gram slots for the tensor-core set-up
-  std::vector<CUtensorMap> maps((size_t)n_sys);
-  std::vector<int64_t> gt_off((size_t)n_sys, -1);
-  int64_t gt_total = 0, n_pre = 0;
-  int gnst = 0;
-  const int gsmem = batched_gram_tc_smem(ctx->max_smem, &gnst);
-  for (int64_t i = 0; i < count && ctx->encode && gsmem > 0; ++i) {
-    const hpscd_sys& sd = sys[i];
-    if (sd.m < 1 || sd.n < 1 || (reinterpret_cast<uintptr_t>(sd.X) & 15) != 0 || (sd.ld * 4) % 16 != 0 ||
-        (uint64_t)sd.ld * 4 >= ((uint64_t)1 << 40))
-      continue;
-    cuuint64_t dims[2] = {(cuuint64_t)sd.m, (cuuint64_t)sd.n};
-    cuuint64_t strides[1] = {(cuuint64_t)sd.ld * 4};
-    cuuint32_t box[2] = {32, 128};
-    cuuint32_t estr[2] = {1, 1};
-    if (ctx->encode(&maps[(size_t)i], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(sd.X), dims,
-                    strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-      continue;
-    const int64_t ldg = 32 * ((sd.n + 31) / 32);
-    gt_off[(size_t)i] = gt_total;
-    gt_total += ldg * (ldg + 1);
-    ++n_pre;
-  }
-  const size_t o_maps = off; off = align256(off + n_sys * sizeof(CUtensorMap));
-  const size_t o_gtoff = off; off = align256(off + n_sys * sizeof(int64_t));
-  const size_t o_gt = off; off = align256(off + (size_t)(gt_total > 0 ? gt_total : 1) * sizeof(float));
-  const size_t o_gq = off; off = align256(off + 2 * sizeof(int));
   if (cudaMalloc(&b->dev, off) != cudaSuccess) {
     cudaGetLastError();
     delete b;
@@ -219,14 +177,6 @@ int create(hpscd_ctx* ctx, const hpscd_sys* sys, int64_t count, const hpscd_opts
   b->gfinal = reinterpret_cast<float*>(base + o_gfinal);
   b->dfinal = reinterpret_cast<float*>(base + o_dfinal);
   b->mn_d = reinterpret_cast<int64_t*>(base + o_mn);
-  b->maps_d = reinterpret_cast<CUtensorMap*>(base + o_maps);
-  b->gt_off_d = reinterpret_cast<int64_t*>(base + o_gtoff);
-  b->gt_d = reinterpret_cast<float*>(base + o_gt);
-  b->gq_d = reinterpret_cast<int*>(base + o_gq);
-  b->gerr_d = b->gq_d + 1;
-  b->n_pre = n_pre;
-  b->gsmem = gsmem;
-  b->gnst = gnst;
   std::vector<int64_t> mn((size_t)2 * n_sys, 0);
   for (int64_t i = 0; i < count; ++i) { mn[(size_t)i] = sys[i].m; mn[(size_t)(count + i)] = sys[i].n; }
 
@@ -244,10 +194,6 @@ int create(hpscd_ctx* ctx, const hpscd_sys* sys, int64_t count, const hpscd_opts
       cudaMemsetAsync(b->res_d, 0, n_sys * sizeof(hpscd_sys_result), st) != cudaSuccess ||
       cudaMemcpyAsync(b->mn_d, mn.data(), mn.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st) !=
           cudaSuccess ||
-      (count > 0 && cudaMemcpyAsync(b->maps_d, maps.data(), (size_t)count * sizeof(CUtensorMap),
-                                    cudaMemcpyHostToDevice, st) != cudaSuccess) ||
-      (count > 0 && cudaMemcpyAsync(b->gt_off_d, gt_off.data(), (size_t)count * sizeof(int64_t),
-                                    cudaMemcpyHostToDevice, st) != cudaSuccess) ||
       cudaStreamSynchronize(st) != cudaSuccess) {
     cudaGetLastError();
     release(b);
@@ -268,14 +214,6 @@ int create(hpscd_ctx* ctx, const hpscd_sys* sys, int64_t count, const hpscd_opts
   p.tol = opts->tol;
   p.max_sweeps = opts->max_sweeps;
   p.stop_rule = opts->stop_rule;
-  p.gt_off = n_pre > 0 ? b->gt_off_d : nullptr;
-  p.gt_sys = b->gt_d;
-  if (n_pre > 0 && batched_gram_tc_prepare(ctx->max_smem) != cudaSuccess) {
-    cudaGetLastError();
-    release(b);
-    delete b;
-    return HPSCD_ERR_CUDA;
-  }
 
   b->params = p;
   b->sys_host.assign(sys, sys + count);
@@ -287,6 +225,7 @@ int create(hpscd_ctx* ctx, const hpscd_sys* sys, int64_t count, const hpscd_opts
     delete b;
     return HPSCD_ERR_CUDA;
   }
+  ctx_retain(ctx);
   *out = b;
   return HPSCD_OK;
 }
@@ -334,16 +273,11 @@ int hpscd_batch_results(hpscd_batch* b, hpscd_sys_result* out) {
   DevGuard g(b->ctx->device);
   if (!g.ok) return HPSCD_ERR_CUDA;
   if (cudaStreamSynchronize(b->ctx->stream) != cudaSuccess) { cudaGetLastError(); return HPSCD_ERR_CUDA; }
-  int gerr = 0;
-  if ((b->count > 0 &&
-       cudaMemcpy(out, b->res_d, (size_t)b->count * sizeof(hpscd_sys_result), cudaMemcpyDeviceToHost) !=
-           cudaSuccess) ||
-      cudaMemcpy(&gerr, b->gerr_d, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
+  if (b->count > 0 &&
+      cudaMemcpy(out, b->res_d, (size_t)b->count * sizeof(hpscd_sys_result), cudaMemcpyDeviceToHost) !=
+          cudaSuccess) {
     cudaGetLastError();
     return HPSCD_ERR_CUDA;
-  }
-  if (gerr) {  // a bounded wait of the tensor-core set-up gave up: every result is suspect
-    for (int64_t i = 0; i < b->count; ++i) out[i].status = HPSCD_ERR_TIMEOUT;
   }
   if (b->launched) {
     hpscd_timing t{};
@@ -352,7 +286,7 @@ int hpscd_batch_results(hpscd_batch* b, hpscd_sys_result* out) {
     for (int64_t i = 0; i < b->count; ++i) passes += out[i].passes;
     t.passes = passes;
     t.grid = b->clusters * b->K;
-    t.kernel_launches = 1 + (b->n_pre > 0 ? 1 : 0) + (b->mlp ? 5 : 0);
+    t.kernel_launches = 1;
     b->ctx->last = t;
   }
   for (int64_t i = 0; i < b->count; ++i)
@@ -375,6 +309,10 @@ int hpscd_batch_set_warm_start(hpscd_batch* b, hpscd_mlp* mlp, const float* thet
     cudaGetLastError();
     return HPSCD_ERR_CUDA;
   }
+  if (mlp != b->mlp) {
+    if (mlp) mlp_retain(mlp);
+    if (b->mlp) mlp_release(b->mlp);
+  }
   b->mlp = mlp;
   b->theta = mlp ? theta : nullptr;
   return capture(b);
@@ -389,10 +327,15 @@ int hpscd_batch_tuning(hpscd_batch* b, hpscd_tuning* out) {
 
 int hpscd_batch_destroy(hpscd_batch* b) {
   if (!b) return HPSCD_OK;
-  DevGuard g(b->ctx->device);
-  cudaStreamSynchronize(b->ctx->stream);
-  release(b);
-  delete b;
+  hpscd_ctx* ctx = b->ctx;
+  {
+    DevGuard g(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    release(b);
+    if (b->mlp) mlp_release(b->mlp);
+    delete b;
+  }
+  ctx_release(ctx);
   return HPSCD_OK;
 }
 

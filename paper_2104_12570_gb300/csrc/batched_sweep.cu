@@ -273,7 +273,7 @@ __device__ void stream_pass(const float* __restrict__ X, int64_t ld, int64_t r0,
 // columns: warp 0 walks each diagonal block with shuffles (its strictly lower
 // part staged in diag_s); every thread t >= 32 owns row t and applies each
 // finished block to it.  r is overwritten.
-__device__ void forward_sub_scaled(const float* __restrict__ Gt, int ldg, int n, float* r, float* da,
+__device__ void forward_sub_scaled(const float* __restrict__ Gt, int n, float* r, float* da,
                                    const float* diag_s) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int nb = (n + 31) / 32;
@@ -295,7 +295,7 @@ __device__ void forward_sub_scaled(const float* __restrict__ Gt, int ldg, int n,
     }
     __syncthreads();
     if (tid >= b0 + 32 && tid < n) {
-      const float4* g4 = reinterpret_cast<const float4*>(Gt + (int64_t)tid * ldg + b0);
+      const float4* g4 = reinterpret_cast<const float4*>(Gt + (int64_t)tid * BLDG + b0);
       float acc = 0.f;
 #pragma unroll
       for (int k4 = 0; k4 < 8; ++k4) {
@@ -369,53 +369,43 @@ __global__ void __launch_bounds__(BNT, 1) batched_sweep_kernel(const BatchParams
     const int vec = ((reinterpret_cast<uintptr_t>(X) & 15) == 0) && (ld % 4 == 0);
 
     // ---- set-up: G, d and G~ = D^{-1} G ----
-    // precomputed by the batch's tensor-core Gram kernel (the system's slot),
-    // or formed here on the CUDA cores (X the TMA cannot address)
-    const bool pre = p.gt_off != nullptr && p.gt_off[sidx] >= 0;
-    const int ldg = pre ? 32 * ((n + 31) / 32) : BLDG;
-    const float* Gs = pre ? p.gt_sys + p.gt_off[sidx] : Gt;
-    if (pre) {
-      for (int c = tid; c < BMAXN; c += BNT) dd_s[c] = c < n ? __ldcg(Gs + (size_t)ldg * ldg + c) : 0.f;
-      __syncthreads();
-    } else {
-      gram_partial(X, ld, r0, mloc, n, uni, Gp);
-      csync();
-      // d = diag(G) (every CTA, rank order)
-      for (int c = tid; c < BMAXN; c += BNT) {
-        float s = 0.f;
-        if (c < n) {
-          for (int k = 0; k < K; ++k)
-            s += __ldcg(p.gpart + ((size_t)(cl * K + k) * BLDG + c) * BLDG + c);
-        }
-        dd_s[c] = s;
+    gram_partial(X, ld, r0, mloc, n, uni, Gp);
+    csync();
+    // d = diag(G) (every CTA, rank order)
+    for (int c = tid; c < BMAXN; c += BNT) {
+      float s = 0.f;
+      if (c < n) {
+        for (int k = 0; k < K; ++k)
+          s += __ldcg(p.gpart + ((size_t)(cl * K + k) * BLDG + c) * BLDG + c);
       }
-      __syncthreads();
-      // rows [j0, j1) of G~ by this CTA: lower entries summed over the cluster's
-      // partials, divided by the row's d; the mirrored entry by the column's d
-      {
-        const int j0 = (int)((int64_t)n * rank / K), j1 = (int)((int64_t)n * (rank + 1) / K);
-        for (int j = j0 + warp; j < j1; j += BNW) {
-          const float dj = dd_s[j];
-          for (int l = lane; l <= j; l += 32) {
-            float s = 0.f;
-            for (int k = 0; k < K; ++k)
-              s += __ldcg(p.gpart + ((size_t)(cl * K + k) * BLDG + j) * BLDG + l);
-            const float dl = dd_s[l];
-            if (l == j) {
-              Gt[(size_t)j * BLDG + j] = dj > 0.f ? 1.f : 0.f;
-            } else {
-              Gt[(size_t)j * BLDG + l] = dj > 0.f ? s / dj : 0.f;
-              Gt[(size_t)l * BLDG + j] = dl > 0.f ? s / dl : 0.f;
-            }
-          }
-          // columns n..32·ceil(n/32)-1 of the row are read (times da = 0) by the substitution
-          for (int l = n + lane; l < ((n + 31) / 32) * 32; l += 32) Gt[(size_t)j * BLDG + l] = 0.f;
-        }
-        if (rank == 0)
-          for (int c = tid; c < n; c += BNT) dg[c] = dd_s[c];
-      }
-      csync();
+      dd_s[c] = s;
     }
+    __syncthreads();
+    // rows [j0, j1) of G~ by this CTA: lower entries summed over the cluster's
+    // partials, divided by the row's d; the mirrored entry by the column's d
+    {
+      const int j0 = (int)((int64_t)n * rank / K), j1 = (int)((int64_t)n * (rank + 1) / K);
+      for (int j = j0 + warp; j < j1; j += BNW) {
+        const float dj = dd_s[j];
+        for (int l = lane; l <= j; l += 32) {
+          float s = 0.f;
+          for (int k = 0; k < K; ++k)
+            s += __ldcg(p.gpart + ((size_t)(cl * K + k) * BLDG + j) * BLDG + l);
+          const float dl = dd_s[l];
+          if (l == j) {
+            Gt[(size_t)j * BLDG + j] = dj > 0.f ? 1.f : 0.f;
+          } else {
+            Gt[(size_t)j * BLDG + l] = dj > 0.f ? s / dj : 0.f;
+            Gt[(size_t)l * BLDG + j] = dl > 0.f ? s / dl : 0.f;
+          }
+        }
+        // columns n..32·ceil(n/32)-1 of the row are read (times da = 0) by the substitution
+        for (int l = n + lane; l < ((n + 31) / 32) * 32; l += 32) Gt[(size_t)j * BLDG + l] = 0.f;
+      }
+      if (rank == 0)
+        for (int c = tid; c < n; c += BNT) dg[c] = dd_s[c];
+    }
+    csync();
     // diagonal blocks of G~ (strictly lower, packed) into shared memory
     for (int idx = tid; idx < ((n + 31) / 32) * DIAGP; idx += BNT) {
       const int b = idx / DIAGP, qq = idx % DIAGP;
@@ -423,7 +413,7 @@ __global__ void __launch_bounds__(BNT, 1) batched_sweep_kernel(const BatchParams
       while ((i * (i + 1)) / 2 <= qq) ++i;
       const int k = qq - (i * (i - 1)) / 2;
       const int row = 32 * b + i, col = 32 * b + k;
-      diag_s[idx] = (row < n) ? __ldcg(Gs + (size_t)row * ldg + col) : 0.f;
+      diag_s[idx] = (row < n) ? __ldcg(Gt + (size_t)row * BLDG + col) : 0.f;
     }
     // residual slice e = y, coefficients, v
     double ysq = 0.0;
@@ -512,7 +502,7 @@ __global__ void __launch_bounds__(BNT, 1) batched_sweep_kernel(const BatchParams
       __syncthreads();  // rvec (h) complete
       // r = h ⊘ d - G~·v, one warp per row
       for (int c = warp; c < n; c += BNW) {
-        const float* grow = Gs + (size_t)c * ldg;
+        const float* grow = Gt + (size_t)c * BLDG;
         float acc = 0.f;
         for (int l = lane; l < n; l += 32) acc = fmaf(__ldcg(grow + l), vsm[l], acc);
 #pragma unroll
@@ -523,7 +513,7 @@ __global__ void __launch_bounds__(BNT, 1) batched_sweep_kernel(const BatchParams
         }
       }
       __syncthreads();
-      forward_sub_scaled(Gs, ldg, n, rvec, da_s, diag_s);
+      forward_sub_scaled(Gt, n, rvec, da_s, diag_s);
       for (int c = tid; c < n; c += BNT) {
         a64_s[c] += (double)da_s[c];
         vsm[c] = da_s[c];

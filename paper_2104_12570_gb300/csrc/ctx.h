@@ -21,7 +21,16 @@ struct hpscd_ctx {
   unsigned long long* trace_dev = nullptr;
   int trace_grid = 0;
   PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  // batches and networks made on this context: hpscd_destroy while any is
+  // alive only marks the context closing; the last one to go frees it
+  int children = 0;
+  bool closing = false;
 };
+
+namespace hpscd {
+void ctx_retain(hpscd_ctx* ctx);
+void ctx_release(hpscd_ctx* ctx);  // frees a closing context with no children left
+}  // namespace hpscd
 
 // Learned warm start inside a batch's graph (mlp.cu): enqueue on `st` the MLP
 // forward pass for systems [0, count) of `sys` (theta: device float[count][16];
@@ -31,4 +40,8 @@ namespace hpscd {
 int mlp_enqueue_warm_start(hpscd_mlp* p, cudaStream_t st, const float* theta, const int64_t* m,
                            const int64_t* n, const hpscd_sys* sys, int64_t count);
 int mlp_device(const hpscd_mlp* p);
+// A batch that starts from the network holds it: hpscd_mlp_destroy while a
+// batch holds it is deferred until the last holder lets go.
+void mlp_retain(hpscd_mlp* p);
+void mlp_release(hpscd_mlp* p);
 }  // namespace hpscd

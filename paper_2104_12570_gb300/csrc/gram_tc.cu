@@ -10,9 +10,9 @@
 // operand's contiguous K-major rows), and accumulates D_IJ = X_I^T X_J in
 // tensor memory (128 columns per tile) with tcgen05.mma issued by one thread.  bfloat16 X: kind::f16 (exact
 // products, float32 accumulation).  float32 X: kind::tf32 on a two-term split
-// x = hi + lo (hi = x truncated to tf32, written back in place; lo = x - hi),
-// accumulating hi·hi + hi·lo + lo·hi, which leaves ~2^-21 relative error per
-// product.  The tensor-core accumulation loses accuracy on long sums of
+// x = hi + lo (hi = x rounded to the nearest tf32, written back in place;
+// lo = x - hi rounded to tf32), accumulating hi·hi + hi·lo + lo·hi, which
+// leaves ~2^-22 relative error per product, of either sign.  The tensor-core accumulation loses accuracy on long sums of
 // positive terms, so the diagonal <X_j, X_j> is summed on the CUDA cores from
 // the same shared-memory tiles (float32, float64 across blocks).  Per-split
 // float32 partials are summed in a fixed order by gram_tc_reduce_kernel into
@@ -199,14 +199,9 @@ __global__ void __launch_bounds__(GT_THREADS, 1)
             const float a0 = __uint_as_float(x.x), a1 = __uint_as_float(x.y);
             const float a2 = __uint_as_float(x.z), a3 = __uint_as_float(x.w);
             dsq[q] = fmaf(a0, a0, fmaf(a1, a1, fmaf(a2, a2, fmaf(a3, a3, dsq[q]))));
-            // split in place: hi (tf32-exact) over x, lo = x - hi in the second half
+            // split in place: hi over x, lo in the second half
             uint4 h, l;
-            h.x = x.x & 0xFFFFE000u; h.y = x.y & 0xFFFFE000u;
-            h.z = x.z & 0xFFFFE000u; h.w = x.w & 0xFFFFE000u;
-            l.x = __float_as_uint(a0 - __uint_as_float(h.x));
-            l.y = __float_as_uint(a1 - __uint_as_float(h.y));
-            l.z = __float_as_uint(a2 - __uint_as_float(h.z));
-            l.w = __float_as_uint(a3 - __uint_as_float(h.w));
+            split_tf32(x, h, l);
             raw4[wt + GT_WORKERS * q] = h;
             lo4[wt + GT_WORKERS * q] = l;
           } else {

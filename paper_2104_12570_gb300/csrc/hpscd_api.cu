@@ -435,6 +435,29 @@ int solve_device(hpscd_ctx* ctx, const void* X, int dtype, int layout, int64_t m
 
 }  // namespace
 
+namespace {
+
+void free_ctx(hpscd_ctx* ctx) {
+  DeviceGuard g(ctx->device);
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  else cudaDeviceSynchronize();
+  if (ctx->ws && ctx->ws_owned) cudaFree(ctx->ws);
+  for (int i = 0; i < 3; ++i)
+    if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
+  if (ctx->ctl_host) cudaFreeHost(ctx->ctl_host);
+  if (ctx->trace_dev) cudaFree(ctx->trace_dev);
+  delete ctx;
+}
+
+}  // namespace
+
+namespace hpscd {
+void ctx_retain(hpscd_ctx* ctx) { ++ctx->children; }
+void ctx_release(hpscd_ctx* ctx) {
+  if (--ctx->children == 0 && ctx->closing) free_ctx(ctx);
+}
+}  // namespace hpscd
+
 extern "C" {
 
 int hpscd_create(hpscd_ctx** out, int device, void* stream) {
@@ -476,15 +499,11 @@ int hpscd_create(hpscd_ctx** out, int device, void* stream) {
 
 int hpscd_destroy(hpscd_ctx* ctx) {
   if (!ctx) return HPSCD_OK;
-  DeviceGuard g(ctx->device);
-  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
-  else cudaDeviceSynchronize();
-  if (ctx->ws && ctx->ws_owned) cudaFree(ctx->ws);
-  for (int i = 0; i < 3; ++i)
-    if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
-  if (ctx->ctl_host) cudaFreeHost(ctx->ctl_host);
-  if (ctx->trace_dev) cudaFree(ctx->trace_dev);
-  delete ctx;
+  if (ctx->children > 0) {  // freed by the last batch or network to go
+    ctx->closing = true;
+    return HPSCD_OK;
+  }
+  free_ctx(ctx);
   return HPSCD_OK;
 }
 

@@ -157,9 +157,6 @@ struct BatchParams {
   float* gfinal;            // [clusters][256*256] G~ = D^{-1} G of each cluster's system
   float* dfinal;            // [clusters][256] d = diag(G)
   int ecap;                 // residual rows held in shared memory per CTA
-  const int64_t* gt_off;    // [count] or null: offset of the system's precomputed slot
-                            // (G~ rows of stride ldg = 32·ceil(n/32), then d), -1: none
-  const float* gt_sys;
   double tol;
   int64_t max_sweeps;
   int stop_rule;
@@ -168,12 +165,5 @@ int batched_smem_bytes(int64_t mmax, int K);
 int batched_ecap(int64_t mmax, int K);
 int batched_max_clusters(int K, int smem, int max_smem);
 cudaError_t launch_batched(const BatchParams& p, int K, int clusters, int smem, cudaStream_t stream);
-// tcgen05 Gram of every TMA-addressable system of a batch into its slot
-int batched_gram_tc_smem(int max_smem, int* nstages);
-cudaError_t batched_gram_tc_prepare(int max_smem);
-cudaError_t launch_batched_gram_tc(const CUtensorMap* maps, const hpscd_sys* sys, const int* order,
-                                   int count, int* queue, const int64_t* gt_off, float* gt, int* err,
-                                   uint64_t timeout_ns, int grid, int smem, int nstages,
-                                   cudaStream_t stream);
 
 }  // namespace hpscd

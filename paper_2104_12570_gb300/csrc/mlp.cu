@@ -351,6 +351,8 @@ using namespace hpscd;
 
 struct hpscd_mlp {
   hpscd_ctx* ctx = nullptr;
+  int users = 0;         // batches that start from this network
+  bool closing = false;  // destroyed while held: freed by the last holder
   int bmax = 0;  // rows of the activation buffers (multiple of 128)
   void* dev = nullptr;
   // float32 masters, gradients, Adam moments: W1 [256][64], b1, W2 [256][256], b2, W3, b3
@@ -503,7 +505,25 @@ int finish(hpscd_mlp* p) {
 
 namespace hpscd {
 
+static void free_mlp(hpscd_mlp* p) {
+  hpscd_ctx* ctx = p->ctx;
+  int prev = -1;
+  cudaGetDevice(&prev);
+  if (prev != ctx->device) cudaSetDevice(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  cudaFree(p->dev);
+  delete p;
+  if (prev >= 0 && prev != ctx->device) cudaSetDevice(prev);
+  ctx_release(ctx);
+}
+
 int mlp_device(const hpscd_mlp* p) { return p->ctx->device; }
+
+void mlp_retain(hpscd_mlp* p) { ++p->users; }
+
+void mlp_release(hpscd_mlp* p) {
+  if (--p->users == 0 && p->closing) free_mlp(p);
+}
 
 int mlp_enqueue_warm_start(hpscd_mlp* p, cudaStream_t st, const float* theta, const int64_t* m,
                            const int64_t* n, const hpscd_sys* sys, int64_t count) {
@@ -604,15 +624,18 @@ int hpscd_mlp_create(hpscd_ctx* ctx, int64_t max_batch, hpscd_mlp** out) {
     return HPSCD_ERR_CUDA;
   }
   if (prev >= 0 && prev != ctx->device) cudaSetDevice(prev);
+  ctx_retain(ctx);
   *out = p;
   return HPSCD_OK;
 }
 
 int hpscd_mlp_destroy(hpscd_mlp* p) {
   if (!p) return HPSCD_OK;
-  cudaStreamSynchronize(p->ctx->stream);
-  cudaFree(p->dev);
-  delete p;
+  if (p->users > 0) {
+    p->closing = true;
+    return HPSCD_OK;
+  }
+  free_mlp(p);
   return HPSCD_OK;
 }
 

@@ -68,6 +68,29 @@ __device__ __forceinline__ void tc_fence_before() {
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
 
+// Two-term tf32 split x = hi + lo of four float32 values.  hi is x rounded to
+// the nearest tf32 (ties away), so lo = x - hi is exact and of either sign;
+// lo is rounded to tf32 as well, so the MMA reads both terms as they are.
+// What the split drops (the low bits of lo, and the lo·lo product that is not
+// issued) is then centred on zero instead of always taking from |x|, which a
+// truncating split does: on data of one sign that biases every coupling low.
+__device__ __forceinline__ uint32_t tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+__device__ __forceinline__ void split_tf32(const uint4& x, uint4& hi, uint4& lo) {
+  hi.x = tf32_rna(__uint_as_float(x.x));
+  hi.y = tf32_rna(__uint_as_float(x.y));
+  hi.z = tf32_rna(__uint_as_float(x.z));
+  hi.w = tf32_rna(__uint_as_float(x.w));
+  lo.x = tf32_rna(__uint_as_float(x.x) - __uint_as_float(hi.x));
+  lo.y = tf32_rna(__uint_as_float(x.y) - __uint_as_float(hi.y));
+  lo.z = tf32_rna(__uint_as_float(x.z) - __uint_as_float(hi.z));
+  lo.w = tf32_rna(__uint_as_float(x.w) - __uint_as_float(hi.w));
+}
+
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
   uint32_t r[32];
   asm volatile(

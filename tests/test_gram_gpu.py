@@ -65,3 +65,29 @@ def test_solve_same_with_either_gram(ctx):
     a = ctx.solve(X, y, tol=0, max_sweeps=5, stop="none").a.cpu().numpy()
     b = ctx.solve(X, y, tol=0, max_sweeps=5, stop="none", debug_flags=2).a.cpu().numpy()
     assert np.linalg.norm(a - b) / np.linalg.norm(b) <= 2e-6
+
+
+def test_gram_one_signed_columns(ctx):
+    """Columns of one sign (uniform on [0, 1)).  The CUDA-core Gram is float32-
+    grade here as on any data.  The tensor-core accumulator drops the low bits
+    of every partial sum, so over one K slice of L accumulation steps an entry
+    can lose up to L ulps of a partial sum bounded by sum_k |x_ki x_kj| <=
+    sqrt(G_ii G_jj): error <= L·2^-23·sqrt(G_ii G_jj).  One slice covers
+    ceil(m / SMs) rows (n <= 256 float32: one tile group per slice) and takes
+    12 steps per 32 rows (4 tf32 K steps × hi·hi, hi·lo, lo·hi).  The diagonal
+    is summed on the CUDA cores and stays float32-grade."""
+    m, n = 200_000, 256
+    g = np.random.default_rng(11)
+    Xh = g.uniform(0.0, 1.0, (n, m)).astype(np.float32)
+    X = torch.from_numpy(Xh).cuda().T
+    Xd = Xh.astype(np.float64)
+    G64 = Xd @ Xd.T
+    nrm = np.sqrt(np.outer(np.diag(G64), np.diag(G64)))
+    Gs = ctx.gram(X, simt=True).cpu().numpy().astype(np.float64)
+    assert (np.abs(Gs - G64) / nrm).max() <= 4e-6
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    L = 12 * (-(-(-(-m // sms)) // 32))
+    Gt = ctx.gram(X).cpu().numpy().astype(np.float64)
+    err = np.abs(Gt - G64) / nrm
+    assert err.max() <= L * 2.0 ** -23 + 4e-6, (err.max(), L)
+    assert np.abs(np.diag(Gt) - np.diag(G64)).max() / np.diag(G64).min() <= 4e-6
