@@ -54,6 +54,10 @@ def load_library(path: str):
     lib.hpscd_oracle_select.argtypes = [vp, ctypes.c_int, ctypes.c_int, i64, i64, i64, dp, i64,
                                         vp, dp, dp]
     lib.hpscd_oracle_select.restype = ctypes.c_int
+    lib.hpscd_oracle_solve_order.argtypes = [vp, ctypes.c_int, ctypes.c_int, i64, i64, i64, dp, dp,
+                                             vp, ctypes.c_double, i64, ctypes.c_int, dp, dp, dp,
+                                             ctypes.POINTER(i64)]
+    lib.hpscd_oracle_solve_order.restype = ctypes.c_int
     return lib
 
 
@@ -124,6 +128,30 @@ def solve_blocks(X, y, *, m, n, thr, layout="col", dtype="f32", a0=None, tol=1e-
     st = lib.hpscd_oracle_solve_blocks(_ptr(X), DTYPES[dtype], LAYOUTS[layout], m, n, ld, _ptr(y64),
                                        _ptr(a064), int(thr), float(tol), int(max_sweeps),
                                        STOP[stop], _ptr(a), _ptr(e), _ptr(hist), ctypes.byref(sw))
+    if st in (1, 4):
+        raise ValueError(f"oracle: {STATUS[st]}")
+    return OracleResult(a, e, hist[: sw.value + 1], sw.value, STATUS[st])
+
+
+def solve_order(X, y, *, m, n, order, layout="col", dtype="f32", a0=None, tol=1e-6,
+                max_sweeps=1000, stop="rel_res", want_e=False, lib=None) -> OracleResult:
+    """Algorithm 1 with the column of every step given: step k of sweep s takes
+    column order[s-1][k] (order: integer array (max_sweeps, n), entries in [0, n))."""
+    _check_x(X, m, n, layout, dtype)
+    lib = lib or _load()
+    y64 = np.ascontiguousarray(y, dtype=np.float64)
+    a064 = None if a0 is None else np.ascontiguousarray(a0, dtype=np.float64)
+    o64 = np.ascontiguousarray(np.asarray(order, dtype=np.int64).reshape(-1))
+    if o64.size != max_sweeps * n:
+        raise ValueError("order must hold max_sweeps * n indices")
+    a = np.zeros(n, dtype=np.float64)
+    e = np.zeros(m, dtype=np.float64) if want_e else None
+    hist = np.full(max_sweeps + 1, np.nan, dtype=np.float64)
+    sw = ctypes.c_int64(0)
+    ld = max(1, m if layout == "col" else n)
+    st = lib.hpscd_oracle_solve_order(_ptr(X), DTYPES[dtype], LAYOUTS[layout], m, n, ld, _ptr(y64),
+                                      _ptr(a064), _ptr(o64), float(tol), int(max_sweeps), STOP[stop],
+                                      _ptr(a), _ptr(e), _ptr(hist), ctypes.byref(sw))
     if st in (1, 4):
         raise ValueError(f"oracle: {STATUS[st]}")
     return OracleResult(a, e, hist[: sw.value + 1], sw.value, STATUS[st])

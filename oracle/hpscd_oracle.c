@@ -428,3 +428,90 @@ int hpscd_oracle_select(const void* X, int dt, int lay, int64_t m, int64_t n, in
   free(e); free(col); free(d); free(da);
   return OR_OK;
 }
+
+/*
+ * Algorithm 1 with a given column order per sweep (Sec. 2: instead of taking
+ * j = 1..n in turn, each step may take a randomly chosen index j), literally,
+ * in float64.  The random indices are an input: step k of sweep s updates
+ * column order[(s-1)·n + k], k = 0..n-1; an index may repeat within a sweep
+ * (drawn with replacement) and a column may be left out of a sweep.
+ *
+ *   a <- a0 (or 0_n); e <- y - X·a; d_j <- <X_j, X_j>
+ *   for s = 1..max_sweeps:
+ *     for k = 0..n-1:
+ *       q     <- order[(s-1)·n + k]
+ *       step  <- <X_q, e> / d_q        (Eq. da2; 0 when d_q == 0)
+ *       e     <- e - X_q·step          (Eq. ek1-ek)
+ *       a_q   <- a_q + step
+ *     hist[s] <- ||e|| / ||y||, then the stopping test (as in Algorithm 1)
+ * order holds max_sweeps·n entries, each in [0, n).  Returns like
+ * hpscd_oracle_solve (OR_INVALID for an index outside [0, n)).
+ */
+int hpscd_oracle_solve_order(const void* X, int dt, int lay, int64_t m, int64_t n, int64_t ld,
+                             const double* y, const double* a0, const int64_t* order,
+                             double tol, int64_t max_sweeps, int stop_rule, double* a_out,
+                             double* e_out, double* hist, int64_t* sweeps_done) {
+  if (!valid_args(X, dt, lay, m, n, ld) || (!y && m > 0) || (!a_out && n > 0) ||
+      max_sweeps < 0 || (stop_rule < 0 || stop_rule > 2) || !(tol >= 0.0) ||
+      (!order && max_sweeps > 0 && n > 0))
+    return OR_INVALID;
+  for (int64_t k = 0; k < max_sweeps * n; ++k)
+    if (order[k] < 0 || order[k] >= n) return OR_INVALID;
+  double* e = (double*)malloc((size_t)(m > 0 ? m : 1) * sizeof(double));
+  double* xq = (double*)malloc((size_t)(m > 0 ? m : 1) * sizeof(double));
+  double* dq = (double*)malloc((size_t)(n > 0 ? n : 1) * sizeof(double));
+  if (!e || !xq || !dq) {
+    free(e); free(xq); free(dq);
+    return OR_NOMEM;
+  }
+  for (int64_t q = 0; q < n; ++q) a_out[q] = a0 ? a0[q] : 0.0;
+  for (int64_t i = 0; i < m; ++i) e[i] = y[i];
+  for (int64_t q = 0; q < n; ++q) {
+    load_column(X, dt, lay, ld, m, q, xq);
+    double ss = 0.0;
+    for (int64_t i = 0; i < m; ++i) ss += xq[i] * xq[i];
+    dq[q] = ss;
+    if (a_out[q] != 0.0)
+      for (int64_t i = 0; i < m; ++i) e[i] = e[i] - xq[i] * a_out[q];
+  }
+  const double ynorm = norm2(y, m);
+  const double scale = ynorm > 0.0 ? ynorm : 1.0;
+  double r_prev = norm2(e, m) / scale;
+  if (hist) hist[0] = r_prev;
+  int status = OR_NOT_CONVERGED;
+  int64_t s_done = 0;
+  if (!isfinite(r_prev)) {
+    status = OR_NONFINITE;
+  } else if ((stop_rule == OR_STOP_REL_RES && r_prev <= tol) ||
+             (stop_rule == OR_STOP_NONE && max_sweeps == 0)) {
+    status = OR_OK;
+  } else {
+    for (int64_t s = 1; s <= max_sweeps; ++s) {
+      for (int64_t k = 0; k < n; ++k) {
+        const int64_t q = order[(s - 1) * n + k];
+        load_column(X, dt, lay, ld, m, q, xq);
+        double g = 0.0;
+        for (int64_t i = 0; i < m; ++i) g += xq[i] * e[i];
+        const double step = dq[q] > 0.0 ? g / dq[q] : 0.0;
+        for (int64_t i = 0; i < m; ++i) e[i] = e[i] - xq[i] * step;
+        a_out[q] = a_out[q] + step;
+      }
+      s_done = s;
+      const double r = norm2(e, m) / scale;
+      if (hist) hist[s] = r;
+      if (!isfinite(r)) { status = OR_NONFINITE; break; }
+      if ((stop_rule == OR_STOP_REL_RES && r <= tol) ||
+          (stop_rule == OR_STOP_REL_CHANGE && (r_prev == 0.0 || fabs(r_prev - r) < tol * r_prev)) ||
+          (stop_rule == OR_STOP_NONE && s == max_sweeps)) {
+        status = OR_OK;
+        break;
+      }
+      r_prev = r;
+    }
+  }
+  if (e_out)
+    for (int64_t i = 0; i < m; ++i) e_out[i] = e[i];
+  if (sweeps_done) *sweeps_done = s_done;
+  free(e); free(xq); free(dq);
+  return status;
+}

@@ -39,6 +39,10 @@ MUTANTS = {
     "select_argmax": ("if (j == 0 || E < best)", "if (j == 0 || E > best)"),
     "select_assign": ("a_out[jhat] += da[jhat];", "a_out[jhat] = da[jhat];"),
     "select_unsquared": ("E += r * r;", "E += r;"),
+    # given column order: the index ignored (natural order); the step applied
+    # to the coefficient of the wrong column
+    "order_ignored": ("const int64_t q = order[(s - 1) * n + k];", "const int64_t q = k;"),
+    "order_coef_of_step": ("a_out[q] = a_out[q] + step;", "a_out[k] = a_out[k] + step;"),
 }
 
 
@@ -119,6 +123,17 @@ def battery(lib):
     ok &= np.allclose(yc - Xc @ a_s, e, atol=1e-10)
     if not ok:
         failed.append("selection")
+
+    # given column order: a fixed permutation every sweep is Algorithm 1 on the
+    # permuted columns
+    pi = np.array([3, 0, 7, 5, 1, 6, 2, 4])
+    ap = solve(Xd[:, pi], y, tol=0, max_sweeps=2, stop="none").a
+    a_pi = np.empty(8)
+    a_pi[pi] = ap
+    ro = oracle.solve_order(np.ascontiguousarray(Xd.T), y, m=30, n=8, order=np.tile(pi, (2, 1)),
+                            dtype="f64", tol=0, max_sweeps=2, stop="none", lib=lib)
+    if not np.allclose(ro.a, a_pi, rtol=1e-10, atol=1e-12):
+        failed.append("order_permutation")
     return failed
 
 

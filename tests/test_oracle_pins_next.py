@@ -141,3 +141,70 @@ def test_reselection_accumulates_and_keeps_the_bookkeeping():
     e = y - X @ a
     assert np.linalg.norm(e) / np.linalg.norm(y) == pytest.approx(hist[-1], rel=1e-9)
     assert np.all(np.diff(hist) <= 1e-15)
+
+
+# ---------------- Algorithm 1 with a given column order (Sec. 2's random index variant) ----------------
+
+def order_solve(s, order, sweeps, **kw):
+    return oracle.solve_order(s.X, s.y, m=s.m, n=s.n, order=order, dtype=s.dtype, tol=0,
+                              max_sweeps=sweeps, stop="none", **kw)
+
+
+def test_natural_order_is_algorithm_1():
+    s = sys64(200, 30, 21)
+    order = np.tile(np.arange(30), (5, 1))
+    o1 = oracle.solve_system(s, tol=0, max_sweeps=5, stop="none")
+    o2 = order_solve(s, order, 5)
+    np.testing.assert_array_equal(o2.a, o1.a)
+    np.testing.assert_array_equal(o2.hist, o1.hist)
+
+
+def test_fixed_permutation_is_algorithm_1_on_permuted_columns():
+    """Taking the columns in the order pi every sweep is Algorithm 1 on the
+    system whose k-th column is X_pi(k); its k-th coefficient is a_pi(k)."""
+    s = sys64(150, 25, 22)
+    pi = np.random.default_rng(3).permutation(25)
+    Xp = np.ascontiguousarray(s.X[pi])  # column-major storage: row k of s.X is column k
+    op = oracle.solve(Xp, s.y, m=s.m, n=s.n, dtype="f64", tol=0, max_sweeps=4, stop="none")
+    oo = order_solve(s, np.tile(pi, (4, 1)), 4)
+    a = np.empty(25)
+    a[pi] = op.a
+    np.testing.assert_allclose(oo.a, a, rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(oo.hist, op.hist, rtol=1e-12)
+
+
+def test_repeated_index_sweep_is_one_projection():
+    """A sweep that takes the same column n times moves only that column, once:
+    after the first step <X_q, e> = 0, so the repeats add nothing."""
+    s = sys64(120, 10, 23)
+    X = s.dense_f64()
+    for q in (0, 4, 9):
+        o = order_solve(s, np.full((1, 10), q), 1, want_e=True)
+        a = np.zeros(10)
+        a[q] = X[:, q] @ s.y / (X[:, q] @ X[:, q])
+        np.testing.assert_allclose(o.a, a, rtol=1e-12, atol=1e-15)
+        assert abs(X[:, q] @ o.e) <= 1e-12 * np.linalg.norm(X[:, q]) * np.linalg.norm(s.y)
+
+
+def test_random_indices_bookkeeping_monotone_and_limit():
+    """Indices drawn with replacement: e = y - X·a, ||e|| never grows, the last
+    step's column is orthogonal to the residual, and the iterates reach the
+    least-squares solution."""
+    s = sys64(300, 20, 24)
+    X = s.dense_f64()
+    order = np.random.default_rng(4).integers(0, 20, size=(400, 20))
+    o = order_solve(s, order, 400, want_e=True)
+    np.testing.assert_allclose(o.e, s.y - X @ o.a, atol=1e-11 * np.linalg.norm(s.y))
+    assert np.all(np.diff(o.hist) <= 1e-15)
+    q = order[-1, -1]
+    assert abs(X[:, q] @ o.e) <= 1e-12 * np.linalg.norm(X[:, q]) * np.linalg.norm(s.y)
+    a_ls = np.linalg.lstsq(X, s.y, rcond=None)[0]
+    np.testing.assert_allclose(o.a, a_ls, rtol=1e-8, atol=1e-10)
+
+
+def test_order_rejects_indices_outside_the_columns():
+    s = sys64(50, 6, 25)
+    with pytest.raises(ValueError):
+        order_solve(s, np.full((2, 6), 6), 2)
+    with pytest.raises(ValueError):
+        order_solve(s, np.full((2, 6), -1), 2)
