@@ -95,6 +95,15 @@ typedef struct {
   int32_t kernel_launches; /* kernels launched by the solve */
 } hpscd_timing;
 
+/* Result of one solve of a batch (hpscd_batch_results) or of an asynchronous
+ * solve (hpscd_solve_async). */
+typedef struct {
+  int64_t sweeps;      /* sweeps made */
+  double rel_res;      /* hist[sweeps] */
+  int32_t status;      /* hpscd_status of the solve */
+  int32_t passes;      /* streaming passes over its X (sweeps + 1) */
+} hpscd_sys_result;
+
 typedef struct hpscd_ctx hpscd_ctx;
 
 /* Create a context bound to CUDA device `device` and stream `stream`
@@ -183,6 +192,48 @@ int hpscd_select(hpscd_ctx* ctx, const void* X, int dtype, int64_t m, int64_t n,
                  const float* y, float* a, const hpscd_opts* opts, int64_t* sel, double* hist,
                  int64_t* steps_done, double* final_rel_res);
 
+/*
+ * Algorithm 1 with the column of every step given (Sec. 2: instead of taking
+ * j = 1..n in turn, a step may take a randomly chosen index j).  Step k of
+ * sweep s (k = 0..n-1, s = 1..max_sweeps) applies the column step of Eq. da2 /
+ * Eq. ek1-ek to column order[(s-1)·n + k]; an index may repeat within a sweep
+ * and a column may be left out.  The caller draws the indices.
+ *   order  HOST int32[opts->max_sweeps · n], every entry in [0, n): copied to
+ *          the workspace before the launch; max_sweeps · n <= 2^28.
+ * A sweep is the restated pass of hpscd_solve with the substitution run over
+ * the steps (couplings G~[order_k][order_l], gathered) and the steps of each
+ * column summed in step order.  Float32 column-major X, n <= 512; refresh_every
+ * is honoured.  Other arguments, results and errors as hpscd_solve
+ * (INVALID_ARG for an index outside [0, n), UNSUPPORTED for bfloat16 X).
+ */
+int hpscd_solve_order(hpscd_ctx* ctx, const void* X, int dtype, int64_t m, int64_t n, int64_t ld,
+                      const float* y, float* a, int a_is_guess, const int32_t* order,
+                      const hpscd_opts* opts, double* hist, int64_t* sweeps_done,
+                      double* final_rel_res);
+
+/*
+ * Asynchronous form of hpscd_solve for column-major X (m >= 1, 1 <= n <= 512):
+ * enqueues the whole solve (set-up and sweep kernels) on the context's stream
+ * and returns without waiting, so that consecutive solves run back to back.
+ *   hist   DEVICE double[opts->max_sweeps + 1] or NULL: residual history.
+ *   res    DEVICE hpscd_sys_result, written when the solve has
+ *          finished: sweeps, rel_res, status (the hpscd_status hpscd_solve
+ *          would return), passes.
+ * X, y, a, hist and res must stay valid until the stream has passed the solve;
+ * solves on one context share its workspace and run in stream order.  The
+ * return value reports only argument and launch errors.  CUDA-event timings of
+ * the most recent asynchronous calls: hpscd_async_timings.
+ */
+int hpscd_solve_async(hpscd_ctx* ctx, const void* X, int dtype, int64_t m, int64_t n, int64_t ld,
+                      const float* y, float* a, int a_is_guess, const hpscd_opts* opts,
+                      double* hist, hpscd_sys_result* res);
+
+/* Waits for the context's stream, then writes the timings of the last `count`
+ * asynchronous solves (oldest first; 1 <= count <= 64 and <= the number of
+ * such calls made) to HOST out[count].  passes is -1 (it is in each call's
+ * result). */
+int hpscd_async_timings(hpscd_ctx* ctx, int64_t count, hpscd_timing* out);
+
 /* Same as hpscd_solve but X, y and a are HOST pointers: the call copies X and y
  * to the device workspace, solves, and copies a back (an end-to-end call). */
 int hpscd_solve_host(hpscd_ctx* ctx, const void* X, int dtype, int layout, int64_t m,
@@ -263,13 +314,7 @@ typedef struct {
   int32_t reserved;    /* must be zero */
 } hpscd_sys;
 
-/* Result of one system of a batch. */
-typedef struct {
-  int64_t sweeps;      /* sweeps made */
-  double rel_res;      /* hist[sweeps] */
-  int32_t status;      /* hpscd_status of this system */
-  int32_t passes;      /* streaming passes over its X (sweeps + 1) */
-} hpscd_sys_result;
+/* Result of one system of a batch: hpscd_sys_result (above). */
 
 /* Launch shape of a batch.  cluster = CTAs that share one system (1, 2, 4 or
  * 8; each CTA owns a slice of its rows and of its residual); 0 = let the

@@ -64,6 +64,26 @@ class SysResult(ctypes.Structure):
                 ("status", ctypes.c_int32), ("passes", ctypes.c_int32)]
 
 
+RESULT_BYTES = ctypes.sizeof(SysResult)
+
+
+def results_buffer(count: int, device=None):
+    """A CUDA buffer for `count` hpscd_sys_result records (rows of RESULT_BYTES bytes)."""
+    import torch
+    return torch.zeros((int(count), RESULT_BYTES), dtype=torch.uint8,
+                       device=device if device is not None else "cuda")
+
+
+def read_results(buf) -> dict:
+    """sweeps / rel_res / status / passes of the records in a results_buffer."""
+    raw = np.ascontiguousarray(buf.cpu().numpy()).reshape(-1, RESULT_BYTES)
+    rec = np.frombuffer(raw.tobytes(), dtype=np.dtype([("sweeps", "<i8"), ("rel_res", "<f8"),
+                                                       ("status", "<i4"), ("passes", "<i4")]))
+    return {"sweeps": rec["sweeps"].copy(), "rel_res": rec["rel_res"].copy(),
+            "status": [STATUS.get(int(c), str(int(c))) for c in rec["status"]],
+            "passes": rec["passes"].copy()}
+
+
 class Tuning(ctypes.Structure):
     _fields_ = [("cluster", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
 
@@ -91,12 +111,22 @@ SIGNATURES = {
                             ctypes.c_int, ctypes.c_int64, ctypes.POINTER(Opts), ctypes.c_void_p,
                             ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)],
                            ctypes.c_int),
+    "hpscd_solve_order": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int64,
+                           ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                           ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(Opts), ctypes.c_void_p,
+                           ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)],
+                          ctypes.c_int),
     "hpscd_select": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int64,
                       ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
                       ctypes.POINTER(Opts), ctypes.c_void_p, ctypes.c_void_p,
                       ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)],
                      ctypes.c_int),
     "hpscd_last_timing": ([ctypes.c_void_p, ctypes.POINTER(Timing)], ctypes.c_int),
+    "hpscd_solve_async": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int64,
+                           ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                           ctypes.c_int, ctypes.POINTER(Opts), ctypes.c_void_p, ctypes.c_void_p],
+                          ctypes.c_int),
+    "hpscd_async_timings": ([ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(Timing)], ctypes.c_int),
     "hpscd_gram": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_int64,
                     ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int], ctypes.c_int),
     "hpscd_solve_noalloc": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int64,
@@ -310,6 +340,45 @@ class Context:
         return {"setup_ms": t.setup_ms, "sweep_ms": t.sweep_ms, "passes": t.passes,
                 "x_bytes": t.x_bytes, "grid": t.grid, "kernel_launches": t.kernel_launches}
 
+    def solve_async(self, X, y, res, *, tol=1e-6, max_sweeps=1000, stop="rel_res", a0=None,
+                    out=None, hist=None):
+        """Enqueue a solve of column-major CUDA X on the current stream and return at
+        once (hpscd_solve_async).  res: a CUDA tensor of RESULT_BYTES bytes (e.g. a
+        row of results_buffer(k)) that receives sweeps / rel_res / status / passes
+        when the solve has finished; hist: optional CUDA float64 (max_sweeps + 1,).
+        Returns the coefficient tensor (valid once the stream has passed the solve)."""
+        import torch
+        ptr, dt, lay, m, n, ld = _describe(X)
+        if lay != COL or not X.is_cuda:
+            raise ValueError("solve_async needs a column-major CUDA X")
+        if not (res.is_cuda and res.is_contiguous() and res.numel() * res.element_size() >= RESULT_BYTES):
+            raise TypeError("res must be a contiguous CUDA buffer of at least RESULT_BYTES bytes")
+        if hist is not None and not (hist.is_cuda and hist.dtype == torch.float64 and
+                                     hist.numel() >= int(max_sweeps) + 1):
+            raise TypeError("hist must be a CUDA float64 tensor of max_sweeps + 1 entries")
+        a = out if out is not None else torch.empty(n, dtype=torch.float32, device=X.device)
+        if a0 is not None:
+            a.copy_(a0)
+        o = make_opts(tol, max_sweeps, stop)
+        self.set_stream(torch.cuda.current_stream(X.device))
+        rc = self._lib.hpscd_solve_async(self._h, ctypes.c_void_p(ptr), dt, m, n, ld,
+                                         ctypes.c_void_p(y.data_ptr()), ctypes.c_void_p(a.data_ptr()),
+                                         1 if a0 is not None else 0, ctypes.byref(o),
+                                         ctypes.c_void_p(hist.data_ptr() if hist is not None else 0),
+                                         ctypes.c_void_p(res.data_ptr()))
+        if rc:
+            raise HpscdError(rc, "hpscd_solve_async")
+        return a
+
+    def async_timings(self, count: int) -> list:
+        """Timings of the last `count` asynchronous solves (waits for the stream)."""
+        ts = (Timing * int(count))()
+        rc = self._lib.hpscd_async_timings(self._h, int(count), ts)
+        if rc:
+            raise HpscdError(rc, "hpscd_async_timings")
+        return [{"setup_ms": t.setup_ms, "sweep_ms": t.sweep_ms, "x_bytes": t.x_bytes, "grid": t.grid,
+                 "kernel_launches": t.kernel_launches} for t in ts]
+
     def workspace_size(self, m, n, dtype="f32", layout="col", **opt_kw) -> int:
         o = make_opts(**opt_kw)
         b = ctypes.c_size_t(0)
@@ -370,6 +439,36 @@ class Context:
                                           1 if a0 is not None else 0, int(thr), ctypes.byref(o),
                                           hist.ctypes.data_as(ctypes.c_void_p), ctypes.byref(sw),
                                           ctypes.byref(rr))
+        return self._finish(rc, hist, sw, rr, a)
+
+    def solve_order(self, X, y, order, *, tol=1e-6, max_sweeps=None, stop="rel_res", a0=None,
+                    out=None) -> SolveResult:
+        """Algorithm 1 with the column of every step given: step k of sweep s takes
+        column order[s-1][k] (order: integer array (max_sweeps, n) on the host,
+        entries in [0, n), e.g. drawn at random with replacement)."""
+        import torch
+        ptr, dt, lay, m, n, ld = _describe(X)
+        if lay != COL or not X.is_cuda:
+            raise ValueError("solve_order needs a column-major CUDA X")
+        ordr = np.ascontiguousarray(np.asarray(order, dtype=np.int32).reshape(-1, n) if n else
+                                    np.zeros((0, 0), np.int32))
+        if max_sweeps is None:
+            max_sweeps = ordr.shape[0]
+        if ordr.size != int(max_sweeps) * n:
+            raise ValueError("order must hold max_sweeps rows of n indices")
+        a = out if out is not None else torch.empty(n, dtype=torch.float32, device=X.device)
+        if a0 is not None:
+            a.copy_(a0)
+        o = make_opts(tol, max_sweeps, stop)
+        hist = np.full(int(max_sweeps) + 1, np.nan)
+        sw, rr = ctypes.c_int64(0), ctypes.c_double(0.0)
+        self.set_stream(torch.cuda.current_stream(X.device))
+        rc = self._lib.hpscd_solve_order(self._h, ctypes.c_void_p(ptr), dt, m, n, ld,
+                                         ctypes.c_void_p(y.data_ptr()), ctypes.c_void_p(a.data_ptr()),
+                                         1 if a0 is not None else 0,
+                                         ordr.ctypes.data_as(ctypes.c_void_p), ctypes.byref(o),
+                                         hist.ctypes.data_as(ctypes.c_void_p), ctypes.byref(sw),
+                                         ctypes.byref(rr))
         return self._finish(rc, hist, sw, rr, a)
 
     def select(self, X, y, F: int, *, tol=0.0, stop="none"):

@@ -21,6 +21,13 @@ struct hpscd_ctx {
   unsigned long long* trace_dev = nullptr;
   int trace_grid = 0;
   PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  // asynchronous solves: CUDA events of the most recent calls (set-up start,
+  // sweep start, sweep end) in a ring, created on the first such call, and
+  // what each call launched
+  static constexpr int RING = 64;
+  cudaEvent_t ring_ev[RING][3] = {};
+  hpscd_timing ring_info[RING] = {};
+  int64_t ring_calls = 0;
   // batches and networks made on this context: hpscd_destroy while any is
   // alive only marks the context closing; the last one to go frees it
   int children = 0;

@@ -30,7 +30,7 @@ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 struct Layout {
   size_t G = 0, Gt = 0, dvec = 0, partial = 0, e = 0, hacc = 0, npart = 0, gw = 0, ypart = 0, hist = 0,
-         ctl = 0, sel = 0;
+         ctl = 0, sel = 0, order = 0;
   size_t xcopy = 0, ycopy = 0, acopy = 0, total = 0;
 };
 
@@ -71,7 +71,7 @@ int check_shape(int dtype, int layout, int64_t m, int64_t n, int64_t ld) {
 
 // Sizes the workspace of a solve.  Returns false for unsupported shapes.
 int make_plan(const hpscd_ctx* ctx, int dtype, int layout, int64_t m, int64_t n, int64_t ld,
-              const hpscd_opts* o, bool host_copies, Plan* P) {
+              const hpscd_opts* o, bool host_copies, Plan* P, int64_t order_entries = 0) {
   if (layout != HPSCD_COL_MAJOR) return HPSCD_ERR_UNSUPPORTED;
   if (n > 512) return HPSCD_ERR_UNSUPPORTED;
   if (!tall_config(dtype, (int)n, ctx->max_smem, &P->cfg)) return HPSCD_ERR_UNSUPPORTED;
@@ -103,6 +103,7 @@ int make_plan(const hpscd_ctx* ctx, int dtype, int layout, int64_t m, int64_t n,
   L.hist = take((size_t)(o->max_sweeps + 1) * sizeof(double));
   L.ctl = take(sizeof(GridCtl));
   L.sel = take((size_t)(o->max_sweeps + 1) * sizeof(int64_t));
+  L.order = take((size_t)(order_entries > 0 ? order_entries : 1) * sizeof(int32_t));
   if (host_copies) {
     L.xcopy = take((size_t)(n > 0 ? n : 1) * (size_t)ld * esize(dtype));
     L.ycopy = take((size_t)(m > 0 ? m : 1) * sizeof(float));
@@ -328,22 +329,36 @@ int solve_empty_rows(hpscd_ctx* ctx, int64_t n, float* a, int a_is_guess, const 
   return HPSCD_OK;
 }
 
+// Result of an asynchronous solve, written after the sweep kernel has finished
+// (every CTA's error report has landed in the control block by then).
+__global__ void copy_result_kernel(const GridCtl* ctl, hpscd_sys_result* res) {
+  res->sweeps = ctl->sweeps;
+  res->rel_res = ctl->final_res;
+  res->status = ctl->err != DEV_OK ? HPSCD_ERR_TIMEOUT : ctl->status;
+  res->passes = (int32_t)ctl->passes;
+}
+
 // The variants of the sweep: Algorithm 1 (thr <= 1, select = 0), Algorithm 2
 // (blocks of thr columns from one residual) and Algorithm 3 (select = 1: one
 // greedily chosen column per pass; sel receives the choices, HOST int64[max_sweeps]).
 int solve_device(hpscd_ctx* ctx, const void* X, int dtype, int layout, int64_t m, int64_t n,
                  int64_t ld, const float* y, float* a, int a_is_guess, const hpscd_opts* o,
                  double* hist, int64_t* sweeps_done, double* final_rel_res, const Plan& P,
-                 int thr = 0, int select = 0, int64_t* sel = nullptr) {
+                 int thr = 0, int select = 0, int64_t* sel = nullptr, const int* order = nullptr,
+                 hpscd_sys_result* async_res = nullptr, double* hist_dev = nullptr) {
   if (m == 0) return solve_empty_rows(ctx, n, a, a_is_guess, o, hist, sweeps_done, final_rel_res);
   char* ws = static_cast<char*>(ctx->ws);
   const Layout& L = P.L;
   float* G = reinterpret_cast<float*>(ws + L.G);
   GridCtl* ctl = reinterpret_cast<GridCtl*>(ws + L.ctl);
   cudaStream_t st = ctx->stream;
+  // an asynchronous call records its events in the ring and returns after the launches
+  const bool async = async_res != nullptr;
+  const int slot = (int)(ctx->ring_calls % hpscd_ctx::RING);
+  cudaEvent_t* ev = async ? ctx->ring_ev[slot] : ctx->ev;
 
   if (cudaMemsetAsync(ctl, 0, sizeof(GridCtl), st) != cudaSuccess) return HPSCD_ERR_CUDA;
-  if (cudaEventRecord(ctx->ev[0], st) != cudaSuccess) return HPSCD_ERR_CUDA;
+  if (cudaEventRecord(ev[0], st) != cudaSuccess) return HPSCD_ERR_CUDA;
   int gram_launches = 0;
   float* Gt = reinterpret_cast<float*>(ws + L.Gt);
   float* dvec = reinterpret_cast<float*>(ws + L.dvec);
@@ -352,7 +367,7 @@ int solve_device(hpscd_ctx* ctx, const void* X, int dtype, int layout, int64_t m
   if (rcg != HPSCD_OK) return rcg;
   if (cudaMemsetAsync(ws + L.hacc, 0, (size_t)3 * P.cfg.npad * sizeof(double), st) != cudaSuccess)
     return HPSCD_ERR_CUDA;
-  if (cudaEventRecord(ctx->ev[1], st) != cudaSuccess) return HPSCD_ERR_CUDA;
+  if (cudaEventRecord(ev[1], st) != cudaSuccess) return HPSCD_ERR_CUDA;
 
   CUtensorMap map;
   memset(&map, 0, sizeof(map));
@@ -375,7 +390,7 @@ int solve_device(hpscd_ctx* ctx, const void* X, int dtype, int layout, int64_t m
   p.npart = reinterpret_cast<double*>(ws + L.npart);
   p.gw = reinterpret_cast<float*>(ws + L.gw);
   p.ypart = reinterpret_cast<double*>(ws + L.ypart);
-  p.hist = reinterpret_cast<double*>(ws + L.hist);
+  p.hist = hist_dev ? hist_dev : reinterpret_cast<double*>(ws + L.hist);
   p.ctl = ctl;
   p.tol = o->tol;
   p.max_sweeps = o->max_sweeps;
@@ -389,6 +404,7 @@ int solve_device(hpscd_ctx* ctx, const void* X, int dtype, int layout, int64_t m
   p.thr = thr;
   p.select = select;
   p.sel_out = select ? reinterpret_cast<int64_t*>(ws + L.sel) : nullptr;
+  p.order = order;
   p.trace = nullptr;
   p.trace_passes = 0;
   if (ctx->trace_passes > 0 && ctx->trace_dev) {
@@ -403,7 +419,19 @@ int solve_device(hpscd_ctx* ctx, const void* X, int dtype, int layout, int64_t m
     cudaGetLastError();
     return HPSCD_ERR_CUDA;
   }
-  if (cudaEventRecord(ctx->ev[2], st) != cudaSuccess) return HPSCD_ERR_CUDA;
+  if (cudaEventRecord(ev[2], st) != cudaSuccess) return HPSCD_ERR_CUDA;
+  if (async) {
+    copy_result_kernel<<<1, 1, 0, st>>>(ctl, async_res);
+    if (cudaGetLastError() != cudaSuccess) return HPSCD_ERR_CUDA;
+    hpscd_timing& t = ctx->ring_info[slot];
+    t = hpscd_timing{};
+    t.passes = -1;
+    t.x_bytes = m * n * esize(dtype);
+    t.grid = P.grid;
+    t.kernel_launches = gram_launches + 2;
+    ++ctx->ring_calls;
+    return HPSCD_OK;
+  }
   if (cudaMemcpyAsync(ctx->ctl_host, ctl, sizeof(GridCtl), cudaMemcpyDeviceToHost, st) != cudaSuccess)
     return HPSCD_ERR_CUDA;
   if (cudaStreamSynchronize(st) != cudaSuccess) return HPSCD_ERR_CUDA;
@@ -444,6 +472,9 @@ void free_ctx(hpscd_ctx* ctx) {
   if (ctx->ws && ctx->ws_owned) cudaFree(ctx->ws);
   for (int i = 0; i < 3; ++i)
     if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
+  for (int r = 0; r < hpscd_ctx::RING; ++r)
+    for (int i = 0; i < 3; ++i)
+      if (ctx->ring_ev[r][i]) cudaEventDestroy(ctx->ring_ev[r][i]);
   if (ctx->ctl_host) cudaFreeHost(ctx->ctl_host);
   if (ctx->trace_dev) cudaFree(ctx->trace_dev);
   delete ctx;
@@ -612,6 +643,82 @@ int hpscd_select(hpscd_ctx* ctx, const void* X, int dtype, int64_t m, int64_t n,
   if ((rc = ensure_ws(ctx, P.L.total))) return rc;
   return solve_device(ctx, X, dtype, HPSCD_COL_MAJOR, m, n, ld, y, a, 0, opts, hist, steps_done,
                       final_rel_res, P, 0, 1, sel);
+}
+
+int hpscd_solve_order(hpscd_ctx* ctx, const void* X, int dtype, int64_t m, int64_t n, int64_t ld,
+                      const float* y, float* a, int a_is_guess, const int32_t* order,
+                      const hpscd_opts* opts, double* hist, int64_t* sweeps_done,
+                      double* final_rel_res) {
+  if (!ctx) return HPSCD_ERR_INVALID_ARG;
+  int rc = check_opts(opts);
+  if (rc) return rc;
+  if ((rc = check_shape(dtype, HPSCD_COL_MAJOR, m, n, ld))) return rc;
+  if ((m > 0 && n > 0 && !X) || (m > 0 && !y) || (n > 0 && !a)) return HPSCD_ERR_INVALID_ARG;
+  if (n > 0 && opts->max_sweeps > ((int64_t)1 << 28) / n) return HPSCD_ERR_UNSUPPORTED;
+  const int64_t entries = opts->max_sweeps * n;
+  if (entries > 0 && !order) return HPSCD_ERR_INVALID_ARG;
+  for (int64_t k = 0; k < entries; ++k)
+    if (order[k] < 0 || order[k] >= n) return HPSCD_ERR_INVALID_ARG;
+  if (dtype != HPSCD_F32) return HPSCD_ERR_UNSUPPORTED;
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return HPSCD_ERR_CUDA;
+  Plan P;
+  if ((rc = make_plan(ctx, dtype, HPSCD_COL_MAJOR, m, n, ld, opts, false, &P, entries))) return rc;
+  if ((rc = ensure_ws(ctx, P.L.total))) return rc;
+  int* order_dev = reinterpret_cast<int*>(static_cast<char*>(ctx->ws) + P.L.order);
+  if (entries > 0 && cudaMemcpyAsync(order_dev, order, (size_t)entries * sizeof(int32_t),
+                                     cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return HPSCD_ERR_CUDA;
+  }
+  return solve_device(ctx, X, dtype, HPSCD_COL_MAJOR, m, n, ld, y, a, a_is_guess, opts, hist,
+                      sweeps_done, final_rel_res, P, 0, 0, nullptr, order_dev);
+}
+
+int hpscd_solve_async(hpscd_ctx* ctx, const void* X, int dtype, int64_t m, int64_t n, int64_t ld,
+                      const float* y, float* a, int a_is_guess, const hpscd_opts* opts,
+                      double* hist, hpscd_sys_result* res) {
+  if (!ctx || !res) return HPSCD_ERR_INVALID_ARG;
+  int rc = check_opts(opts);
+  if (rc) return rc;
+  if ((rc = check_shape(dtype, HPSCD_COL_MAJOR, m, n, ld))) return rc;
+  if (m < 1 || n < 1 || !X || !y || !a) return HPSCD_ERR_INVALID_ARG;
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return HPSCD_ERR_CUDA;
+  if (!ctx->ring_ev[0][0]) {
+    for (int r = 0; r < hpscd_ctx::RING; ++r)
+      for (int i = 0; i < 3; ++i)
+        if (cudaEventCreate(&ctx->ring_ev[r][i]) != cudaSuccess) {
+          cudaGetLastError();
+          return HPSCD_ERR_CUDA;
+        }
+  }
+  Plan P;
+  if ((rc = make_plan(ctx, dtype, HPSCD_COL_MAJOR, m, n, ld, opts, false, &P))) return rc;
+  if ((rc = ensure_ws(ctx, P.L.total))) return rc;
+  return solve_device(ctx, X, dtype, HPSCD_COL_MAJOR, m, n, ld, y, a, a_is_guess, opts, nullptr,
+                      nullptr, nullptr, P, 0, 0, nullptr, nullptr, res, hist);
+}
+
+int hpscd_async_timings(hpscd_ctx* ctx, int64_t count, hpscd_timing* out) {
+  if (!ctx || !out || count < 1 || count > hpscd_ctx::RING || count > ctx->ring_calls)
+    return HPSCD_ERR_INVALID_ARG;
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return HPSCD_ERR_CUDA;
+  if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return HPSCD_ERR_CUDA;
+  }
+  for (int64_t k = 0; k < count; ++k) {
+    const int slot = (int)((ctx->ring_calls - count + k) % hpscd_ctx::RING);
+    out[k] = ctx->ring_info[slot];
+    if (cudaEventElapsedTime(&out[k].setup_ms, ctx->ring_ev[slot][0], ctx->ring_ev[slot][1]) != cudaSuccess ||
+        cudaEventElapsedTime(&out[k].sweep_ms, ctx->ring_ev[slot][1], ctx->ring_ev[slot][2]) != cudaSuccess) {
+      cudaGetLastError();
+      return HPSCD_ERR_CUDA;
+    }
+  }
+  return HPSCD_OK;
 }
 
 int hpscd_solve_host(hpscd_ctx* ctx, const void* X, int dtype, int layout, int64_t m,

@@ -55,6 +55,14 @@ __device__ __forceinline__ float zero_elem<float>() { return 0.f; }
 template <>
 __device__ __forceinline__ uint16_t zero_elem<uint16_t>() { return 0; }
 
+// Row segment of the couplings of one step to the 32 steps of a block, for a
+// given column order: g[k] = row[oc[k]] (oc: the block's columns), 0 past lim.
+__device__ __forceinline__ void gather_seg32(const float* __restrict__ row, const int* oc, int lim,
+                                             float (&g)[32]) {
+#pragma unroll
+  for (int k = 0; k < 32; ++k) g[k] = (k < lim) ? __ldg(row + oc[k]) : 0.f;
+}
+
 __device__ __forceinline__ void load_seg32(const float* __restrict__ src, float (&g)[32]) {
   const float4* row = reinterpret_cast<const float4*>(src);
 #pragma unroll
@@ -121,9 +129,13 @@ __device__ __forceinline__ bool warp_wait_flag(const int* flag, int want, uint64
 // (Algorithm 2) the couplings inside a block of thr columns are masked.
 // flags: [0] blocks solved, [1 + w] warp w's rows ready; r (in: g ⊘ d) and da
 // are shared arrays of length npad.  Returns false when a wait gave up.
+// ORD: the unknowns are the steps of a given column order (o: step -> column,
+// shared, -1 past n): step t couples to earlier step l through G~[o_t][o_l];
+// diag_s then holds the gathered diagonal blocks of this sweep.
+template <bool ORD>
 __device__ bool forward_substitution(const float* __restrict__ Gt, int ldG, int n, int npad,
                                      float* r, float* da, const float* diag_s, int thr,
-                                     int* flags, uint64_t timeout_ns) {
+                                     int* flags, uint64_t timeout_ns, const int* o = nullptr) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   for (int c = n + tid; c < npad; c += NT) da[c] = 0.f;
   if (tid <= NW) flags[tid] = 0;
@@ -153,8 +165,13 @@ __device__ bool forward_substitution(const float* __restrict__ Gt, int ldG, int 
     const int t = tid;
     float rt = (t < n) ? r[t] : 0.f;
     float seg[32];
-    load_seg32(Gt + (int64_t)(t < n ? t : 0) * ldG, seg);
-    mask_seg32(seg, t, 0, thr);
+    const float* grow = Gt + (int64_t)(t < n ? (ORD ? o[t] : t) : 0) * ldG;
+    if constexpr (ORD) {
+      gather_seg32(grow, o, n, seg);
+    } else {
+      load_seg32(grow, seg);
+      mask_seg32(seg, t, 0, thr);
+    }
     for (int b = 0; b < warp; ++b) {
       if (!warp_wait_flag(&flags[0], b + 1, timeout_ns)) { ok = false; break; }
       const float* dab = da + 32 * b;
@@ -168,8 +185,12 @@ __device__ bool forward_substitution(const float* __restrict__ Gt, int ldG, int 
       }
       rt -= (a0 + a1) + (a2 + a3);
       if (b + 1 < warp) {
-        load_seg32(Gt + (int64_t)(t < n ? t : 0) * ldG + 32 * (b + 1), seg);
-        mask_seg32(seg, t, 32 * (b + 1), thr);
+        if constexpr (ORD) {
+          gather_seg32(grow, o + 32 * (b + 1), n - 32 * (b + 1), seg);
+        } else {
+          load_seg32(grow + 32 * (b + 1), seg);
+          mask_seg32(seg, t, 32 * (b + 1), thr);
+        }
       }
     }
     if (t < npad) r[t] = rt;
@@ -289,7 +310,7 @@ __device__ __forceinline__ void chunk_compute(const T* __restrict__ st, int warp
   }
 }
 
-template <typename T, int CW, int NCH>
+template <typename T, int CW, int NCH, bool ORD>
 __global__ void __launch_bounds__(NT, 1)
     tall_sweep_kernel(const __grid_constant__ CUtensorMap tmap, const TallParams p) {
   constexpr int C = NW * CW;          // columns per chunk
@@ -609,10 +630,44 @@ __global__ void __launch_bounds__(NT, 1)
       // scratch for the argmax: the row-sum buffer is free between passes
       const int jhat = select_step(n, NPAD, rvec, dd_s, da_s, red_hi, reinterpret_cast<int*>(red_lo));
       if (blockIdx.x == 0 && tid == 0 && p.sel_out) p.sel_out[pass] = jhat;
+    } else if constexpr (ORD) {
+      // the steps of sweep pass + 1 take the columns order[pass·n + k]: gather
+      // their r and the diagonal blocks of their couplings, substitute over the
+      // steps, then sum the steps of each column in step order (identical in
+      // every CTA).  Between passes the row-sum buffer holds the steps' da and
+      // columns, vsm their r; the flags live in red_lo as in the plain sweep.
+      float* dstep = red_hi;
+      int* o_s = reinterpret_cast<int*>(red_hi + NPAD);
+      float* rstep = vsm;
+      const int* ord = p.order + (size_t)pass * n;
+      for (int k = tid; k < NPAD; k += NT) o_s[k] = k < n ? __ldg(ord + k) : -1;
+      named_sync(NT);
+      for (int k = tid; k < NPAD; k += NT) rstep[k] = k < n ? rvec[o_s[k]] : 0.f;
+      for (int idx = tid; idx < ((n + 31) / 32) * DIAG_PACK; idx += NT) {
+        const int b = idx / DIAG_PACK, q = idx % DIAG_PACK;
+        int i = 1;
+        while ((i * (i + 1)) / 2 <= q) ++i;
+        const int k = q - (i * (i - 1)) / 2;
+        diag_s[idx] = (32 * b + i < n) ? __ldg(p.Gt + (int64_t)o_s[32 * b + i] * p.ldG + o_s[32 * b + k])
+                                       : 0.f;
+      }
+      if (!forward_substitution<true>(p.Gt, p.ldG, n, NPAD, rstep, dstep, diag_s, 1,
+                                      reinterpret_cast<int*>(red_lo), p.timeout_ns, o_s)) {
+        err = DEV_TIMEOUT_BARRIER;
+        break;
+      }
+      for (int c = tid; c < NPAD; c += NT) {
+        float acc = 0.f;
+        if (c < n)
+          for (int k = 0; k < n; ++k)
+            if (o_s[k] == c) acc += dstep[k];
+        da_s[c] = acc;
+      }
+      named_sync(NT);
     } else {
       // the row-sum buffers are free between passes: flags of the substitution
-      if (!forward_substitution(p.Gt, p.ldG, n, NPAD, rvec, da_s, diag_s, p.thr,
-                                reinterpret_cast<int*>(red_lo), p.timeout_ns)) {
+      if (!forward_substitution<false>(p.Gt, p.ldG, n, NPAD, rvec, da_s, diag_s, p.thr,
+                                       reinterpret_cast<int*>(red_lo), p.timeout_ns)) {
         err = DEV_TIMEOUT_BARRIER;
         break;
       }
@@ -652,10 +707,10 @@ __global__ void __launch_bounds__(NT, 1)
   }
 }
 
-template <typename T, int CW, int NCH>
+template <typename T, int CW, int NCH, bool ORD = false>
 cudaError_t launch_one(const TallConfig& cfg, const CUtensorMap* tmap, const TallParams& p,
                        int grid, cudaStream_t stream) {
-  auto kern = tall_sweep_kernel<T, CW, NCH>;
+  auto kern = tall_sweep_kernel<T, CW, NCH, ORD>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        cfg.smem_bytes);
   if (e != cudaSuccess) return e;
@@ -723,6 +778,18 @@ cudaError_t launch_tall_sweep(int dtype, const TallConfig& cfg, const CUtensorMa
                               const TallParams& p, int grid, cudaStream_t stream) {
 #define HPSCD_TALL_CASE(T, W, N)                                        \
   if (cfg.cpw == W && cfg.rpl == N) return launch_one<T, W, N>(cfg, tmap, p, grid, stream);
+#define HPSCD_TALL_ORD_CASE(W, N)                                       \
+  if (cfg.cpw == W && cfg.rpl == N) return launch_one<float, W, N, true>(cfg, tmap, p, grid, stream);
+  if (p.order) {  // the given-order variant: float32 only
+    if (dtype != HPSCD_F32) return cudaErrorInvalidValue;
+    HPSCD_TALL_ORD_CASE(1, 1)
+    HPSCD_TALL_ORD_CASE(2, 1)
+    HPSCD_TALL_ORD_CASE(4, 1)
+    HPSCD_TALL_ORD_CASE(4, 2)
+    HPSCD_TALL_ORD_CASE(4, 4)
+    HPSCD_TALL_ORD_CASE(4, 8)
+    return cudaErrorInvalidConfiguration;
+  }
   if (dtype == HPSCD_F32) {
     HPSCD_TALL_CASE(float, 1, 1)
     HPSCD_TALL_CASE(float, 2, 1)
@@ -739,6 +806,7 @@ cudaError_t launch_tall_sweep(int dtype, const TallConfig& cfg, const CUtensorMa
     HPSCD_TALL_CASE(uint16_t, 8, 4)
   }
 #undef HPSCD_TALL_CASE
+#undef HPSCD_TALL_ORD_CASE
   return cudaErrorInvalidConfiguration;
 }
 

@@ -108,8 +108,10 @@ def _matvec_f64(sysm: System, a: np.ndarray) -> np.ndarray:
 
 
 def make_system(m: int, n: int, seed: int = 0, *, layout: str = "col", dtype: str = "f32",
-                noise: float = 0.0, consistent_rhs_dtype: str = "f32") -> System:
-    """X iid N(0,1), a_true iid U(-1,1), y = X·a_true + noise·N(0,1).
+                noise: float = 0.0, consistent_rhs_dtype: str = "f32", scale: float = 1.0,
+                diag: float = 0.0) -> System:
+    """X = scale·Z + diag·I with Z iid N(0,1) (I the m x n identity), a_true iid
+    U(-1,1), y = X·a_true + noise·N(0,1).
 
     The system solved is the STORED X (after rounding to the storage dtype);
     y is formed from those stored values in float64 and then rounded to
@@ -117,12 +119,23 @@ def make_system(m: int, n: int, seed: int = 0, *, layout: str = "col", dtype: st
     if layout not in ("col", "row") or dtype not in ("f32", "bf16", "f64"):
         raise ValueError("bad layout/dtype")
     shape = (n, m) if layout == "col" else (m, n)
+
+    def shaped(Z):
+        if scale != 1.0:
+            Z *= Z.dtype.type(scale)
+        if diag:
+            k = min(m, n)
+            Z.reshape(-1)[: k * (shape[1] + 1): shape[1] + 1] += Z.dtype.type(diag)
+        return Z
+
     if dtype == "f64":
         X = np.empty(shape, dtype=np.float64)
         _fill_chunks(X.reshape(-1), seed, 1, "normal")
+        X = shaped(X)
     else:
         Xf = np.empty(shape, dtype=np.float32)
         _fill_chunks(Xf.reshape(-1), seed, 1, "normal")
+        Xf = shaped(Xf)
         X = f32_to_bf16_bits(Xf).reshape(shape) if dtype == "bf16" else Xf
     a_true = np.empty(n, dtype=np.float64)
     _fill_chunks(a_true, seed, 2, "uniform", -1.0, 1.0)
@@ -148,6 +161,11 @@ WORKLOADS = {
     "wide_2000x200k_f32": dict(m=2000, n=200_000, layout="row", dtype="f32", noise=0.0),
     # tall, consistent, bfloat16 storage (4.1 GB of X)
     "tall_4Mx512_bf16": dict(m=4_000_000, n=512, layout="col", dtype="bf16", noise=0.0),
+    # square, consistent, float32 row-major (67 MB of X): I + 0.5·Z/sqrt(n), whose
+    # singular values lie in about [0.5, 1.5], so the sweep converges in tens of
+    # sweeps (a square Gaussian X has cond ~ n and the sweep barely moves)
+    "square_4096_f32": dict(m=4096, n=4096, layout="row", dtype="f32", noise=0.0,
+                            scale=0.5 / 64.0, diag=1.0),
 }
 
 

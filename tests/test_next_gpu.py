@@ -116,3 +116,67 @@ def test_full_size_blocks_and_selection(ctx):
     osel, oa, ohist = oracle.select(s.X, s.y, m=s.m, n=s.n, F=20)
     np.testing.assert_array_equal(sel, osel)
     np.testing.assert_allclose(r.hist, ohist, rtol=1e-5)
+
+
+# ---- Algorithm 1 with the column of every step given (Sec. 2's random-index variant) ----
+
+@pytest.mark.parametrize("m,n,kind", [(2000, 256, "replace"), (2000, 256, "perm"), (777, 130, "replace"),
+                                      (333, 40, "perm"), (4099, 97, "replace"), (5000, 512, "replace"),
+                                      (300, 33, "same")])
+def test_order_equal_sweeps_match_oracle(ctx, m, n, kind):
+    s = synth.make_system(m, n, seed=m + n, noise=0.05)
+    X, y = to_gpu(s)
+    g = np.random.default_rng(m)
+    sweeps = 4
+    if kind == "replace":
+        order = g.integers(0, n, size=(sweeps, n))
+    elif kind == "perm":
+        order = np.stack([g.permutation(n) for _ in range(sweeps)])
+    else:
+        order = np.full((sweeps, n), n // 2)
+    for k in (1, sweeps):
+        r = ctx.solve_order(X, y, order[:k], tol=0, stop="none")
+        o = oracle.solve_order(s.X, s.y, m=m, n=n, order=order[:k], tol=0, max_sweeps=k, stop="none")
+        assert r.status == "ok" and r.sweeps == k
+        assert rel(r.a.cpu().numpy(), o.a) <= 1e-5, (m, n, kind, k)
+        np.testing.assert_allclose(r.hist, o.hist, rtol=1e-5, atol=1e-7)
+
+
+def test_natural_order_is_the_plain_sweep(ctx):
+    s = synth.make_system(3000, 200, seed=13, noise=0.05)
+    X, y = to_gpu(s)
+    r1 = ctx.solve(X, y, tol=0, max_sweeps=5, stop="none")
+    r2 = ctx.solve_order(X, y, np.tile(np.arange(200), (5, 1)), tol=0, stop="none")
+    assert torch.equal(r1.a, r2.a)
+    np.testing.assert_array_equal(r1.hist, r2.hist)
+
+
+def test_order_stopping_rule_warm_start_and_bad_index(ctx):
+    s = synth.make_system(4000, 128, seed=17, noise=0.05)
+    X, y = to_gpu(s)
+    order = np.random.default_rng(2).integers(0, 128, size=(200, 128))
+    r = ctx.solve_order(X, y, order, tol=1e-7, stop="rel_change")
+    o = oracle.solve_order(s.X, s.y, m=s.m, n=s.n, order=order, tol=1e-7, max_sweeps=200,
+                           stop="rel_change")
+    assert r.status == "ok" and abs(r.sweeps - o.sweeps) <= 1
+    a0 = (s.a_true + 0.1).astype(np.float32)
+    r = ctx.solve_order(X, y, order[:3], tol=0, stop="none", a0=torch.from_numpy(a0).cuda())
+    o = oracle.solve_order(s.X, s.y, m=s.m, n=s.n, order=order[:3], a0=a0, tol=0, max_sweeps=3,
+                           stop="none")
+    assert rel(r.a.cpu().numpy(), o.a) <= 1e-5
+    bad = order[:2].copy()
+    bad[1, 5] = 128
+    with pytest.raises(hp.HpscdError):
+        ctx.solve_order(X, y, bad, tol=0, stop="none")
+
+
+@pytest.mark.slow
+def test_full_size_random_order(ctx):
+    """The 1,000,000 x 256 benchmark system, 3 sweeps of indices drawn with replacement."""
+    s = synth.workload("tall_1Mx256_f32", seed=0)
+    X, y = to_gpu(s)
+    order = np.random.default_rng(7).integers(0, 256, size=(3, 256))
+    r = ctx.solve_order(X, y, order, tol=0, stop="none")
+    o = oracle.solve_order(s.X, s.y, m=s.m, n=s.n, order=order, tol=0, max_sweeps=3, stop="none")
+    assert rel(r.a.cpu().numpy(), o.a) <= 1e-5
+    np.testing.assert_allclose(r.hist, o.hist, rtol=1e-5)

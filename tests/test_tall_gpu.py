@@ -215,3 +215,34 @@ def test_full_size_tall_1Mx256(ctx):
     assert rel(r.a.cpu().numpy(), o.a) <= RTOL_F32
     np.testing.assert_allclose(r.hist, o.hist, rtol=1e-5)
     assert r.timing["grid"] >= 1
+
+
+def test_async_solves_equal_the_synchronous_ones(ctx):
+    """hpscd_solve_async: several solves enqueued back to back (different systems
+    and stopping rules) give the synchronous call's coefficients, history, sweep
+    count and status; their event timings come back per call."""
+    systems = [synth.make_system(m, n, seed=m + n, noise=0.05) for m, n in
+               ((20000, 256), (7777, 130), (4099, 97))]
+    dev = [(torch.from_numpy(s.X).cuda().T, torch.from_numpy(s.y).cuda()) for s in systems]
+    kw = [dict(tol=1e-6, max_sweeps=60, stop="rel_change"), dict(tol=0, max_sweeps=4, stop="none"),
+          dict(tol=1e-9, max_sweeps=6, stop="rel_res")]
+    res = hp.results_buffer(6)
+    outs, hists = [], []
+    for k in range(6):
+        X, y = dev[k % 3]
+        hist = torch.full((61,), float("nan"), dtype=torch.float64, device="cuda")
+        outs.append(ctx.solve_async(X, y, res[k], hist=hist, **kw[k % 3]))
+        hists.append(hist)
+    times = ctx.async_timings(6)
+    got = hp.read_results(res)
+    for k in range(6):
+        X, y = dev[k % 3]
+        r = ctx.solve(X, y, **kw[k % 3])
+        assert got["status"][k] == r.status == ("not_converged" if k % 3 == 2 else "ok")
+        assert got["sweeps"][k] == r.sweeps and got["passes"][k] == r.sweeps + 1
+        assert got["rel_res"][k] == r.rel_res
+        assert torch.equal(outs[k], r.a)
+        np.testing.assert_array_equal(hists[k][: r.sweeps + 1].cpu().numpy(), r.hist)
+        assert times[k]["sweep_ms"] > 0 and times[k]["setup_ms"] > 0
+    with pytest.raises(hp.HpscdError):
+        ctx.async_timings(65)

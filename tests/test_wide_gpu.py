@@ -70,3 +70,35 @@ def test_full_size_wide_2000x200k(ctx):
     assert rel(r.a.cpu().numpy(), o.a) <= RTOL_F32
     _, nrm = oracle.residual(s.X, s.y, r.a.cpu().numpy(), m=s.m, n=s.n, layout="row")
     assert nrm / np.linalg.norm(s.y.astype(np.float64)) <= 2e-6
+
+
+@pytest.mark.parametrize("n,layout", [(777, "row"), (1024, "row"), (300, "col"), (512, "col")])
+def test_square_equal_sweeps_matches_oracle(ctx, n, layout):
+    """Square systems (the paper's third shape): row-major through the cluster
+    sweep, column-major (n <= 512) through the tall sweep, at equal sweeps."""
+    s = synth.make_system(n, n, seed=n, layout=layout, scale=0.5 / np.sqrt(n), diag=1.0)
+    X = torch.from_numpy(s.X).cuda()
+    if layout == "col":
+        X = X.T
+    y = torch.from_numpy(s.y).cuda()
+    for sweeps in (1, 3):
+        r = ctx.solve(X, y, tol=0, max_sweeps=sweeps, stop="none")
+        o = oracle.solve_system(s, tol=0, max_sweeps=sweeps, stop="none")
+        assert r.status == "ok" and r.sweeps == sweeps
+        assert rel(r.a.cpu().numpy(), o.a) <= RTOL_F32, (n, layout, sweeps)
+        np.testing.assert_allclose(r.hist, o.hist, rtol=1e-4, atol=2e-7)
+
+
+@pytest.mark.slow
+def test_full_size_square_4096(ctx):
+    """The 4096 x 4096 square benchmark system to relative residual 1e-6: the
+    sweep count and iterate of the oracle, and the oracle's own residual of a."""
+    s = synth.workload("square_4096_f32")
+    X, y = gpu(s)
+    r = ctx.solve(X, y, tol=1e-6, max_sweeps=200, stop="rel_res")
+    o = oracle.solve_system(s, tol=1e-6, max_sweeps=200, stop="rel_res")
+    assert r.status == "ok" and o.status == "ok" and abs(r.sweeps - o.sweeps) <= 1
+    o = oracle.solve_system(s, tol=0, max_sweeps=r.sweeps, stop="none")
+    assert rel(r.a.cpu().numpy(), o.a) <= RTOL_F32
+    _, nrm = oracle.residual(s.X, s.y, r.a.cpu().numpy(), m=s.m, n=s.n, layout="row")
+    assert nrm / np.linalg.norm(s.y.astype(np.float64)) <= 2e-6
