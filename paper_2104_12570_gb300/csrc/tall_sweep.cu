@@ -103,7 +103,11 @@ __device__ __forceinline__ void st_release_cta(int* p, int v) {
 __device__ __forceinline__ bool warp_wait_flag(const int* flag, int want, uint64_t timeout_ns) {
   int ok = 1;
   if ((threadIdx.x & 31) == 0) {
-    if (ld_acquire_cta(flag) < want) {
+    // the hand-offs of the substitution take well under a microsecond: spin
+    // without the timer first, then bound the wait by the timeout
+    uint32_t spin = 0;
+    while (spin < 4096 && ld_acquire_cta(flag) < want) ++spin;
+    if (spin == 4096) {
       const uint64_t t0 = global_timer_ns();
       for (uint32_t it = 0;; ++it) {
         if (ld_acquire_cta(flag) >= want) break;
@@ -145,12 +149,12 @@ __device__ bool forward_substitution(const float* __restrict__ Gt, int ldG, int 
   bool ok = true;
   if (warp == 0) {
     for (int b = 0; b < nb && ok; ++b) {
-      if (b > 0 && !warp_wait_flag(&flags[1 + b], 1, timeout_ns)) { ok = false; break; }
       const int i = 32 * b + lane;
       float seg[32];
       const float* dl = diag_s + b * DIAG_PACK + (lane * (lane - 1)) / 2;
 #pragma unroll
       for (int k = 0; k < 32; ++k) seg[k] = (k < lane) ? dl[k] : 0.f;
+      if (b > 0 && !warp_wait_flag(&flags[1 + b], 1, timeout_ns)) { ok = false; break; }
       float ri = (i < n) ? r[i] : 0.f;
 #pragma unroll
       for (int k = 0; k < 32; ++k) {
@@ -174,14 +178,15 @@ __device__ bool forward_substitution(const float* __restrict__ Gt, int ldG, int 
     }
     for (int b = 0; b < warp; ++b) {
       if (!warp_wait_flag(&flags[0], b + 1, timeout_ns)) { ok = false; break; }
-      const float* dab = da + 32 * b;
+      const float4* dab = reinterpret_cast<const float4*>(da + 32 * b);
       float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
 #pragma unroll
       for (int k = 0; k < 32; k += 4) {
-        a0 = fmaf(seg[k], dab[k], a0);
-        a1 = fmaf(seg[k + 1], dab[k + 1], a1);
-        a2 = fmaf(seg[k + 2], dab[k + 2], a2);
-        a3 = fmaf(seg[k + 3], dab[k + 3], a3);
+        const float4 d4 = dab[k / 4];
+        a0 = fmaf(seg[k], d4.x, a0);
+        a1 = fmaf(seg[k + 1], d4.y, a1);
+        a2 = fmaf(seg[k + 2], d4.z, a2);
+        a3 = fmaf(seg[k + 3], d4.w, a3);
       }
       rt -= (a0 + a1) + (a2 + a3);
       if (b + 1 < warp) {
