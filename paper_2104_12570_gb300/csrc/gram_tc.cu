@@ -132,7 +132,11 @@ __global__ void __launch_bounds__(GT_THREADS, 1)
   } else if (warp == 1) {
     // ---------------- MMA issuer: warp 1, lane 0 ----------------
     if (lane == 0) {
-      const uint32_t idesc = make_idesc(FMT, BLK);
+      // Two tiles (I, J) and (I, J+1) whose J blocks sit next to each other in the
+      // stage and whose accumulators are adjacent in tensor memory are one MMA of
+      // N = 256 (the B operand spans both blocks): the shared A operand is read
+      // once and a third fewer MMAs are issued.
+      const uint32_t idesc128 = make_idesc(FMT, BLK), idesc256 = make_idesc(FMT, 2 * BLK);
       for (int64_t kb = 0; kb < nkb; ++kb) {
         const int s = (int)(kb % nst);
         const uint32_t par = (uint32_t)((kb / nst) & 1);
@@ -142,6 +146,9 @@ __global__ void __launch_bounds__(GT_THREADS, 1)
         for (int t = 0; t < ntile; ++t) {
           const uint32_t d_tmem = tmem + (uint32_t)(BLK * t);
           const int si = p.grp.tile_si[g][t], sj = p.grp.tile_sj[g][t];
+          const bool pair = t + 1 < ntile && p.grp.tile_si[g][t + 1] == si &&
+                            p.grp.tile_sj[g][t + 1] == sj + 1;
+          const uint32_t idesc = pair ? idesc256 : idesc128;
 #pragma unroll
           for (int k = 0; k < 4; ++k) {
             const uint32_t koff = k * 32;
@@ -156,6 +163,7 @@ __global__ void __launch_bounds__(GT_THREADS, 1)
               mma_issue<TF32>(d_tmem, al, bh, idesc, 1u);
             }
           }
+          if (pair) ++t;
         }
         mma_commit(&empty[s]);
       }

@@ -269,3 +269,18 @@ def test_empty_and_degenerate_shapes():
     # y = 0: relative residual falls back to the absolute norm
     r = run(np.ones((4, 2)), np.zeros(4), tol=1e-12, max_sweeps=3, stop="rel_res")
     assert r.sweeps == 0 and np.all(r.a == 0)
+
+
+def test_nonfinite_inputs_are_reported():
+    """A NaN in y makes ||e_0|| NaN (reported before any sweep); an infinite
+    entry of X makes d_j infinite and the first column step NaN (reported after
+    sweep 1)."""
+    s = synth.make_system(60, 8, seed=12, dtype="f64", consistent_rhs_dtype="f64")
+    y = s.y.copy()
+    y[4] = np.nan
+    o = oracle.solve(s.X, y, m=s.m, n=s.n, dtype="f64", tol=1e-6, max_sweeps=10)
+    assert o.status == "nonfinite" and o.sweeps == 0
+    X = s.X.copy()
+    X[2, 7] = np.inf
+    o = oracle.solve(X, s.y, m=s.m, n=s.n, dtype="f64", tol=1e-6, max_sweeps=10)
+    assert o.status == "nonfinite" and o.sweeps == 1
