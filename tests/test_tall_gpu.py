@@ -203,6 +203,24 @@ def test_host_entry_point_end_to_end(ctx):
     assert rel(r.a, oracle_same(s, 3).a) <= RTOL_F32
 
 
+@pytest.mark.parametrize("m,n,dtype,ld_pad", [(600_001, 200, "f32", 0), (300_007, 130, "bf16", 0),
+                                               (262_145, 64, "f32", 1), (131_071, 96, "f32", 0)])
+def test_host_entry_point_large_ragged_bf16_unaligned(ctx, m, n, dtype, ld_pad):
+    """hpscd_solve_host on tall systems: ragged row counts, bfloat16 storage, and
+    an unaligned leading dimension (the CUDA-core set-up)."""
+    s = synth.make_system(m, n, seed=m % 1000, dtype=dtype, noise=0.01)
+    Xh = s.X
+    if ld_pad:
+        buf = np.zeros((n, m + ld_pad), dtype=s.X.dtype)
+        buf[:, :m] = s.X
+        Xh = buf[:, :m]
+    r = ctx.solve_host(Xh.T, s.y, tol=0, max_sweeps=3, stop="none")
+    o = oracle_same(s, 3)
+    assert r.status == "ok" and r.sweeps == 3
+    assert rel(r.a, o.a) <= (RTOL_F32 if dtype == "f32" else 1e-3)
+    np.testing.assert_allclose(r.hist, o.hist, rtol=1e-4)
+
+
 @pytest.mark.slow
 def test_full_size_tall_1Mx256(ctx):
     """The 1,000,000 x 256 float32 noisy least-squares workload, in the launch
