@@ -273,12 +273,29 @@ __device__ void stream_pass(const float* __restrict__ X, int64_t ld, int64_t r0,
 // columns: warp 0 walks each diagonal block with shuffles (its strictly lower
 // part staged in diag_s); every thread t >= 32 owns row t and applies each
 // finished block to it.  r is overwritten.
+__device__ __forceinline__ void cp_async16(float* dst, const float* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+
+// stage: shared scratch of BMAXN rows × SEGP floats, free between passes; each
+// thread below the block copies its row's segment of the block there with
+// cp.async before the walk (no registers held), so the copy overlaps the walk.
+constexpr int SEGP = 36;  // row pitch of the staged segments (16-byte rows, conflict-free float4 reads)
+static_assert(BMAXN * SEGP <= 2 * REDF, "the staged segments fit the pass scratch");
 __device__ void forward_sub_scaled(const float* __restrict__ Gt, int n, float* r, float* da,
-                                   const float* diag_s) {
+                                   const float* diag_s, float* stage) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int nb = (n + 31) / 32;
   for (int b = 0; b < nb; ++b) {
     const int b0 = 32 * b;
+    const bool mine = tid >= b0 + 32 && tid < n;
+    if (mine) {
+      const float* src = Gt + (int64_t)tid * BLDG + b0;
+      float* dst = stage + tid * SEGP;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) cp_async16(dst + 4 * q, src + 4 * q);
+      asm volatile("cp.async.commit_group;" ::: "memory");
+    }
     if (warp == 0) {
       const int i = b0 + lane;
       float seg[32];
@@ -294,12 +311,13 @@ __device__ void forward_sub_scaled(const float* __restrict__ Gt, int n, float* r
       da[i] = (i < n) ? ri : 0.f;
     }
     __syncthreads();
-    if (tid >= b0 + 32 && tid < n) {
-      const float4* g4 = reinterpret_cast<const float4*>(Gt + (int64_t)tid * BLDG + b0);
+    if (mine) {
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
+      const float4* g4 = reinterpret_cast<const float4*>(stage + tid * SEGP);
       float acc = 0.f;
 #pragma unroll
       for (int k4 = 0; k4 < 8; ++k4) {
-        const float4 g = __ldcg(g4 + k4);
+        const float4 g = g4[k4];
         acc = fmaf(g.x, da[b0 + 4 * k4], acc);
         acc = fmaf(g.y, da[b0 + 4 * k4 + 1], acc);
         acc = fmaf(g.z, da[b0 + 4 * k4 + 2], acc);
@@ -500,20 +518,28 @@ __global__ void __launch_bounds__(BNT, 1) batched_sweep_kernel(const BatchParams
       r_prev = rel;
       if (stop) break;
       __syncthreads();  // rvec (h) complete
-      // r = h ⊘ d - G~·v, one warp per row
-      for (int c = warp; c < n; c += BNW) {
-        const float* grow = Gt + (size_t)c * BLDG;
-        float acc = 0.f;
-        for (int l = lane; l < n; l += 32) acc = fmaf(__ldcg(grow + l), vsm[l], acc);
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(FULL_MASK, acc, off);
-        if (lane == 0) {
-          const float dc = dd_s[c];
-          rvec[c] = (dc > 0.f ? rvec[c] / dc : 0.f) - acc;
+      // r = h ⊘ d - G~·v, one thread per row: the row's float4 loads are
+      // independent of one another, so they are in flight together (columns past
+      // n read zeros of G~ and of v up to the next multiple of 4)
+      for (int c = tid; c < n; c += BNT) {
+        const float4* g4 = reinterpret_cast<const float4*>(Gt + (size_t)c * BLDG);
+        const float4* v4 = reinterpret_cast<const float4*>(vsm);
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+        const int nq = (n + 3) / 4;
+#pragma unroll 8
+        for (int q = 0; q < nq; ++q) {
+          const float4 g = __ldcg(g4 + q);
+          const float4 w = v4[q];
+          a0 = fmaf(g.x, w.x, a0);
+          a1 = fmaf(g.y, w.y, a1);
+          a2 = fmaf(g.z, w.z, a2);
+          a3 = fmaf(g.w, w.w, a3);
         }
+        const float dc = dd_s[c];
+        rvec[c] = (dc > 0.f ? rvec[c] / dc : 0.f) - ((a0 + a1) + (a2 + a3));
       }
       __syncthreads();
-      forward_sub_scaled(Gt, n, rvec, da_s, diag_s);
+      forward_sub_scaled(Gt, n, rvec, da_s, diag_s, uni);  // uni is free between passes
       for (int c = tid; c < n; c += BNT) {
         a64_s[c] += (double)da_s[c];
         vsm[c] = da_s[c];
