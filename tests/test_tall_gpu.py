@@ -1,7 +1,7 @@
 """Parity of the CUDA tall sweep (column-major X, n <= 512) with the float64
 CPU oracle of Algorithm 1, through the C ABI.
 
-Tolerance (BASELINE): relative coefficient error <= 1e-5 for float32 arithmetic
+Tolerance: relative coefficient error <= 1e-5 for float32 arithmetic
 against the oracle at the same sweep count, and <= 1e-3 for bfloat16 storage
 (the oracle solves the same bfloat16-valued system, so storage rounding is not
 part of the error; the GPU's float32 accumulation is).
