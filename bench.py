@@ -227,13 +227,15 @@ def batched_comparison(hp, synth, ctx):
     m, n, th = synth.rbf_params(4096, seed=0)
     keep, a, b = ws.build_batch(ctx, fam, m, n, th, max_sweeps=4)
     systems = b.systems
-    best, tms = hp.autotune_batch(ctx, systems, trial_sweeps=3)
+    best, tms = hp.autotune_batch(ctx, systems, trial_sweeps=10)
     b.close()
     del keep, a, systems
     out = {"workload": "rbf_batch_4096 (RBF features of U[0,1]^4 inputs, width 0.3; "
                        "y = f_theta(x))",
            "stop": f"{ws.STOP}<{ws.TOL}, max_sweeps {ws.MAX_SWEEPS}",
-           "x_bytes": int((m * n * 4).sum()), "autotune_ms_per_3_sweeps": tms, "cluster": best}
+           "x_bytes": int((m * n * 4).sum()),
+           "autotune_ms_per_10_sweeps": {f"cluster{k}_panel{p}": v for (k, p), v in tms.items()},
+           "cluster": best[0], "panel": best[1]}
     if not os.path.exists(ws.WEIGHTS):
         out["warm"] = "no trained weights"
         return out

@@ -318,10 +318,15 @@ typedef struct {
 
 /* Launch shape of a batch.  cluster = CTAs that share one system (1, 2, 4 or
  * 8; each CTA owns a slice of its rows and of its residual); 0 = let the
- * library pick.  hpscd_autotune_batch fills this by timing candidates. */
+ * library pick.  panel = the width of the column panels of a streaming pass,
+ * as columns per warp: 0 = the narrowest that covers the system's columns
+ * (4 for n <= 64, 8 for n <= 128, 16 above), 1 = twice that, 2 = 16 for every
+ * system (wider panels: fewer row sums per panel, taller row panels).
+ * hpscd_autotune_batch fills both by timing candidates. */
 typedef struct {
   int32_t cluster;
-  int32_t reserved[7]; /* must be zero */
+  int32_t panel;
+  int32_t reserved[6]; /* must be zero */
 } hpscd_tuning;
 
 typedef struct hpscd_batch hpscd_batch;
@@ -357,11 +362,14 @@ int hpscd_batch_tuning(hpscd_batch* b, hpscd_tuning* out);
 int hpscd_batch_destroy(hpscd_batch* b);
 
 /*
- * Autotuner: plans the batch with each candidate cluster size that fits,
- * times `trial_sweeps` sweeps of every system (stop rule NONE, systems' a and
- * hist written as by a solve) with CUDA events, and returns the fastest in
- * *out (ms_per_candidate: HOST double[4] or NULL, the time of clusters 1, 2,
- * 4, 8; a candidate that does not fit reads as a negative number).
+ * Autotuner: plans the batch with each candidate (cluster 1, 2, 4, 8) × (panel
+ * 0, 1, 2) that fits, times with CUDA events a launch of `trial_sweeps` sweeps
+ * of every system and one of none (stop rule NONE; the systems' a and hist are
+ * written as by a solve), and returns in *out the candidate whose sweeps take
+ * least time (the difference; the set-up is paid once per solve).
+ * ms_per_candidate: HOST double[12] or NULL, that sweep time of candidate
+ * (cluster index c, panel p) at [3·c + p]; a candidate that does not fit reads
+ * as a negative number.
  */
 int hpscd_autotune_batch(hpscd_ctx* ctx, const hpscd_sys* sys, int64_t count, int dtype,
                          int64_t trial_sweeps, hpscd_tuning* out, double* ms_per_candidate);

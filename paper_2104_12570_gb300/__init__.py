@@ -85,7 +85,7 @@ def read_results(buf) -> dict:
 
 
 class Tuning(ctypes.Structure):
-    _fields_ = [("cluster", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+    _fields_ = [("cluster", ctypes.c_int32), ("panel", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
 
 
 SIGNATURES = {
@@ -552,7 +552,7 @@ class Batch:
     The tensors must stay alive while the batch is used (the batch keeps them)."""
 
     def __init__(self, ctx: "Context", systems, *, tol=1e-6, max_sweeps=1000, stop="rel_res",
-                 cluster: int = 0):
+                 cluster: int = 0, panel: int = 0):
         import torch
         self._lib = ctx._lib
         self.ctx = ctx
@@ -562,6 +562,7 @@ class Batch:
         o = make_opts(tol, max_sweeps, stop)
         t = Tuning()
         t.cluster = int(cluster)
+        t.panel = int(panel)
         dev = self.systems[0][0].device if self.systems else torch.device("cuda", ctx.device)
         ctx.set_stream(torch.cuda.current_stream(dev))
         h = ctypes.c_void_p()
@@ -578,6 +579,12 @@ class Batch:
         t = Tuning()
         self._lib.hpscd_batch_tuning(self._h, ctypes.byref(t))
         return t.cluster
+
+    @property
+    def panel(self) -> int:
+        t = Tuning()
+        self._lib.hpscd_batch_tuning(self._h, ctypes.byref(t))
+        return t.panel
 
     def launch(self):
         rc = self._lib.hpscd_batch_launch(self._h)
@@ -759,17 +766,20 @@ class MLP:
 
 
 def autotune_batch(ctx: "Context", systems, trial_sweeps: int = 4):
-    """(best cluster size, {cluster: ms of trial_sweeps sweeps of every system})."""
+    """((cluster, panel) of the fastest candidate, {(cluster, panel): ms of
+    trial_sweeps sweeps of every system}) over clusters 1, 2, 4, 8 and panel
+    policies 0, 1, 2 (see Batch)."""
     import torch
     arr = _sys_array(systems)
     t = Tuning()
-    ms = (ctypes.c_double * 4)()
+    ms = (ctypes.c_double * 12)()
     ctx.set_stream(torch.cuda.current_stream(systems[0][0].device))
     rc = ctx._lib.hpscd_autotune_batch(ctx._h, arr, len(systems), F32, int(trial_sweeps),
                                        ctypes.byref(t), ms)
     if rc:
         raise HpscdError(rc, "hpscd_autotune_batch")
-    return t.cluster, {k: ms[i] for i, k in enumerate((1, 2, 4, 8)) if ms[i] >= 0}
+    return (t.cluster, t.panel), {(k, p): ms[3 * i + p] for i, k in enumerate((1, 2, 4, 8))
+                                  for p in range(3) if ms[3 * i + p] >= 0}
 
 
 def _host_f32(y, m):

@@ -122,7 +122,7 @@ bool candidate(const hpscd_ctx* ctx, int64_t mmax, int K, int* smem, int* cluste
 }
 
 int create(hpscd_ctx* ctx, const hpscd_sys* sys, int64_t count, const hpscd_opts* opts, int K,
-           hpscd_batch** out) {
+           int panel, hpscd_batch** out) {
   int64_t mmax = 0;
   int rc = check_systems(sys, count, &mmax);
   if (rc) return rc;
@@ -211,6 +211,7 @@ int create(hpscd_ctx* ctx, const hpscd_sys* sys, int64_t count, const hpscd_opts
   p.gfinal = b->gfinal;
   p.dfinal = b->dfinal;
   p.ecap = b->ecap;
+  p.panel = panel;
   p.tol = opts->tol;
   p.max_sweeps = opts->max_sweeps;
   p.stop_rule = opts->stop_rule;
@@ -242,16 +243,17 @@ int hpscd_batch_create(hpscd_ctx* ctx, const hpscd_sys* sys, int64_t count, int 
   if (dtype != HPSCD_F32) return HPSCD_ERR_UNSUPPORTED;
   int rc = check_batch_opts(opts);
   if (rc) return rc;
-  int K = 0;
+  int K = 0, panel = 0;
   if (tuning) {
-    for (int i = 0; i < 7; ++i)
+    for (int i = 0; i < 6; ++i)
       if (tuning->reserved[i]) return HPSCD_ERR_INVALID_ARG;
     K = tuning->cluster;
-    if (K < 0) return HPSCD_ERR_INVALID_ARG;
+    panel = tuning->panel;
+    if (K < 0 || panel < 0 || panel > 2) return HPSCD_ERR_INVALID_ARG;
   }
   DevGuard g(ctx->device);
   if (!g.ok) return HPSCD_ERR_CUDA;
-  return create(ctx, sys, count, opts, K, out);
+  return create(ctx, sys, count, opts, K, panel, out);
 }
 
 int hpscd_batch_launch(hpscd_batch* b) {
@@ -322,6 +324,7 @@ int hpscd_batch_tuning(hpscd_batch* b, hpscd_tuning* out) {
   if (!b || !out) return HPSCD_ERR_INVALID_ARG;
   memset(out, 0, sizeof(*out));
   out->cluster = b->K;
+  out->panel = b->params.panel;
   return HPSCD_OK;
 }
 
@@ -354,30 +357,51 @@ int hpscd_autotune_batch(hpscd_ctx* ctx, const hpscd_sys* sys, int64_t count, in
   o.max_sweeps = trial_sweeps;
   o.stop_rule = HPSCD_STOP_NONE;
   std::vector<hpscd_sys_result> res((size_t)count);
-  double best = -1.0;
-  int bestK = 0;
-  const int Ks[4] = {1, 2, 4, 8};
-  for (int ci = 0; ci < 4; ++ci) {
-    if (ms_per_candidate) ms_per_candidate[ci] = -1.0;
+  // event time of a batch planned with (K, panel) and `sweeps` sweeps: the mean
+  // of two launches after a warm-up; < 0 when the shape does not fit
+  auto time_batch = [&](int K, int panel, int64_t sweeps, double* ms) -> int {
+    hpscd_opts os = o;
+    os.max_sweeps = sweeps;
     hpscd_batch* b = nullptr;
-    int rc = create(ctx, trial.data(), count, &o, Ks[ci], &b);
-    if (rc == HPSCD_ERR_UNSUPPORTED) continue;
+    int rc = create(ctx, trial.data(), count, &os, K, panel, &b);
+    if (rc == HPSCD_ERR_UNSUPPORTED) { *ms = -1.0; return HPSCD_OK; }
     if (rc) return rc;
     float total = 0.f;
     for (int rep = 0; rep < 3 && rc == HPSCD_OK; ++rep) {
       rc = hpscd_batch_launch(b);
       if (rc == HPSCD_OK) rc = hpscd_batch_results(b, res.data());
-      if (rep > 0) total += ctx->last.sweep_ms;  // first launch is a warm-up
+      if (rep > 0) total += ctx->last.sweep_ms;
     }
     hpscd_batch_destroy(b);
+    *ms = total / 2.0;
+    return rc;
+  };
+  double best = -1.0;
+  int bestK = 0, bestP = 0;
+  const int Ks[4] = {1, 2, 4, 8};
+  if (ms_per_candidate)
+    for (int i = 0; i < 12; ++i) ms_per_candidate[i] = -1.0;
+  for (int ci = 0; ci < 4; ++ci) {
+    // the set-up (the Gram of every system) depends on the cluster size only
+    double t0 = 0.0;
+    int rc = time_batch(Ks[ci], 0, 0, &t0);
     if (rc) return rc;
-    const double ms = total / 2.0;
-    if (ms_per_candidate) ms_per_candidate[ci] = ms;
-    if (best < 0.0 || ms < best) { best = ms; bestK = Ks[ci]; }
+    if (t0 < 0.0) continue;  // this cluster size does not fit
+    for (int pi = 0; pi < 3; ++pi) {
+      double tt = 0.0;
+      if ((rc = time_batch(Ks[ci], pi, trial_sweeps, &tt))) return rc;
+      if (tt < 0.0) continue;
+      // candidates are compared on the sweeps alone (the set-up is paid once per
+      // solve and does not depend on the panel)
+      const double ms = tt - t0 > 0.0 ? tt - t0 : 0.0;
+      if (ms_per_candidate) ms_per_candidate[3 * ci + pi] = ms;
+      if (best < 0.0 || ms < best) { best = ms; bestK = Ks[ci]; bestP = pi; }
+    }
   }
   if (bestK == 0) return HPSCD_ERR_UNSUPPORTED;
   memset(out, 0, sizeof(*out));
   out->cluster = bestK;
+  out->panel = bestP;
   return HPSCD_OK;
 }
 

@@ -453,7 +453,9 @@ __global__ void __launch_bounds__(BNT, 1) batched_sweep_kernel(const BatchParams
     __syncthreads();
 
     // column split of the streaming pass
-    const int cpw = n <= 64 ? 4 : (n <= 128 ? 8 : 16);
+    // columns per warp: the narrowest that covers n with the CTA's warps, or wider
+    const int cpw0 = n <= 64 ? 4 : (n <= 128 ? 8 : 16);
+    const int cpw = p.panel >= 2 ? 16 : (cpw0 << p.panel) > 16 ? 16 : (cpw0 << p.panel);
     int nwc = (n + cpw - 1) / cpw;
     nwc = nwc < 1 ? 1 : nwc;
     { int pw = 1; while (pw < nwc) pw *= 2; nwc = pw; }

@@ -42,12 +42,14 @@ WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights", "r
 
 def build_batch(ctx, fam, m, n, th, device="cuda", tol=TOL, stop=STOP, max_sweeps=MAX_SWEEPS,
                 cluster=0):
-    """(keep, a list, Batch) for the systems (m, n, th) of the family."""
+    """(keep, a list, Batch) for the systems (m, n, th) of the family; cluster is
+    the CTAs per system or a (cluster, panel) pair from autotune_batch."""
     import torch
     keep, sysd = synth.device_rbf_batch(fam, m, n, th, device)
     a = [torch.zeros(int(k), dtype=torch.float32, device=device) for k in n]
+    k, panel = cluster if isinstance(cluster, tuple) else (cluster, 0)
     b = hp.Batch(ctx, [(X, y, ai, False) for (X, y), ai in zip(sysd, a)], tol=tol,
-                 max_sweeps=max_sweeps, stop=stop, cluster=cluster)
+                 max_sweeps=max_sweeps, stop=stop, cluster=k, panel=panel)
     return (keep, sysd), a, b
 
 

@@ -65,15 +65,15 @@ def gaussian_batch(specs, seed=0, noise=0.05):
     return host, dev, keep
 
 
-@pytest.mark.parametrize("cluster", [1, 2, 4, 8])
-def test_equal_sweeps_match_oracle(ctx, cluster):
-    host, dev, keep = gaussian_batch(SPECS, seed=cluster)
+@pytest.mark.parametrize("cluster,panel", [(1, 0), (2, 0), (4, 0), (8, 0), (1, 1), (1, 2), (4, 2)])
+def test_equal_sweeps_match_oracle(ctx, cluster, panel):
+    host, dev, keep = gaussian_batch(SPECS, seed=cluster + 10 * panel)
     sweeps = 4
     hists = [torch.full((sweeps + 1,), float("nan"), dtype=torch.float64, device="cuda")
              for _ in dev]
     systems = [tuple(d) + (h,) for d, h in zip(dev, hists)]
-    b = hp.Batch(ctx, systems, tol=0, max_sweeps=sweeps, stop="none", cluster=cluster)
-    assert b.cluster == cluster
+    b = hp.Batch(ctx, systems, tol=0, max_sweeps=sweeps, stop="none", cluster=cluster, panel=panel)
+    assert b.cluster == cluster and b.panel == panel
     r = b.run()
     for i, s in enumerate(host):
         o = oracle.solve_system(s, tol=0, max_sweeps=sweeps, stop="none")
@@ -192,11 +192,12 @@ def test_rbf_family_equal_sweeps(ctx):
     b.close()
 
 
-def test_autotuner_picks_a_cluster_size(ctx):
+def test_autotuner_picks_cluster_and_panel(ctx):
     fam = synth.rbf_family(0)
     m, n, th = synth.rbf_params(300, seed=9)
     keep, sysd = synth.device_rbf_batch(fam, m, n, th, "cuda")
     systems = [(X, y, torch.zeros(int(k), device="cuda"), False) for (X, y), k in zip(sysd, n)]
     best, ms = hp.autotune_batch(ctx, systems, trial_sweeps=3)
-    assert best in (1, 2, 4, 8) and best in ms
-    assert ms[best] == min(ms.values()) and all(v > 0 for v in ms.values())
+    assert best[0] in (1, 2, 4, 8) and best[1] in (0, 1, 2) and best in ms
+    assert ms[best] == min(ms.values()) and all(v >= 0 for v in ms.values())
+    assert {p for (k, p) in ms if k == 1} == {0, 1, 2}  # every panel policy timed
