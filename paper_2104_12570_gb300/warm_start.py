@@ -190,38 +190,66 @@ def main():
                     help="self-training rounds: after each, the training systems are solved again "
                          "from the network's prediction (same rule and cap) and the network is "
                          "retrained on those further-converged solutions")
+    ap.add_argument("--init", default="",
+                    help="weights (.npy) to continue from: the first labels are solved from this "
+                         "network's prediction instead of from a cold start")
     args = ap.parse_args()
     import torch
     ctx = hp.Context(0)
     fam = synth.rbf_family(0)
     m, n, th = synth.rbf_params(args.train, seed=1)
+    rounds_log = []
+    prev_meta = {}
+    if args.init:
+        jp = os.path.splitext(args.init)[0] + ".json"
+        if os.path.exists(jp):
+            with open(jp) as f:
+                prev_meta = json.load(f)
+        rounds_log = list(prev_meta.get("label_rounds", []))
     t0 = time.time()
+    init = load(ctx, args.init) if args.init else None
     if args.labels and os.path.exists(args.labels):
         z = np.load(args.labels)
         labels, sw, res = z["labels"], z["sweeps"], z["res"]
     else:
-        labels, sw, res = solve_family(ctx, fam, m, n, th)
+        labels, sw, res = solve_family(ctx, fam, m, n, th, mlp=init)
         if args.labels:
             np.savez(args.labels, labels=labels, sweeps=sw, res=res)
+    if init is not None:
+        init.close()
     t1 = time.time()
-    print(json.dumps({"labels_s": t1 - t0, "label_sweeps_mean": float(sw.mean()),
-                      "label_hit_cap": int((sw >= MAX_SWEEPS).sum())}), flush=True)
+    rounds_log.append({"round": len(rounds_log), "label_sweeps_mean": float(sw.mean()),
+                       "label_hit_cap": int((sw >= MAX_SWEEPS).sum())})
+    print(json.dumps({"labels_s": t1 - t0, **rounds_log[-1]}), flush=True)
     mlp, hist = train(ctx, th, m, n, labels, epochs=args.epochs, batch=args.batch, lr=args.lr,
                       log=lambda h: print(json.dumps(h), flush=True))
-    for rnd in range(1, args.rounds):
+    for _ in range(1, args.rounds):
         labels, sw, res = solve_family(ctx, fam, m, n, th, mlp=mlp)
-        print(json.dumps({"round": rnd, "label_sweeps_mean": float(sw.mean()),
-                          "label_hit_cap": int((sw >= MAX_SWEEPS).sum())}), flush=True)
+        rounds_log.append({"round": len(rounds_log), "label_sweeps_mean": float(sw.mean()),
+                           "label_hit_cap": int((sw >= MAX_SWEEPS).sum())})
+        print(json.dumps(rounds_log[-1]), flush=True)
         mlp.close()
         mlp, hist = train(ctx, th, m, n, labels, epochs=args.epochs, batch=args.batch, lr=args.lr,
                           log=lambda h: print(json.dumps(h), flush=True))
     t2 = time.time()
     me, ne, te = synth.rbf_params(args.eval, seed=0)
     ev = evaluate(ctx, fam, mlp, me, ne, te)
-    meta = {"train_systems": args.train, "epochs": args.epochs, "batch": args.batch, "lr": args.lr,
-            "rounds": args.rounds,
-            "train_s": t2 - t1, "labels_s": t1 - t0, "final": hist[-1], "eval": ev,
-            "stop": f"{STOP}<{TOL}, max_sweeps {MAX_SWEEPS}"}
+    made_by = f"python -m paper_2104_12570_gb300.warm_start --rounds {args.rounds}" + \
+              (f" --init {os.path.basename(args.init)}" if args.init else "") + " (GB300)"
+    meta = {
+        "what": "warm-start MLP phi(theta, m, n) -> a for the RBF family (synth.rbf_family(0)); "
+                "float32 parameters in the order W1 [256][18], b1, W2 [256][256], b2, W3 [256][256], b3",
+        "trained_on": f"{args.train:,} systems synth.rbf_params({args.train}, seed=1); labels = the "
+                      f"batched sweep's solutions ({STOP} < {TOL}, at most {MAX_SWEEPS} sweeps): round 0 "
+                      "from a cold start, each later round from the previous round's network "
+                      "(self-training: the same rule and cap, continued from the prediction)",
+        "training": {"rounds_total": len(rounds_log), "epochs": args.epochs, "batch": args.batch,
+                     "lr": args.lr, "schedule": "cosine to 1e-5", "optimizer": "Adam(0.9, 0.999, 1e-8)",
+                     "final": hist[-1], "labels_s_this_run_first": t1 - t0, "train_s_this_run": t2 - t1},
+        "label_rounds": rounds_log,
+        "made_by": (prev_meta.get("made_by", "") + ", then " if prev_meta else "") + made_by,
+        f"eval_{args.eval}_seed0": ev,
+    }
     save(mlp, args.out, meta)
     print(json.dumps(meta), flush=True)
     torch.cuda.synchronize()
