@@ -53,7 +53,12 @@ def sweep_kernel_bytes(m, n, esz, passes):
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    """nvidia-smi clocks and throttle reasons sampled during the timed region.
+
+    The sampler starts before the region and waits for its first reading, so
+    that it is running when the region starts; each reading is stamped with the
+    host clock, and the summary keeps the readings taken inside the region
+    (mark() bounds it), with 30 ms of slack for the sampling period."""
 
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
@@ -63,22 +68,29 @@ class ClockSampler:
         self.index = index
         self.proc = None
         self.lines = []
+        self.window = None
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", "20"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            t0 = time.perf_counter()
+            while not self.lines and time.perf_counter() - t0 < 3.0:
+                time.sleep(0.005)
         except (OSError, FileNotFoundError):
             self.proc = None
         return self
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.perf_counter(), line.strip()))
+
+    def mark(self, start, end):
+        self.window = (start - 0.03, end + 0.03)
 
     def __exit__(self, *exc):
         if self.proc:
@@ -91,7 +103,11 @@ class ClockSampler:
     def summary(self):
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        lines = self.lines
+        if self.window:
+            inside = [x for x in lines if self.window[0] <= x[0] <= self.window[1]]
+            lines = inside or lines
+        for _, ln in lines:
             parts = [x.strip() for x in ln.split(",")]
             if len(parts) < 7:
                 continue
@@ -106,7 +122,7 @@ class ClockSampler:
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "in_timed_region": lines is not self.lines}
 
 
 def traffic_from_profile(src_sha):
@@ -447,12 +463,14 @@ def main():
     ctx.solve_async(X, y, res[0], tol=TOL, max_sweeps=MAX_SWEEPS, stop=STOP, out=a)
     with ClockSampler(local) as clk:
         barrier()
+        t_start = time.perf_counter()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ev0.record()
         for k in range(args.steps):
             ctx.solve_async(X, y, res[k], tol=TOL, max_sweeps=MAX_SWEEPS, stop=STOP, out=a)
         ev1.record()
         barrier()
+        clk.mark(t_start, time.perf_counter())
     ms = ev0.elapsed_time(ev1) / args.steps
     got = hp.read_results(res)
     if any(st != "ok" for st in got["status"]):

@@ -24,7 +24,6 @@ struct hpscd_batch {
   hpscd_sys_result* res_d = nullptr;
   float* gpart = nullptr;
   float* gfinal = nullptr;
-  float* dfinal = nullptr;
   cudaStream_t cap = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -161,7 +160,6 @@ int create(hpscd_ctx* ctx, const hpscd_sys* sys, int64_t count, const hpscd_opts
   const size_t o_res = off; off = align256(off + n_sys * sizeof(hpscd_sys_result));
   const size_t o_gpart = off; off = align256(off + (size_t)grid * 256 * 256 * sizeof(float));
   const size_t o_gfinal = off; off = align256(off + (size_t)clusters * 256 * 256 * sizeof(float));
-  const size_t o_dfinal = off; off = align256(off + (size_t)clusters * 256 * sizeof(float));
   const size_t o_mn = off; off = align256(off + 2 * n_sys * sizeof(int64_t));
   if (cudaMalloc(&b->dev, off) != cudaSuccess) {
     cudaGetLastError();
@@ -175,7 +173,6 @@ int create(hpscd_ctx* ctx, const hpscd_sys* sys, int64_t count, const hpscd_opts
   b->res_d = reinterpret_cast<hpscd_sys_result*>(base + o_res);
   b->gpart = reinterpret_cast<float*>(base + o_gpart);
   b->gfinal = reinterpret_cast<float*>(base + o_gfinal);
-  b->dfinal = reinterpret_cast<float*>(base + o_dfinal);
   b->mn_d = reinterpret_cast<int64_t*>(base + o_mn);
   std::vector<int64_t> mn((size_t)2 * n_sys, 0);
   for (int64_t i = 0; i < count; ++i) { mn[(size_t)i] = sys[i].m; mn[(size_t)(count + i)] = sys[i].n; }
@@ -209,7 +206,6 @@ int create(hpscd_ctx* ctx, const hpscd_sys* sys, int64_t count, const hpscd_opts
   p.res = b->res_d;
   p.gpart = b->gpart;
   p.gfinal = b->gfinal;
-  p.dfinal = b->dfinal;
   p.ecap = b->ecap;
   p.panel = panel;
   p.tol = opts->tol;

@@ -353,7 +353,6 @@ __global__ void __launch_bounds__(BNT, 1) batched_sweep_kernel(const BatchParams
   const int cl = blockIdx.x / K;  // cluster index
   float* Gp = p.gpart + (size_t)blockIdx.x * BLDG * BLDG;
   float* Gt = p.gfinal + (size_t)cl * BLDG * BLDG;
-  float* dg = p.dfinal + (size_t)cl * BLDG;
 
   auto csync = [&]() {
     if constexpr (K > 1) {
@@ -420,8 +419,6 @@ __global__ void __launch_bounds__(BNT, 1) batched_sweep_kernel(const BatchParams
         // columns n..32·ceil(n/32)-1 of the row are read (times da = 0) by the substitution
         for (int l = n + lane; l < ((n + 31) / 32) * 32; l += 32) Gt[(size_t)j * BLDG + l] = 0.f;
       }
-      if (rank == 0)
-        for (int c = tid; c < n; c += BNT) dg[c] = dd_s[c];
     }
     csync();
     // diagonal blocks of G~ (strictly lower, packed) into shared memory

@@ -157,7 +157,6 @@ struct BatchParams {
   hpscd_sys_result* res;    // device [count]
   float* gpart;             // [grid][256*256] partial Gram of each CTA
   float* gfinal;            // [clusters][256*256] G~ = D^{-1} G of each cluster's system
-  float* dfinal;            // [clusters][256] d = diag(G)
   int ecap;                 // residual rows held in shared memory per CTA
   int panel;                // columns per warp of a streaming pass: 0 narrowest, 1 twice, 2 sixteen
   double tol;
