@@ -154,6 +154,23 @@ def dist_env():
         os.environ.get("LOCAL_RANK", 0))
 
 
+def max_over_ranks(ms, world, device):
+    """The slowest rank's time per step (every rank gets it); ms itself at N = 1."""
+    if world <= 1:
+        return float(ms)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(bytes_per_rank, world, ms):
+    """Whole-job GB/s: every rank solves its own system (replicas, weak scaling), so
+    the job moves world × bytes_per_rank in the slowest rank's time."""
+    return world * bytes_per_rank / (ms * 1e-3) / 1e9
+
+
 def run_reference(args, rank, world):
     """The oracle (float64 CPU Algorithm 1) on the same workload, on host cores."""
     if rank != 0:
@@ -481,13 +498,10 @@ def main():
     launches = int(round(np.mean([t["kernel_launches"] for t in times]) * args.steps))
     sweeps_timed = int(got["sweeps"][-1])
     setup_ms = float(np.mean([t["setup_ms"] for t in times]))
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, world, dev)
     p_mean = float(np.mean(passes))
     nbytes = algorithmic_bytes(s.m, s.n, esz, p_mean)
-    value = world * nbytes / (ms * 1e-3) / 1e9
+    value = job_value(nbytes, world, ms)
 
     # end to end through the C ABI from pinned host memory
     e2e = None
