@@ -58,6 +58,9 @@ def load_library(path: str):
                                              vp, ctypes.c_double, i64, ctypes.c_int, dp, dp, dp,
                                              ctypes.POINTER(i64)]
     lib.hpscd_oracle_solve_order.restype = ctypes.c_int
+    lib.hpscd_oracle_select_swap.argtypes = [vp, ctypes.c_int, ctypes.c_int, i64, i64, i64, dp, i64,
+                                             i64, vp, vp, dp, dp, ctypes.POINTER(i64)]
+    lib.hpscd_oracle_select_swap.restype = ctypes.c_int
     return lib
 
 
@@ -171,6 +174,27 @@ def select(X, y, *, m, n, F, layout="col", dtype="f32"):
     if st != 0:
         raise ValueError(f"oracle select: {STATUS[st]}")
     return sel[:F], a, hist
+
+
+def select_swap(X, y, *, m, n, F, R, layout="col", dtype="f32", lib=None):
+    """Algorithm 3 for F steps, then at most R swap steps of the feature-removal
+    loop: (sel[F], swaps (R, 2) with -1 rows after the last, a, hist[F + 1 + nswaps])."""
+    _check_x(X, m, n, layout, dtype)
+    lib = lib or _load()
+    y64 = np.ascontiguousarray(y, dtype=np.float64)
+    sel = np.zeros(max(F, 1), dtype=np.int64)
+    swaps = np.full(2 * max(R, 1), -1, dtype=np.int64)
+    a = np.zeros(n, dtype=np.float64)
+    hist = np.full(F + 1 + R, np.nan, dtype=np.float64)
+    ns = ctypes.c_int64(0)
+    ld = max(1, m if layout == "col" else n)
+    st = lib.hpscd_oracle_select_swap(_ptr(X), DTYPES[dtype], LAYOUTS[layout], m, n, ld, _ptr(y64),
+                                      int(F), int(R), _ptr(sel), _ptr(swaps), _ptr(a), _ptr(hist),
+                                      ctypes.byref(ns))
+    if st != 0:
+        raise ValueError(f"oracle select_swap: {STATUS[st]}")
+    k = ns.value
+    return sel[:F], swaps[: 2 * R].reshape(R, 2), a, hist[: F + 1 + k]
 
 
 def residual(X, y, a, *, m, n, layout="col", dtype="f32"):

@@ -515,3 +515,89 @@ int hpscd_oracle_solve_order(const void* X, int dt, int lay, int64_t m, int64_t 
   free(e); free(xq); free(dq);
   return status;
 }
+
+/*
+ * Algorithm 3 followed by the feature-removal loop of Sec. 8, literally, in
+ * float64.  The loop is one sentence in the paper: a feature is removed when,
+ * for the updated errors, a feature not yet selected gives lower errors than an
+ * existing one.  Read as an exact swap step over the selected set
+ * S = {k : a_k != 0}, repeated at most R times:
+ *   for every k in S and j not in S (d_j > 0):
+ *     e'    <- e + X_k·a_k                          (k removed)
+ *     dj    <- <X_j, e'> / <X_j, X_j>               (j refitted, Eq. da2)
+ *     E_kj  <- sum_i (e'_i - X_ij·dj)^2
+ *   (k*, j*) <- argmin E_kj (lowest k, then lowest j, on ties)
+ *   if E_k*j* < ||e||^2:  a_k* <- 0,  a_j* <- dj*,  e <- e' - X_j*·dj*
+ *   else stop.
+ * Outputs: sel[F] as hpscd_oracle_select; swaps[2·R] the (k*, j*) of each swap
+ * made (-1 after the last); hist[F + 1 + R] (after the F steps, the residual
+ * ||e|| / ||y|| after each swap); *nswaps.  Returns OR_OK or OR_INVALID /
+ * OR_NOMEM.
+ */
+int hpscd_oracle_select_swap(const void* X, int dt, int lay, int64_t m, int64_t n, int64_t ld,
+                             const double* y, int64_t F, int64_t R, int64_t* sel,
+                             int64_t* swaps, double* a_out, double* hist, int64_t* nswaps) {
+  if (R < 0 || (!swaps && R > 0) || !nswaps) return OR_INVALID;
+  int st = hpscd_oracle_select(X, dt, lay, m, n, ld, y, F, sel, a_out, hist);
+  if (st != OR_OK) return st;
+  double* e = (double*)malloc((size_t)(m > 0 ? m : 1) * sizeof(double));
+  double* ep = (double*)malloc((size_t)(m > 0 ? m : 1) * sizeof(double));
+  double* xk = (double*)malloc((size_t)(m > 0 ? m : 1) * sizeof(double));
+  double* xj = (double*)malloc((size_t)(m > 0 ? m : 1) * sizeof(double));
+  double* dd = (double*)malloc((size_t)n * sizeof(double));
+  if (!e || !ep || !xk || !xj || !dd) {
+    free(e); free(ep); free(xk); free(xj); free(dd);
+    return OR_NOMEM;
+  }
+  /* the residual of the selection's coefficients, recomputed from a */
+  for (int64_t i = 0; i < m; ++i) e[i] = y[i];
+  for (int64_t c = 0; c < n; ++c) {
+    load_column(X, dt, lay, ld, m, c, xk);
+    double q = 0.0;
+    for (int64_t i = 0; i < m; ++i) q += xk[i] * xk[i];
+    dd[c] = q;
+    if (a_out[c] != 0.0)
+      for (int64_t i = 0; i < m; ++i) e[i] = e[i] - xk[i] * a_out[c];
+  }
+  const double ynorm = norm2(y, m);
+  const double scale = ynorm > 0.0 ? ynorm : 1.0;
+  int64_t done = 0;
+  for (int64_t r = 0; r < R; ++r) {
+    double ee = 0.0;
+    for (int64_t i = 0; i < m; ++i) ee += e[i] * e[i];
+    int64_t bk = -1, bj = -1;
+    double bestE = 0.0, bestd = 0.0;
+    for (int64_t k = 0; k < n; ++k) {
+      if (a_out[k] == 0.0) continue;
+      load_column(X, dt, lay, ld, m, k, xk);
+      for (int64_t i = 0; i < m; ++i) ep[i] = e[i] + xk[i] * a_out[k];
+      for (int64_t j = 0; j < n; ++j) {
+        if (a_out[j] != 0.0 || !(dd[j] > 0.0)) continue;
+        load_column(X, dt, lay, ld, m, j, xj);
+        double t = 0.0;
+        for (int64_t i = 0; i < m; ++i) t += xj[i] * ep[i];
+        const double dj = t / dd[j];
+        double E = 0.0;
+        for (int64_t i = 0; i < m; ++i) {
+          const double u = ep[i] - xj[i] * dj;
+          E += u * u;
+        }
+        if (bk < 0 || E < bestE) { bestE = E; bk = k; bj = j; bestd = dj; }
+      }
+    }
+    if (bk < 0 || !(bestE < ee)) break;
+    load_column(X, dt, lay, ld, m, bk, xk);
+    load_column(X, dt, lay, ld, m, bj, xj);
+    for (int64_t i = 0; i < m; ++i) e[i] = (e[i] + xk[i] * a_out[bk]) - xj[i] * bestd;
+    a_out[bk] = 0.0;
+    a_out[bj] = bestd;
+    swaps[2 * done] = bk;
+    swaps[2 * done + 1] = bj;
+    ++done;
+    if (hist) hist[F + done] = norm2(e, m) / scale;
+  }
+  for (int64_t r = done; r < R; ++r) { swaps[2 * r] = -1; swaps[2 * r + 1] = -1; }
+  *nswaps = done;
+  free(e); free(ep); free(xk); free(xj); free(dd);
+  return OR_OK;
+}

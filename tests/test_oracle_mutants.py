@@ -43,6 +43,12 @@ MUTANTS = {
     # to the coefficient of the wrong column
     "order_ignored": ("const int64_t q = order[(s - 1) * n + k];", "const int64_t q = k;"),
     "order_coef_of_step": ("a_out[q] = a_out[q] + step;", "a_out[k] = a_out[k] + step;"),
+    # the swap steps: a swap kept although it does not lower the error; the
+    # removed column's contribution not put back into the residual
+    "swap_accepts_worse": ("if (bk < 0 || !(bestE < ee)) break;",
+                           "if (bk < 0 || !(bestE < 1.5 * ee)) break;"),
+    "swap_forgets_removed": ("e[i] = (e[i] + xk[i] * a_out[bk]) - xj[i] * bestd;",
+                             "e[i] = e[i] - xj[i] * bestd;"),
 }
 
 
@@ -134,6 +140,17 @@ def battery(lib):
                             dtype="f64", tol=0, max_sweeps=2, stop="none", lib=lib)
     if not np.allclose(ro.a, a_pi, rtol=1e-10, atol=1e-12):
         failed.append("order_permutation")
+
+    # swap steps after the greedy selection: the planted support is recovered,
+    # every swap lowers the error and e = y - X·a at the end
+    gs = np.random.default_rng(1)
+    Xw = gs.standard_normal((200, 3)) @ gs.standard_normal((3, 16)) + 0.5 * gs.standard_normal((200, 16))
+    yw = Xw[:, [1, 5, 9]] @ np.array([1.0, -0.8, 0.6]) + 0.05 * gs.standard_normal(200)
+    sel_w, sw_w, a_w, h_w = oracle.select_swap(np.ascontiguousarray(Xw.T), yw, m=200, n=16, F=3, R=4,
+                                               dtype="f64", lib=lib)
+    if not (sw_w.tolist() == [[10, 5], [9, 11], [11, 9], [-1, -1]] and np.all(np.diff(h_w) < 0) and
+            abs(h_w[-1] - np.linalg.norm(yw - Xw @ a_w) / np.linalg.norm(yw)) <= 1e-12):
+        failed.append("swap")
     return failed
 
 

@@ -208,3 +208,77 @@ def test_order_rejects_indices_outside_the_columns():
         order_solve(s, np.full((2, 6), 6), 2)
     with pytest.raises(ValueError):
         order_solve(s, np.full((2, 6), -1), 2)
+
+
+# ---------------- the feature-removal loop of Sec. 8 (swap steps after Algorithm 3) ----------------
+
+def test_swap_with_no_rounds_is_algorithm_3():
+    s = sys64(120, 30, 31)
+    sel, a, hist = oracle.select(s.X, s.y, m=s.m, n=s.n, F=8, dtype="f64")
+    sel2, swaps, a2, hist2 = oracle.select_swap(s.X, s.y, m=s.m, n=s.n, F=8, R=0, dtype="f64")
+    np.testing.assert_array_equal(sel2, sel)
+    np.testing.assert_array_equal(a2, a)
+    np.testing.assert_array_equal(hist2, hist)
+
+
+def test_swaps_recover_the_planted_support_greedy_missed():
+    """Correlated columns (three latent factors) and a planted support {1, 5, 9}:
+    the greedy steps take {10, 9, 1}; the swap steps exchange 10 -> 5, 9 -> 11,
+    11 -> 9 and end on the planted support.  Every swap lowers the error, the
+    refitted column is orthogonal to the residual it leaves (Eq. res-x), and
+    e = y - X·a holds."""
+    g = np.random.default_rng(1)
+    m, n = 200, 16
+    base = g.standard_normal((m, 3))
+    X = base @ g.standard_normal((3, n)) + 0.5 * g.standard_normal((m, n))
+    y = X[:, [1, 5, 9]] @ np.array([1.0, -0.8, 0.6]) + 0.05 * g.standard_normal(m)
+    Xs = np.ascontiguousarray(X.T)
+    sel, swaps, a, hist = oracle.select_swap(Xs, y, m=m, n=n, F=3, R=4, dtype="f64")
+    assert sorted(sel.tolist()) == [1, 9, 10]
+    assert swaps.tolist() == [[10, 5], [9, 11], [11, 9], [-1, -1]]
+    assert sorted(np.flatnonzero(a).tolist()) == [1, 5, 9]
+    assert np.all(np.diff(hist) < 0)
+    e = y - X @ a
+    assert abs(X[:, 9] @ e) <= 1e-10 * np.linalg.norm(X[:, 9]) * np.linalg.norm(e)
+    assert hist[-1] == pytest.approx(np.linalg.norm(e) / np.linalg.norm(y), rel=1e-12)
+
+
+def test_swap_is_the_best_exchange_and_keeps_the_bookkeeping():
+    """Each swap is the single exchange (drop k, add j refitted on the residual
+    without k) of least error: brute force over every exchange by a least-squares
+    fit of the one new coefficient (numpy lstsq) agrees; e = y - X·a throughout."""
+    g = np.random.default_rng(13)
+    m, n = 150, 12
+    base = g.standard_normal(m)
+    X = np.stack([base * (0.6 if c % 3 == 0 else 0.1) + g.standard_normal(m) for c in range(n)], axis=1)
+    y = X @ g.standard_normal(n) * 0.5 + X[:, 2] * 2.0
+    Xs = np.ascontiguousarray(X.T)
+    sel, swaps0, a0, hist0 = oracle.select_swap(Xs, y, m=m, n=n, F=4, R=0, dtype="f64")
+    sel, swaps, a1, hist1 = oracle.select_swap(Xs, y, m=m, n=n, F=4, R=1, dtype="f64")
+    e0 = y - X @ a0
+    best, pair = None, None
+    for k in np.flatnonzero(a0):
+        ep = e0 + X[:, k] * a0[k]
+        for j in range(n):
+            if a0[j] != 0:
+                continue
+            coef = np.linalg.lstsq(X[:, [j]], ep, rcond=None)[0][0]
+            E = np.sum((ep - X[:, j] * coef) ** 2)
+            if best is None or E < best:
+                best, pair = E, (k, j)
+    if best < e0 @ e0:
+        assert tuple(swaps[0]) == pair
+        np.testing.assert_allclose(np.sum((y - X @ a1) ** 2), best, rtol=1e-10)
+    else:
+        assert tuple(swaps[0]) == (-1, -1)
+    np.testing.assert_allclose(hist1[-1], np.linalg.norm(y - X @ a1) / np.linalg.norm(y), rtol=1e-12)
+
+
+def test_no_swap_when_the_selection_is_already_best():
+    g = np.random.default_rng(14)
+    Q, _ = np.linalg.qr(g.standard_normal((60, 10)))
+    y = Q @ np.array([5.0, 4.0, 3.0, 0.1, 0.1, 0.1, 0.1, 0.1, 0.1, 0.1])
+    sel, swaps, a, hist = oracle.select_swap(np.ascontiguousarray(Q.T), y, m=60, n=10, F=3, R=4,
+                                             dtype="f64")
+    assert sorted(sel.tolist()) == [0, 1, 2]
+    assert np.all(swaps == -1) and len(hist) == 4
