@@ -346,6 +346,17 @@ def next_algorithms(hp, synth, ctx, X, y, s, reps=3):
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / reps
+    ctx.select_swap(X, y, F, 8)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        rs, sel_s, swaps = ctx.select_swap(X, y, F, 8)
+    e1.record()
+    torch.cuda.synchronize()
+    out["alg3_select_32_then_swaps_8"] = {
+        "ms": e0.elapsed_time(e1) / reps, "swaps_made": int((swaps[:, 0] >= 0).sum()),
+        "passes": int(rs.timing["passes"]), "rel_res_after": float(rs.rel_res)}
     out["alg3_select_32"] = {"ms": ms, "ms_per_step": r.timing["sweep_ms"] / (F + 1),
                              "sweep_kernel_GBps": sweep_kernel_bytes(s.m, s.n, esz, r.timing["passes"])
                              / (r.timing["sweep_ms"] * 1e-3) / 1e9,

@@ -234,6 +234,29 @@ int hpscd_solve_async(hpscd_ctx* ctx, const void* X, int dtype, int64_t m, int64
  * result). */
 int hpscd_async_timings(hpscd_ctx* ctx, int64_t count, hpscd_timing* out);
 
+/*
+ * Algorithm 3 followed by the feature-removal loop of Sec. 8: after the F =
+ * opts->max_sweeps selection steps of hpscd_select, at most swap_rounds swap
+ * steps.  A swap step drops a selected column k (a_k != 0) and adds an
+ * unselected column j refitted on the residual without k
+ * (a_j = <X_j, e + X_k·a_k> / <X_j, X_j>, Eq. da2), choosing the pair of least
+ * resulting error (lowest k, then j, on ties), and is made only if that error
+ * is below the current one; the loop ends at the first step that finds none.
+ * Each swap step costs one streaming pass over X (the couplings come from G).
+ * If a stopping rule ends the selection before F steps, no swap is tried.
+ *   sel    HOST int64[max_sweeps]: as hpscd_select.
+ *   swaps  HOST int64[2·swap_rounds]: (k, j) of each swap made, -1 after.
+ *   hist   HOST double[max_sweeps + swap_rounds + 1] or NULL: ||e||/||y|| after
+ *          each selection step, then after each swap.
+ *   steps_done: selection steps + swaps made.
+ * Column-major X (m >= 1, 1 <= n <= 512); 0 <= swap_rounds <= 2^20.  Errors as
+ * hpscd_select.
+ */
+int hpscd_select_swap(hpscd_ctx* ctx, const void* X, int dtype, int64_t m, int64_t n, int64_t ld,
+                      const float* y, float* a, const hpscd_opts* opts, int64_t swap_rounds,
+                      int64_t* sel, int64_t* swaps, double* hist, int64_t* steps_done,
+                      double* final_rel_res);
+
 /* Same as hpscd_solve but X, y and a are HOST pointers: the call copies X and y
  * to the device workspace, solves, and copies a back (an end-to-end call). */
 int hpscd_solve_host(hpscd_ctx* ctx, const void* X, int dtype, int layout, int64_t m,

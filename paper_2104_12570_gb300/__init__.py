@@ -116,6 +116,11 @@ SIGNATURES = {
                            ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(Opts), ctypes.c_void_p,
                            ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)],
                           ctypes.c_int),
+    "hpscd_select_swap": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int64,
+                           ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                           ctypes.POINTER(Opts), ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                           ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64),
+                           ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "hpscd_select": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int64,
                       ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
                       ctypes.POINTER(Opts), ctypes.c_void_p, ctypes.c_void_p,
@@ -440,6 +445,30 @@ class Context:
                                           hist.ctypes.data_as(ctypes.c_void_p), ctypes.byref(sw),
                                           ctypes.byref(rr))
         return self._finish(rc, hist, sw, rr, a)
+
+    def select_swap(self, X, y, F: int, R: int, *, tol=0.0, stop="none"):
+        """Algorithm 3 for F steps, then at most R swap steps of the feature-removal
+        loop (Sec. 8); returns (SolveResult, chosen column per selection step,
+        (R, 2) array of the (dropped, added) pair of each swap, -1 after the last)."""
+        import torch
+        ptr, dt, lay, m, n, ld = _describe(X)
+        if lay != COL or not X.is_cuda:
+            raise ValueError("select_swap needs a column-major CUDA X")
+        a = torch.empty(n, dtype=torch.float32, device=X.device)
+        o = make_opts(tol, F, stop)
+        hist = np.full(int(F) + int(R) + 1, np.nan)
+        sel = np.full(max(int(F), 1), -1, dtype=np.int64)
+        swaps = np.full(2 * max(int(R), 1), -1, dtype=np.int64)
+        sw, rr = ctypes.c_int64(0), ctypes.c_double(0.0)
+        self.set_stream(torch.cuda.current_stream(X.device))
+        rc = self._lib.hpscd_select_swap(self._h, ctypes.c_void_p(ptr), dt, m, n, ld,
+                                         ctypes.c_void_p(y.data_ptr()), ctypes.c_void_p(a.data_ptr()),
+                                         ctypes.byref(o), int(R), sel.ctypes.data_as(ctypes.c_void_p),
+                                         swaps.ctypes.data_as(ctypes.c_void_p),
+                                         hist.ctypes.data_as(ctypes.c_void_p), ctypes.byref(sw),
+                                         ctypes.byref(rr))
+        return (self._finish(rc, hist, sw, rr, a), sel[: int(F)],
+                swaps[: 2 * int(R)].reshape(int(R), 2))
 
     def solve_order(self, X, y, order, *, tol=1e-6, max_sweeps=None, stop="rel_res", a0=None,
                     out=None) -> SolveResult:

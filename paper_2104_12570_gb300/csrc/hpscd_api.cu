@@ -30,7 +30,7 @@ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 struct Layout {
   size_t G = 0, Gt = 0, dvec = 0, partial = 0, e = 0, hacc = 0, npart = 0, gw = 0, ypart = 0, hist = 0,
-         ctl = 0, sel = 0, order = 0;
+         ctl = 0, sel = 0, order = 0, swp = 0;
   size_t xcopy = 0, ycopy = 0, acopy = 0, total = 0;
 };
 
@@ -71,7 +71,8 @@ int check_shape(int dtype, int layout, int64_t m, int64_t n, int64_t ld) {
 
 // Sizes the workspace of a solve.  Returns false for unsupported shapes.
 int make_plan(const hpscd_ctx* ctx, int dtype, int layout, int64_t m, int64_t n, int64_t ld,
-              const hpscd_opts* o, bool host_copies, Plan* P, int64_t order_entries = 0) {
+              const hpscd_opts* o, bool host_copies, Plan* P, int64_t order_entries = 0,
+              int64_t swap_rounds = 0) {
   if (layout != HPSCD_COL_MAJOR) return HPSCD_ERR_UNSUPPORTED;
   if (n > 512) return HPSCD_ERR_UNSUPPORTED;
   if (!tall_config(dtype, (int)n, ctx->max_smem, &P->cfg)) return HPSCD_ERR_UNSUPPORTED;
@@ -104,6 +105,7 @@ int make_plan(const hpscd_ctx* ctx, int dtype, int layout, int64_t m, int64_t n,
   L.ctl = take(sizeof(GridCtl));
   L.sel = take((size_t)(o->max_sweeps + 1) * sizeof(int64_t));
   L.order = take((size_t)(order_entries > 0 ? order_entries : 1) * sizeof(int32_t));
+  L.swp = take((size_t)2 * (swap_rounds > 0 ? swap_rounds : 1) * sizeof(int64_t));
   if (host_copies) {
     L.xcopy = take((size_t)(n > 0 ? n : 1) * (size_t)ld * esize(dtype));
     L.ycopy = take((size_t)(m > 0 ? m : 1) * sizeof(float));
@@ -345,7 +347,8 @@ int solve_device(hpscd_ctx* ctx, const void* X, int dtype, int layout, int64_t m
                  int64_t ld, const float* y, float* a, int a_is_guess, const hpscd_opts* o,
                  double* hist, int64_t* sweeps_done, double* final_rel_res, const Plan& P,
                  int thr = 0, int select = 0, int64_t* sel = nullptr, const int* order = nullptr,
-                 hpscd_sys_result* async_res = nullptr, double* hist_dev = nullptr) {
+                 hpscd_sys_result* async_res = nullptr, double* hist_dev = nullptr,
+                 int swap_rounds = 0, int64_t* swaps = nullptr) {
   if (m == 0) return solve_empty_rows(ctx, n, a, a_is_guess, o, hist, sweeps_done, final_rel_res);
   char* ws = static_cast<char*>(ctx->ws);
   const Layout& L = P.L;
@@ -404,6 +407,11 @@ int solve_device(hpscd_ctx* ctx, const void* X, int dtype, int layout, int64_t m
   p.thr = thr;
   p.select = select;
   p.sel_out = select ? reinterpret_cast<int64_t*>(ws + L.sel) : nullptr;
+  p.swap_rounds = select ? swap_rounds : 0;
+  p.swap_out = (select && swap_rounds > 0) ? reinterpret_cast<int64_t*>(ws + L.swp) : nullptr;
+  if (p.swap_out && cudaMemsetAsync(p.swap_out, 0xff, (size_t)2 * swap_rounds * sizeof(int64_t), st) !=
+                        cudaSuccess)
+    return HPSCD_ERR_CUDA;
   p.order = order;
   p.trace = nullptr;
   p.trace_passes = 0;
@@ -436,16 +444,22 @@ int solve_device(hpscd_ctx* ctx, const void* X, int dtype, int layout, int64_t m
     return HPSCD_ERR_CUDA;
   if (cudaStreamSynchronize(st) != cudaSuccess) return HPSCD_ERR_CUDA;
   const GridCtl c = *ctx->ctl_host;
-  if (hist && c.sweeps >= 0 && c.sweeps <= o->max_sweeps) {
+  const int64_t last = o->max_sweeps + p.swap_rounds;  // passes a solve may make, less one
+  if (hist && c.sweeps >= 0 && c.sweeps <= last) {
     if (cudaMemcpy(hist, p.hist, (size_t)(c.sweeps + 1) * sizeof(double), cudaMemcpyDeviceToHost) !=
         cudaSuccess)
       return HPSCD_ERR_CUDA;
   }
-  if (sel && select && c.sweeps > 0 && c.sweeps <= o->max_sweeps) {
-    if (cudaMemcpy(sel, p.sel_out, (size_t)c.sweeps * sizeof(int64_t), cudaMemcpyDeviceToHost) !=
+  const int64_t nsel = c.sweeps < o->max_sweeps ? c.sweeps : o->max_sweeps;
+  if (sel && select && nsel > 0 && c.sweeps <= last) {
+    if (cudaMemcpy(sel, p.sel_out, (size_t)nsel * sizeof(int64_t), cudaMemcpyDeviceToHost) !=
         cudaSuccess)
       return HPSCD_ERR_CUDA;
   }
+  if (swaps && p.swap_out &&
+      cudaMemcpy(swaps, p.swap_out, (size_t)2 * swap_rounds * sizeof(int64_t), cudaMemcpyDeviceToHost) !=
+          cudaSuccess)
+    return HPSCD_ERR_CUDA;
   if (sweeps_done) *sweeps_done = c.sweeps;
   if (final_rel_res) *final_rel_res = c.final_res;
   hpscd_timing t{};
@@ -643,6 +657,30 @@ int hpscd_select(hpscd_ctx* ctx, const void* X, int dtype, int64_t m, int64_t n,
   if ((rc = ensure_ws(ctx, P.L.total))) return rc;
   return solve_device(ctx, X, dtype, HPSCD_COL_MAJOR, m, n, ld, y, a, 0, opts, hist, steps_done,
                       final_rel_res, P, 0, 1, sel);
+}
+
+int hpscd_select_swap(hpscd_ctx* ctx, const void* X, int dtype, int64_t m, int64_t n, int64_t ld,
+                      const float* y, float* a, const hpscd_opts* opts, int64_t swap_rounds,
+                      int64_t* sel, int64_t* swaps, double* hist, int64_t* steps_done,
+                      double* final_rel_res) {
+  if (!ctx) return HPSCD_ERR_INVALID_ARG;
+  int rc = check_opts(opts);
+  if (rc) return rc;
+  if ((rc = check_shape(dtype, HPSCD_COL_MAJOR, m, n, ld))) return rc;
+  if (m < 1 || n < 1 || !X || !y || !a || (!sel && opts->max_sweeps > 0) || swap_rounds < 0 ||
+      swap_rounds > (1 << 20) || (!swaps && swap_rounds > 0))
+    return HPSCD_ERR_INVALID_ARG;
+  if (opts->refresh_every != 0) return HPSCD_ERR_UNSUPPORTED;
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return HPSCD_ERR_CUDA;
+  // the workspace holds the history of the selection steps and the swap steps
+  hpscd_opts osz = *opts;
+  osz.max_sweeps = opts->max_sweeps + swap_rounds;
+  Plan P;
+  if ((rc = make_plan(ctx, dtype, HPSCD_COL_MAJOR, m, n, ld, &osz, false, &P, 0, swap_rounds))) return rc;
+  if ((rc = ensure_ws(ctx, P.L.total))) return rc;
+  return solve_device(ctx, X, dtype, HPSCD_COL_MAJOR, m, n, ld, y, a, 0, opts, hist, steps_done,
+                      final_rel_res, P, 0, 1, sel, nullptr, nullptr, nullptr, (int)swap_rounds, swaps);
 }
 
 int hpscd_solve_order(hpscd_ctx* ctx, const void* X, int dtype, int64_t m, int64_t n, int64_t ld,

@@ -102,6 +102,8 @@ struct TallParams {
   int select;         // 1: Algorithm 3 — each pass adds the one column with the largest
                       // <X_j,e>^2 / <X_j,X_j> (greedy selection) instead of a sweep
   int64_t* sel_out;   // Algorithm 3: column chosen after pass p, [max_sweeps]
+  int swap_rounds;    // Algorithm 3 then at most this many swap steps (Sec. 8's removal loop)
+  int64_t* swap_out;  // the (dropped, added) pair of each swap step, [swap_rounds][2]; -1: none
   const int* order;   // or null: step k of sweep s takes column order[(s-1)·n + k]
                       // ([max_sweeps][n], each in [0, n); the random-index variant)
   unsigned long long* trace;  // optional: per-pass phase timestamps (see hpscd_trace)

@@ -236,6 +236,78 @@ __device__ int select_step(int n, int npad, const float* r, const float* d, floa
   return bj;
 }
 
+// A swap step of the feature-removal loop (Sec. 8), after the selection steps:
+// over the selected columns k (a_k != 0) and the others j (d_j > 0), the error
+// after dropping k and refitting j on the residual without it is
+//   E_kj = ||e||^2 + 2 a_k h_k + a_k^2 d_k - t^2 / d_j,  t = h_j + a_k G_jk,
+// with h = X^T e = r·d and G_jk = G~_kj·d_k (row k of G~).  Thread j scores its
+// column against every k; a block argmin (lowest k, then j, on ties) picks the
+// pair.  When E < ||e||^2 the step's update is da_k = -a_k, da_j = t / d_j and
+// the function returns k (and j through *jout); otherwise it returns -1.
+// ks: shared int scratch of npad entries (the selected columns); fscr/iscr: as
+// select_step (fscr holds doubles here, 2·NW of them).
+__device__ int swap_step(int n, int npad, const float* r, const float* d, const double* a64,
+                         const float* __restrict__ Gt, int ldG, double ee, float* da, int* ks,
+                         double* fscr, int* iscr, int* jout) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) {
+    int c = 0;
+    for (int k = 0; k < n; ++k)
+      if (a64[k] != 0.0) ks[1 + c++] = k;
+    ks[0] = c;
+  }
+  named_sync(NT);
+  const int ns = ks[0];
+  double best = 0.0;
+  int bk = 0x7fffffff, bj = 0x7fffffff;
+  for (int j = tid; j < n; j += NT) {
+    const double dj = (double)d[j];
+    if (a64[j] != 0.0 || !(dj > 0.0)) continue;
+    const double hj = (double)r[j] * dj;
+    for (int q = 0; q < ns; ++q) {
+      const int k = ks[1 + q];
+      const double ak = a64[k], dk = (double)d[k];
+      const double hk = (double)r[k] * dk;
+      const double t = hj + ak * ((double)__ldg(Gt + (int64_t)k * ldG + j) * dk);
+      const double E = ee + 2.0 * ak * hk + ak * ak * dk - t * t / dj;
+      if (bk == 0x7fffffff || E < best || (E == best && (k < bk || (k == bk && j < bj)))) {
+        best = E; bk = k; bj = j;
+      }
+    }
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const double ob = __shfl_xor_sync(FULL_MASK, best, off);
+    const int ok = __shfl_xor_sync(FULL_MASK, bk, off);
+    const int oj = __shfl_xor_sync(FULL_MASK, bj, off);
+    if (ok != 0x7fffffff &&
+        (bk == 0x7fffffff || ob < best || (ob == best && (ok < bk || (ok == bk && oj < bj))))) {
+      best = ob; bk = ok; bj = oj;
+    }
+  }
+  if (lane == 0) { fscr[warp] = best; iscr[warp] = bk; iscr[NW + warp] = bj; }
+  named_sync(NT);
+  best = fscr[0]; bk = iscr[0]; bj = iscr[NW];
+  for (int w = 1; w < NW; ++w) {
+    const int ok = iscr[w], oj = iscr[NW + w];
+    if (ok != 0x7fffffff &&
+        (bk == 0x7fffffff || fscr[w] < best || (fscr[w] == best && (ok < bk || (ok == bk && oj < bj))))) {
+      best = fscr[w]; bk = ok; bj = oj;
+    }
+  }
+  const bool take = bk != 0x7fffffff && best < ee;
+  double delta = 0.0;
+  if (take) {
+    const double dk = (double)d[bk], dj = (double)d[bj];
+    delta = ((double)r[bj] * dj + a64[bk] * ((double)__ldg(Gt + (int64_t)bk * ldG + bj) * dk)) / dj;
+  }
+  for (int c = tid; c < npad; c += NT)
+    da[c] = !take ? 0.f : (c == bk ? (float)(-a64[bk]) : (c == bj ? (float)delta : 0.f));
+  named_sync(NT);
+  *jout = take ? bj : -1;
+  return take ? bk : -1;
+}
+
 // Error-free product and sum (Ogita, Rump, Oishi, "Accurate sum and dot
 // product", SIAM J. Sci. Comput. 26(6), 2005): Dot2 keeps the running sum as an
 // unevaluated float pair, giving float64-grade accuracy for the true-residual pass.
@@ -315,9 +387,14 @@ __device__ __forceinline__ void chunk_compute(const T* __restrict__ st, int warp
   }
 }
 
-template <typename T, int CW, int NCH, bool ORD>
+// KMODE 0: the sweep (Algorithm 1, or Algorithm 2 with thr); 1: a given column
+// order per sweep (float32); 2: greedy selection (Algorithm 3) and its swap steps.
+// Separate instantiations keep each mode's code out of the others.
+template <typename T, int CW, int NCH, int KMODE>
 __global__ void __launch_bounds__(NT, 1)
     tall_sweep_kernel(const __grid_constant__ CUtensorMap tmap, const TallParams p) {
+  constexpr bool ORD = KMODE == 1;
+  constexpr bool SEL = KMODE == 2;
   constexpr int C = NW * CW;          // columns per chunk
   constexpr int NPAD = C * NCH;       // padded column count
   constexpr int CPW = CW * NCH;       // columns per warp over a whole row
@@ -616,25 +693,44 @@ __global__ void __launch_bounds__(NT, 1)
     const double rel = ynorm > 0.0 ? enorm / ynorm : enorm;
     if (blockIdx.x == 0 && tid == 0) p.hist[pass] = rel;
     sweeps = pass;
+    // after the selection steps of Algorithm 3, up to swap_rounds swap steps
+    const bool swap_phase = SEL && p.swap_rounds > 0 && pass >= p.max_sweeps;
     bool stop = false;
     if (!isfinite(rel)) {
       status = HPSCD_ERR_NONFINITE; stop = true;
-    } else if (p.stop_rule == HPSCD_STOP_REL_RES && rel <= p.tol) {
+    } else if (!swap_phase && p.stop_rule == HPSCD_STOP_REL_RES && rel <= p.tol) {
       status = HPSCD_OK; stop = true;
-    } else if (p.stop_rule == HPSCD_STOP_REL_CHANGE && pass >= 1 &&
+    } else if (!swap_phase && p.stop_rule == HPSCD_STOP_REL_CHANGE && pass >= 1 &&
                (r_prev == 0.0 || fabs(r_prev - rel) < p.tol * r_prev)) {
       status = HPSCD_OK; stop = true;
-    } else if (pass == p.max_sweeps) {
-      status = (p.stop_rule == HPSCD_STOP_NONE) ? HPSCD_OK : HPSCD_ERR_NOT_CONVERGED;
+    } else if (pass == p.max_sweeps + (SEL ? p.swap_rounds : 0)) {
+      status = (p.stop_rule == HPSCD_STOP_NONE || swap_phase) ? HPSCD_OK : HPSCD_ERR_NOT_CONVERGED;
       stop = true;
     }
     r_prev = rel;
     if (stop) break;
 
-    if (p.select) {
+    int removed = -1;  // a swap step's dropped column (its coefficient becomes exactly 0)
+    if constexpr (SEL) {
+    if (swap_phase) {
+      // scratch: the row-sum buffers are free between passes
+      int jin = -1;
+      removed = swap_step(n, NPAD, rvec, dd_s, a64_s, p.Gt, p.ldG, scal[0], da_s,
+                          reinterpret_cast<int*>(red_hi) + 4 * NW, reinterpret_cast<double*>(red_lo),
+                          reinterpret_cast<int*>(red_hi), &jin);
+      if (blockIdx.x == 0 && tid == 0 && p.swap_out) {
+        p.swap_out[2 * (pass - p.max_sweeps)] = removed;
+        p.swap_out[2 * (pass - p.max_sweeps) + 1] = jin;
+      }
+      if (removed < 0) {  // no exchange lowers the error: done
+        status = HPSCD_OK;
+        break;
+      }
+    } else {
       // scratch for the argmax: the row-sum buffer is free between passes
       const int jhat = select_step(n, NPAD, rvec, dd_s, da_s, red_hi, reinterpret_cast<int*>(red_lo));
       if (blockIdx.x == 0 && tid == 0 && p.sel_out) p.sel_out[pass] = jhat;
+    }
     } else if constexpr (ORD) {
       // the steps of sweep pass + 1 take the columns order[pass·n + k]: gather
       // their r and the diagonal blocks of their couplings, substitute over the
@@ -681,7 +777,8 @@ __global__ void __launch_bounds__(NT, 1)
     const int64_t nx = pass + 1;
     const bool next_refresh = p.refresh_every > 0 && nx % p.refresh_every == 0;
     for (int c = tid; c < NPAD; c += NT) {
-      a64_s[c] += (double)da_s[c];
+      if constexpr (SEL) a64_s[c] = (c == removed) ? 0.0 : a64_s[c] + (double)da_s[c];
+      else a64_s[c] += (double)da_s[c];
       vsm[c] = next_refresh ? (float)a64_s[c] : da_s[c];
     }
     named_sync(NT);
@@ -712,10 +809,10 @@ __global__ void __launch_bounds__(NT, 1)
   }
 }
 
-template <typename T, int CW, int NCH, bool ORD = false>
+template <typename T, int CW, int NCH, int KMODE = 0>
 cudaError_t launch_one(const TallConfig& cfg, const CUtensorMap* tmap, const TallParams& p,
                        int grid, cudaStream_t stream) {
-  auto kern = tall_sweep_kernel<T, CW, NCH, ORD>;
+  auto kern = tall_sweep_kernel<T, CW, NCH, KMODE>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        cfg.smem_bytes);
   if (e != cudaSuccess) return e;
@@ -784,7 +881,9 @@ cudaError_t launch_tall_sweep(int dtype, const TallConfig& cfg, const CUtensorMa
 #define HPSCD_TALL_CASE(T, W, N)                                        \
   if (cfg.cpw == W && cfg.rpl == N) return launch_one<T, W, N>(cfg, tmap, p, grid, stream);
 #define HPSCD_TALL_ORD_CASE(W, N)                                       \
-  if (cfg.cpw == W && cfg.rpl == N) return launch_one<float, W, N, true>(cfg, tmap, p, grid, stream);
+  if (cfg.cpw == W && cfg.rpl == N) return launch_one<float, W, N, 1>(cfg, tmap, p, grid, stream);
+#define HPSCD_TALL_SEL_CASE(T, W, N)                                    \
+  if (cfg.cpw == W && cfg.rpl == N) return launch_one<T, W, N, 2>(cfg, tmap, p, grid, stream);
   if (p.order) {  // the given-order variant: float32 only
     if (dtype != HPSCD_F32) return cudaErrorInvalidValue;
     HPSCD_TALL_ORD_CASE(1, 1)
@@ -793,6 +892,24 @@ cudaError_t launch_tall_sweep(int dtype, const TallConfig& cfg, const CUtensorMa
     HPSCD_TALL_ORD_CASE(4, 2)
     HPSCD_TALL_ORD_CASE(4, 4)
     HPSCD_TALL_ORD_CASE(4, 8)
+    return cudaErrorInvalidConfiguration;
+  }
+  if (p.select) {  // selection and swap steps
+    if (dtype == HPSCD_F32) {
+      HPSCD_TALL_SEL_CASE(float, 1, 1)
+      HPSCD_TALL_SEL_CASE(float, 2, 1)
+      HPSCD_TALL_SEL_CASE(float, 4, 1)
+      HPSCD_TALL_SEL_CASE(float, 4, 2)
+      HPSCD_TALL_SEL_CASE(float, 4, 4)
+      HPSCD_TALL_SEL_CASE(float, 4, 8)
+    } else {
+      HPSCD_TALL_SEL_CASE(uint16_t, 1, 1)
+      HPSCD_TALL_SEL_CASE(uint16_t, 2, 1)
+      HPSCD_TALL_SEL_CASE(uint16_t, 4, 1)
+      HPSCD_TALL_SEL_CASE(uint16_t, 8, 1)
+      HPSCD_TALL_SEL_CASE(uint16_t, 8, 2)
+      HPSCD_TALL_SEL_CASE(uint16_t, 8, 4)
+    }
     return cudaErrorInvalidConfiguration;
   }
   if (dtype == HPSCD_F32) {
@@ -812,6 +929,7 @@ cudaError_t launch_tall_sweep(int dtype, const TallConfig& cfg, const CUtensorMa
   }
 #undef HPSCD_TALL_CASE
 #undef HPSCD_TALL_ORD_CASE
+#undef HPSCD_TALL_SEL_CASE
   return cudaErrorInvalidConfiguration;
 }
 

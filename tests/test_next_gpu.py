@@ -180,3 +180,49 @@ def test_full_size_random_order(ctx):
     o = oracle.solve_order(s.X, s.y, m=s.m, n=s.n, order=order, tol=0, max_sweeps=3, stop="none")
     assert rel(r.a.cpu().numpy(), o.a) <= 1e-5
     np.testing.assert_allclose(r.hist, o.hist, rtol=1e-5)
+
+
+# ---- the feature-removal loop of Sec. 8: swap steps after Algorithm 3 ----
+
+@pytest.mark.parametrize("seed,m,n,k_lat,supp,F,R", [(1, 200, 16, 3, 3, 3, 4), (3, 200, 16, 3, 3, 3, 4),
+                                                     (100, 20000, 96, 4, 5, 5, 6),
+                                                     (101, 20000, 96, 4, 5, 5, 6)])
+def test_swap_steps_match_oracle(ctx, seed, m, n, k_lat, supp, F, R):
+    """Correlated columns where the greedy steps miss part of the planted support:
+    the swap steps (dropped and added columns) are index work and must match the
+    oracle exactly; coefficients and history at 1e-5."""
+    if m == 200:
+        # the same draws as the oracle pins use
+        g = np.random.default_rng(seed)
+        base = g.standard_normal((m, 3))
+        Xd = base @ g.standard_normal((3, n)) + 0.5 * g.standard_normal((m, n))
+        y = Xd[:, [1, 5, 9]] @ np.array([1.0, -0.8, 0.6]) + 0.05 * g.standard_normal(m)
+        s = synth.System(X=np.ascontiguousarray(Xd.T).astype(np.float32), y=y.astype(np.float32),
+                         a_true=np.zeros(n), m=m, n=n, layout="col", dtype="f32")
+    else:
+        g = np.random.default_rng(seed)
+        base = g.standard_normal((m, k_lat))
+        Xd = base @ g.standard_normal((k_lat, n)) + 0.4 * g.standard_normal((m, n))
+        sp = g.choice(n, supp, replace=False)
+        w = g.uniform(0.5, 1.5, supp) * np.where(g.random(supp) < 0.5, -1, 1)
+        y = Xd[:, sp] @ w + 0.05 * g.standard_normal(m)
+        s = synth.System(X=np.ascontiguousarray(Xd.T).astype(np.float32), y=y.astype(np.float32),
+                         a_true=np.zeros(n), m=m, n=n, layout="col", dtype="f32")
+    X, yv = to_gpu(s)
+    r, sel, swaps = ctx.select_swap(X, yv, F, R)
+    osel, oswaps, oa, ohist = oracle.select_swap(s.X, s.y, m=m, n=n, F=F, R=R)
+    np.testing.assert_array_equal(sel, osel)
+    np.testing.assert_array_equal(swaps, oswaps)
+    assert (oswaps[:, 0] >= 0).sum() >= 2  # the case exercises the loop
+    assert r.status == "ok" and r.sweeps == F + (oswaps[:, 0] >= 0).sum()
+    assert rel(r.a.cpu().numpy(), oa) <= 1e-5
+    np.testing.assert_allclose(r.hist, ohist, rtol=1e-5)
+
+
+def test_swap_with_no_rounds_is_selection(ctx):
+    s = planted(3000, 64, 11, [4, 9, 30], noise=0.01)
+    X, y = to_gpu(s)
+    r0, sel0 = ctx.select(X, y, 6)
+    r1, sel1, swaps = ctx.select_swap(X, y, 6, 0)
+    np.testing.assert_array_equal(sel0, sel1)
+    assert torch.equal(r0.a, r1.a) and swaps.shape == (0, 2)
