@@ -248,6 +248,33 @@ def _describe(X):
     raise ValueError("X must be column-major (stride (1, ld)) or row-major (stride (ld, 1))")
 
 
+def _check_vec(v, length: int, name: str, device=None):
+    """v must be a contiguous float32 CUDA vector of `length` entries (on `device`
+    when given): the library reads and writes exactly that many entries."""
+    import torch
+    if not (isinstance(v, torch.Tensor) and v.is_cuda and v.dtype == torch.float32
+            and v.is_contiguous() and v.numel() == length
+            and (device is None or v.device == device)):
+        raise TypeError(f"{name} must be a contiguous float32 CUDA vector of length {length}"
+                        + (f" on {device}" if device is not None else ""))
+
+
+def _coef_out(X, n, out, a0):
+    """The coefficient vector of a device solve: `out` (checked) or a new one,
+    filled from a0 (n entries) when a warm start is given."""
+    import torch
+    if out is not None:
+        _check_vec(out, n, "out", X.device)
+        a = out
+    else:
+        a = torch.empty(n, dtype=torch.float32, device=X.device)
+    if a0 is not None:
+        if int(getattr(a0, "numel", lambda: np.size(a0))()) != n:
+            raise ValueError(f"a0 must have n = {n} entries")
+        a.copy_(a0 if isinstance(a0, torch.Tensor) else torch.as_tensor(np.asarray(a0, np.float32)))
+    return a
+
+
 @dataclass
 class SolveResult:
     a: object
@@ -272,6 +299,16 @@ class Context:
         self._children = weakref.WeakSet()  # batches and networks made on this context
         if timeout_s is not None:
             self.set_timeout(timeout_s)
+
+    def _device_args(self, X, y):
+        """X must be a CUDA tensor on this context's device and y a float32 CUDA
+        vector of its m rows there (the kernels dereference both)."""
+        import torch
+        if not (isinstance(X, torch.Tensor) and X.is_cuda):
+            raise TypeError("X must be a CUDA tensor (use solve_host for host arrays)")
+        if X.device.index != self.device:
+            raise ValueError(f"X is on {X.device}, the context on cuda:{self.device}")
+        _check_vec(y, X.shape[0], "y", X.device)
 
     @staticmethod
     def _stream_handle(stream):
@@ -354,16 +391,15 @@ class Context:
         Returns the coefficient tensor (valid once the stream has passed the solve)."""
         import torch
         ptr, dt, lay, m, n, ld = _describe(X)
-        if lay != COL or not X.is_cuda:
+        self._device_args(X, y)
+        if lay != COL:
             raise ValueError("solve_async needs a column-major CUDA X")
-        if not (res.is_cuda and res.is_contiguous() and res.numel() * res.element_size() >= RESULT_BYTES):
+        if not (isinstance(res, torch.Tensor) and res.is_cuda and res.device == X.device and res.is_contiguous() and res.numel() * res.element_size() >= RESULT_BYTES):
             raise TypeError("res must be a contiguous CUDA buffer of at least RESULT_BYTES bytes")
         if hist is not None and not (hist.is_cuda and hist.dtype == torch.float64 and
                                      hist.numel() >= int(max_sweeps) + 1):
             raise TypeError("hist must be a CUDA float64 tensor of max_sweeps + 1 entries")
-        a = out if out is not None else torch.empty(n, dtype=torch.float32, device=X.device)
-        if a0 is not None:
-            a.copy_(a0)
+        a = _coef_out(X, n, out, a0)
         o = make_opts(tol, max_sweeps, stop)
         self.set_stream(torch.cuda.current_stream(X.device))
         rc = self._lib.hpscd_solve_async(self._h, ctypes.c_void_p(ptr), dt, m, n, ld,
@@ -406,14 +442,8 @@ class Context:
         """Solve X·a ≈ y on the GPU (X, y, a0, out: CUDA tensors on this device)."""
         import torch
         ptr, dt, lay, m, n, ld = _describe(X)
-        if not (isinstance(y, torch.Tensor) and y.is_cuda and y.dtype == torch.float32
-                and y.numel() == m and y.is_contiguous()):
-            raise TypeError("y must be a contiguous float32 CUDA tensor of length m")
-        if not X.is_cuda:
-            raise TypeError("X must be a CUDA tensor (use solve_host for host arrays)")
-        a = out if out is not None else torch.empty(n, dtype=torch.float32, device=X.device)
-        if a0 is not None:
-            a.copy_(a0)
+        self._device_args(X, y)
+        a = _coef_out(X, n, out, a0)
         o = make_opts(tol, max_sweeps, stop, refresh_every, debug_flags)
         hist = np.full(int(max_sweeps) + 1, np.nan)
         sw, rr = ctypes.c_int64(0), ctypes.c_double(0.0)
@@ -430,11 +460,10 @@ class Context:
         """Algorithm 2: blocks of thr columns take their steps from one residual."""
         import torch
         ptr, dt, lay, m, n, ld = _describe(X)
-        if lay != COL or not X.is_cuda:
+        self._device_args(X, y)
+        if lay != COL:
             raise ValueError("solve_blocks needs a column-major CUDA X")
-        a = out if out is not None else torch.empty(n, dtype=torch.float32, device=X.device)
-        if a0 is not None:
-            a.copy_(a0)
+        a = _coef_out(X, n, out, a0)
         o = make_opts(tol, max_sweeps, stop)
         hist = np.full(int(max_sweeps) + 1, np.nan)
         sw, rr = ctypes.c_int64(0), ctypes.c_double(0.0)
@@ -452,7 +481,8 @@ class Context:
         (R, 2) array of the (dropped, added) pair of each swap, -1 after the last)."""
         import torch
         ptr, dt, lay, m, n, ld = _describe(X)
-        if lay != COL or not X.is_cuda:
+        self._device_args(X, y)
+        if lay != COL:
             raise ValueError("select_swap needs a column-major CUDA X")
         a = torch.empty(n, dtype=torch.float32, device=X.device)
         o = make_opts(tol, F, stop)
@@ -477,7 +507,8 @@ class Context:
         entries in [0, n), e.g. drawn at random with replacement)."""
         import torch
         ptr, dt, lay, m, n, ld = _describe(X)
-        if lay != COL or not X.is_cuda:
+        self._device_args(X, y)
+        if lay != COL:
             raise ValueError("solve_order needs a column-major CUDA X")
         ordr = np.ascontiguousarray(np.asarray(order, dtype=np.int32).reshape(-1, n) if n else
                                     np.zeros((0, 0), np.int32))
@@ -485,9 +516,7 @@ class Context:
             max_sweeps = ordr.shape[0]
         if ordr.size != int(max_sweeps) * n:
             raise ValueError("order must hold max_sweeps rows of n indices")
-        a = out if out is not None else torch.empty(n, dtype=torch.float32, device=X.device)
-        if a0 is not None:
-            a.copy_(a0)
+        a = _coef_out(X, n, out, a0)
         o = make_opts(tol, max_sweeps, stop)
         hist = np.full(int(max_sweeps) + 1, np.nan)
         sw, rr = ctypes.c_int64(0), ctypes.c_double(0.0)
@@ -504,7 +533,8 @@ class Context:
         """Algorithm 3: F greedy selection steps; returns (SolveResult, chosen column per step)."""
         import torch
         ptr, dt, lay, m, n, ld = _describe(X)
-        if lay != COL or not X.is_cuda:
+        self._device_args(X, y)
+        if lay != COL:
             raise ValueError("select needs a column-major CUDA X")
         a = torch.empty(n, dtype=torch.float32, device=X.device)
         o = make_opts(tol, F, stop)
@@ -524,6 +554,8 @@ class Context:
         """G = X^T X (n×n float32 CUDA tensor) for a column-major CUDA X."""
         import torch
         ptr, dt, lay, m, n, ld = _describe(X)
+        if not (isinstance(X, torch.Tensor) and X.is_cuda and X.device.index == self.device):
+            raise TypeError(f"X must be a CUDA tensor on cuda:{self.device}")
         if lay != COL:
             raise ValueError("gram needs a column-major X")
         G = torch.empty(n, n, dtype=torch.float32, device=X.device)
@@ -540,7 +572,9 @@ class Context:
         memory makes the copies asynchronous).  Returns a as a numpy array."""
         ptr, dt, lay, m, n, ld = _describe(X)
         y_np = _host_f32(y, m)
-        a = np.zeros(n, dtype=np.float32) if a0 is None else np.array(a0, dtype=np.float32)
+        a = np.zeros(n, dtype=np.float32) if a0 is None else np.array(a0, dtype=np.float32).ravel()
+        if a.size != n:
+            raise ValueError(f"a0 must have n = {n} entries")
         o = make_opts(tol, max_sweeps, stop, refresh_every)
         hist = np.full(int(max_sweeps) + 1, np.nan)
         sw, rr = ctypes.c_int64(0), ctypes.c_double(0.0)
@@ -567,6 +601,10 @@ def _sys_array(systems, hist_len=0):
                     and v.is_contiguous() and v.numel() == ln):
                 raise TypeError("y and a must be contiguous float32 CUDA vectors of length m, n")
         arr[i].X, arr[i].y, arr[i].a = ptr, y.data_ptr(), a.data_ptr()
+        if hist is not None and not (isinstance(hist, torch.Tensor) and hist.is_cuda
+                                     and hist.dtype == torch.float64 and hist.is_contiguous()
+                                     and hist.numel() >= hist_len):
+            raise TypeError(f"hist must be a contiguous float64 CUDA tensor of at least {hist_len} entries")
         arr[i].hist = hist.data_ptr() if hist is not None else None
         arr[i].m, arr[i].n, arr[i].ld = m, n, ld
         arr[i].a_is_guess = 1 if guess else 0
@@ -587,7 +625,7 @@ class Batch:
         self.ctx = ctx
         self.systems = list(systems)
         self.count = len(self.systems)
-        self._sys = _sys_array(self.systems)
+        self._sys = _sys_array(self.systems, int(max_sweeps) + 1)
         o = make_opts(tol, max_sweeps, stop)
         t = Tuning()
         t.cluster = int(cluster)
@@ -644,8 +682,9 @@ class Batch:
             rc = self._lib.hpscd_batch_set_warm_start(self._h, None, None)
             self._theta = None
         else:
-            if not (theta.is_cuda and theta.dtype.is_floating_point and theta.is_contiguous()
-                    and tuple(theta.shape) == (self.count, 16)):
+            import torch
+            if not (isinstance(theta, torch.Tensor) and theta.is_cuda and theta.dtype == torch.float32
+                    and theta.is_contiguous() and tuple(theta.shape) == (self.count, 16)):
                 raise TypeError("theta must be a contiguous float32 CUDA tensor (count, 16)")
             self._theta = theta
             self._mlp = mlp
@@ -731,16 +770,29 @@ class MLP:
             raise HpscdError(rc, "hpscd_mlp_get_params")
         return out
 
-    @staticmethod
-    def _shapes(m, n):
-        m = np.ascontiguousarray(m, dtype=np.int64)
-        n = np.ascontiguousarray(n, dtype=np.int64)
+    def _batch_args(self, theta, m, n, target=None):
+        """(m, n) as int64 host arrays after checking theta (B, 16) and target
+        (B, 256): contiguous float32 CUDA tensors on the context's device."""
+        import torch
+        m = np.ascontiguousarray(m, dtype=np.int64).ravel()
+        n = np.ascontiguousarray(n, dtype=np.int64).ravel()
+        B = len(m)
+        if len(n) != B:
+            raise ValueError("m and n must have one entry per row of theta")
+        dev = torch.device("cuda", self.ctx.device)
+        for t, cols, name in ((theta, MLP_THETA, "theta"), (target, MLP_OUT, "target")):
+            if t is None and name == "target":
+                continue
+            if not (isinstance(t, torch.Tensor) and t.is_cuda and t.device == dev
+                    and t.dtype == torch.float32 and t.is_contiguous()
+                    and tuple(t.shape) == (B, cols)):
+                raise TypeError(f"{name} must be a contiguous float32 CUDA tensor ({B}, {cols}) on {dev}")
         return m, n
 
     def predict(self, theta, m, n):
         """(B, 256) float32 CUDA predictions for theta (B, 16) CUDA, m, n host ints."""
         import torch
-        m, n = self._shapes(m, n)
+        m, n = self._batch_args(theta, m, n)
         B = len(m)
         out = torch.empty(B, MLP_OUT, dtype=torch.float32, device=theta.device)
         rc = self._lib.hpscd_mlp_predict(self._h, ctypes.c_void_p(theta.data_ptr()),
@@ -753,7 +805,7 @@ class MLP:
 
     def gradients(self, theta, m, n, target):
         """(loss, flat float32 gradient) of the masked mean-squared error."""
-        m, n = self._shapes(m, n)
+        m, n = self._batch_args(theta, m, n, target)
         g = np.empty(self.n_params, dtype=np.float32)
         loss = ctypes.c_double(0.0)
         rc = self._lib.hpscd_mlp_gradients(self._h, ctypes.c_void_p(theta.data_ptr()),
@@ -766,7 +818,7 @@ class MLP:
         return loss.value, g
 
     def train_step(self, theta, m, n, target, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8) -> float:
-        m, n = self._shapes(m, n)
+        m, n = self._batch_args(theta, m, n, target)
         loss = ctypes.c_double(0.0)
         rc = self._lib.hpscd_mlp_train_step(self._h, ctypes.c_void_p(theta.data_ptr()),
                                             m.ctypes.data_as(ctypes.c_void_p),
@@ -799,7 +851,7 @@ def autotune_batch(ctx: "Context", systems, trial_sweeps: int = 4):
     trial_sweeps sweeps of every system}) over clusters 1, 2, 4, 8 and panel
     policies 0, 1, 2 (see Batch)."""
     import torch
-    arr = _sys_array(systems)
+    arr = _sys_array(systems, int(trial_sweeps) + 1)
     t = Tuning()
     ms = (ctypes.c_double * 12)()
     ctx.set_stream(torch.cuda.current_stream(systems[0][0].device))

@@ -185,6 +185,49 @@ def test_degenerate_shapes(ctx):
         ctx.solve(torch.zeros(10, 600, device="cuda").T.contiguous().T[:, :600], y)
 
 
+def test_binding_rejects_arguments_the_kernels_would_misread(ctx):
+    """Vectors of the wrong length, type or device, and host X for a device call,
+    are refused before anything is launched; the context stays usable."""
+    s = synth.make_system(300, 20, seed=12)
+    X, y = to_gpu(s)
+    bad = [dict(y=y[:-1]), dict(y=y.double()), dict(y=y.cpu()),
+           dict(out=torch.empty(19, device="cuda")), dict(out=torch.empty(20, device="cuda").double()),
+           dict(a0=torch.zeros(21, device="cuda"))]
+    for kw in bad:
+        args = dict(y=y)
+        args.update(kw)
+        yy = args.pop("y")
+        with pytest.raises((TypeError, ValueError)):
+            ctx.solve(X, yy, tol=0, max_sweeps=1, stop="none", **args)
+    with pytest.raises((TypeError, ValueError)):
+        ctx.solve_blocks(X, y[:-1], 5, tol=0, max_sweeps=1, stop="none")
+    with pytest.raises((TypeError, ValueError)):
+        ctx.select(X, y.double(), 3)
+    with pytest.raises((TypeError, ValueError)):
+        ctx.solve_order(X, y, np.zeros((1, 20), np.int32), out=torch.empty(3, device="cuda"))
+    with pytest.raises((TypeError, ValueError)):
+        ctx.gram(X.cpu())
+    with pytest.raises((TypeError, ValueError)):
+        ctx.solve_host(s.X.T, s.y, a0=np.zeros(7))
+    b = hp.Batch(ctx, [(X, y, torch.zeros(20, device="cuda"), False)], tol=0, max_sweeps=1, stop="none")
+    net = hp.MLP(ctx, max_batch=8)
+    with pytest.raises(TypeError):
+        b.set_warm_start(net, torch.zeros(1, 16, device="cuda", dtype=torch.float64))
+    with pytest.raises(TypeError):
+        net.predict(torch.zeros(2, 16, device="cuda", dtype=torch.float64), [300, 300], [10, 10])
+    with pytest.raises((TypeError, ValueError)):
+        net.train_step(torch.zeros(2, 16, device="cuda"), [300, 300], [10], torch.zeros(2, 256, device="cuda"))
+    with pytest.raises(TypeError):
+        net.gradients(torch.zeros(2, 16, device="cuda"), [300, 300], [10, 10], torch.zeros(2, 255, device="cuda"))
+    with pytest.raises(TypeError):
+        hp.Batch(ctx, [(X, y, torch.zeros(20, device="cuda"), False,
+                        torch.zeros(1, device="cuda", dtype=torch.float64))], tol=0, max_sweeps=1,
+                 stop="none")
+    b.close()
+    net.close()
+    r = ctx.solve(X, y, tol=0, max_sweeps=2, stop="none")
+    assert rel(r.a.cpu().numpy(), oracle_same(s, 2).a) <= RTOL_F32
+
 def test_barrier_timeout_returns_status_and_context_survives(ctx):
     s = synth.make_system(20_000, 32, seed=10)
     X, y = to_gpu(s)
