@@ -7,6 +7,7 @@ Rebuilds only when a source or header is newer than the library.
 from __future__ import annotations
 
 import glob
+import json
 import os
 import shutil
 import subprocess
@@ -17,6 +18,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libhpscd.so")
+INFO = os.path.join(OUT, "build_info.json")  # the nvcc command lines of the last build
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
               "-I", os.path.join(ROOT, "include")]
@@ -39,7 +41,7 @@ def _deps():
 
 
 def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+    if not (os.path.exists(LIB) and os.path.exists(INFO)):
         return False
     t = os.path.getmtime(LIB)
     return all(os.path.getmtime(p) <= t for p in _deps())
@@ -62,16 +64,21 @@ def build(force: bool = False, verbose: bool = False) -> str:
             raise RuntimeError(f"nvcc failed on {src}:\n{r.stdout}\n{r.stderr}")
         if verbose:
             print(r.stderr)
-        return obj
+        return obj, cmd
 
     with ThreadPoolExecutor(max(1, min(len(srcs), os.cpu_count() or 1))) as ex:
-        objs = list(ex.map(compile_one, srcs))
+        done = list(ex.map(compile_one, srcs))
+    objs = [o for o, _ in done]
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "static", "-ldl", "-lrt", "-lpthread"]
-    r = subprocess.run(cmd, capture_output=True, text=True)
+    link = [cc, *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "static", "-ldl", "-lrt", "-lpthread"]
+    r = subprocess.run(link, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB)
+    ver = subprocess.run([cc, "--version"], capture_output=True, text=True).stdout.strip().splitlines()
+    with open(INFO, "w") as f:
+        json.dump({"nvcc": ver[-1] if ver else "", "compile": [c for _, c in done], "link": link}, f,
+                  indent=1)
     return LIB
 
 

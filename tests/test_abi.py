@@ -37,9 +37,16 @@ def test_library_exports_every_declared_symbol():
 
 
 def test_library_is_built_for_sm_103a_only():
-    path = hp.lib_path()
-    data = open(path, "rb").read()
-    assert b"sm_103a" in data or b"sm_103" in data
+    """Every compile and the link name exactly one target, sm_103a (read from the
+    command lines the build records beside the library)."""
+    import json
+    from paper_2104_12570_gb300 import build
+    hp.load()
+    info = json.load(open(build.INFO))
+    for cmd in info["compile"] + [info["link"]]:
+        targets = [cmd[i + 1] for i, a in enumerate(cmd) if a == "-gencode"]
+        assert targets == ["arch=compute_103a,code=sm_103a"], cmd
+        assert not any(a.startswith(("-arch", "--gpu-architecture")) for a in cmd), cmd
 
 
 def test_status_strings_and_null_context():
