@@ -421,6 +421,45 @@ def square_workload(hp, synth, ctx, dev, reps=3):
             "us_per_sweep": 1e3 * float(r.timing["sweep_ms"]) / max(1, r.timing["passes"])}
 
 
+def profile_wide(hp, synth, cols, blocks=512):
+    """The wide cluster kernel alone on a 2,000 x `cols` float32 row-major
+    consistent system, solved to relative residual 1e-6 (profiler captures and
+    the kernel's own trace; not a bench line).  The trace stamps CTA 0's global
+    timer at five points of each of the first `blocks` column blocks: after the
+    copy wait and partial dots, after the CTA's reduction, after the cluster
+    exchange, after the block's chain, after the residual update."""
+    import torch
+    s = synth.workload("wide_2000x200k_f32", seed=0, n=int(cols))
+    dev = torch.device("cuda", 0)
+    ctx = hp.Context(0)
+    X = torch.from_numpy(s.X).to(dev)
+    y = torch.from_numpy(s.y).to(dev)
+    r = ctx.solve(X, y, tol=1e-6, max_sweeps=200, stop="rel_res")  # warm-up, untraced
+    ctx.set_trace(blocks)
+    r = ctx.solve(X, y, tol=1e-6, max_sweeps=200, stop="rel_res")
+    t = ctx.trace_raw()[: 6 * blocks].reshape(blocks, 6)
+    t = t[t[:, 4] > 0]
+    ctx.set_trace(0)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    r = ctx.solve(X, y, tol=1e-6, max_sweeps=200, stop="rel_res")
+    e1.record()
+    torch.cuda.synchronize()
+    out = {"profile_wide": True, "m": s.m, "n": s.n, "status": r.status, "sweeps": int(r.sweeps),
+           "ms_to_tol": e0.elapsed_time(e1), "sweep_kernel_ms": float(r.timing["sweep_ms"]),
+           "blocks_per_sweep": -(-s.n // 64)}
+    if len(t) > 2:
+        prev = t[:-1, 4]
+        ph = {"copy_wait_and_dots_us": t[1:, 0] - prev, "cta_reduce_us": t[1:, 1] - t[1:, 0],
+              "cluster_exchange_us": t[1:, 2] - t[1:, 1], "chain_us": t[1:, 3] - t[1:, 2],
+              "residual_update_us": t[1:, 4] - t[1:, 3], "block_us": t[1:, 4] - prev}
+        out["trace_blocks"] = int(len(t) - 1)
+        out["median_per_block"] = {k: float(np.median(v)) / 1e3 for k, v in ph.items()}
+    print(json.dumps(out), flush=True)
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -441,7 +480,14 @@ def main():
                     help="override m (smaller case for profiler captures; not a bench line)")
     ap.add_argument("--profile-small", action="store_true",
                     help="run only the small batched + MLP case used for profiler captures")
+    ap.add_argument("--profile-wide", type=int, default=0, metavar="COLS",
+                    help="run only the wide kernel on a 2,000 x COLS system (profiler captures)")
     args = ap.parse_args()
+    if args.profile_wide:
+        import paper_2104_12570_gb300 as hp
+        from paper_2104_12570_gb300 import synth
+        profile_wide(hp, synth, args.profile_wide)
+        return
     if args.profile_small:
         import paper_2104_12570_gb300 as hp
         from paper_2104_12570_gb300 import synth

@@ -376,6 +376,20 @@ class Context:
         spread = float((ends.max() - ends.min()) / 1e3) if ends.size else None
         return {"passes": rows, "pass1_stream_end_spread_us": spread}
 
+    def trace_raw(self) -> np.ndarray:
+        """The device timestamps (ns, global timer) of the last traced solve, 6
+        words per traced pass (tall sweep) or column block (wide sweep), then the
+        tall sweep's per-CTA end-of-streaming times; 0 where nothing was stamped."""
+        P = getattr(self, "_trace_passes", 0)
+        if not P:
+            return np.zeros(0, dtype=np.int64)
+        buf = (ctypes.c_ulonglong * (P * 6 + 4096))()
+        got = ctypes.c_int64(0)
+        rc = self._lib.hpscd_get_trace(self._h, buf, P * 6 + 4096, ctypes.byref(got))
+        if rc:
+            raise HpscdError(rc)
+        return np.frombuffer(buf, dtype=np.uint64)[: got.value].astype(np.int64)
+
     def timing(self) -> dict:
         t = Timing()
         self._lib.hpscd_last_timing(self._h, ctypes.byref(t))
