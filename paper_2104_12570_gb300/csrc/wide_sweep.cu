@@ -110,7 +110,9 @@ __global__ void __launch_bounds__(256) wide_gram_blocks_kernel(const float* __re
     }
   }
   // store the block as  d_i on the diagonal and H_ik = G_ik / d_i below it
-  // (the couplings pre-divided by the row's denominator; 0 for a zero column)
+  // (the couplings pre-divided by the row's denominator; 0 for a zero column),
+  // transposed: entry (i, k) at [k][i], so the chain's lanes (one row each)
+  // read consecutive words of column k
   __shared__ float gs[WW][WW + 1];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
@@ -119,7 +121,7 @@ __global__ void __launch_bounds__(256) wide_gram_blocks_kernel(const float* __re
   __syncthreads();
   float* out = Gb + b * (WW * WW);
   for (int idx = tid; idx < WW * WW; idx += 256) {
-    const int i = idx / WW, k = idx % WW;
+    const int k = idx / WW, i = idx % WW;
     const float di = gs[i][i];
     float v;
     if (k == i) v = di;
@@ -344,6 +346,7 @@ __global__ void __launch_bounds__(WNT, 1)
         // the ⊘ step on the block's numerators (elementwise, off the chain),
         // then da_k = s_k - sum_{l<k} H_kl da_l with H = D^{-1}·(strict lower G):
         // lane owns block rows lane (slot 0) and lane + 32 (slot 1)
+        // Gb holds the block transposed: entry (i, k) at Gb[k * WW + i]
         const float d_0 = (c0 + lane < n) ? Gb[lane * WW + lane] : 0.f;
         const float d_1 = (c0 + lane + 32 < n) ? Gb[(lane + 32) * WW + lane + 32] : 0.f;
         float s_0 = d_0 > 0.f ? gsum[lane] / d_0 : 0.f;
@@ -351,8 +354,8 @@ __global__ void __launch_bounds__(WNT, 1)
         float m_0 = 0.f, m_1 = 0.f;
 #pragma unroll
         for (int k = 0; k < 32; ++k) {
-          const float h0 = Gb[lane * WW + k];
-          const float h1 = Gb[(lane + 32) * WW + k];
+          const float h0 = Gb[k * WW + lane];
+          const float h1 = Gb[k * WW + lane + 32];
           const float qk = __shfl_sync(FULL_MASK, s_0, k);
           if (lane == k) m_0 = qk;
           if (lane > k) s_0 = fmaf(-h0, qk, s_0);
@@ -360,7 +363,7 @@ __global__ void __launch_bounds__(WNT, 1)
         }
 #pragma unroll
         for (int k = 0; k < 32; ++k) {
-          const float h1 = Gb[(lane + 32) * WW + 32 + k];
+          const float h1 = Gb[(32 + k) * WW + lane + 32];
           const float qk = __shfl_sync(FULL_MASK, s_1, k);
           if (lane == k) m_1 = qk;
           if (lane > k) s_1 = fmaf(-h1, qk, s_1);
