@@ -374,8 +374,9 @@ __global__ void __launch_bounds__(WNT, 1)
       __syncthreads();
       stamp(3);
       // 4. e <- e - X_block·da for this CTA's rows; a += da (CTA 0).  Four
-      //    threads per row, 16 columns each, walked from a row-dependent start
-      //    so the rows of a warp spread over the banks.
+      //    threads per row, 16 columns each, walked from a start that depends
+      //    on the row and on the part (parts 0 and 2, 1 and 3 share banks), so
+      //    the 32 lanes of a warp read 32 different banks at every step.
       // the bound is a multiple of 32: every lane of a warp takes the same trip
       // count, as the full-mask shuffles below require
       const int nt4 = ((4 * rows_box + 31) / 32) * 32;
@@ -385,9 +386,10 @@ __global__ void __launch_bounds__(WNT, 1)
         if (r < rows) {
           const float* xr = st + r * WW + 16 * part;
           const float* dr = da_s + 16 * part;
+          const int sh = r + 8 * (part >> 1);
 #pragma unroll
           for (int j = 0; j < 16; j += 2) {
-            const int c0i = (j + r) & 15, c1i = (j + 1 + r) & 15;
+            const int c0i = (j + sh) & 15, c1i = (j + 1 + sh) & 15;
             acc0 = fmaf(xr[c0i], dr[c0i], acc0);
             acc1 = fmaf(xr[c1i], dr[c1i], acc1);
           }
