@@ -278,6 +278,23 @@ def test_full_size_tall_1Mx256(ctx):
     assert r.timing["grid"] >= 1
 
 
+@pytest.mark.slow
+def test_full_size_precision_mode_4Mx512_bf16(ctx):
+    """The 4,000,000 x 512 bfloat16 system in the benchmark's precision-mode
+    configuration (refresh every 4 passes, relative residual 1e-6): the oracle's
+    float64 residual of the GPU's coefficients meets the tolerance, and one sweep
+    equals the oracle's first sweep (bfloat16-storage tolerance)."""
+    s = synth.workload("tall_4Mx512_bf16", seed=0)
+    X, y = to_gpu(s)
+    r = ctx.solve(X, y, tol=1e-6, max_sweeps=100, stop="rel_res", refresh_every=4)
+    assert r.status == "ok" and r.rel_res <= 1e-6
+    _, nrm = oracle.residual(s.X, s.y, r.a.cpu().numpy(), m=s.m, n=s.n, dtype="bf16")
+    assert nrm / np.linalg.norm(s.y.astype(np.float64)) <= 1.1e-6
+    r1 = ctx.solve(X, y, tol=0, max_sweeps=1, stop="none", refresh_every=4)
+    o1 = oracle_same(s, 1)
+    assert rel(r1.a.cpu().numpy(), o1.a) <= RTOL_BF16
+    np.testing.assert_allclose(r1.hist, o1.hist, rtol=1e-4)
+
 def test_async_solves_equal_the_synchronous_ones(ctx):
     """hpscd_solve_async: several solves enqueued back to back (different systems
     and stopping rules) give the synchronous call's coefficients, history, sweep
