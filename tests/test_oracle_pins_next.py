@@ -282,3 +282,72 @@ def test_no_swap_when_the_selection_is_already_best():
                                              dtype="f64")
     assert sorted(sel.tolist()) == [0, 1, 2]
     assert np.all(swaps == -1) and len(hist) == 4
+
+
+# ---------------- worked 2 x 2 example, closed forms by hand ----------------
+#
+# X = [[1, 1], [0, 1]] (rows), so X_1 = (1, 0), X_2 = (1, 1), d = (1, 2); y = (2, 1),
+# whose unique solution is a = (1, 1).  Every iterate below is a dyadic rational,
+# so float64 reproduces it exactly.
+
+X22 = np.array([[1.0, 1.0], [0.0, 1.0]])
+Y22 = np.array([2.0, 1.0])
+
+
+def _col22():
+    return np.ascontiguousarray(X22.T)  # column-major storage
+
+
+def test_worked_2x2_algorithm_2_is_jacobi_in_closed_form():
+    """thr = 2 puts both columns in one block: every step uses the residual at the
+    start of the sweep (Jacobi on G = [[1, 1], [1, 2]]).  The error a - (1, 1)
+    is multiplied by M = I - D^-1 G = [[0, -1], [-1/2, 0]] each sweep, so from
+    a = 0: after 2k sweeps a = (1 - 2^-k)(1, 1), e = (2^(1-k), 2^-k); after 2k + 1
+    sweeps a = (1 + 2^-k, 1 + 2^-(k+1)), e = -(3, 1)·2^-(k+1)."""
+    for s in range(1, 9):
+        k = s // 2
+        if s % 2 == 0:
+            a = [1 - 2.0 ** -k, 1 - 2.0 ** -k]
+            e = [2.0 ** (1 - k), 2.0 ** -k]
+        else:
+            a = [1 + 2.0 ** -k, 1 + 2.0 ** -(k + 1)]
+            e = [-3 * 2.0 ** -(k + 1), -(2.0 ** -(k + 1))]
+        r = oracle.solve_blocks(_col22(), Y22, m=2, n=2, thr=2, dtype="f64", tol=0, max_sweeps=s,
+                                stop="none", want_e=True)
+        np.testing.assert_array_equal(r.a, a)
+        np.testing.assert_array_equal(r.e, e)
+        assert r.hist[s] == pytest.approx(np.hypot(*e) / np.sqrt(5.0), rel=1e-15)
+
+
+def test_worked_2x2_algorithm_3_alternates_in_closed_form():
+    """Greedy selection from a = 0: step 1 compares E_1 = 1 with E_2 = 1/2 and takes
+    column 2; from then on the column orthogonal to the residual gains nothing and
+    the steps alternate 2, 1, 2, 1, ...  After 2k steps a = (1 - 2^-k, 1 + 2^-k),
+    e = (0, -2^-k); after 2k + 1 steps a = (1 - 2^-k, 1 + 2^-(k+1)),
+    e = 2^-(k+1)·(1, -1)."""
+    for F in range(1, 9):
+        sel, a, hist = oracle.select(_col22(), Y22, m=2, n=2, F=F, dtype="f64")
+        assert list(sel) == [1 if i % 2 == 0 else 0 for i in range(F)]  # 0-based
+        k = F // 2
+        if F % 2 == 0:
+            a_cf, e_cf = [1 - 2.0 ** -k, 1 + 2.0 ** -k], [0.0, -(2.0 ** -k)]
+        else:
+            a_cf, e_cf = [1 - 2.0 ** -k, 1 + 2.0 ** -(k + 1)], [2.0 ** -(k + 1), -(2.0 ** -(k + 1))]
+        np.testing.assert_array_equal(a, a_cf)
+        assert hist[F] == pytest.approx(np.hypot(*e_cf) / np.sqrt(5.0), rel=1e-15)
+
+
+def test_worked_2x2_given_order_repeating_one_column():
+    """Sweep 1 takes column 2 twice, sweep 2 column 1 twice: the repeat of a column
+    right after its own step finds <X_j, e> = 0 and changes nothing, so
+    a = (0, 3/2), e = (1/2, -1/2) after sweep 1 and a = (1/2, 3/2), e = (0, -1/2)
+    after sweep 2."""
+    order = np.array([[1, 1], [0, 0]])
+    r1 = oracle.solve_order(_col22(), Y22, m=2, n=2, order=order[:1], dtype="f64", tol=0,
+                            max_sweeps=1, stop="none", want_e=True)
+    np.testing.assert_array_equal(r1.a, [0.0, 1.5])
+    np.testing.assert_array_equal(r1.e, [0.5, -0.5])
+    r2 = oracle.solve_order(_col22(), Y22, m=2, n=2, order=order, dtype="f64", tol=0,
+                            max_sweeps=2, stop="none", want_e=True)
+    np.testing.assert_array_equal(r2.a, [0.5, 1.5])
+    np.testing.assert_array_equal(r2.e, [0.0, -0.5])
