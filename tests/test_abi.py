@@ -71,3 +71,18 @@ def test_layout_detection():
     assert (dt, lay, m, n, ld) == (hp.BF16, hp.ROW, 7, 5, 5)
     with pytest.raises(TypeError):
         hp._describe(np.zeros((3, 3), dtype=np.float64))
+
+
+def test_every_entry_point_refuses_null_handles():
+    """With null handles and pointers (and zero sizes) every entry point returns
+    HPSCD_ERR_INVALID_ARG without touching a device; the destroy calls accept NULL."""
+    lib = hp.load()
+    destroy = {"hpscd_destroy", "hpscd_batch_destroy", "hpscd_mlp_destroy"}
+    for name, (args, _) in sorted(hp.SIGNATURES.items()):
+        if name in ("hpscd_status_string", "hpscd_mlp_param_count"):
+            continue
+        vals = [0 if a in (ctypes.c_int, ctypes.c_int64, ctypes.c_size_t)
+                else 0.0 if a in (ctypes.c_double, ctypes.c_float) else None for a in args]
+        rc = getattr(lib, name)(*vals)
+        assert rc == (0 if name in destroy else 1), (name, rc)
+    assert lib.hpscd_mlp_param_count() > 0
