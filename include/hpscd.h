@@ -22,7 +22,17 @@
  *     the initial guess); when y = 0 the absolute norm ||e_s||_2 is used.  The
  *     norms are accumulated in float64 on the device.
  *   - Stopping rules, tested once per sweep after column n:
- *       HPSCD_STOP_REL_RES:    stop after sweep s >= 0 when hist[s] <= tol;
+ *       HPSCD_STOP_REL_RES:    stop after sweep s >= 0 when hist[s] <= tol,
+ *                              tested on the true residual: the residual the
+ *                              sweeps update is rounded to float32 at every
+ *                              step, so when it first meets tol one more pass
+ *                              over X recomputes e = y - X·a for the float32
+ *                              coefficients to be returned (compensated,
+ *                              float64-grade accumulation) and hist[s] becomes
+ *                              that value; the solve stops if it meets tol and
+ *                              otherwise sweeps on from the recomputed e
+ *                              (hpscd_select and the batched sweep test the
+ *                              updated residual);
  *       HPSCD_STOP_REL_CHANGE: stop after sweep s >= 1 when
  *                              |hist[s-1] - hist[s]| < tol * hist[s-1]
  *                              (or hist[s-1] == 0);
@@ -101,7 +111,7 @@ typedef struct {
   int64_t sweeps;      /* sweeps made */
   double rel_res;      /* hist[sweeps] */
   int32_t status;      /* hpscd_status of the solve */
-  int32_t passes;      /* streaming passes over its X (sweeps + 1) */
+  int32_t passes;      /* streaming passes over its X */
 } hpscd_sys_result;
 
 typedef struct hpscd_ctx hpscd_ctx;
@@ -297,20 +307,26 @@ int hpscd_get_trace(hpscd_ctx* ctx, unsigned long long* out, int64_t words, int6
  * that cannot allocate device memory when they solve: cudaMalloc/cudaFree can
  * synchronize the device and stall other streams, and some callers run where a
  * framework's caching allocator or a fixed memory budget owns device memory).
- * Same arguments and results as hpscd_solve for a column-major X on the CURRENT
- * device, on `stream` (a cudaStream_t, NULL = default stream), with no context:
- * the call allocates nothing (no cudaMalloc, cudaFree or allocating library
- * routine).  Its device scratch is one static 24 MiB array in the library,
- * which every GPU that loads the library holds until the process exits.
+ * Same arguments and stopping rules as hpscd_solve for a column-major X on the
+ * CURRENT device, on `stream` (a cudaStream_t, NULL = default stream), with no
+ * context: the call allocates nothing (no cudaMalloc, cudaFree or allocating
+ * library routine).  X, y and a must be device (or managed) memory that the
+ * current device addresses; anything else returns HPSCD_ERR_INVALID_ARG.
+ * Its device scratch is one static 24 MiB array in the library, which every
+ * GPU that loads the library holds until the process exits.
  * Limits: 1 <= m <= 1,048,576, 1 <= n <= 256, max_sweeps <= 4096 and
  * opts->debug_flags == 0; larger problems return HPSCD_ERR_UNSUPPORTED.
- * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call before
- * any stream capture.  Every call shares the array and clears what must start
- * at zero, so calls that overlap on the GPU (other streams, other host
- * threads) race and must be serialized by the caller.  Device-side waits are
- * bounded at 5 s.  hist, sweeps_done and final_rel_res are HOST pointers (may
- * be NULL); the call returns after the result is complete.
+ * The set-up always forms G = X^T X on the CUDA cores (the tensor-core set-up
+ * of hpscd_solve needs more partial storage than the array holds), so the
+ * results agree with hpscd_solve's to float32 tolerance, not bit for bit.
+ * The call is synchronous: it ends with a device-to-host copy of the result
+ * into pageable memory and a stream synchronization, so it must not be issued
+ * on a stream that is being captured.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current.
+ * Every call shares the array and clears what must start at zero, so calls
+ * that overlap on the GPU (other streams, other host threads) race and must be
+ * serialized by the caller.  Device-side waits are bounded at 5 s.  hist,
+ * sweeps_done and final_rel_res are HOST pointers (may be NULL).
  */
 int hpscd_solve_noalloc(void* stream, const void* X, int dtype, int64_t m, int64_t n, int64_t ld,
                         const float* y, float* a, int a_is_guess, const hpscd_opts* opts,

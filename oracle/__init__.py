@@ -26,12 +26,16 @@ STATUS = {0: "ok", 1: "invalid", 2: "not_converged", 3: "nonfinite", 4: "nomem"}
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (plain -O2, no fast-math) into oracle/_build."""
+    """Compile the oracle with gcc (plain -O2, no fast-math) into oracle/_build,
+    with OpenMP for the threaded Algorithm 1 of the CPU baseline when the
+    compiler has it (without it that function runs on one thread)."""
     os.makedirs(os.path.dirname(_LIB), exist_ok=True)
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-std=c11",
-                               "-fno-fast-math", "-ffp-contract=off", "-o", tmp, _SRC, "-lm"])
+        base = ["gcc", "-O2", "-fPIC", "-shared", "-std=c11", "-fno-fast-math",
+                "-ffp-contract=off", "-o", tmp, _SRC, "-lm"]
+        if subprocess.run(base[:1] + ["-fopenmp"] + base[1:], capture_output=True).returncode != 0:
+            subprocess.check_call(base)
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -61,6 +65,10 @@ def load_library(path: str):
     lib.hpscd_oracle_select_swap.argtypes = [vp, ctypes.c_int, ctypes.c_int, i64, i64, i64, dp, i64,
                                              i64, vp, vp, dp, dp, ctypes.POINTER(i64)]
     lib.hpscd_oracle_select_swap.restype = ctypes.c_int
+    lib.hpscd_oracle_solve_mt.argtypes = [vp, ctypes.c_int, ctypes.c_int, i64, i64, i64, dp, dp,
+                                          ctypes.c_double, i64, ctypes.c_int, ctypes.c_int, dp, dp,
+                                          ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_int)]
+    lib.hpscd_oracle_solve_mt.restype = ctypes.c_int
     return lib
 
 
@@ -114,6 +122,29 @@ def solve(X, y, *, m, n, layout="col", dtype="f32", a0=None, tol=1e-6, max_sweep
     if st in (1, 4):
         raise ValueError(f"oracle: {STATUS[st]}")
     return OracleResult(a, e, hist[: sw.value + 1], sw.value, STATUS[st])
+
+
+def solve_mt(X, y, *, m, n, layout="col", dtype="f32", a0=None, tol=1e-6, max_sweeps=1000,
+             stop="rel_res", threads=1, lib=None):
+    """Algorithm 1 with its row loops split over `threads` OpenMP threads (the CPU
+    baseline); equal to solve() at threads = 1.  Returns (OracleResult without e,
+    threads actually used)."""
+    _check_x(X, m, n, layout, dtype)
+    lib = lib or _load()
+    y64 = np.ascontiguousarray(y, dtype=np.float64)
+    a064 = None if a0 is None else np.ascontiguousarray(a0, dtype=np.float64)
+    a = np.zeros(n, dtype=np.float64)
+    hist = np.full(max_sweeps + 1, np.nan, dtype=np.float64)
+    sw = ctypes.c_int64(0)
+    used = ctypes.c_int(0)
+    ld = max(1, m if layout == "col" else n)
+    st = lib.hpscd_oracle_solve_mt(_ptr(X), DTYPES[dtype], LAYOUTS[layout], m, n, ld, _ptr(y64),
+                                   _ptr(a064), float(tol), int(max_sweeps), STOP[stop],
+                                   int(threads), _ptr(a), _ptr(hist), ctypes.byref(sw),
+                                   ctypes.byref(used))
+    if st in (1, 4):
+        raise ValueError(f"oracle: {STATUS[st]}")
+    return OracleResult(a, None, hist[: sw.value + 1], sw.value, STATUS[st]), used.value
 
 
 def solve_blocks(X, y, *, m, n, thr, layout="col", dtype="f32", a0=None, tol=1e-6,

@@ -273,6 +273,179 @@ int hpscd_oracle_solve(const void* X, int dt, int lay, int64_t m, int64_t n, int
 }
 
 /*
+ * Algorithm 1 as hpscd_oracle_solve (initial guess a0 or 0_n, REL_RES /
+ * REL_CHANGE / NONE once per sweep), with the two row loops of every column
+ * step -- the dot <X_j, e> and the correction e <- e - X_j·da -- split over
+ * `threads` threads (OpenMP; the CPU baseline).  The column order stays
+ * sequential: thread t owns rows [m·t/T, m·(t+1)/T), sums its part of the dot
+ * in row order, and every thread adds the T parts in thread order, so all of
+ * them take the same da.  With threads = 1 this is hpscd_oracle_solve's
+ * arithmetic exactly; with T > 1 only the summation order of the dots and
+ * norms differs.  *threads_used receives T (1 when built without OpenMP).
+ * Column-major or row-major X (row-major is copied to column-major float64
+ * first, as hpscd_oracle_solve does).
+ */
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+static double dot_rows(const void* X, int dt, int64_t base, const double* e, int64_t i0, int64_t i1) {
+  double s = 0.0;
+  if (dt == OR_F32) {
+    const float* p = (const float*)X + base;
+    for (int64_t i = i0; i < i1; ++i) s += (double)p[i] * e[i];
+  } else if (dt == OR_BF16) {
+    const uint16_t* p = (const uint16_t*)X + base;
+    for (int64_t i = i0; i < i1; ++i) s += bf16_to_f64(p[i]) * e[i];
+  } else {
+    const double* p = (const double*)X + base;
+    for (int64_t i = i0; i < i1; ++i) s += p[i] * e[i];
+  }
+  return s;
+}
+
+static void axpy_rows(const void* X, int dt, int64_t base, double da, double* e, int64_t i0, int64_t i1) {
+  if (dt == OR_F32) {
+    const float* p = (const float*)X + base;
+    for (int64_t i = i0; i < i1; ++i) e[i] -= (double)p[i] * da;
+  } else if (dt == OR_BF16) {
+    const uint16_t* p = (const uint16_t*)X + base;
+    for (int64_t i = i0; i < i1; ++i) e[i] -= bf16_to_f64(p[i]) * da;
+  } else {
+    const double* p = (const double*)X + base;
+    for (int64_t i = i0; i < i1; ++i) e[i] -= p[i] * da;
+  }
+}
+
+int hpscd_oracle_solve_mt(const void* X, int dt, int lay, int64_t m, int64_t n, int64_t ld,
+                          const double* y, const double* a0, double tol, int64_t max_sweeps,
+                          int stop_rule, int threads, double* a_out, double* hist,
+                          int64_t* sweeps_done, int* threads_used) {
+  if (!valid_args(X, dt, lay, m, n, ld) || (!y && m > 0) || (!a_out && n > 0) ||
+      max_sweeps < 0 || (stop_rule < 0 || stop_rule > 2) || !(tol >= 0.0) || threads < 1)
+    return OR_INVALID;
+#ifndef _OPENMP
+  threads = 1;
+#endif
+  if (threads_used) *threads_used = threads;
+  const void* Xc = X;
+  int dtc = dt;
+  int64_t ldc = ld;
+  double* Xcopy = NULL;
+  if (lay == OR_ROW && m > 0 && n > 0) {
+    Xcopy = (double*)malloc((size_t)m * (size_t)n * sizeof(double));
+    if (!Xcopy) return OR_NOMEM;
+    for (int64_t i = 0; i < m; ++i)
+      for (int64_t j = 0; j < n; ++j) Xcopy[j * m + i] = x_elem(X, dt, lay, ld, i, j);
+    Xc = Xcopy;
+    dtc = OR_F64;
+    ldc = m;
+  }
+  const int T = threads;
+  double* e = (double*)malloc((size_t)(m > 0 ? m : 1) * sizeof(double));
+  double* d = (double*)malloc((size_t)(n > 0 ? n : 1) * sizeof(double));
+  double* part = (double*)calloc((size_t)2 * T * 8, sizeof(double));  /* [2][T] at a stride of 8 */
+  if (!e || !d || !part) {
+    free(e); free(d); free(part); free(Xcopy);
+    return OR_NOMEM;
+  }
+  for (int64_t j = 0; j < n; ++j) a_out[j] = a0 ? a0[j] : 0.0;
+  int status = OR_NOT_CONVERGED;
+  int64_t s_done = 0;
+  int stop = 0;
+  double ynorm = 0.0, r_prev = 0.0;
+
+#pragma omp parallel num_threads(T)
+  {
+#ifdef _OPENMP
+    const int t = omp_get_thread_num();
+#else
+    const int t = 0;
+#endif
+    const int64_t i0 = m * t / T, i1 = m * (t + 1) / T;
+    /* e <- y - X·a, d_j <- <X_j, X_j>, ||y||: each thread its rows, then in thread order */
+    for (int64_t i = i0; i < i1; ++i) e[i] = y[i];
+    for (int64_t j = 0; j < n; ++j)
+      if (a_out[j] != 0.0) axpy_rows(Xc, dtc, j * ldc, a_out[j], e, i0, i1);
+    for (int64_t j = 0; j < n; ++j) {
+      double sq = 0.0;
+      if (dtc == OR_F32) {
+        const float* p = (const float*)Xc + j * ldc;
+        for (int64_t i = i0; i < i1; ++i) sq += (double)p[i] * (double)p[i];
+      } else if (dtc == OR_BF16) {
+        const uint16_t* p = (const uint16_t*)Xc + j * ldc;
+        for (int64_t i = i0; i < i1; ++i) sq += bf16_to_f64(p[i]) * bf16_to_f64(p[i]);
+      } else {
+        const double* p = (const double*)Xc + j * ldc;
+        for (int64_t i = i0; i < i1; ++i) sq += p[i] * p[i];
+      }
+      part[((j & 1) * T + t) * 8] = sq;
+#pragma omp barrier
+      if (t == 0) {
+        double tot = 0.0;
+        for (int k = 0; k < T; ++k) tot += part[((j & 1) * T + k) * 8];
+        d[j] = tot;
+      }
+    }
+    double yy = 0.0, ee = 0.0;
+    for (int64_t i = i0; i < i1; ++i) { yy += y[i] * y[i]; ee += e[i] * e[i]; }
+#pragma omp barrier
+    part[t * 8] = yy;
+    part[(T + t) * 8] = ee;
+#pragma omp barrier
+    if (t == 0) {
+      double ys = 0.0, es = 0.0;
+      for (int k = 0; k < T; ++k) { ys += part[k * 8]; es += part[(T + k) * 8]; }
+      ynorm = sqrt(ys);
+      const double scale = ynorm > 0.0 ? ynorm : 1.0;
+      r_prev = sqrt(es) / scale;
+      if (hist) hist[0] = r_prev;
+      if (!isfinite(r_prev)) { status = OR_NONFINITE; stop = 1; }
+      else if (stop_rule == OR_STOP_REL_RES && r_prev <= tol) { status = OR_OK; stop = 1; }
+      else if (stop_rule == OR_STOP_NONE && max_sweeps == 0) { status = OR_OK; stop = 1; }
+    }
+#pragma omp barrier
+    for (int64_t sw = 1; sw <= max_sweeps && !stop; ++sw) {
+      for (int64_t j = 0; j < n; ++j) {
+        /* da <- <X_j, e> / d_j (Eq. da2); e <- e - X_j·da (Eq. ek1-ek); a_j += da */
+        part[((j & 1) * T + t) * 8] = dot_rows(Xc, dtc, j * ldc, e, i0, i1);
+#pragma omp barrier
+        double num = 0.0;
+        for (int k = 0; k < T; ++k) num += part[((j & 1) * T + k) * 8];
+        const double da = d[j] > 0.0 ? num / d[j] : 0.0;
+        axpy_rows(Xc, dtc, j * ldc, da, e, i0, i1);
+        if (t == 0) a_out[j] += da;
+      }
+      double es = 0.0;
+      for (int64_t i = i0; i < i1; ++i) es += e[i] * e[i];
+#pragma omp barrier
+      part[t * 8] = es;
+#pragma omp barrier
+      if (t == 0) {
+        double tot = 0.0;
+        for (int k = 0; k < T; ++k) tot += part[k * 8];
+        const double r = sqrt(tot) / (ynorm > 0.0 ? ynorm : 1.0);
+        s_done = sw;
+        if (hist) hist[sw] = r;
+        if (!isfinite(r)) { status = OR_NONFINITE; stop = 1; }
+        else if (stop_rule == OR_STOP_REL_RES && r <= tol) { status = OR_OK; stop = 1; }
+        else if (stop_rule == OR_STOP_REL_CHANGE && (r_prev == 0.0 || fabs(r_prev - r) < tol * r_prev)) {
+          status = OR_OK; stop = 1;
+        } else if (stop_rule == OR_STOP_NONE && sw == max_sweeps) { status = OR_OK; stop = 1; }
+        r_prev = r;
+      }
+#pragma omp barrier
+    }
+  }
+  if (sweeps_done) *sweeps_done = s_done;
+  free(e);
+  free(d);
+  free(part);
+  free(Xcopy);
+  return status;
+}
+
+/*
  * Algorithm 2 (HPSCDP, Sec. 7), literally, in float64.
  *
  *   a <- a0 (or 0_n); e <- y - X·a

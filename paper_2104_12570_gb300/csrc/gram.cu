@@ -113,7 +113,11 @@ __global__ void gram_reduce_kernel(const double* __restrict__ partial, int ntile
 
 }  // namespace
 
-GramPlan gram_plan(int64_t m, int npad, int sms) {
+GramPlan gram_plan(int64_t m, int npad, int sms) { return gram_plan_capped(m, npad, sms, 0); }
+
+// As gram_plan, with at most max_ksplit row splits when max_ksplit > 0 (the
+// partial tiles then take less memory).
+GramPlan gram_plan_capped(int64_t m, int npad, int sms, int max_ksplit) {
   GramPlan gp;
   gp.npad = ((npad + GT - 1) / GT) * GT;
   const int nb = gp.npad / GT;
@@ -122,6 +126,7 @@ GramPlan gram_plan(int64_t m, int npad, int sms) {
   if (want < 1) want = 1;
   int64_t maxsplit = (m + 1023) / 1024;
   if (maxsplit < 1) maxsplit = 1;
+  if (max_ksplit > 0 && maxsplit > max_ksplit) maxsplit = max_ksplit;
   gp.ksplit = (int)(want < maxsplit ? want : maxsplit);
   int64_t rps = (m + gp.ksplit - 1) / gp.ksplit;
   rps = ((rps + GKB - 1) / GKB) * GKB;

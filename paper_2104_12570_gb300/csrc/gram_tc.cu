@@ -16,7 +16,9 @@
 // positive terms, so the diagonal <X_j, X_j> is summed on the CUDA cores from
 // the same shared-memory tiles (float32, float64 across blocks).  Per-split
 // float32 partials are summed in a fixed order by gram_tc_reduce_kernel into
-// the symmetric G.
+// the symmetric G.  The same workers also form X^T y and ||y||^2 from those
+// tiles (y read alongside), the dot products of the sweep's starting residual
+// e = y of a cold start, so the sweep does not need a pass over X to form them.
 #include <string.h>
 
 #include "kernels.h"
@@ -179,18 +181,73 @@ __global__ void __launch_bounds__(GT_THREADS, 1)
   // permutes chunks within a column's 128 bytes); float32 per 64 K blocks,
   // float64 across them.  The tensor-core accumulation drifts on long sums of
   // positive terms, so these replace its diagonal.
+  // <X_j, y> (when p.y is given): the chunk a worker reads holds K rows
+  // 4c..4c+3 (float32; 8c..8c+7 for bfloat16) of its column, c = the logical
+  // chunk (w & 7) XOR (column & 7) of the 128-byte swizzle; the column index
+  // w/8 + 16q has (column & 7) = (w/8) & 7 for every q, so each worker needs
+  // the same YR values of y per K block, loaded one block ahead.
+  // Float64 accumulation: every 64 K blocks the 8 workers that share a column
+  // (8 consecutive lanes) sum their float32 partials with shuffles, and lane j
+  // of the 8 keeps the float64 totals of q = j, j+8, j+16, j+24.
   constexpr int MAXQ = 32;  // 16-byte chunks per worker per stage (nload <= 4)
+  constexpr int YR = TF32 ? 4 : 8;  // rows of a 16-byte chunk
   const int wt = tid - GT_WORK_WARP0 * 32;
   const bool worker = warp >= GT_WORK_WARP0 && warp < GT_WORK_WARP0 + GT_WORKERS / 32;
-  double dsq64[MAXQ];
-  if (worker) {
-    float dsq[MAXQ];
+  bool any_diag = false;
+  for (int k = 0; k < nload; ++k) any_diag |= p.grp.diag_slot[g][k] != 0;
+  const bool want_y = p.y != nullptr && (any_diag || g == 0);
+  const int jl = lane & 7;
+  double dsq64[MAXQ / 8], xy64[MAXQ / 8], y2_64 = 0.0;
 #pragma unroll
-    for (int q = 0; q < MAXQ; ++q) { dsq[q] = 0.f; dsq64[q] = 0.0; }
+  for (int k = 0; k < MAXQ / 8; ++k) { dsq64[k] = 0.0; xy64[k] = 0.0; }
+  if (worker) {
+    float dsq[MAXQ], xy[MAXQ], y2 = 0.f;
+#pragma unroll
+    for (int q = 0; q < MAXQ; ++q) { dsq[q] = 0.f; xy[q] = 0.f; }
     const int nq = 8 * nload;
+    const int yoff = YR * ((wt & 7) ^ ((wt >> 3) & 7));  // first K row of the worker's chunk
+    float yv[YR], yn[YR];
+    // rows r0 + kb·KB + yoff.. are a multiple of 4 (KB, yoff and the split
+    // length are): 16-byte loads when y is 16-byte aligned and the rows exist
+    const bool yvec = (reinterpret_cast<uintptr_t>(p.y) & 15) == 0;
+    auto load_y = [&](int64_t kb, float (&dst)[YR]) {
+      const int64_t row0 = r0 + kb * KB + yoff;
+      if (want_y && kb < nkb && yvec && row0 + YR <= p.m) {
+#pragma unroll
+        for (int r = 0; r < YR; r += 4) {
+          const float4 t = __ldg(reinterpret_cast<const float4*>(p.y + row0 + r));
+          dst[r] = t.x; dst[r + 1] = t.y; dst[r + 2] = t.z; dst[r + 3] = t.w;
+        }
+      } else {
+#pragma unroll
+        for (int r = 0; r < YR; ++r)
+          dst[r] = (want_y && kb < nkb && row0 + r < p.m) ? __ldg(p.y + row0 + r) : 0.f;
+      }
+    };
+    load_y(0, yv);
+    auto flush = [&]() {
+#pragma unroll
+      for (int q = 0; q < MAXQ; ++q) {
+        if (q < nq) {
+          float a = dsq[q], b = xy[q];
+          a += __shfl_xor_sync(FULL_MASK, a, 1);
+          b += __shfl_xor_sync(FULL_MASK, b, 1);
+          a += __shfl_xor_sync(FULL_MASK, a, 2);
+          b += __shfl_xor_sync(FULL_MASK, b, 2);
+          a += __shfl_xor_sync(FULL_MASK, a, 4);
+          b += __shfl_xor_sync(FULL_MASK, b, 4);
+          if ((q & 7) == jl) { dsq64[q >> 3] += (double)a; xy64[q >> 3] += (double)b; }
+        }
+        dsq[q] = 0.f;
+        xy[q] = 0.f;
+      }
+      y2_64 += (double)y2;
+      y2 = 0.f;
+    };
     for (int64_t kb = 0; kb < nkb; ++kb) {
       const int s = (int)(kb % nst);
       const uint32_t par = (uint32_t)((kb / nst) & 1);
+      load_y(kb + 1, yn);  // the next block's rows, in flight while this one is worked on
       int ok = 1;
       if (lane == 0) ok = wait(&full[s], par) ? 1 : 0;
       ok = __shfl_sync(FULL_MASK, ok, 0);
@@ -200,6 +257,8 @@ __global__ void __launch_bounds__(GT_THREADS, 1)
       uint4* raw4 = reinterpret_cast<uint4*>(st);
       uint4* lo4 = reinterpret_cast<uint4*>(st + stage_raw);
 #pragma unroll
+      for (int r = 0; r < YR; ++r) y2 = fmaf(yv[r], yv[r], y2);
+#pragma unroll
       for (int q = 0; q < MAXQ; ++q) {
         if (q < nq) {
           const uint4 x = raw4[wt + GT_WORKERS * q];
@@ -207,6 +266,7 @@ __global__ void __launch_bounds__(GT_THREADS, 1)
             const float a0 = __uint_as_float(x.x), a1 = __uint_as_float(x.y);
             const float a2 = __uint_as_float(x.z), a3 = __uint_as_float(x.w);
             dsq[q] = fmaf(a0, a0, fmaf(a1, a1, fmaf(a2, a2, fmaf(a3, a3, dsq[q]))));
+            xy[q] = fmaf(a0, yv[0], fmaf(a1, yv[1], fmaf(a2, yv[2], fmaf(a3, yv[3], xy[q]))));
             // split in place: hi over x, lo in the second half
             uint4 h, l;
             split_tf32(x, h, l);
@@ -218,23 +278,22 @@ __global__ void __launch_bounds__(GT_THREADS, 1)
             for (int h = 0; h < 4; ++h) {
               const float lo16 = __uint_as_float(w4[h] << 16), hi16 = __uint_as_float(w4[h] & 0xffff0000u);
               dsq[q] = fmaf(lo16, lo16, fmaf(hi16, hi16, dsq[q]));
+              xy[q] = fmaf(lo16, yv[2 * h], fmaf(hi16, yv[2 * h + 1], xy[q]));
             }
           }
         }
       }
-      if ((kb & 63) == 63) {
-#pragma unroll
-        for (int q = 0; q < MAXQ; ++q) { dsq64[q] += (double)dsq[q]; dsq[q] = 0.f; }
-      }
+      if ((kb & 63) == 63) flush();
       if constexpr (TF32) fence_proxy_async_smem();  // the split is visible to the MMAs
       __syncwarp();
       if (lane == 0) {
         if constexpr (TF32) mbar_arrive(&ready[s]);
         else mbar_arrive(&empty[s]);
       }
-    }
 #pragma unroll
-    for (int q = 0; q < MAXQ; ++q) dsq64[q] += (double)dsq[q];
+      for (int r = 0; r < YR; ++r) yv[r] = yn[r];
+    }
+    flush();
   }
 
   // ---------------- epilogue ----------------
@@ -249,16 +308,24 @@ __global__ void __launch_bounds__(GT_THREADS, 1)
   tc_fence_after();
   const int fail = __syncthreads_or((!ok || *vfail) ? 1 : 0);
   if (!fail && worker) {
-    // column sums of squares: the 8 workers 8a..8a+7 share columns a + 16q
+    // column totals: lane j of each 8-lane group holds q = 8k + j, the
+    // column wt/8 + 16j of stage slot k
 #pragma unroll
-    for (int q = 0; q < MAXQ; ++q) {
-      double v = dsq64[q];
-      v += __shfl_xor_sync(FULL_MASK, v, 1);
-      v += __shfl_xor_sync(FULL_MASK, v, 2);
-      v += __shfl_xor_sync(FULL_MASK, v, 4);
-      const int lcol = wt / 8 + 16 * q;  // column within the streamed slots
-      if ((wt & 7) == 0 && q < 8 * nload && p.grp.diag_slot[g][lcol / BLK])
-        p.dpart[(size_t)blockIdx.x * p.npad + p.grp.load_blk[g][lcol / BLK] * BLK + lcol % BLK] = v;
+    for (int k = 0; k < MAXQ / 8; ++k) {
+      const int lcol = wt / 8 + 16 * jl;  // column within slot k
+      if (k < nload && p.grp.diag_slot[g][k]) {
+        const size_t at = (size_t)blockIdx.x * p.npad + p.grp.load_blk[g][k] * BLK + lcol;
+        p.dpart[at] = dsq64[k];
+        if (p.y) p.hpart[at] = xy64[k];
+      }
+    }
+    // ||y||^2 of the split: workers 0..7 of group 0 read every K row once
+    if (p.y && g == 0 && wt < 8) {
+      double v = y2_64;
+      v += __shfl_xor_sync(0xffu, v, 1);
+      v += __shfl_xor_sync(0xffu, v, 2);
+      v += __shfl_xor_sync(0xffu, v, 4);
+      if (wt == 0) p.y2part[blockIdx.x] = v;
     }
     // tensor memory: worker warp w reads lane quarter w % 4 (rows 32·(w%4)..+31)
     const int quarter = warp & 3;
@@ -294,13 +361,16 @@ __global__ void __launch_bounds__(GT_THREADS, 1)
 //   stage 1: tmp[s][i][j..j+3] = sum over the splits of slice s of the lower
 //            partials (float4 loads, independent across threads; one thread
 //            per slice, row and 4 columns), and d_i = sum_k dpart[k][i] (the
-//            CUDA-core diagonal, float64);
+//            CUDA-core diagonal, float64), and when asked (X^T y)_i and ||y||^2
+//            summed over the splits the same way;
 //   stage 2: G_ij = G_ji = sum_s tmp[s][i][j], G_ii = d_i; optionally
 //            G~ = D^{-1} G in both triangles and d as float32.
 constexpr int RED_SLICES = 16;
 __global__ void gram_tc_reduce1_kernel(const float* __restrict__ partial,
                                        const double* __restrict__ dpart, int ksplit, int npad,
-                                       float* __restrict__ tmp, double* __restrict__ d64) {
+                                       float* __restrict__ tmp, double* __restrict__ d64,
+                                       const double* __restrict__ hpart, const double* __restrict__ y2part,
+                                       double* __restrict__ h0, double* __restrict__ y2) {
   const int n4 = npad / 4;
   const int64_t total = (int64_t)RED_SLICES * npad * n4;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
@@ -322,6 +392,16 @@ __global__ void gram_tc_reduce1_kernel(const float* __restrict__ partial,
       double dd = 0.0;
       for (int k = 0; k < ksplit; ++k) dd += dpart[(size_t)k * npad + i];
       d64[i] = dd;
+      if (h0) {
+        double hh = 0.0;
+        for (int k = 0; k < ksplit; ++k) hh += hpart[(size_t)k * npad + i];
+        h0[i] = hh;
+        if (i == 0) {
+          double yy = 0.0;
+          for (int k = 0; k < ksplit; ++k) yy += y2part[k];
+          *y2 = yy;
+        }
+      }
     }
   }
 }
@@ -428,13 +508,16 @@ bool gram_tc_plan(int dtype, int64_t m, int n, int sms, int max_smem, GramTCPlan
   gp->partial_bytes = (size_t)gp->ksplit * gp->npad * gp->npad * sizeof(float) +
                       (size_t)gp->ksplit * gp->npad * sizeof(double) +
                       (size_t)RED_SLICES * gp->npad * gp->npad * sizeof(float) +
-                      (size_t)gp->npad * sizeof(double);
+                      (size_t)gp->npad * sizeof(double) +
+                      (size_t)gp->ksplit * gp->npad * sizeof(double) +  // X^T y partials
+                      (size_t)gp->ksplit * sizeof(double);              // ||y||^2 partials
   return true;
 }
 
 cudaError_t launch_gram_tc(const CUtensorMap* tmap, int dtype, int64_t m, const GramTCPlan& gp,
                            float* partial, int* err, uint64_t timeout_ns, float* G, int ldG,
-                           cudaStream_t stream, int n, float* Gt, float* dvec) {
+                           cudaStream_t stream, int n, float* Gt, float* dvec, const float* y,
+                           double* h0, double* y2) {
   GramTCParams p{};
   p.m = m;
   p.npad = gp.npad;
@@ -446,6 +529,13 @@ cudaError_t launch_gram_tc(const CUtensorMap* tmap, int dtype, int64_t m, const 
   p.err = err;
   p.timeout_ns = timeout_ns;
   p.nstages = gp.nstages;
+  float* tmp = reinterpret_cast<float*>(reinterpret_cast<char*>(p.dpart) +
+                                        (size_t)gp.ksplit * gp.npad * sizeof(double));
+  double* d64 = reinterpret_cast<double*>(tmp + (size_t)RED_SLICES * gp.npad * gp.npad);
+  const bool with_y = y && h0 && y2;
+  p.y = with_y ? y : nullptr;
+  p.hpart = d64 + gp.npad;
+  p.y2part = p.hpart + (size_t)gp.ksplit * gp.npad;
   dim3 grid(gp.ksplit, gp.grp.ngroups);
   cudaError_t e;
   if (dtype == HPSCD_F32) {
@@ -461,12 +551,10 @@ cudaError_t launch_gram_tc(const CUtensorMap* tmap, int dtype, int64_t m, const 
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  float* tmp = reinterpret_cast<float*>(reinterpret_cast<char*>(p.dpart) +
-                                        (size_t)gp.ksplit * gp.npad * sizeof(double));
-  double* d64 = reinterpret_cast<double*>(tmp + (size_t)RED_SLICES * gp.npad * gp.npad);
   const int64_t t1 = (int64_t)RED_SLICES * gp.npad * (gp.npad / 4);
-  gram_tc_reduce1_kernel<<<(unsigned)((t1 + 255) / 256), 256, 0, stream>>>(partial, p.dpart, gp.ksplit,
-                                                                          gp.npad, tmp, d64);
+  gram_tc_reduce1_kernel<<<(unsigned)((t1 + 255) / 256), 256, 0, stream>>>(
+      partial, p.dpart, gp.ksplit, gp.npad, tmp, d64, p.hpart, p.y2part, with_y ? h0 : nullptr,
+      with_y ? y2 : nullptr);
   const int64_t t2 = (int64_t)gp.npad * gp.npad;
   gram_tc_reduce2_kernel<<<(unsigned)((t2 + 255) / 256), 256, 0, stream>>>(tmp, d64, gp.npad, n, G, ldG,
                                                                           Gt, dvec);

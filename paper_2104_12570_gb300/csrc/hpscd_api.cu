@@ -30,7 +30,7 @@ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 struct Layout {
   size_t G = 0, Gt = 0, dvec = 0, partial = 0, e = 0, hacc = 0, npart = 0, gw = 0, ypart = 0, hist = 0,
-         ctl = 0, sel = 0, order = 0, swp = 0;
+         ctl = 0, sel = 0, order = 0, swp = 0, h0 = 0, y2 = 0;
   size_t xcopy = 0, ycopy = 0, acopy = 0, total = 0;
 };
 
@@ -106,6 +106,8 @@ int make_plan(const hpscd_ctx* ctx, int dtype, int layout, int64_t m, int64_t n,
   L.sel = take((size_t)(o->max_sweeps + 1) * sizeof(int64_t));
   L.order = take((size_t)(order_entries > 0 ? order_entries : 1) * sizeof(int32_t));
   L.swp = take((size_t)2 * (swap_rounds > 0 ? swap_rounds : 1) * sizeof(int64_t));
+  L.h0 = take((size_t)P->ldG * sizeof(double));
+  L.y2 = take(sizeof(double));
   if (host_copies) {
     L.xcopy = take((size_t)(n > 0 ? n : 1) * (size_t)ld * esize(dtype));
     L.ycopy = take((size_t)(m > 0 ? m : 1) * sizeof(float));
@@ -178,18 +180,23 @@ int encode_gram_map(hpscd_ctx* ctx, const void* X, int dtype, int64_t m, int64_t
 // CUDA-core kernel.  `err` receives a device-side failure flag.
 // When Gt is given, also G~ = D^{-1} G and d (fused into the tensor-core
 // path's reduction; one extra kernel after the CUDA-core path).
+// When y, h0 and y2 are given and the tensor-core kernel runs, it also forms
+// h0 = X^T y and *y2 = ||y||^2 from the same read of X (*got_h0 = true).
 int run_gram(hpscd_ctx* ctx, const void* X, int dtype, int64_t m, int64_t n, int64_t ld,
              const Plan& P, void* partial, float* G, int ldG, int* err, bool force_simt,
-             int* launches, float* Gt = nullptr, float* dvec = nullptr) {
+             int* launches, float* Gt = nullptr, float* dvec = nullptr, const float* y = nullptr,
+             double* h0 = nullptr, double* y2 = nullptr, bool* got_h0 = nullptr) {
   CUtensorMap gmap;
   memset(&gmap, 0, sizeof(gmap));
+  if (got_h0) *got_h0 = false;
   if (!force_simt && P.tc_ok && encode_gram_map(ctx, X, dtype, m, n, ld, &gmap)) {
     if (launch_gram_tc(&gmap, dtype, m, P.gtc, static_cast<float*>(partial), err,
                        (uint64_t)(ctx->timeout_s * 1e9), G, ldG, ctx->stream, (int)n, Gt,
-                       dvec) != cudaSuccess) {
+                       dvec, y, h0, y2) != cudaSuccess) {
       cudaGetLastError();
       return HPSCD_ERR_CUDA;
     }
+    if (got_h0) *got_h0 = y && h0 && y2;
     *launches = 3;
     return HPSCD_OK;
   }
@@ -365,8 +372,14 @@ int solve_device(hpscd_ctx* ctx, const void* X, int dtype, int layout, int64_t m
   int gram_launches = 0;
   float* Gt = reinterpret_cast<float*>(ws + L.Gt);
   float* dvec = reinterpret_cast<float*>(ws + L.dvec);
+  // a cold start takes X^T y and ||y||^2 from the set-up's read of X, so the
+  // sweep kernel makes no pass of its own before the first sweep
+  double* h0 = reinterpret_cast<double*>(ws + L.h0);
+  double* y2 = reinterpret_cast<double*>(ws + L.y2);
+  bool got_h0 = false;
   int rcg = run_gram(ctx, X, dtype, m, n, ld, P, ws + L.partial, G, P.ldG, &ctl->err,
-                     (o->debug_flags & HPSCD_DEBUG_SIMT_GRAM) != 0, &gram_launches, Gt, dvec);
+                     (o->debug_flags & HPSCD_DEBUG_SIMT_GRAM) != 0, &gram_launches, Gt, dvec,
+                     a_is_guess ? nullptr : y, h0, y2, &got_h0);
   if (rcg != HPSCD_OK) return rcg;
   if (cudaMemsetAsync(ws + L.hacc, 0, (size_t)3 * P.cfg.npad * sizeof(double), st) != cudaSuccess)
     return HPSCD_ERR_CUDA;
@@ -413,6 +426,9 @@ int solve_device(hpscd_ctx* ctx, const void* X, int dtype, int layout, int64_t m
                         cudaSuccess)
     return HPSCD_ERR_CUDA;
   p.order = order;
+  p.h0 = got_h0 ? h0 : nullptr;
+  p.y2 = got_h0 ? y2 : nullptr;
+  p.confirm = select ? 0 : 1;
   p.trace = nullptr;
   p.trace_passes = 0;
   if (ctx->trace_passes > 0 && ctx->trace_dev) {

@@ -17,6 +17,7 @@ struct GramPlan {
   size_t partial_bytes;  // float64 partial tiles
 };
 GramPlan gram_plan(int64_t m, int npad, int sms);
+GramPlan gram_plan_capped(int64_t m, int npad, int sms, int max_ksplit);  // <= max_ksplit splits
 cudaError_t launch_gram(const void* X, int dtype, int64_t m, int n, int64_t ld, const GramPlan& gp,
                         double* partial, float* G, int ldG, cudaStream_t stream);
 
@@ -56,13 +57,18 @@ struct GramTCParams {
   int* err;
   uint64_t timeout_ns;
   int nstages;
+  const float* y;   // or null: also form X^T y and ||y||^2
+  double* hpart;    // [ksplit][npad] per-split X^T y (the diagonal tiles' workers)
+  double* y2part;   // [ksplit] per-split ||y||^2
 };
 bool gram_tc_plan(int dtype, int64_t m, int n, int sms, int max_smem, GramTCPlan* gp);
 // G = X^T X into G (ldG); when Gt is given, also G~ = D^{-1} G (ldG, rows and
-// columns >= n zero) and d = diag(G) (float32, dvec).
+// columns >= n zero) and d = diag(G) (float32, dvec).  When y, h0 and y2 are
+// given, also h0 = X^T y (float64 [npad]) and *y2 = ||y||^2 (float64).
 cudaError_t launch_gram_tc(const CUtensorMap* tmap, int dtype, int64_t m, const GramTCPlan& gp,
                            float* partial, int* err, uint64_t timeout_ns, float* G, int ldG,
-                           cudaStream_t stream, int n, float* Gt, float* dvec);
+                           cudaStream_t stream, int n, float* Gt, float* dvec,
+                           const float* y = nullptr, double* h0 = nullptr, double* y2 = nullptr);
 
 // ---- persistent tall sweep (column-major X, n <= 512) ----
 constexpr int MODE_COPY = 0, MODE_NORMAL = 1, MODE_REFRESH = 2;
@@ -108,6 +114,11 @@ struct TallParams {
                       // ([max_sweeps][n], each in [0, n); the random-index variant)
   unsigned long long* trace;  // optional: per-pass phase timestamps (see hpscd_trace)
   int trace_passes;           // capacity of trace in passes
+  const double* h0;   // or null: X^T y of a cold start from the set-up (float64 [npad]);
+                      // pass 0 then reads nothing (e_0 = y, r_0 = h0 ⊘ d)
+  const double* y2;   // ||y||^2 (float64), given with h0
+  int confirm;        // 1: under REL_RES a tracked residual at the tolerance is confirmed
+                      // by a pass that recomputes e = y - X·a of the returned a
 };
 
 struct TallConfig {

@@ -82,6 +82,18 @@ int noalloc_setup(int dev, NoallocDevice** out) {
 
 inline size_t up256(size_t x) { return (x + 255) / 256 * 256; }
 
+// The kernels dereference X, y and a: each must be device (or managed) memory
+// that device `dev` can address.  cudaPointerGetAttributes allocates nothing.
+bool on_device(const void* ptr, int dev) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (at.type == cudaMemoryTypeManaged) return true;
+  return at.type == cudaMemoryTypeDevice && at.device == dev;
+}
+
 }  // namespace
 
 extern "C" int hpscd_solve_noalloc(void* stream, const void* X, int dtype, int64_t m, int64_t n,
@@ -102,6 +114,7 @@ extern "C" int hpscd_solve_noalloc(void* stream, const void* X, int dtype, int64
 
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return HPSCD_ERR_CUDA; }
+  if (!on_device(X, dev) || !on_device(y, dev) || !on_device(a, dev)) return HPSCD_ERR_INVALID_ARG;
   NoallocDevice* d = nullptr;
   int rc = noalloc_setup(dev, &d);
   if (rc != HPSCD_OK) return rc;
@@ -110,14 +123,7 @@ extern "C" int hpscd_solve_noalloc(void* stream, const void* X, int dtype, int64
   // ---- plan (same kernels and geometry as hpscd_solve, fewer Gram row splits) ----
   TallConfig cfg;
   if (!tall_config(dtype, (int)n, d->max_smem, &cfg)) return HPSCD_ERR_UNSUPPORTED;
-  GramPlan gp = gram_plan(m, cfg.npad, d->sms);
-  if (gp.ksplit > NOALLOC_MAX_KSPLIT) {
-    int64_t rps = (m + NOALLOC_MAX_KSPLIT - 1) / NOALLOC_MAX_KSPLIT;
-    rps = (rps + 31) / 32 * 32;
-    gp.rows_per_split = rps;
-    gp.ksplit = (int)((m + rps - 1) / rps);
-    gp.partial_bytes = (size_t)gp.ksplit * gp.ntile * 64 * 64 * sizeof(double);
-  }
+  const GramPlan gp = gram_plan_capped(m, cfg.npad, d->sms, NOALLOC_MAX_KSPLIT);
   const int64_t ntiles = (m + cfg.rows - 1) / cfg.rows;
   int64_t grid64 = d->sms > 256 ? 256 : d->sms;
   if (ntiles < grid64) grid64 = ntiles;
@@ -202,6 +208,7 @@ extern "C" int hpscd_solve_noalloc(void* stream, const void* X, int dtype, int64
   p.stall_barrier = 0;
   p.trace = nullptr;
   p.trace_passes = 0;
+  p.confirm = 1;  // REL_RES is confirmed on the true residual, as in hpscd_solve
   if (launch_tall_sweep(dtype, cfg, &map, p, grid, st) != cudaSuccess) {
     cudaGetLastError();
     return HPSCD_ERR_CUDA;

@@ -359,12 +359,15 @@ __device__ __forceinline__ void comp_add(float x, float& s, float& c) {
 
 // One chunk's work for one warp: lane partials of X^T e_in for the warp's
 // columns (phase B) and, unless the pass only copies y, the lane's partial row
-// sums of X·v (phase A; Dot2 pairs on a true-residual pass).
+// sums of X·v (phase A).  On a true-residual pass v = a_hi + a_lo (vsm / vreg
+// hold a_hi = fl32(a), vlo holds a_lo = fl32(a - a_hi)): X·a_hi is summed as
+// Dot2 pairs and X·a_lo, 2^-24 smaller, is added to the pair's low part.
 template <int MODE, typename T, int CW, int CPW, bool VREG>
 __device__ __forceinline__ void chunk_compute(const T* __restrict__ st, int warp, int lane,
                                               int ch, const float (&ein)[4],
                                               float (&gacc)[CPW], const float (&vreg)[VREG ? CPW : 1],
-                                              const float* __restrict__ vsm, float (&ph)[4],
+                                              const float* __restrict__ vsm,
+                                              const float* __restrict__ vlo, float (&ph)[4],
                                               float (&pl)[4]) {
   constexpr int C = NW * CW;
 #pragma unroll
@@ -378,10 +381,16 @@ __device__ __forceinline__ void chunk_compute(const T* __restrict__ st, int warp
       float vk;
       if constexpr (VREG) vk = vreg[j];
       else vk = vsm[ch * C + warp * CW + jj];
+      float vl = 0.f;
+      if constexpr (MODE == MODE_REFRESH) vl = vlo[ch * C + warp * CW + jj];
 #pragma unroll
       for (int r = 0; r < 4; ++r) {
-        if constexpr (MODE == MODE_NORMAL) ph[r] = fmaf(xv[r], vk, ph[r]);
-        else dot2_step(xv[r], vk, ph[r], pl[r]);
+        if constexpr (MODE == MODE_NORMAL) {
+          ph[r] = fmaf(xv[r], vk, ph[r]);
+        } else {
+          dot2_step(xv[r], vk, ph[r], pl[r]);
+          pl[r] = fmaf(xv[r], vl, pl[r]);
+        }
       }
     }
   }
@@ -412,7 +421,8 @@ __global__ void __launch_bounds__(NT, 1)
   float* da_s = rvec + NPAD;
   float* dd_s = da_s + NPAD;
   float* vsm = dd_s + NPAD;
-  double* a64_s = reinterpret_cast<double*>(vsm + NPAD);
+  float* vlo = vsm + NPAD;      // a_lo of a true-residual pass (0 otherwise)
+  double* a64_s = reinterpret_cast<double*>(vlo + NPAD);
   double* scal = a64_s + NPAD;  // [0]: ||e||^2, [1]: ||y||^2, [2..33]: scratch
   uint64_t* full = reinterpret_cast<uint64_t*>(scal + 40);
   uint64_t* empty = full + 16;
@@ -440,6 +450,7 @@ __global__ void __launch_bounds__(NT, 1)
     a64_s[c] = (c < n && p.warm) ? (double)p.a_in[c] : 0.0;
     dd_s[c] = (c < n) ? p.dvec[c] : 0.f;
     da_s[c] = 0.f;
+    vlo[c] = 0.f;
   }
   for (int idx = tid; idx < ((n + 31) / 32) * DIAG_PACK; idx += NT) {
     const int b = idx / DIAG_PACK, q = idx % DIAG_PACK;
@@ -485,6 +496,8 @@ __global__ void __launch_bounds__(NT, 1)
   int status = HPSCD_ERR_NOT_CONVERGED;
   double r_prev = 0.0, ynorm = 0.0;
   int64_t pass = 0, sweeps = 0;
+  int64_t sw = 0;          // sweeps (or selection steps) reflected in the residual of a pass
+  bool confirm_next = false;
   uint64_t qbase = 0;
 
   // optional trace: CTA 0 records, per pass, the global time at the start of
@@ -495,15 +508,27 @@ __global__ void __launch_bounds__(NT, 1)
   auto stamp = [&](int64_t ps, int k) {
     if (tr && ps < p.trace_passes) tr[ps * TRACE_FIELDS + k] = global_timer_ns();
   };
+  // A cold start whose X^T y and ||y||^2 the set-up formed (p.h0) makes pass 0
+  // virtual: e_0 = y is not materialised and the first streamed pass reads y.
+  // A confirmation pass (REL_RES with p.confirm) follows a pass whose tracked
+  // residual met the tolerance: it recomputes e = y - X·a for the float32
+  // coefficients that would be returned, and the rule is tested on that.
   for (pass = 0;; ++pass) {
     stamp(pass, 0);
+    const bool conf = confirm_next;
+    confirm_next = false;
+    if (pass > 0 && !conf) ++sw;
+    const bool virt = pass == 0 && p.h0 != nullptr && !p.warm;
     const int mode = (pass == 0) ? (p.warm ? MODE_REFRESH : MODE_COPY)
-                                 : ((p.refresh_every > 0 && pass % p.refresh_every == 0)
-                                        ? MODE_REFRESH
-                                        : MODE_NORMAL);
-    const float* __restrict__ ein_src = (pass == 0) ? p.y : p.e;
+                     : (conf || (p.refresh_every > 0 && sw % p.refresh_every == 0)) ? MODE_REFRESH
+                                                                                      : MODE_NORMAL;
+    // the residual the pass starts from (y until a pass has written e)
+    const float* __restrict__ ein_src = (pass == 0 || (pass == 1 && p.h0 && !p.warm)) ? p.y : p.e;
+    const int buf = (int)(pass & 1);
+    const int hb = (int)(pass % 3);
     double nrm = 0.0, ysq = 0.0;
     bool ok = true;
+    if (!virt) {
     float ein[4];
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
@@ -548,11 +573,11 @@ __global__ void __launch_bounds__(NT, 1)
         }
         if (ok) {
           if (mode == MODE_NORMAL)
-            chunk_compute<MODE_NORMAL, T, CW, CPW, V_IN_REGS>(st, warp, lane, ch, ein, gacc, v, vsm, ph, pl);
+            chunk_compute<MODE_NORMAL, T, CW, CPW, V_IN_REGS>(st, warp, lane, ch, ein, gacc, v, vsm, vlo, ph, pl);
           else if (mode == MODE_REFRESH)
-            chunk_compute<MODE_REFRESH, T, CW, CPW, V_IN_REGS>(st, warp, lane, ch, ein, gacc, v, vsm, ph, pl);
+            chunk_compute<MODE_REFRESH, T, CW, CPW, V_IN_REGS>(st, warp, lane, ch, ein, gacc, v, vsm, vlo, ph, pl);
           else
-            chunk_compute<MODE_COPY, T, CW, CPW, V_IN_REGS>(st, warp, lane, ch, ein, gacc, v, vsm, ph, pl);
+            chunk_compute<MODE_COPY, T, CW, CPW, V_IN_REGS>(st, warp, lane, ch, ein, gacc, v, vsm, vlo, ph, pl);
         }
         if (ch == NCH - 1) {
           // the panel's row sums go to the cross-warp reduction buffer
@@ -573,6 +598,7 @@ __global__ void __launch_bounds__(NT, 1)
       if (fail) { err = DEV_TIMEOUT_COPY; break; }
       if (rr >= 0 && rrow < m) {
         float e_new;
+        double e64 = 0.0;
         if (mode == MODE_NORMAL) {
           float sacc = 0.f;
 #pragma unroll
@@ -588,10 +614,13 @@ __global__ void __launch_bounds__(NT, 1)
             comp_add(red_hi[(rb * NW + w) * PR + rr], sh, sc);
             sl += red_lo[(rb * NW + w) * PR + rr];
           }
-          e_new = (float)(((double)red_y - (double)sh) - ((double)sc + (double)sl));
+          e64 = ((double)red_y - (double)sh) - ((double)sc + (double)sl);
+          e_new = (float)e64;
         }
         p.e[rrow] = e_new;
-        nrm = fma((double)e_new, (double)e_new, nrm);
+        // a true-residual pass takes the norm of y - X·a before e is rounded to float32
+        if (mode != MODE_REFRESH) e64 = (double)e_new;
+        nrm = fma(e64, e64, nrm);
         if (pass == 0) ysq = fma((double)red_y, (double)red_y, ysq);
       }
 #pragma unroll
@@ -605,8 +634,6 @@ __global__ void __launch_bounds__(NT, 1)
 
     // publish this CTA's partials: h into hacc[pass % 3] (float64 atomics),
     // G~·w rows into gw[pass % 2], ||e||^2 into npart[pass % 2]
-    const int buf = (int)(pass & 1);
-    const int hb = (int)(pass % 3);
     // this CTA's rows of G~·w (w = da_p, or a_0 on a warm pass 0), one warp per
     // row c = blockIdx.x + k·grid; the rows are spread over the CTAs and
     // published with the partials, so after the barrier r costs n loads
@@ -646,7 +673,9 @@ __global__ void __launch_bounds__(NT, 1)
       p.npart[(size_t)buf * grid + blockIdx.x] = a;
       if (pass == 0) p.ypart[blockIdx.x] = b;
     }
-    const unsigned expected = (unsigned)grid + ((p.stall_barrier && pass == 0) ? 1u : 0u);
+    // the test hook stalls the first grid barrier taken (pass 1 when pass 0 is virtual)
+    const int64_t first_barrier = (p.h0 && !p.warm) ? 1 : 0;
+    const unsigned expected = (unsigned)grid + ((p.stall_barrier && pass == first_barrier) ? 1u : 0u);
     if (!grid_barrier_named(p.ctl, expected, p.timeout_ns, NT, &flags[1])) {
       err = DEV_TIMEOUT_BARRIER;
       break;
@@ -658,16 +687,23 @@ __global__ void __launch_bounds__(NT, 1)
     // more (its readers passed this barrier) and none adds to before the next one
     if (blockIdx.x == 0)
       for (int c = tid; c < NPAD; c += NT) p.hacc[(size_t)((pass + 2) % 3) * NPAD + c] = 0.0;
+    }  // !virt
     if (tid < NPAD) {
       float rv = 0.f;
       if (tid < n && dd_s[tid] > 0.f) {
-        const double hd = __ldcg(p.hacc + (size_t)hb * NPAD + tid);
-        const double gwc = (pass > 0 || p.warm) ? (double)__ldcg(p.gw + (size_t)buf * NPAD + tid) : 0.0;
-        rv = (float)(hd / (double)dd_s[tid] - gwc);
+        if (virt) {
+          rv = (float)(__ldg(p.h0 + tid) / (double)dd_s[tid]);
+        } else {
+          const double hd = __ldcg(p.hacc + (size_t)hb * NPAD + tid);
+          const double gwc = (pass > 0 || p.warm) ? (double)__ldcg(p.gw + (size_t)buf * NPAD + tid) : 0.0;
+          rv = (float)(hd / (double)dd_s[tid] - gwc);
+        }
       }
       rvec[tid] = rv;
     }
-    if (warp == 0) {
+    if (warp == 0 && virt) {
+      if (lane == 0) { const double y2 = __ldg(p.y2); scal[0] = y2; scal[1] = y2; }
+    } else if (warp == 0) {
       // at most 8 CTAs per lane (grid <= 256); loads issued together
       double av[8], bv[8];
 #pragma unroll
@@ -691,24 +727,46 @@ __global__ void __launch_bounds__(NT, 1)
     if (pass == 0) ynorm = sqrt(scal[1]);
     const double enorm = sqrt(scal[0]);
     const double rel = ynorm > 0.0 ? enorm / ynorm : enorm;
-    if (blockIdx.x == 0 && tid == 0) p.hist[pass] = rel;
-    sweeps = pass;
+    if (blockIdx.x == 0 && tid == 0) p.hist[sw] = rel;  // a confirmation overwrites the tracked value
+    sweeps = sw;
+    // e_out is y - X·a for exactly the float32 coefficients a_out would get:
+    // pass 0 (a = 0, or the float32 guess) and a confirmation pass
+    const bool exact = pass == 0 || conf;
     // after the selection steps of Algorithm 3, up to swap_rounds swap steps
-    const bool swap_phase = SEL && p.swap_rounds > 0 && pass >= p.max_sweeps;
+    const bool swap_phase = SEL && p.swap_rounds > 0 && sw >= p.max_sweeps;
     bool stop = false;
     if (!isfinite(rel)) {
       status = HPSCD_ERR_NONFINITE; stop = true;
     } else if (!swap_phase && p.stop_rule == HPSCD_STOP_REL_RES && rel <= p.tol) {
-      status = HPSCD_OK; stop = true;
-    } else if (!swap_phase && p.stop_rule == HPSCD_STOP_REL_CHANGE && pass >= 1 &&
+      if (exact || !p.confirm) { status = HPSCD_OK; stop = true; }
+      else confirm_next = true;
+    } else if (!swap_phase && p.stop_rule == HPSCD_STOP_REL_CHANGE && sw >= 1 &&
                (r_prev == 0.0 || fabs(r_prev - rel) < p.tol * r_prev)) {
       status = HPSCD_OK; stop = true;
-    } else if (pass == p.max_sweeps + (SEL ? p.swap_rounds : 0)) {
+    }
+    if (!stop && !confirm_next && sw == p.max_sweeps + (SEL ? p.swap_rounds : 0)) {
       status = (p.stop_rule == HPSCD_STOP_NONE || swap_phase) ? HPSCD_OK : HPSCD_ERR_NOT_CONVERGED;
       stop = true;
     }
     r_prev = rel;
     if (stop) break;
+    if (confirm_next) {
+      // the next pass recomputes e = y - X·a for a = fl32(a64), the coefficients
+      // that would be returned, and applies no step (da = 0)
+      for (int c = tid; c < NPAD; c += NT) {
+        const float hi = (float)a64_s[c];
+        a64_s[c] = (double)hi;
+        vsm[c] = hi;
+        vlo[c] = 0.f;
+        da_s[c] = 0.f;
+      }
+      named_sync(NT);
+      if constexpr (V_IN_REGS) {
+#pragma unroll
+        for (int j = 0; j < CPW; ++j) v[j] = vsm[(j / CW) * C + warp * CW + (j % CW)];
+      }
+      continue;
+    }
 
     int removed = -1;  // a swap step's dropped column (its coefficient becomes exactly 0)
     if constexpr (SEL) {
@@ -719,8 +777,8 @@ __global__ void __launch_bounds__(NT, 1)
                           reinterpret_cast<int*>(red_hi) + 4 * NW, reinterpret_cast<double*>(red_lo),
                           reinterpret_cast<int*>(red_hi), &jin);
       if (blockIdx.x == 0 && tid == 0 && p.swap_out) {
-        p.swap_out[2 * (pass - p.max_sweeps)] = removed;
-        p.swap_out[2 * (pass - p.max_sweeps) + 1] = jin;
+        p.swap_out[2 * (sw - p.max_sweeps)] = removed;
+        p.swap_out[2 * (sw - p.max_sweeps) + 1] = jin;
       }
       if (removed < 0) {  // no exchange lowers the error: done
         status = HPSCD_OK;
@@ -729,7 +787,7 @@ __global__ void __launch_bounds__(NT, 1)
     } else {
       // scratch for the argmax: the row-sum buffer is free between passes
       const int jhat = select_step(n, NPAD, rvec, dd_s, da_s, red_hi, reinterpret_cast<int*>(red_lo));
-      if (blockIdx.x == 0 && tid == 0 && p.sel_out) p.sel_out[pass] = jhat;
+      if (blockIdx.x == 0 && tid == 0 && p.sel_out) p.sel_out[sw] = jhat;
     }
     } else if constexpr (ORD) {
       // the steps of sweep pass + 1 take the columns order[pass·n + k]: gather
@@ -740,7 +798,7 @@ __global__ void __launch_bounds__(NT, 1)
       float* dstep = red_hi;
       int* o_s = reinterpret_cast<int*>(red_hi + NPAD);
       float* rstep = vsm;
-      const int* ord = p.order + (size_t)pass * n;
+      const int* ord = p.order + (size_t)sw * n;
       for (int k = tid; k < NPAD; k += NT) o_s[k] = k < n ? __ldg(ord + k) : -1;
       named_sync(NT);
       for (int k = tid; k < NPAD; k += NT) rstep[k] = k < n ? rvec[o_s[k]] : 0.f;
@@ -774,12 +832,15 @@ __global__ void __launch_bounds__(NT, 1)
       }
     }
     stamp(pass, 5);
-    const int64_t nx = pass + 1;
+    const int64_t nx = sw + 1;
     const bool next_refresh = p.refresh_every > 0 && nx % p.refresh_every == 0;
     for (int c = tid; c < NPAD; c += NT) {
       if constexpr (SEL) a64_s[c] = (c == removed) ? 0.0 : a64_s[c] + (double)da_s[c];
       else a64_s[c] += (double)da_s[c];
-      vsm[c] = next_refresh ? (float)a64_s[c] : da_s[c];
+      // a refresh forms y - X·a from a itself: a = hi + lo, both float32
+      const float hi = (float)a64_s[c];
+      vsm[c] = next_refresh ? hi : da_s[c];
+      vlo[c] = next_refresh ? (float)(a64_s[c] - (double)hi) : 0.f;
     }
     named_sync(NT);
     if constexpr (V_IN_REGS) {
@@ -804,7 +865,7 @@ __global__ void __launch_bounds__(NT, 1)
       p.ctl->status = (err != DEV_OK) ? HPSCD_ERR_TIMEOUT : status;
       p.ctl->sweeps = sweeps;
       p.ctl->final_res = r_prev;
-      p.ctl->passes = pass + 1;
+      p.ctl->passes = pass + 1 - ((p.h0 && !p.warm) ? 1 : 0);  // passes over X made
     }
   }
 }
@@ -866,7 +927,7 @@ bool tall_config(int dtype, int n, int max_smem, TallConfig* cfg) {
   cfg->box_cols = c;
   cfg->threads = NT;
   const int nblk = cfg->npad >= 32 ? cfg->npad / 32 : 1;
-  const int fixed = 1024 /*align*/ + 4 * NW * PR * 4 + cfg->npad * (4 * 4 + 8) + 40 * 8 +
+  const int fixed = 1024 /*align*/ + 4 * NW * PR * 4 + cfg->npad * (5 * 4 + 8) + 40 * 8 +
                     32 * 8 + 16 + nblk * DIAG_PACK * 4;
   int nst = (max_smem - 256 - fixed) / cfg->stage_bytes;
   if (nst > 12) nst = 12;

@@ -284,3 +284,25 @@ def test_nonfinite_inputs_are_reported():
     X[2, 7] = np.inf
     o = oracle.solve(X, s.y, m=s.m, n=s.n, dtype="f64", tol=1e-6, max_sweeps=10)
     assert o.status == "nonfinite" and o.sweeps == 1
+
+
+@pytest.mark.parametrize("layout,dtype,stop", [("col", "f32", "rel_change"), ("col", "bf16", "rel_res"),
+                                               ("row", "f32", "none")])
+def test_threaded_oracle_is_algorithm_1(layout, dtype, stop):
+    """The CPU baseline's threaded Algorithm 1 (row loops split over threads,
+    column order sequential): bitwise the sequential oracle at one thread, and
+    the same iterates up to summation order at several."""
+    s = synth.make_system(3001, 40, seed=31, noise=0.01, layout=layout, dtype=dtype)
+    a0 = np.linspace(-0.5, 0.5, s.n)
+    kw = dict(tol=1e-8, max_sweeps=12, stop=stop)
+    ref = oracle.solve_system(s, a0=a0, **kw)
+    one, used1 = oracle.solve_mt(s.X, s.y, m=s.m, n=s.n, layout=layout, dtype=dtype, a0=a0,
+                                 threads=1, **kw)
+    assert used1 == 1 and one.sweeps == ref.sweeps and one.status == ref.status
+    np.testing.assert_array_equal(one.a, ref.a)
+    np.testing.assert_array_equal(one.hist, ref.hist)
+    many, _ = oracle.solve_mt(s.X, s.y, m=s.m, n=s.n, layout=layout, dtype=dtype, a0=a0,
+                              threads=5, **kw)
+    assert many.sweeps == ref.sweeps
+    np.testing.assert_allclose(many.a, ref.a, rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(many.hist, ref.hist, rtol=1e-12)

@@ -31,8 +31,9 @@ def rel(a, b):
     return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
 
 
-def solve_noalloc(X, y, a_out, **kw):
-    """Call hpscd_solve_noalloc on torch's current stream (argument marshalling only)."""
+def solve_noalloc(X, y, a_out, guess=False, **kw):
+    """Call hpscd_solve_noalloc on torch's current stream (argument marshalling only).
+    guess: a_out holds the initial guess (a_is_guess = 1)."""
     lib = hp.load()
     _, dt, lay, m, n, ld = hp._describe(X)
     assert lay == hp.COL
@@ -42,7 +43,8 @@ def solve_noalloc(X, y, a_out, **kw):
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
     rc = lib.hpscd_solve_noalloc(stream, ctypes.c_void_p(X.data_ptr()), dt, m, n, ld,
                                  ctypes.c_void_p(y.data_ptr()), ctypes.c_void_p(a_out.data_ptr()),
-                                 0, ctypes.byref(o), hist.ctypes.data_as(ctypes.c_void_p),
+                                 1 if guess else 0, ctypes.byref(o),
+                                 hist.ctypes.data_as(ctypes.c_void_p),
                                  ctypes.byref(sw), ctypes.byref(rr))
     return rc, hist[: sw.value + 1], sw.value
 
@@ -62,12 +64,44 @@ def test_two_calls_in_a_row_match_hpscd_solve():
     kw = dict(tol=0.0, max_sweeps=6, stop="none")
     ref = ctx.solve(X, y, **kw)
     ctx.close()
-    for _ in range(2):
-        a = torch.full((s.n,), float("nan"), device="cuda")
+    outs = [torch.full((s.n,), float("nan"), device="cuda") for _ in range(3)]
+    torch.cuda.synchronize()
+    free = []
+    for a in outs:
         rc, hist, sweeps = solve_noalloc(X, y, a, **kw)
+        free.append(torch.cuda.mem_get_info()[0])
         assert rc == 0 and sweeps == ref.sweeps == 6
         assert rel(a.cpu().numpy(), ref.a.cpu().numpy()) <= RTOL_F32
         np.testing.assert_allclose(hist, ref.hist, rtol=1e-5, atol=1e-7)
+    # the defining property: once the first call has run (it may load the
+    # library's kernels), further calls take no device memory at all
+    assert free[1] == free[0] and free[2] == free[0]
+
+
+def test_warm_start_matches_hpscd_solve():
+    s = synth.make_system(60_000, 128, seed=23, noise=0.01)
+    X, y = gpu_system(s)
+    guess = torch.from_numpy((s.a_true + 0.05 * np.random.default_rng(1).standard_normal(s.n))
+                             .astype(np.float32)).cuda()
+    ctx = hp.Context(0)
+    kw = dict(tol=0.0, max_sweeps=3, stop="none")
+    ref = ctx.solve(X, y, a0=guess, **kw)
+    ctx.close()
+    for _ in range(2):
+        a = guess.clone()
+        rc, hist, sweeps = solve_noalloc(X, y, a, guess=True, **kw)
+        assert rc == 0 and sweeps == 3
+        assert rel(a.cpu().numpy(), ref.a.cpu().numpy()) <= RTOL_F32
+        np.testing.assert_allclose(hist, ref.hist, rtol=1e-5, atol=1e-7)
+
+
+def test_refuses_host_pointers():
+    s = synth.make_system(1000, 8, seed=24)
+    X, y = gpu_system(s)
+    a = torch.empty(s.n, device="cuda")
+    y_host = torch.from_numpy(s.y)  # pageable host memory: the kernels cannot read it
+    rc, _, _ = solve_noalloc(X, y_host, a, tol=1e-6, max_sweeps=5, stop="rel_res")
+    assert rc == 1  # HPSCD_ERR_INVALID_ARG, nothing launched
 
 
 def test_bf16_and_limits():
