@@ -31,8 +31,7 @@
  *                              float64-grade accumulation) and hist[s] becomes
  *                              that value; the solve stops if it meets tol and
  *                              otherwise sweeps on from the recomputed e
- *                              (hpscd_select and the batched sweep test the
- *                              updated residual);
+ *                              (hpscd_select tests the updated residual);
  *       HPSCD_STOP_REL_CHANGE: stop after sweep s >= 1 when
  *                              |hist[s-1] - hist[s]| < tol * hist[s-1]
  *                              (or hist[s-1] == 0);

@@ -335,8 +335,8 @@ int hpscd_oracle_solve_mt(const void* X, int dt, int lay, int64_t m, int64_t n, 
   if (lay == OR_ROW && m > 0 && n > 0) {
     Xcopy = (double*)malloc((size_t)m * (size_t)n * sizeof(double));
     if (!Xcopy) return OR_NOMEM;
-    for (int64_t i = 0; i < m; ++i)
-      for (int64_t j = 0; j < n; ++j) Xcopy[j * m + i] = x_elem(X, dt, lay, ld, i, j);
+    for (int64_t c = 0; c < n; ++c)
+      for (int64_t r = 0; r < m; ++r) Xcopy[c * m + r] = x_elem(X, dt, lay, ld, r, c);
     Xc = Xcopy;
     dtc = OR_F64;
     ldc = m;
@@ -412,9 +412,9 @@ int hpscd_oracle_solve_mt(const void* X, int dt, int lay, int64_t m, int64_t n, 
 #pragma omp barrier
         double num = 0.0;
         for (int k = 0; k < T; ++k) num += part[((j & 1) * T + k) * 8];
-        const double da = d[j] > 0.0 ? num / d[j] : 0.0;
+        const double dj = d[j], da = dj > 0.0 ? num / dj : 0.0;
         axpy_rows(Xc, dtc, j * ldc, da, e, i0, i1);
-        if (t == 0) a_out[j] += da;
+        if (t == 0) a_out[j] = a_out[j] + da;
       }
       double es = 0.0;
       for (int64_t i = i0; i < i1; ++i) es += e[i] * e[i];

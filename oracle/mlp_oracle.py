@@ -17,6 +17,13 @@ Algorithm 1: biased moments, bias correction, step lr * m_hat / (sqrt(v_hat) + e
 Parameter layout (flat): W1 [256][18], b1 [256], W2 [256][256], b2 [256],
 W3 [256][256], b3 [256], row-major W[out][in].
 
+store (optional, default none): a rounding applied where an implementation
+stores an intermediate in a narrower format -- H1 and H2 in the forward pass,
+dOut, dZ2 and dZ1 in the backward pass.  The ReLU masks [Z > 0] are decisions
+taken in floating point; a check of such an implementation evaluates them, and
+everything after them, in that implementation's precision by passing its
+rounding here.  With store = None the arithmetic is plain float64.
+
 Parity status: pinned in tests/test_mlp_oracle.py (central finite
 differences, closed forms of degenerate networks, the output mask, Adam's
 first step).
@@ -54,12 +61,17 @@ def features(theta, m, n) -> np.ndarray:
     return np.concatenate([theta, (n / 256.0)[:, None], (np.log(np.maximum(m, 1.0)) / np.log(16384.0))[:, None]], axis=1)
 
 
-def forward(flat, phi):
+def _keep(x):
+    return x
+
+
+def forward(flat, phi, store=None):
+    st = store or _keep
     W1, b1, W2, b2, W3, b3 = unpack(flat)
     Z1 = phi @ W1.T + b1
-    H1 = np.maximum(Z1, 0.0)
+    H1 = st(np.maximum(Z1, 0.0))
     Z2 = H1 @ W2.T + b2
-    H2 = np.maximum(Z2, 0.0)
+    H2 = st(np.maximum(Z2, 0.0))
     out = H2 @ W3.T + b3
     return out, (phi, Z1, H1, Z2, H2)
 
@@ -77,26 +89,28 @@ def loss(flat, theta, m, n, target) -> float:
     return float((d * d).sum() / C) if C > 0 else 0.0
 
 
-def loss_and_grads(flat, theta, m, n, target, phi=None):
+def loss_and_grads(flat, theta, m, n, target, phi=None, store=None):
     """(L, dL/dparams as a flat float64 vector).  phi overrides the features
-    (e.g. with the values a lower-precision implementation actually used)."""
+    (e.g. with the values a lower-precision implementation actually used);
+    store: see the module docstring."""
+    st = store or _keep
     W1, b1, W2, b2, W3, b3 = unpack(flat)
     if phi is None:
         phi = features(theta, m, n)
-    out, (phi, Z1, H1, Z2, H2) = forward(flat, phi)
+    out, (phi, Z1, H1, Z2, H2) = forward(flat, phi, store)
     mask = output_mask(n, len(n))
     C = mask.sum()
     d = (out - np.asarray(target, dtype=np.float64)) * mask
     L = float((d * d).sum() / C) if C > 0 else 0.0
-    dOut = 2.0 * d / C if C > 0 else np.zeros_like(d)
+    dOut = st(2.0 * d / C if C > 0 else np.zeros_like(d))
     gW3 = dOut.T @ H2
     gb3 = dOut.sum(axis=0)
     dH2 = dOut @ W3
-    dZ2 = dH2 * (Z2 > 0)
+    dZ2 = st(dH2 * (H2 > 0))
     gW2 = dZ2.T @ H1
     gb2 = dZ2.sum(axis=0)
     dH1 = dZ2 @ W2
-    dZ1 = dH1 * (Z1 > 0)
+    dZ1 = st(dH1 * (H1 > 0))
     gW1 = dZ1.T @ phi
     gb1 = dZ1.sum(axis=0)
     return L, pack([gW1, gb1, gW2, gb2, gW3, gb3])

@@ -48,7 +48,7 @@ constexpr int REDF = 8192;          // floats of one row-sum reduction buffer
 
 // Shared-memory plan of one CTA (byte offsets from a 128-byte aligned base).
 struct BSmem {
-  int e, uni, hred, hpart, rvec, da, dd, v, a64, diag, scal, total;
+  int e, uni, hred, hpart, h64, rvec, da, dd, v, a64, diag, scal, total;
 };
 
 __host__ __device__ inline BSmem bsmem_plan(int ecap) {
@@ -63,8 +63,9 @@ __host__ __device__ inline BSmem bsmem_plan(int ecap) {
   const int gstage = 2 * BMAXN * GPITCH * 4;  // Gram staging (double buffer)
   const int red = 2 * REDF * 4;               // row-sum reduction (double buffer)
   s.uni = take(gstage > red ? gstage : red);
-  s.hred = take(BNW * BMAXN * 4);
-  s.hpart = take(2 * BMAXN * 4);
+  s.hred = take(BNW * BMAXN * 8);   // float64 row-group sums of h
+  s.hpart = take(2 * BMAXN * 8);    // float64 CTA partials of h (exchanged in the cluster)
+  s.h64 = take(BMAXN * 8);          // h of the pass, summed over the cluster
   s.rvec = take(BMAXN * 4);
   s.da = take(BMAXN * 4);
   s.dd = take(BMAXN * 4);
@@ -195,7 +196,7 @@ __device__ void gram_partial(const float* __restrict__ X, int64_t ld, int64_t r0
 template <int CPW>
 __device__ void stream_pass(const float* __restrict__ X, int64_t ld, int64_t r0, int mloc, int n,
                             int nwc, int vec, float* e_s, const float* vsm, float* red,
-                            float* hred, double& nrm_out) {
+                            double* hred, double& nrm_out) {
   constexpr int RPL = 16 / CPW;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int nwr = BNW / nwc;
@@ -257,16 +258,54 @@ __device__ void stream_pass(const float* __restrict__ X, int64_t ld, int64_t r0,
       }
     }
   }
-  // lane partials of h -> one value per (row group, column)
+  // lane partials of h -> one value per (row group, column), summed in float64
 #pragma unroll
   for (int j = 0; j < CPW; ++j) {
-    float s = h[j];
+    double s = (double)h[j];
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(FULL_MASK, s, off);
     const int col = wc * CPW + j;
     if (lane == 0 && col < n) hred[wr * BMAXN + col] = s;
   }
   nrm_out = nrm;
+}
+
+// Loads that the compiler may not hoist out of the sweep loop: the confirmation
+// step reads these descriptor fields only when it runs, so they do not stay
+// live (in registers) across the streaming passes.
+__device__ __forceinline__ const float* ld_volatile_ptr(const float* const* addr) {
+  const float* v;
+  asm volatile("ld.volatile.global.u64 %0, [%1];" : "=l"(v) : "l"(addr));
+  return v;
+}
+__device__ __forceinline__ int ld_volatile_s32(const int32_t* addr) {
+  int v;
+  asm volatile("ld.volatile.global.s32 %0, [%1];" : "=r"(v) : "l"(addr));
+  return v;
+}
+
+// The residual of the coefficients ahi (shared, float32) on this CTA's rows:
+// e = y - X·ahi with Dot2 accumulation (Ogita, Rump, Oishi 2005), one thread
+// per row; returns this thread's share of ||y - X·ahi||^2 in float64, taken
+// before e is rounded to float32.
+__device__ double true_residual_rows(const float* __restrict__ X, int64_t ld, int64_t r0, int mloc,
+                                     int n, const float* __restrict__ y, const float* ahi,
+                                     float* e_s) {
+  double t2 = 0.0;
+  for (int i = threadIdx.x; i < mloc; i += BNT) {
+    float s = 0.f, c = 0.f;
+    for (int j = 0; j < n; ++j) {
+      const float xv = __ldg(X + (int64_t)j * ld + r0 + i), av = ahi[j];
+      const float pr = xv * av, pe = fmaf(xv, av, -pr);
+      const float t = s + pr, z = t - s;
+      c += ((s - (t - z)) + (pr - z)) + pe;
+      s = t;
+    }
+    const double ed = ((double)__ldg(y + r0 + i) - (double)s) - (double)c;
+    e_s[i] = (float)ed;
+    t2 = fma(ed, ed, t2);
+  }
+  return t2;
 }
 
 // Forward substitution da_j = r_j - sum_{l<j} G~_jl da_l in blocks of 32
@@ -337,8 +376,9 @@ __global__ void __launch_bounds__(BNT, 1) batched_sweep_kernel(const BatchParams
   const BSmem L = bsmem_plan(p.ecap);
   float* e_s = reinterpret_cast<float*>(base + L.e);
   float* uni = reinterpret_cast<float*>(base + L.uni);
-  float* hred = reinterpret_cast<float*>(base + L.hred);
-  float* hpart = reinterpret_cast<float*>(base + L.hpart);  // [2][BMAXN]
+  double* hred = reinterpret_cast<double*>(base + L.hred);
+  double* hpart = reinterpret_cast<double*>(base + L.hpart);  // [2][BMAXN]
+  double* h64 = reinterpret_cast<double*>(base + L.h64);
   float* rvec = reinterpret_cast<float*>(base + L.rvec);
   float* da_s = reinterpret_cast<float*>(base + L.da);
   float* dd_s = reinterpret_cast<float*>(base + L.dd);
@@ -461,7 +501,11 @@ __global__ void __launch_bounds__(BNT, 1) batched_sweep_kernel(const BatchParams
     double ynorm = 0.0, r_prev = 0.0;
     int status = HPSCD_ERR_NOT_CONVERGED;
     int64_t pass = 0;
+    int refills = 0;       // passes that only re-formed h from a recomputed e (no step, no test)
+    int confirms = 0;      // true-residual passes made
+    bool refill = false;   // this pass is such a refill
     for (pass = 0;; ++pass) {
+      const int64_t sw = pass - refills;  // sweeps reflected in e
       double nrm = 0.0;
       if (cpw == 4) stream_pass<4>(X, ld, r0, mloc, n, nwc, vec, e_s, vsm, uni, hred, nrm);
       else if (cpw == 8) stream_pass<8>(X, ld, r0, mloc, n, nwc, vec, e_s, vsm, uni, hred, nrm);
@@ -471,7 +515,7 @@ __global__ void __launch_bounds__(BNT, 1) batched_sweep_kernel(const BatchParams
       const int buf = (int)(pass & 1);
       const int nwr = BNW / nwc;
       for (int c = tid; c < n; c += BNT) {
-        float s = 0.f;
+        double s = 0.0;
         for (int w = 0; w < nwr; ++w) s += hred[w * BMAXN + c];
         hpart[buf * BMAXN + c] = s;
       }
@@ -488,35 +532,74 @@ __global__ void __launch_bounds__(BNT, 1) batched_sweep_kernel(const BatchParams
           if (pass == 0) ysum += ld_cluster_f64(mapa_u32(smem_u32(&scal[18]), (uint32_t)k));
         }
         for (int c = tid; c < n; c += BNT) {
-          float s = 0.f;
+          double s = 0.0;
           for (int k = 0; k < K; ++k)
-            s += ld_cluster_f32(mapa_u32(smem_u32(&hpart[buf * BMAXN + c]), (uint32_t)k));
-          rvec[c] = s;
+            s += ld_cluster_f64(mapa_u32(smem_u32(&hpart[buf * BMAXN + c]), (uint32_t)k));
+          h64[c] = s;
         }
       } else {
         enorm2 = scal[16 + buf];
         ysum = scal[18];
-        for (int c = tid; c < n; c += BNT) rvec[c] = hpart[buf * BMAXN + c];
+        for (int c = tid; c < n; c += BNT) h64[c] = hpart[buf * BMAXN + c];
       }
       if (pass == 0) ynorm = sqrt(ysum);
       const double enorm = sqrt(enorm2);
-      const double rel = ynorm > 0.0 ? enorm / ynorm : enorm;
-      if (rank == 0 && tid == 0 && sd.hist) sd.hist[pass] = rel;
+      double rel = ynorm > 0.0 ? enorm / ynorm : enorm;
       bool stop = false;
-      if (!isfinite(rel)) {
-        status = HPSCD_ERR_NONFINITE; stop = true;
-      } else if (p.stop_rule == HPSCD_STOP_REL_RES && rel <= p.tol) {
-        status = HPSCD_OK; stop = true;
-      } else if (p.stop_rule == HPSCD_STOP_REL_CHANGE && pass >= 1 &&
-                 (r_prev == 0.0 || fabs(r_prev - rel) < p.tol * r_prev)) {
-        status = HPSCD_OK; stop = true;
-      } else if (pass == p.max_sweeps) {
-        status = (p.stop_rule == HPSCD_STOP_NONE) ? HPSCD_OK : HPSCD_ERR_NOT_CONVERGED;
-        stop = true;
+      const bool tested = !refill;
+      refill = false;
+      if (tested) {
+        if (rank == 0 && tid == 0 && sd.hist) sd.hist[sw] = rel;
+        if (!isfinite(rel)) {
+          status = HPSCD_ERR_NONFINITE; stop = true;
+        } else if (p.stop_rule == HPSCD_STOP_REL_RES && rel <= p.tol) {
+          if (pass == 0 && !ld_volatile_s32(&p.sys[sidx].a_is_guess)) {
+            status = HPSCD_OK; stop = true;  // e = y exactly
+          } else {
+            // confirm on the true residual of the float32 coefficients to be
+            // returned: e = y - X·fl32(a) on every CTA's rows, ||e|| over the cluster
+            __syncthreads();
+            for (int c = tid; c < BMAXN; c += BNT) {
+              const float hi = (float)a64_s[c];
+              a64_s[c] = (double)hi;
+              vsm[c] = hi;
+            }
+            __syncthreads();
+            double t2 = true_residual_rows(X, ld, r0, mloc, n, ld_volatile_ptr(&p.sys[sidx].y), vsm, e_s);
+            t2 = block_sum_f64(t2, scal);
+            ++confirms;
+            if (tid == 0) scal[20] = t2;
+            csync();
+            double tot = 0.0;
+            if constexpr (K > 1) {
+              for (int k = 0; k < K; ++k) tot += ld_cluster_f64(mapa_u32(smem_u32(&scal[20]), (uint32_t)k));
+            } else {
+              tot = scal[20];
+            }
+            rel = ynorm > 0.0 ? sqrt(tot) / ynorm : sqrt(tot);
+            if (rank == 0 && tid == 0 && sd.hist) sd.hist[sw] = rel;
+            if (!isfinite(rel)) { status = HPSCD_ERR_NONFINITE; stop = true; }
+            else if (rel <= p.tol) { status = HPSCD_OK; stop = true; }
+            else if (sw == p.max_sweeps) { status = HPSCD_ERR_NOT_CONVERGED; stop = true; }
+            else refill = true;  // the next pass forms h from the recomputed e, with v = 0
+          }
+        } else if (p.stop_rule == HPSCD_STOP_REL_CHANGE && sw >= 1 &&
+                   (r_prev == 0.0 || fabs(r_prev - rel) < p.tol * r_prev)) {
+          status = HPSCD_OK; stop = true;
+        } else if (sw == p.max_sweeps) {
+          status = (p.stop_rule == HPSCD_STOP_NONE) ? HPSCD_OK : HPSCD_ERR_NOT_CONVERGED;
+          stop = true;
+        }
+        r_prev = rel;
       }
-      r_prev = rel;
       if (stop) break;
-      __syncthreads();  // rvec (h) complete
+      if (refill) {
+        ++refills;
+        for (int c = tid; c < BMAXN; c += BNT) { vsm[c] = 0.f; da_s[c] = 0.f; }
+        __syncthreads();
+        continue;
+      }
+      __syncthreads();  // h64 complete
       // r = h ⊘ d - G~·v, one thread per row: the row's float4 loads are
       // independent of one another, so they are in flight together (columns past
       // n read zeros of G~ and of v up to the next multiple of 4)
@@ -535,7 +618,7 @@ __global__ void __launch_bounds__(BNT, 1) batched_sweep_kernel(const BatchParams
           a3 = fmaf(g.w, w.w, a3);
         }
         const float dc = dd_s[c];
-        rvec[c] = (dc > 0.f ? rvec[c] / dc : 0.f) - ((a0 + a1) + (a2 + a3));
+        rvec[c] = (float)((dc > 0.f ? h64[c] / (double)dc : 0.0) - (double)((a0 + a1) + (a2 + a3)));
       }
       __syncthreads();
       forward_sub_scaled(Gt, n, rvec, da_s, diag_s, uni);  // uni is free between passes
@@ -549,10 +632,11 @@ __global__ void __launch_bounds__(BNT, 1) batched_sweep_kernel(const BatchParams
       for (int c = tid; c < n; c += BNT) sd.a[c] = (float)a64_s[c];
       if (tid == 0) {
         hpscd_sys_result rr;
-        rr.sweeps = pass;
+        rr.sweeps = pass - refills;
         rr.rel_res = r_prev;
         rr.status = status;
-        rr.passes = (int32_t)(pass + 1 > 0x7fffffff ? 0x7fffffff : pass + 1);
+        const int64_t np_ = pass + 1 + confirms;
+        rr.passes = (int32_t)(np_ > 0x7fffffff ? 0x7fffffff : np_);
         p.res[sidx] = rr;
       }
     }

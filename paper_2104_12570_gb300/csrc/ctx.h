@@ -16,6 +16,7 @@ struct hpscd_ctx {
   double timeout_s = 5.0;
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
   hpscd::GridCtl* ctl_host = nullptr;  // pinned
+  double* host_scratch = nullptr;      // pinned, 2 doubles (the wide path's confirmation)
   hpscd_timing last{};
   int trace_passes = 0;                  // 0: tracing off
   unsigned long long* trace_dev = nullptr;

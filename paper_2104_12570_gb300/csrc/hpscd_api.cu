@@ -212,8 +212,8 @@ int run_gram(hpscd_ctx* ctx, const void* X, int dtype, int64_t m, int64_t n, int
 
 // ---- wide systems: row-major X, m <= 4096 (the cluster sweep) ----
 struct WideLayout {
-  size_t Gb = 0, e = 0, a64 = 0, dsw = 0, atmp = 0, ysq = 0, hist = 0, ctl = 0, xcopy = 0, ycopy = 0,
-         acopy = 0, total = 0;
+  size_t Gb = 0, e = 0, a64 = 0, dsw = 0, atmp = 0, ysq = 0, hist = 0, ctl = 0, r2 = 0, tsum = 0,
+         xcopy = 0, ycopy = 0, acopy = 0, total = 0;
 };
 
 int make_wide_plan(const hpscd_ctx* ctx, int dtype, int64_t m, int64_t n, int64_t ld,
@@ -235,6 +235,8 @@ int make_wide_plan(const hpscd_ctx* ctx, int dtype, int64_t m, int64_t n, int64_
   L->ysq = take(sizeof(double));
   L->hist = take((size_t)(o->max_sweeps + 1) * sizeof(double));
   L->ctl = take(sizeof(GridCtl));
+  L->r2 = take((size_t)m * sizeof(double));
+  L->tsum = take(2 * sizeof(double));
   if (host_copies) {
     L->xcopy = take((size_t)m * ld * sizeof(float));
     L->ycopy = take((size_t)m * sizeof(float));
@@ -297,27 +299,76 @@ int solve_wide(hpscd_ctx* ctx, const void* X, int64_t m, int64_t n, int64_t ld, 
     cudaGetLastError();
     return HPSCD_ERR_CUDA;
   }
+  // Under REL_RES the cluster kernel stops on the residual it updates; the stop
+  // is then confirmed on e = y - X·a for the float32 a it returned (Dot2, all
+  // SMs).  If that misses the tolerance the sweeps go on from the recomputed e.
+  int64_t before = 0;  // sweeps made by earlier launches of this solve
+  int64_t conf_at[8];
+  double conf_val[8];
+  int nconf = 0;
+  int status = HPSCD_ERR_NOT_CONVERGED;
+  GridCtl c{};
+  double final_res = 0.0;
+  double* tsum = reinterpret_cast<double*>(ws + L.tsum);
+  for (;;) {
+    if (cudaMemcpyAsync(ctx->ctl_host, ctl, sizeof(GridCtl), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      return HPSCD_ERR_CUDA;
+    c = *ctx->ctl_host;
+    const int64_t total = before + c.sweeps;
+    final_res = c.final_res;
+    status = c.status;
+    if (c.err != DEV_OK || c.status != HPSCD_OK || o->stop_rule != HPSCD_STOP_REL_RES || nconf == 8) {
+      c.sweeps = total;
+      break;
+    }
+    if (launch_wide_confirm(static_cast<const float*>(X), m, n, ld, y, a, p.e,
+                            reinterpret_cast<double*>(ws + L.r2), tsum, st) != cudaSuccess ||
+        cudaMemcpyAsync(ctx->host_scratch, tsum, sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaMemcpyAsync(ctx->host_scratch + 1, p.ysq, sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+      cudaGetLastError();
+      return HPSCD_ERR_CUDA;
+    }
+    const double ynorm = sqrt(ctx->host_scratch[1]);
+    const double rel = ynorm > 0.0 ? sqrt(ctx->host_scratch[0]) / ynorm : sqrt(ctx->host_scratch[0]);
+    conf_at[nconf] = total;
+    conf_val[nconf++] = rel;
+    final_res = rel;
+    c.sweeps = total;
+    if (!isfinite(rel)) { status = HPSCD_ERR_NONFINITE; break; }
+    if (rel <= o->tol) { status = HPSCD_OK; break; }
+    if (total >= o->max_sweeps) { status = HPSCD_ERR_NOT_CONVERGED; break; }
+    WideParams q = p;
+    q.hist = p.hist + total;  // the continuation's sweep 0 is sweep `total` of the solve
+    q.max_sweeps = o->max_sweeps - total;
+    if (cudaMemsetAsync(ctl, 0, sizeof(GridCtl), st) != cudaSuccess ||
+        launch_wide_continue(n, cfg, &map, q, reinterpret_cast<float*>(ws + L.atmp), st) != cudaSuccess) {
+      cudaGetLastError();
+      return HPSCD_ERR_CUDA;
+    }
+    before = total;
+  }
   if (cudaEventRecord(ctx->ev[2], st) != cudaSuccess) return HPSCD_ERR_CUDA;
-  if (cudaMemcpyAsync(ctx->ctl_host, ctl, sizeof(GridCtl), cudaMemcpyDeviceToHost, st) != cudaSuccess)
-    return HPSCD_ERR_CUDA;
-  if (cudaStreamSynchronize(st) != cudaSuccess) return HPSCD_ERR_CUDA;
-  const GridCtl c = *ctx->ctl_host;
+  if (cudaEventSynchronize(ctx->ev[2]) != cudaSuccess) return HPSCD_ERR_CUDA;
   if (hist && c.sweeps >= 0 && c.sweeps <= o->max_sweeps) {
     if (cudaMemcpy(hist, p.hist, (size_t)(c.sweeps + 1) * sizeof(double), cudaMemcpyDeviceToHost) !=
         cudaSuccess)
       return HPSCD_ERR_CUDA;
+    for (int k = 0; k < nconf; ++k)
+      if (conf_at[k] <= c.sweeps) hist[conf_at[k]] = conf_val[k];  // the confirmed (true) values
   }
   if (sweeps_done) *sweeps_done = c.sweeps;
-  if (final_rel_res) *final_rel_res = c.final_res;
+  if (final_rel_res) *final_rel_res = final_res;
   hpscd_timing t{};
   cudaEventElapsedTime(&t.sweep_ms, ctx->ev[0], ctx->ev[2]);
-  t.passes = c.passes;
+  t.passes = c.sweeps;
   t.x_bytes = m * n * 4;
   t.grid = cfg.csize;
-  t.kernel_launches = 6;
+  t.kernel_launches = 6 + 4 * nconf;
   ctx->last = t;
   if (c.err != DEV_OK) return HPSCD_ERR_TIMEOUT;
-  return c.status;
+  return status;
 }
 
 // m == 0: nothing to sweep; y = 0, so every recorded residual is the absolute norm 0.
@@ -506,6 +557,7 @@ void free_ctx(hpscd_ctx* ctx) {
     for (int i = 0; i < 3; ++i)
       if (ctx->ring_ev[r][i]) cudaEventDestroy(ctx->ring_ev[r][i]);
   if (ctx->ctl_host) cudaFreeHost(ctx->ctl_host);
+  if (ctx->host_scratch) cudaFreeHost(ctx->host_scratch);
   if (ctx->trace_dev) cudaFree(ctx->trace_dev);
   delete ctx;
 }
@@ -543,6 +595,11 @@ int hpscd_create(hpscd_ctx** out, int device, void* stream) {
     if (cudaEventCreate(&c->ev[i]) != cudaSuccess) { hpscd_destroy(c); return HPSCD_ERR_CUDA; }
   if (cudaMallocHost(reinterpret_cast<void**>(&c->ctl_host), sizeof(GridCtl)) != cudaSuccess) {
     c->ctl_host = nullptr;
+    hpscd_destroy(c);
+    return HPSCD_ERR_CUDA;
+  }
+  if (cudaMallocHost(reinterpret_cast<void**>(&c->host_scratch), 2 * sizeof(double)) != cudaSuccess) {
+    c->host_scratch = nullptr;
     hpscd_destroy(c);
     return HPSCD_ERR_CUDA;
   }

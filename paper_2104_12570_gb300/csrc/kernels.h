@@ -152,6 +152,7 @@ struct WideParams {
   uint64_t timeout_ns;
   unsigned long long* trace;  // optional: per-block phase stamps of the first blocks
   int trace_passes;
+  int continuing;             // 1: a continuation after a failed confirmation (no stop at sweep 0)
 };
 struct WideConfig {
   int csize, rows_box, nstages, smem_bytes;
@@ -160,6 +161,12 @@ bool wide_config(int64_t m, int max_smem, WideConfig* cfg);
 cudaError_t launch_wide(const float* X, int64_t m, int64_t n, int64_t ld, const WideConfig& cfg,
                         const CUtensorMap* tmap, WideParams p, const float* y, const float* a_in,
                         int warm, float* a_tmp, cudaStream_t stream);
+// e = y - X·a (Dot2, float64-grade) for the float32 a, and *sum = ||y - X·a||^2 (float64)
+cudaError_t launch_wide_confirm(const float* X, int64_t m, int64_t n, int64_t ld, const float* y,
+                                const float* a, float* e, double* r2, double* sum, cudaStream_t stream);
+// sweeps on from the residual p.e of the coefficients p.a_out (after launch_wide_confirm)
+cudaError_t launch_wide_continue(int64_t n, const WideConfig& cfg, const CUtensorMap* tmap,
+                                 WideParams p, float* a_tmp, cudaStream_t stream);
 
 // ---- batched sweep: many column-major systems, one persistent launch ----
 struct BatchParams {

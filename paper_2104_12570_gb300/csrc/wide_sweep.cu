@@ -153,6 +153,53 @@ __global__ void __launch_bounds__(256) wide_residual_kernel(const float* __restr
   if (lane == 0) e[row] = (float)((double)y[row] - v);
 }
 
+// ---- the true residual of the returned coefficients ----
+// e = y - X·a with Dot2 accumulation per row (one warp per row) and the row's
+// (y - X·a)^2 in float64 before e is rounded to float32.
+__global__ void __launch_bounds__(256) wide_true_residual_kernel(const float* __restrict__ X,
+                                                                 int64_t m, int64_t n, int64_t ld,
+                                                                 const float* __restrict__ y,
+                                                                 const float* __restrict__ a,
+                                                                 float* __restrict__ e,
+                                                                 double* __restrict__ r2) {
+  const int64_t row = (int64_t)blockIdx.x * 8 + threadIdx.x / 32;
+  const int lane = threadIdx.x & 31;
+  if (row >= m) return;
+  const float* xr = X + row * ld;
+  float s = 0.f, c = 0.f;
+  for (int64_t j = lane; j < n; j += 32) {
+    const float xv = __ldg(xr + j), av = __ldg(a + j);
+    const float p = xv * av, pe = fmaf(xv, av, -p);
+    const float t = s + p, z = t - s;
+    c += ((s - (t - z)) + (p - z)) + pe;
+    s = t;
+  }
+  double v = (double)s + (double)c;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(FULL_MASK, v, off);
+  if (lane == 0) {
+    const double ed = (double)y[row] - v;
+    e[row] = (float)ed;
+    r2[row] = ed * ed;
+  }
+}
+
+// *out = sum of r2[0..m) in a fixed order (one CTA)
+__global__ void wide_sum_kernel(const double* __restrict__ r2, int64_t m, double* __restrict__ out) {
+  __shared__ double ws[32];
+  double v = 0.0;
+  for (int64_t i = threadIdx.x; i < m; i += blockDim.x) v += r2[i];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(FULL_MASK, v, off);
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x / 32] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x / 32); ++w) t += ws[w];
+    *out = t;
+  }
+}
+
 // ---- the cluster sweep ----
 __global__ void __launch_bounds__(WNT, 1)
     wide_sweep_kernel(const __grid_constant__ CUtensorMap tmap, const WideParams p) {
@@ -251,7 +298,7 @@ __global__ void __launch_bounds__(WNT, 1)
   if (me == 0 && tid == 0) p.hist[0] = rel;
   if (err == DEV_OK) {
     if (!isfinite(rel)) status = HPSCD_ERR_NONFINITE;
-    else if (p.stop_rule == HPSCD_STOP_REL_RES && rel <= p.tol) status = HPSCD_OK;
+    else if (p.stop_rule == HPSCD_STOP_REL_RES && rel <= p.tol && !p.continuing) status = HPSCD_OK;
     else if (p.max_sweeps == 0) status = (p.stop_rule == HPSCD_STOP_NONE) ? HPSCD_OK : HPSCD_ERR_NOT_CONVERGED;
     else status = -1;  // keep sweeping
   }
@@ -493,19 +540,11 @@ bool wide_config(int64_t m, int max_smem, WideConfig* cfg) {
   return true;
 }
 
-cudaError_t launch_wide(const float* X, int64_t m, int64_t n, int64_t ld, const WideConfig& cfg,
-                        const CUtensorMap* tmap, WideParams p, const float* y, const float* a_in,
-                        int warm, float* a_tmp, cudaStream_t stream) {
-  const int64_t nblk = (n + WW - 1) / WW;
-  wide_gram_blocks_kernel<<<(unsigned)nblk, 256, 0, stream>>>(X, m, n, ld, p.Gb);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  wide_init_kernel<<<256, 256, 0, stream>>>(a_in, warm, p.a64, a_tmp, n);
-  wide_ynorm_kernel<<<1, 256, 0, stream>>>(y, m, p.ysq);
-  wide_residual_kernel<<<(unsigned)((m + 7) / 8), 256, 0, stream>>>(X, m, n, ld, y, a_tmp, p.e);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(wide_sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           cfg.smem_bytes);
+namespace {
+cudaError_t launch_sweep_cluster(const WideConfig& cfg, const CUtensorMap* tmap, WideParams p,
+                                 cudaStream_t stream) {
+  cudaError_t e = cudaFuncSetAttribute(wide_sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       cfg.smem_bytes);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(wide_sweep_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   if (e != cudaSuccess) return e;
@@ -524,8 +563,42 @@ cudaError_t launch_wide(const float* X, int64_t m, int64_t n, int64_t ld, const 
   attr[0].val.clusterDim.z = 1;
   lc.attrs = attr;
   lc.numAttrs = 1;
-  e = cudaLaunchKernelEx(&lc, wide_sweep_kernel, *tmap, p);
+  return cudaLaunchKernelEx(&lc, wide_sweep_kernel, *tmap, p);
+}
+}  // namespace
+
+cudaError_t launch_wide(const float* X, int64_t m, int64_t n, int64_t ld, const WideConfig& cfg,
+                        const CUtensorMap* tmap, WideParams p, const float* y, const float* a_in,
+                        int warm, float* a_tmp, cudaStream_t stream) {
+  const int64_t nblk = (n + WW - 1) / WW;
+  wide_gram_blocks_kernel<<<(unsigned)nblk, 256, 0, stream>>>(X, m, n, ld, p.Gb);
+  cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  wide_init_kernel<<<256, 256, 0, stream>>>(a_in, warm, p.a64, a_tmp, n);
+  wide_ynorm_kernel<<<1, 256, 0, stream>>>(y, m, p.ysq);
+  wide_residual_kernel<<<(unsigned)((m + 7) / 8), 256, 0, stream>>>(X, m, n, ld, y, a_tmp, p.e);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  p.continuing = 0;
+  if ((e = launch_sweep_cluster(cfg, tmap, p, stream)) != cudaSuccess) return e;
+  wide_finish_kernel<<<256, 256, 0, stream>>>(p.a64, p.a_out, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_wide_confirm(const float* X, int64_t m, int64_t n, int64_t ld, const float* y,
+                                const float* a, float* e, double* r2, double* sum, cudaStream_t stream) {
+  wide_true_residual_kernel<<<(unsigned)((m + 7) / 8), 256, 0, stream>>>(X, m, n, ld, y, a, e, r2);
+  wide_sum_kernel<<<1, 256, 0, stream>>>(r2, m, sum);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_wide_continue(int64_t n, const WideConfig& cfg, const CUtensorMap* tmap,
+                                 WideParams p, float* a_tmp, cudaStream_t stream) {
+  // a64 <- the float32 coefficients the residual p.e was recomputed for
+  wide_init_kernel<<<256, 256, 0, stream>>>(p.a_out, 1, p.a64, a_tmp, n);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  p.continuing = 1;
+  if ((e = launch_sweep_cluster(cfg, tmap, p, stream)) != cudaSuccess) return e;
   wide_finish_kernel<<<256, 256, 0, stream>>>(p.a64, p.a_out, n);
   return cudaGetLastError();
 }
