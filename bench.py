@@ -9,8 +9,15 @@ residual norm falls below 1e-7, inputs already resident in HBM.
 
 Prints one JSON line.  value = algorithmic HBM bytes of a solve / time per
 solve (GB/s; X is 1.02 GB, larger than L2, so no flush is needed between
-steps).  Under torchrun every rank solves its own system (independent
-replicas, weak scaling); rank 0 prints.
+steps).  Algorithmic bytes (the method's, not the implementation's): each
+sweep reads X once (elem·m·n) and, while the residual e lives in HBM, reads
+and writes it (8m); the set-up reads X and y once.  Passes a kernel makes
+beyond that (a true-residual confirmation) are not counted.  Under torchrun
+every rank solves its own system (independent replicas, weak scaling); rank 0
+prints.  The other workloads (wide, square, bfloat16 precision mode, batched
++ learned warm start) follow in the same line, each with its CPU oracle
+baseline (all host cores and one core) and the float64 oracle's check of the
+GPU result.
 """
 from __future__ import annotations
 
@@ -43,13 +50,38 @@ def peaks():
     return FALLBACK_HBM_GBS, "fallback"
 
 
-def algorithmic_bytes(m, n, esz, passes):
-    """Set-up reads X once; each streaming pass reads X once and reads+writes e."""
-    return esz * m * n * (passes + 1) + passes * 8 * m + 4 * m
+def sweep_bytes(m, n, esz, sweeps, e_in_hbm=True):
+    """Algorithmic bytes of `sweeps` sweeps: X once per sweep, plus the read and
+    write of e (8m) when e is not kept on chip."""
+    return sweeps * (esz * m * n + (8 * m if e_in_hbm else 0))
 
 
-def sweep_kernel_bytes(m, n, esz, passes):
-    return passes * (esz * m * n + 8 * m)
+def setup_bytes(m, n, esz):
+    """The set-up's read of X (Gram matrix, X^T y) and of y."""
+    return esz * m * n + 4 * m
+
+
+def solve_bytes(m, n, esz, sweeps, e_in_hbm=True):
+    return setup_bytes(m, n, esz) + sweep_bytes(m, n, esz, sweeps, e_in_hbm)
+
+
+def cpu_info():
+    """(logical cores, CPU model) of this host."""
+    model = ""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.split(":")[0].strip() in ("Model name", "Model"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if not model and os.path.exists("/proc/cpuinfo"):
+        for ln in open("/proc/cpuinfo"):
+            if ln.lower().startswith("model name"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    return os.cpu_count() or 1, model
 
 
 class ClockSampler:
@@ -171,57 +203,123 @@ def job_value(bytes_per_rank, world, ms):
     return world * bytes_per_rank / (ms * 1e-3) / 1e9
 
 
+def oracle_leg(s, stop, tol, max_sweeps, threads, sweeps_cap=None):
+    """The CPU oracle's threaded Algorithm 1 (column order sequential, row loops
+    over `threads` threads) on system s; sweeps_cap bounds the sweeps timed
+    (the time is then extrapolated by the caller).  Returns (result, seconds,
+    threads used)."""
+    import oracle
+    ms = max_sweeps if sweeps_cap is None else min(max_sweeps, sweeps_cap)
+    t = time.perf_counter()
+    r, used = oracle.solve_mt(s.X, s.y, m=s.m, n=s.n, layout=s.layout, dtype=s.dtype, tol=tol,
+                              max_sweeps=ms, stop=stop if sweeps_cap is None else "none",
+                              threads=threads)
+    return r, time.perf_counter() - t, used
+
+
+def cpu_baseline(s, esz, stop, tol, max_sweeps, e_in_hbm=True, one_core_sweeps=None, what=""):
+    """The oracle timed on this host's cores: on min(nproc, m / 8192) threads to
+    the stopping rule (every column step synchronises the threads, so on
+    shorter columns more threads only add barrier time), and on one core (to
+    the rule, or one_core_sweeps sweeps extrapolated to the threaded run's
+    sweep count).  value: GB/s on the same algorithmic bytes as the GPU line."""
+    nproc, model = cpu_info()
+    threads = max(1, min(nproc, s.m // 8192))
+    r_all, t_all, used = oracle_leg(s, stop, tol, max_sweeps, threads)
+    nb = solve_bytes(s.m, s.n, esz, r_all.sweeps, e_in_hbm)
+    out = {"value": nb / t_all / 1e9, "unit": "GB/s", "cores": used, "kind": "oracle",
+           "ms_to_tol": t_all * 1e3, "sweeps": int(r_all.sweeps), "status": r_all.status,
+           "nproc": nproc, "cpu_model": model,
+           "threads_rule": "min(nproc, m // 8192): one barrier per column step"}
+    if used == 1:
+        out["one_core"] = {"value": out["value"], "ms_to_tol": out["ms_to_tol"],
+                           "sweeps": int(r_all.sweeps), "timed": "the same run (1 thread)"}
+        out["sample"] = f"full solve of {what} to {stop}<{tol} on 1 thread"
+    elif one_core_sweeps is None:
+        r1, t1, _ = oracle_leg(s, stop, tol, max_sweeps, 1)
+        out["one_core"] = {"value": nb / t1 / 1e9, "ms_to_tol": t1 * 1e3, "sweeps": int(r1.sweeps),
+                           "timed": "full solve"}
+        out["sample"] = f"full solve of {what} to {stop}<{tol} on {used} threads and on 1"
+    else:
+        k = max(1, min(one_core_sweeps, max(1, r_all.sweeps)))
+        _, t1, _ = oracle_leg(s, stop, tol, max_sweeps, 1, sweeps_cap=k)
+        per_sweep = t1 / k  # the set-up (d, e) is inside; a slight overestimate per sweep
+        t1x = per_sweep * max(1, r_all.sweeps)
+        out["one_core"] = {"value": nb / t1x / 1e9, "ms_to_tol": t1x * 1e3,
+                           "timed": f"{k} sweep(s), extrapolated to {r_all.sweeps}"}
+        out["sample"] = (f"{what}: full solve on {used} threads; on 1 thread {k} sweep(s) timed "
+                         f"and extrapolated to the threaded run's {r_all.sweeps} sweeps")
+    return out, r_all
+
+
+def oracle_check(s, a_gpu, gpu_sweeps, gpu_rel_res, r_oracle=None):
+    """The float64 oracle's view of a GPU result: the residual y - X·a of the
+    returned coefficients, and the coefficient error against the oracle's
+    iterate when both made the same number of sweeps."""
+    import oracle
+    a = np.asarray(a_gpu, dtype=np.float64)
+    _, nrm = oracle.residual(s.X, s.y, a, m=s.m, n=s.n, layout=s.layout, dtype=s.dtype)
+    ny = float(np.linalg.norm(s.y.astype(np.float64)))
+    out = {"true_rel_res": nrm / ny if ny > 0 else nrm, "gpu_reported_rel_res": float(gpu_rel_res),
+           "gpu_sweeps": int(gpu_sweeps)}
+    if r_oracle is not None:
+        out["oracle_sweeps"] = int(r_oracle.sweeps)
+        out["oracle_rel_res"] = float(r_oracle.rel_res)
+        if int(r_oracle.sweeps) == int(gpu_sweeps):
+            out["coef_rel_err_equal_sweeps"] = float(np.linalg.norm(a - r_oracle.a) /
+                                                     max(np.linalg.norm(r_oracle.a), 1e-300))
+    return out
+
+
+def roofline_block(bytes_, ms, peak, peak_kind, kernel, traffic=None):
+    ach = bytes_ / (ms * 1e-3) / 1e9
+    return {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+            "peak_kind": peak_kind, "kernel": kernel, "traffic": traffic, "kernel_ms": ms,
+            "algorithmic_bytes": bytes_}
+
+
 def run_reference(args, rank, world):
-    """The oracle (float64 CPU Algorithm 1) on the same workload, on host cores."""
+    """The reference arm: the oracle (float64 CPU Algorithm 1, its row loops on
+    every host core) on the benchmark workload, one full solve per step."""
     if rank != 0:
         return
-    import oracle
+    import oracle  # noqa: F401
     from paper_2104_12570_gb300 import synth
     s = synth.workload(WORKLOAD, seed=0)
-    times = []
-    res = None
+    nproc, model = cpu_info()
+    times, res, used = [], None, 1
     for i in range(args.warmup + args.steps):
-        t = time.perf_counter()
-        res = oracle.solve_system(s, tol=TOL, max_sweeps=MAX_SWEEPS, stop=STOP)
-        dt = time.perf_counter() - t
+        res, dt, used = oracle_leg(s, STOP, TOL, MAX_SWEEPS, nproc)
         if i >= args.warmup:
             times.append(dt)
     sec = sum(times) / len(times)
-    nbytes = algorithmic_bytes(s.m, s.n, 4, res.sweeps + 1)
-    val = nbytes / sec / 1e9
+    val = solve_bytes(s.m, s.n, 4, res.sweeps) / sec / 1e9
     out = {"impl": "reference", "metric": METRIC, "value": val, "unit": "GB/s",
            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": WORKLOAD, "m": s.m, "n": s.n, "stop": f"{STOP}<{TOL}",
                       "sweeps": res.sweeps},
-           "cpu_baseline": {"value": val, "unit": "GB/s", "cores": 1, "kind": "oracle",
+           "cpu_baseline": {"value": val, "unit": "GB/s", "cores": used, "kind": "oracle",
+                            "nproc": nproc, "cpu_model": model,
                             "sample": f"full solve of {WORKLOAD} ({res.sweeps} sweeps) per step"},
            "e2e": {"value": val, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
 
-def cpu_baseline_leg(s, budget_s=30.0):
-    import oracle
-    t = time.perf_counter()
-    r = oracle.solve_system(s, tol=TOL, max_sweeps=MAX_SWEEPS, stop=STOP)
-    dt = time.perf_counter() - t
-    nbytes = algorithmic_bytes(s.m, s.n, 4, r.sweeps + 1)
-    return {"value": nbytes / dt / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
-            "sample": f"one full solve of {WORKLOAD} ({r.sweeps} sweeps, {dt:.1f} s)",
-            "seconds": dt}
-
-
-def precision_comparison(hp, synth, ctx, dev, steps=5, warmup=3):
+def precision_comparison(hp, synth, ctx, dev, peak, peak_kind, steps=5, warmup=3, cpu=True):
     """Time to relative residual 1e-6 on the 4,000,000 x 512 consistent system: X
-    stored bfloat16 (float32 accumulation, true-residual refresh every 4 passes)
-    against the same values stored float32 (plain float32 sweep)."""
+    stored bfloat16 (float32 accumulation, true-residual refresh every 4 sweeps)
+    against the same values stored float32 (plain float32 sweep).  The stop is
+    confirmed on y - X·a of the returned float32 coefficients (a Dot2 pass)."""
     import torch
     s = synth.workload("tall_4Mx512_bf16", seed=0)
     Xb = torch.from_numpy(s.X.view(np.int16)).view(torch.bfloat16).to(dev).T
     y = torch.from_numpy(s.y).to(dev)
     out = {"workload": "tall_4Mx512 (X iid N(0,1) rounded to bfloat16, consistent)",
-           "stop": "rel_res<=1e-6"}
+           "stop": "rel_res<=1e-6 (confirmed on the true residual)",
+           "bytes": "set-up: elem·m·n + 4m; per sweep: elem·m·n + 8m (e in HBM)"}
+    results = {}
     for name, X, kw in (("bf16_refresh4", Xb, dict(refresh_every=4)),
                         ("f32_plain", None, {})):
         if X is None:
@@ -238,18 +336,25 @@ def precision_comparison(hp, synth, ctx, dev, steps=5, warmup=3):
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / steps
         esz = 2 if X.dtype == torch.bfloat16 else 4
-        nbytes = algorithmic_bytes(s.m, s.n, esz, r.timing["passes"])
-        out[name] = {"ms_to_tol": ms, "GBps": nbytes / (ms * 1e-3) / 1e9, "sweeps": int(r.sweeps),
-                     "rel_res": float(r.rel_res), "setup_ms": float(r.timing["setup_ms"]),
-                     "sweep_kernel_ms": float(r.timing["sweep_ms"]),
-                     "sweep_kernel_GBps": sweep_kernel_bytes(s.m, s.n, esz, r.timing["passes"])
-                     / (r.timing["sweep_ms"] * 1e-3) / 1e9}
+        sw = int(r.sweeps)
+        out[name] = {"ms_to_tol": ms, "GBps": solve_bytes(s.m, s.n, esz, sw) / (ms * 1e-3) / 1e9,
+                     "sweeps": sw, "passes": int(r.timing["passes"]), "rel_res": float(r.rel_res),
+                     "setup_ms": float(r.timing["setup_ms"]),
+                     "roofline": roofline_block(sweep_bytes(s.m, s.n, esz, sw), float(r.timing["sweep_ms"]),
+                                                peak, peak_kind, "tall_sweep_kernel")}
+        out[name]["frac_of_peak"] = out[name]["GBps"] / peak
+        results[name] = r.a.cpu().numpy()
         del X
     out["bf16_speedup_time_to_tol"] = out["f32_plain"]["ms_to_tol"] / out["bf16_refresh4"]["ms_to_tol"]
+    if cpu:
+        cb, ro = cpu_baseline(s, 2, "rel_res", 1e-6, 100, one_core_sweeps=1, what="tall_4Mx512_bf16")
+        out["cpu_baseline"] = cb
+        for name, a in results.items():
+            out[name]["oracle_check"] = oracle_check(s, a, out[name]["sweeps"], out[name]["rel_res"], ro)
     return out
 
 
-def batched_comparison(hp, synth, ctx):
+def batched_comparison(hp, synth, ctx, peak, peak_kind, cpu=True):
     """The batched + learned-warm-start workload: 4096 RBF systems (m log-uniform
     in [256, 16384], n uniform in [8, 256]) swept to a relative change of ||e||
     below 1e-6 (at most 10^4 sweeps) in one persistent graph-captured launch,
@@ -266,6 +371,7 @@ def batched_comparison(hp, synth, ctx):
     out = {"workload": "rbf_batch_4096 (RBF features of U[0,1]^4 inputs, width 0.3; "
                        "y = f_theta(x))",
            "stop": f"{ws.STOP}<{ws.TOL}, max_sweeps {ws.MAX_SWEEPS}",
+           "bytes": "per system: set-up 4·m·n + 4m, per sweep 4·m·n (e in shared memory)",
            "x_bytes": int((m * n * 4).sum()),
            "autotune_ms_per_10_sweeps": {f"cluster{k}_panel{p}": v for (k, p), v in tms.items()},
            "cluster": best[0], "panel": best[1]}
@@ -274,9 +380,91 @@ def batched_comparison(hp, synth, ctx):
         return out
     mlp = ws.load(ctx)
     ev = ws.evaluate(ctx, fam, mlp, m, n, th, reps=1, cluster=best)
+    # the same comparison on 256 systems of the batch (seed 4) with a 10^5-sweep
+    # cap, so that the cap clips (almost) no system in either arm; 8 CTAs per
+    # system, since the longest single system bounds the launch
+    g = np.random.default_rng(4)
+    sub = np.sort(g.choice(len(m), size=256, replace=False))
+    ev_unclipped = ws.evaluate(ctx, fam, mlp, m[sub], n[sub], th[sub], reps=1, cluster=(8, 0),
+                               max_sweeps=100_000)
     mlp.close()
+    for k in ("cold", "warm"):
+        if isinstance(ev.get(k), dict):
+            ev[k]["frac_of_peak"] = ev[k]["GBps"] / peak
     out.update(ev)
+    out["subsample_256_cap_1e5"] = ev_unclipped
+    if cpu:
+        out["cpu_baseline"], out["oracle_check"] = batched_cpu_and_check(
+            hp, synth, ctx, ws, fam, m, n, th, ev["cold"]["elem_sweeps"])
     return out
+
+
+def batched_cpu_and_check(hp, synth, ctx, ws, fam, m, n, th, gpu_elem_sweeps, count=256, sweeps=20):
+    """CPU baseline and parity sample of the batched workload: `count` systems
+    drawn from the batch (seed 3), `sweeps` sweeps each (stop rule none), by the
+    oracle on every host core (one system per thread) and on one core (a
+    quarter of them); the throughput in element-sweeps (m·n per sweep) gives
+    the CPU time of the GPU's cold workload.  The same systems swept on the GPU
+    give the coefficient error against the oracle at equal sweeps, per system
+    against its bound max(1e-5, 8·cond(X)·2^-24)."""
+    import torch
+    from concurrent.futures import ThreadPoolExecutor
+    import oracle
+    nproc, model = cpu_info()
+    g = np.random.default_rng(3)
+    idx = np.sort(g.choice(len(m), size=count, replace=False))
+    syst = [synth.rbf_system(fam, int(m[i]), int(n[i]), th[i]) for i in idx]
+    elem = float(sum(s.m * s.n for s in syst)) * sweeps
+
+    def one(s):
+        r, _ = oracle.solve_mt(s.X, s.y, m=s.m, n=s.n, tol=0, max_sweeps=sweeps, stop="none", threads=1)
+        return r
+
+    t = time.perf_counter()
+    with ThreadPoolExecutor(nproc) as ex:
+        ores = list(ex.map(one, syst))
+    t_all = time.perf_counter() - t
+    q = syst[: max(1, count // 4)]
+    t = time.perf_counter()
+    for s in q:
+        one(s)
+    t_one = time.perf_counter() - t
+    elem_one = float(sum(s.m * s.n for s in q)) * sweeps
+    rate_all, rate_one = elem / t_all, elem_one / t_one
+    cold_s_all, cold_s_one = gpu_elem_sweeps / rate_all, gpu_elem_sweeps / rate_one
+    xbytes_per_elem = 4.0
+    cb = {"value": len(m) / cold_s_all, "unit": "systems/s", "cores": nproc, "kind": "oracle",
+          "nproc": nproc, "cpu_model": model,
+          "GBps": rate_all * xbytes_per_elem / 1e9,
+          "s_for_the_cold_batch": cold_s_all,
+          "one_core": {"value": len(m) / cold_s_one, "s_for_the_cold_batch": cold_s_one,
+                       "GBps": rate_one * xbytes_per_elem / 1e9},
+          "sample": (f"{count} systems of the batch x {sweeps} sweeps on {nproc} threads (one "
+                     f"system per thread), {len(q)} of them on 1 thread; time of the GPU's cold "
+                     "workload (sum of sweeps x m x n) at that element-sweep rate")}
+    # the same systems on the GPU, equal sweeps
+    keep, sysd = synth.device_rbf_batch(fam, m[idx], n[idx], th[idx], "cuda")
+    a = [torch.zeros(int(k), dtype=torch.float32, device="cuda") for k in n[idx]]
+    b = hp.Batch(ctx, [(X, y, ai, False) for (X, y), ai in zip(sysd, a)], tol=0, max_sweeps=sweeps,
+                 stop="none")
+    b.run()
+    ratios, errs = [], []
+    for s, ai, o in zip(syst, a, ores):
+        err = float(np.linalg.norm(ai.cpu().numpy().astype(np.float64) - o.a) /
+                    max(np.linalg.norm(o.a), 1e-300))
+        Xd = s.dense_f64()
+        ev = np.linalg.eigvalsh(Xd.T @ Xd)  # cond(X) = sqrt(cond(X^T X))
+        kappa = float(np.sqrt(ev[-1] / max(ev[0], ev[-1] * 1e-300)))
+        bound = max(1e-5, 8 * kappa * 2.0 ** -24)
+        errs.append(err)
+        ratios.append(err / bound)
+    b.close()
+    chk = {"systems": count, "sweeps": sweeps, "coef_rel_err_median": float(np.median(errs)),
+           "coef_rel_err_max": float(np.max(errs)),
+           "max_err_over_bound": float(np.max(ratios)),
+           "within_1e-5": int(np.sum(np.array(errs) <= 1e-5)),
+           "bound": "max(1e-5, 8·cond(X)·2^-24) per system"}
+    return cb, chk
 
 
 def profile_small(hp, synth):
@@ -334,7 +522,8 @@ def next_algorithms(hp, synth, ctx, X, y, s, reps=3):
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / reps
         out[name] = {"ms_to_tol": ms, "sweeps": int(r.sweeps), "rel_res": float(r.rel_res),
-                     "sweep_kernel_GBps": sweep_kernel_bytes(s.m, s.n, esz, r.timing["passes"])
+                     "GBps": solve_bytes(s.m, s.n, esz, int(r.sweeps)) / (ms * 1e-3) / 1e9,
+                     "sweep_kernel_GBps": sweep_bytes(s.m, s.n, esz, int(r.sweeps))
                      / (r.timing["sweep_ms"] * 1e-3) / 1e9}
     F = 32
     ctx.select(X, y, F)
@@ -357,68 +546,57 @@ def next_algorithms(hp, synth, ctx, X, y, s, reps=3):
     out["alg3_select_32_then_swaps_8"] = {
         "ms": e0.elapsed_time(e1) / reps, "swaps_made": int((swaps[:, 0] >= 0).sum()),
         "passes": int(rs.timing["passes"]), "rel_res_after": float(rs.rel_res)}
-    out["alg3_select_32"] = {"ms": ms, "ms_per_step": r.timing["sweep_ms"] / (F + 1),
-                             "sweep_kernel_GBps": sweep_kernel_bytes(s.m, s.n, esz, r.timing["passes"])
+    out["alg3_select_32"] = {"ms": ms, "ms_per_step": r.timing["sweep_ms"] / max(1, r.timing["passes"]),
+                             "sweep_kernel_GBps": sweep_bytes(s.m, s.n, esz, r.timing["passes"])
                              / (r.timing["sweep_ms"] * 1e-3) / 1e9,
                              "rel_res_after": float(r.rel_res), "first_selected": sel[:8].tolist()}
     return out
 
 
-def wide_comparison(hp, synth, ctx, dev, reps=2):
-    """The wide workload: 2,000 x 200,000 float32 row-major consistent system
-    (infinitely many solutions) swept to relative residual 1e-6 by the cluster
-    kernel (the transposed path)."""
+def rowmajor_line(hp, synth, ctx, dev, name, desc, peak, peak_kind, reps=3, flush=False, cpu=True):
+    """A row-major workload (the wide cluster kernel) solved to relative residual
+    1e-6, the stop confirmed on the true residual of the returned a.  Bytes: the
+    set-up reads X (the per-block Gram and the initial residual) and each sweep
+    reads X once; e stays in shared memory.  With flush, a buffer larger than L2
+    is written before each timed solve (X is smaller than L2)."""
     import torch
-    s = synth.workload("wide_2000x200k_f32", seed=0)
+    s = synth.workload(name, seed=0)
     X = torch.from_numpy(s.X).to(dev)  # (m, n) row-major
     y = torch.from_numpy(s.y).to(dev)
+    buf = torch.empty(256 << 20, dtype=torch.uint8, device=dev) if flush else None
     r = ctx.solve(X, y, tol=1e-6, max_sweeps=200, stop="rel_res")
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
+    times = []
     for _ in range(reps):
-        r = ctx.solve(X, y, tol=1e-6, max_sweeps=200, stop="rel_res")
-    e1.record()
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / reps
-    xb = 4 * s.m * s.n
-    return {"workload": "wide_2000x200k_f32 (row-major, consistent)", "stop": "rel_res<=1e-6",
-            "status": r.status, "sweeps": int(r.sweeps), "rel_res": float(r.rel_res), "ms_to_tol": ms,
-            "sweep_kernel_ms": float(r.timing["sweep_ms"]),
-            "GBps": xb * (r.timing["passes"] + 1) / (ms * 1e-3) / 1e9,
-            "ms_per_sweep": float(r.timing["sweep_ms"]) / max(1, r.timing["passes"])}
-
-
-def square_workload(hp, synth, ctx, dev, reps=3):
-    """The square workload: 4096 x 4096 float32 row-major consistent system
-    (I + 0.5·Z/sqrt(n), cond ~ 4.7) swept to relative residual 1e-6 by the
-    cluster kernel.  X (67 MB) fits in L2, so each repetition starts after a
-    write of a buffer larger than L2."""
-    import torch
-    s = synth.workload("square_4096_f32", seed=0)
-    X = torch.from_numpy(s.X).to(dev)
-    y = torch.from_numpy(s.y).to(dev)
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    r = ctx.solve(X, y, tol=1e-6, max_sweeps=200, stop="rel_res")
-    ms = []
-    for _ in range(reps):
-        flush.fill_(1)
+        if buf is not None:
+            buf.fill_(1)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
         r = ctx.solve(X, y, tol=1e-6, max_sweeps=200, stop="rel_res")
         e1.record()
         torch.cuda.synchronize()
-        ms.append(e0.elapsed_time(e1))
-    ms = sorted(ms)[len(ms) // 2]
-    xb = 4 * s.m * s.n
-    return {"workload": "square_4096_f32 (row-major, consistent, I + 0.5·Z/64)",
-            "stop": "rel_res<=1e-6", "l2": "flushed before each solve (256 MB write)",
-            "status": r.status, "sweeps": int(r.sweeps), "rel_res": float(r.rel_res),
-            "ms_to_tol": ms, "sweep_kernel_ms": float(r.timing["sweep_ms"]),
-            "setup_ms": float(r.timing["setup_ms"]),
-            "GBps": xb * (r.timing["passes"] + 1) / (ms * 1e-3) / 1e9,
-            "us_per_sweep": 1e3 * float(r.timing["sweep_ms"]) / max(1, r.timing["passes"])}
+        times.append(e0.elapsed_time(e1))
+    ms = sorted(times)[len(times) // 2]
+    sw = int(r.sweeps)
+    nb = solve_bytes(s.m, s.n, 4, sw, e_in_hbm=False)
+    out = {"workload": desc, "stop": "rel_res<=1e-6 (confirmed on the true residual)",
+           "l2": "flushed before each solve (256 MB write)" if flush else "X larger than L2",
+           "status": r.status, "sweeps": sw, "rel_res": float(r.rel_res), "ms_to_tol": ms,
+           "ms_per_sweep": float(r.timing["sweep_ms"]) / max(1, sw),
+           "GBps": nb / (ms * 1e-3) / 1e9, "frac_of_peak": nb / (ms * 1e-3) / 1e9 / peak,
+           "bytes": "set-up 4·m·n + 4m, per sweep 4·m·n (e in shared memory)",
+           "roofline": roofline_block(sweep_bytes(s.m, s.n, 4, sw, e_in_hbm=False), ms, peak,
+                                      peak_kind, "wide_sweep_kernel (set-up and confirmation inside)")}
+    a_gpu = r.a.cpu().numpy()
+    del X
+    if cpu:
+        cb, ro = cpu_baseline(s, 4, "rel_res", 1e-6, 200, e_in_hbm=False, what=name)
+        out["cpu_baseline"] = cb
+        import oracle
+        o = oracle.solve_system(s, tol=0, max_sweeps=sw, stop="none") if ro.sweeps != sw else ro
+        out["oracle_check"] = oracle_check(s, a_gpu, sw, r.rel_res, o)
+        out["oracle_check"]["oracle_sweeps_to_rule"] = int(ro.sweeps)
+    return out
 
 
 def profile_wide(hp, synth, cols, blocks=512):
@@ -557,7 +735,8 @@ def main():
     setup_ms = float(np.mean([t["setup_ms"] for t in times]))
     ms = max_over_ranks(ms, world, dev)
     p_mean = float(np.mean(passes))
-    nbytes = algorithmic_bytes(s.m, s.n, esz, p_mean)
+    sw_mean = float(np.mean(got["sweeps"]))
+    nbytes = solve_bytes(s.m, s.n, esz, sw_mean)
     value = job_value(nbytes, world, ms)
 
     # end to end through the C ABI from pinned host memory
@@ -572,15 +751,25 @@ def main():
         for _ in range(e2e_steps):
             rh = ctx.solve_host(Xh, yh, tol=TOL, max_sweeps=MAX_SWEEPS, stop=STOP)
         e2e_s = (time.perf_counter() - t) / e2e_steps
-        e2e_val = world * algorithmic_bytes(s.m, s.n, esz, rh.timing["passes"]) / e2e_s / 1e9
+        e2e_val = world * solve_bytes(s.m, s.n, esz, int(rh.sweeps)) / e2e_s / 1e9
+        # the host link alone: one copy of the same pinned X to the device
+        Xd_probe = torch.empty(s.X.shape, dtype=torch.float32, device=dev)
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c0.record()
+        Xd_probe.copy_(Xh.T, non_blocking=True)
+        c1.record()
+        torch.cuda.synchronize()
+        h2d_ms = c0.elapsed_time(c1)
+        del Xd_probe
         e2e = {"value": e2e_val, "unit": "GB/s", "h2d_bytes_per_step": int(s.X.nbytes + s.y.nbytes),
                "d2h_bytes_per_step": int(4 * s.n + 8 * (rh.sweeps + 1) + 48),
-               "ms_per_step": e2e_s * 1e3}
+               "ms_per_step": e2e_s * 1e3, "h2d_copy_ms": h2d_ms,
+               "h2d_GBps": s.X.nbytes / (h2d_ms * 1e-3) / 1e9}
 
     if rank == 0:
         peak, peak_kind = peaks()
         k_ms = float(np.mean(sweep_ms))
-        k_bytes = sweep_kernel_bytes(s.m, s.n, esz, p_mean)
+        k_bytes = sweep_bytes(s.m, s.n, esz, sw_mean)
         achieved = k_bytes / (k_ms * 1e-3) / 1e9
         tr = traffic_from_profile(kernel_sha())
         out = {
@@ -591,6 +780,7 @@ def main():
             "config": {"workload": WORKLOAD, "m": s.m, "n": s.n, "layout": "col-major",
                        "stop": f"{STOP}<{TOL}", "sweeps": sweeps_timed,
                        "passes_per_solve": p_mean, "l2": "inputs larger than L2 (1.02 GB X)",
+                       "bytes": "set-up 4·m·n + 4m, per sweep 4·m·n + 8m (e in HBM)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_kind": peak_kind,
@@ -601,20 +791,27 @@ def main():
             "gpu_launches": int(launches),
             "clocks": clk.summary(),
         }
-        if not args.no_cpu_baseline:
-            out["cpu_baseline"] = cpu_baseline_leg(s)
+        cpu = not args.no_cpu_baseline
+        if cpu:
+            out["cpu_baseline"], ro = cpu_baseline(s, esz, STOP, TOL, MAX_SWEEPS, what=WORKLOAD)
+            out["oracle_check"] = oracle_check(s, a.cpu().numpy(), sweeps_timed,
+                                               float(got["rel_res"][-1]), ro)
         if not args.no_next and not args.rows:
             out["next_algorithms"] = next_algorithms(hp, synth, ctx, X, y, s)
         if not args.no_wide and not args.rows:
-            out["wide"] = wide_comparison(hp, synth, ctx, dev)
-            out["square"] = square_workload(hp, synth, ctx, dev)
+            out["wide"] = rowmajor_line(hp, synth, ctx, dev, "wide_2000x200k_f32",
+                                        "wide_2000x200k_f32 (row-major, consistent)", peak,
+                                        peak_kind, reps=3, cpu=cpu)
+            out["square"] = rowmajor_line(hp, synth, ctx, dev, "square_4096_f32",
+                                          "square_4096_f32 (row-major, consistent, I + 0.5·Z/64)",
+                                          peak, peak_kind, reps=3, flush=True, cpu=cpu)
         if not args.no_compare and not args.rows:
             del X
             torch.cuda.empty_cache()
-            out["precision_mode"] = precision_comparison(hp, synth, ctx, dev)
+            out["precision_mode"] = precision_comparison(hp, synth, ctx, dev, peak, peak_kind, cpu=cpu)
         if not args.no_batched and not args.rows:
             torch.cuda.empty_cache()
-            out["batched"] = batched_comparison(hp, synth, ctx)
+            out["batched"] = batched_comparison(hp, synth, ctx, peak, peak_kind, cpu=cpu)
         print(json.dumps(out), flush=True)
     ctx.close()
     if world > 1:

@@ -261,9 +261,10 @@ __device__ void stream_pass(const float* __restrict__ X, int64_t ld, int64_t r0,
   // lane partials of h -> one value per (row group, column), summed in float64
 #pragma unroll
   for (int j = 0; j < CPW; ++j) {
-    double s = (double)h[j];
+    float sf = h[j];
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(FULL_MASK, s, off);
+    for (int off = 16; off > 0; off >>= 1) sf += __shfl_xor_sync(FULL_MASK, sf, off);
+    const double s = (double)sf;
     const int col = wc * CPW + j;
     if (lane == 0 && col < n) hred[wr * BMAXN + col] = s;
   }

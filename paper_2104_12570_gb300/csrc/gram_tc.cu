@@ -44,9 +44,22 @@ constexpr int GT_THREADS = 192;  // 6 warps: producer, MMA issuer, 4 workers
 constexpr int GT_WORK_WARP0 = 2;
 constexpr int GT_WORKERS = 128;
 
+// 1-D tiled TMA load of `box` elements of `map` from coordinate c0 (rows past
+// the tensor's end read as zero), completing on `bar`.
+__device__ __forceinline__ void tma_load_1d(void* dst, const CUtensorMap* map, uint64_t* bar, int32_t c0) {
+  asm volatile(
+      "cp.async.bulk.tensor.1d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2}], [%3];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(smem_u32(bar))
+      : "memory");
+}
+
+constexpr int YSTAGE_BYTES = 256;  // one K block of y (64 floats at most)
+
 template <bool TF32>
 __global__ void __launch_bounds__(GT_THREADS, 1)
-    gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const GramTCParams p) {
+    gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap ymap,
+                   const GramTCParams p) {
   constexpr int KB = TF32 ? 32 : 64;         // rows of X per 128-byte K block
   constexpr uint32_t FMT = TF32 ? 2u : 1u;
   extern __shared__ unsigned char smem_raw[];
@@ -58,7 +71,9 @@ __global__ void __launch_bounds__(GT_THREADS, 1)
   const int stage_raw = nload * ATOM_BYTES;
   const int stage_bytes = stage_raw * (TF32 ? 2 : 1);
   const int nst = p.nstages;
-  uint64_t* full = reinterpret_cast<uint64_t*>(base + (size_t)nst * stage_bytes);
+  // y's K block of each stage (by TMA with the X tiles when p.y_tma)
+  float* ystage = reinterpret_cast<float*>(base + (size_t)nst * stage_bytes);
+  uint64_t* full = reinterpret_cast<uint64_t*>(base + (size_t)nst * stage_bytes + nst * YSTAGE_BYTES);
   uint64_t* ready = full + 8;
   uint64_t* empty = ready + 8;
   uint64_t* done = empty + 8;
@@ -118,10 +133,13 @@ __global__ void __launch_bounds__(GT_THREADS, 1)
         const int s = (int)(kb % nst);
         if (kb >= nst && !wait(&empty[s], (uint32_t)(((kb / nst) - 1) & 1))) break;
         unsigned char* dst = base + (size_t)s * stage_bytes;
-        mbar_arrive_expect_tx(&full[s], (uint32_t)stage_raw);
+        mbar_arrive_expect_tx(&full[s], (uint32_t)stage_raw + (p.y_tma ? KB * 4u : 0u));
         for (int b = 0; b < nload; ++b)
           tma_load_2d(dst + b * ATOM_BYTES, &tmap, &full[s], (int32_t)(r0 + kb * KB),
                       p.grp.load_blk[g][b] * BLK);
+        if (p.y_tma)
+          tma_load_1d(reinterpret_cast<unsigned char*>(ystage) + s * YSTAGE_BYTES, &ymap, &full[s],
+                      (int32_t)(r0 + kb * KB));
       }
       // the copies issued land before the CTA may retire
       for (int64_t k = kb - nst > 0 ? kb - nst : 0; k < kb; ++k) {
@@ -207,12 +225,16 @@ __global__ void __launch_bounds__(GT_THREADS, 1)
     const int nq = 8 * nload;
     const int yoff = YR * ((wt & 7) ^ ((wt >> 3) & 7));  // first K row of the worker's chunk
     float yv[YR], yn[YR];
-    // rows r0 + kb·KB + yoff.. are a multiple of 4 (KB, yoff and the split
-    // length are): 16-byte loads when y is 16-byte aligned and the rows exist
+    // without the TMA copy of y (y not 16-byte aligned): rows r0 + kb·KB + yoff..
+    // from global memory, one K block ahead
     const bool yvec = (reinterpret_cast<uintptr_t>(p.y) & 15) == 0;
+    const bool yglob = want_y && !p.y_tma;
     auto load_y = [&](int64_t kb, float (&dst)[YR]) {
       const int64_t row0 = r0 + kb * KB + yoff;
-      if (want_y && kb < nkb && yvec && row0 + YR <= p.m) {
+      if (!yglob) {
+#pragma unroll
+        for (int r = 0; r < YR; ++r) dst[r] = 0.f;
+      } else if (kb < nkb && yvec && row0 + YR <= p.m) {
 #pragma unroll
         for (int r = 0; r < YR; r += 4) {
           const float4 t = __ldg(reinterpret_cast<const float4*>(p.y + row0 + r));
@@ -225,6 +247,10 @@ __global__ void __launch_bounds__(GT_THREADS, 1)
       }
     };
     load_y(0, yv);
+    // X^T y is needed only for the columns of this group's diagonal tiles
+    bool dsl[MAXQ / 8];
+#pragma unroll
+    for (int k = 0; k < MAXQ / 8; ++k) dsl[k] = want_y && k < nload && p.grp.diag_slot[g][k] != 0;
     auto flush = [&]() {
 #pragma unroll
       for (int q = 0; q < MAXQ; ++q) {
@@ -256,6 +282,15 @@ __global__ void __launch_bounds__(GT_THREADS, 1)
       unsigned char* st = base + (size_t)s * stage_bytes;
       uint4* raw4 = reinterpret_cast<uint4*>(st);
       uint4* lo4 = reinterpret_cast<uint4*>(st + stage_raw);
+      if (want_y && p.y_tma) {
+        const float4* ys = reinterpret_cast<const float4*>(
+            reinterpret_cast<const unsigned char*>(ystage) + s * YSTAGE_BYTES) + yoff / 4;
+#pragma unroll
+        for (int r = 0; r < YR; r += 4) {
+          const float4 t = ys[r / 4];
+          yv[r] = t.x; yv[r + 1] = t.y; yv[r + 2] = t.z; yv[r + 3] = t.w;
+        }
+      }
 #pragma unroll
       for (int r = 0; r < YR; ++r) y2 = fmaf(yv[r], yv[r], y2);
 #pragma unroll
@@ -266,7 +301,8 @@ __global__ void __launch_bounds__(GT_THREADS, 1)
             const float a0 = __uint_as_float(x.x), a1 = __uint_as_float(x.y);
             const float a2 = __uint_as_float(x.z), a3 = __uint_as_float(x.w);
             dsq[q] = fmaf(a0, a0, fmaf(a1, a1, fmaf(a2, a2, fmaf(a3, a3, dsq[q]))));
-            xy[q] = fmaf(a0, yv[0], fmaf(a1, yv[1], fmaf(a2, yv[2], fmaf(a3, yv[3], xy[q]))));
+            if (dsl[q >> 3])
+              xy[q] = fmaf(a0, yv[0], fmaf(a1, yv[1], fmaf(a2, yv[2], fmaf(a3, yv[3], xy[q]))));
             // split in place: hi over x, lo in the second half
             uint4 h, l;
             split_tf32(x, h, l);
@@ -278,7 +314,7 @@ __global__ void __launch_bounds__(GT_THREADS, 1)
             for (int h = 0; h < 4; ++h) {
               const float lo16 = __uint_as_float(w4[h] << 16), hi16 = __uint_as_float(w4[h] & 0xffff0000u);
               dsq[q] = fmaf(lo16, lo16, fmaf(hi16, hi16, dsq[q]));
-              xy[q] = fmaf(lo16, yv[2 * h], fmaf(hi16, yv[2 * h + 1], xy[q]));
+              if (dsl[q >> 3]) xy[q] = fmaf(lo16, yv[2 * h], fmaf(hi16, yv[2 * h + 1], xy[q]));
             }
           }
         }
@@ -290,8 +326,10 @@ __global__ void __launch_bounds__(GT_THREADS, 1)
         if constexpr (TF32) mbar_arrive(&ready[s]);
         else mbar_arrive(&empty[s]);
       }
+      if (yglob) {
 #pragma unroll
-      for (int r = 0; r < YR; ++r) yv[r] = yn[r];
+        for (int r = 0; r < YR; ++r) yv[r] = yn[r];
+      }
     }
     flush();
   }
@@ -492,11 +530,11 @@ bool gram_tc_plan(int dtype, int64_t m, int n, int sms, int max_smem, GramTCPlan
   gp->maxload = maxload;
   const int kb_rows = f32 ? 32 : 64;
   const int stage = maxload * ATOM_BYTES * (f32 ? 2 : 1);
-  int nst = (max_smem - 2048) / stage;
+  int nst = (max_smem - 2048) / (stage + YSTAGE_BYTES);
   if (nst > 6) nst = 6;
   if (nst < 2) return false;
   gp->nstages = nst;
-  gp->smem_bytes = nst * stage + 1024 + 256;
+  gp->smem_bytes = nst * stage + nst * YSTAGE_BYTES + 1024 + 256;
   // one CTA per SM: each CTA allocates all 512 tensor-memory columns
   if (gp->smem_bytes < max_smem / 2 + 4096) gp->smem_bytes = max_smem / 2 + 4096;
   int ksplit = sms / G.ngroups;
@@ -517,7 +555,7 @@ bool gram_tc_plan(int dtype, int64_t m, int n, int sms, int max_smem, GramTCPlan
 cudaError_t launch_gram_tc(const CUtensorMap* tmap, int dtype, int64_t m, const GramTCPlan& gp,
                            float* partial, int* err, uint64_t timeout_ns, float* G, int ldG,
                            cudaStream_t stream, int n, float* Gt, float* dvec, const float* y,
-                           double* h0, double* y2) {
+                           double* h0, double* y2, const CUtensorMap* ymap) {
   GramTCParams p{};
   p.m = m;
   p.npad = gp.npad;
@@ -534,6 +572,10 @@ cudaError_t launch_gram_tc(const CUtensorMap* tmap, int dtype, int64_t m, const 
   double* d64 = reinterpret_cast<double*>(tmp + (size_t)RED_SLICES * gp.npad * gp.npad);
   const bool with_y = y && h0 && y2;
   p.y = with_y ? y : nullptr;
+  p.y_tma = (with_y && ymap) ? 1 : 0;
+  CUtensorMap ym;
+  if (ymap) ym = *ymap;
+  else memset(&ym, 0, sizeof(ym));
   p.hpart = d64 + gp.npad;
   p.y2part = p.hpart + (size_t)gp.ksplit * gp.npad;
   dim3 grid(gp.ksplit, gp.grp.ngroups);
@@ -542,12 +584,12 @@ cudaError_t launch_gram_tc(const CUtensorMap* tmap, int dtype, int64_t m, const 
     e = cudaFuncSetAttribute(gram_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              gp.smem_bytes);
     if (e != cudaSuccess) return e;
-    gram_tc_kernel<true><<<grid, GT_THREADS, gp.smem_bytes, stream>>>(*tmap, p);
+    gram_tc_kernel<true><<<grid, GT_THREADS, gp.smem_bytes, stream>>>(*tmap, ym, p);
   } else {
     e = cudaFuncSetAttribute(gram_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              gp.smem_bytes);
     if (e != cudaSuccess) return e;
-    gram_tc_kernel<false><<<grid, GT_THREADS, gp.smem_bytes, stream>>>(*tmap, p);
+    gram_tc_kernel<false><<<grid, GT_THREADS, gp.smem_bytes, stream>>>(*tmap, ym, p);
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;

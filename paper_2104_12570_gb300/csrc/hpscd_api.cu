@@ -190,9 +190,24 @@ int run_gram(hpscd_ctx* ctx, const void* X, int dtype, int64_t m, int64_t n, int
   memset(&gmap, 0, sizeof(gmap));
   if (got_h0) *got_h0 = false;
   if (!force_simt && P.tc_ok && encode_gram_map(ctx, X, dtype, m, n, ld, &gmap)) {
+    // y's K blocks by TMA: a 1-D map of y (rows past m read as zero), boxes of
+    // one K block (32 rows for float32 X, 64 for bfloat16)
+    CUtensorMap ymap;
+    memset(&ymap, 0, sizeof(ymap));
+    bool ytma = false;
+    if (y && (reinterpret_cast<uintptr_t>(y) & 15) == 0 && m < ((int64_t)1 << 32)) {
+      cuuint64_t dims[1] = {(cuuint64_t)m};
+      cuuint64_t strides[1] = {0};
+      cuuint32_t box[1] = {(cuuint32_t)(dtype == HPSCD_F32 ? 32 : 64)};
+      cuuint32_t estr[1] = {1};
+      ytma = ctx->encode(&ymap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 1, const_cast<float*>(y), dims,
+                         strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                         CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    }
     if (launch_gram_tc(&gmap, dtype, m, P.gtc, static_cast<float*>(partial), err,
                        (uint64_t)(ctx->timeout_s * 1e9), G, ldG, ctx->stream, (int)n, Gt,
-                       dvec, y, h0, y2) != cudaSuccess) {
+                       dvec, y, h0, y2, ytma ? &ymap : nullptr) != cudaSuccess) {
       cudaGetLastError();
       return HPSCD_ERR_CUDA;
     }
@@ -213,7 +228,7 @@ int run_gram(hpscd_ctx* ctx, const void* X, int dtype, int64_t m, int64_t n, int
 // ---- wide systems: row-major X, m <= 4096 (the cluster sweep) ----
 struct WideLayout {
   size_t Gb = 0, e = 0, a64 = 0, dsw = 0, atmp = 0, ysq = 0, hist = 0, ctl = 0, r2 = 0, tsum = 0,
-         xcopy = 0, ycopy = 0, acopy = 0, total = 0;
+         rpart = 0, xcopy = 0, ycopy = 0, acopy = 0, total = 0;
 };
 
 int make_wide_plan(const hpscd_ctx* ctx, int dtype, int64_t m, int64_t n, int64_t ld,
@@ -237,6 +252,7 @@ int make_wide_plan(const hpscd_ctx* ctx, int dtype, int64_t m, int64_t n, int64_
   L->ctl = take(sizeof(GridCtl));
   L->r2 = take((size_t)m * sizeof(double));
   L->tsum = take(2 * sizeof(double));
+  L->rpart = take((size_t)m * 32 * sizeof(double));
   if (host_copies) {
     L->xcopy = take((size_t)m * ld * sizeof(float));
     L->ycopy = take((size_t)m * sizeof(float));
@@ -284,6 +300,7 @@ int solve_wide(hpscd_ctx* ctx, const void* X, int64_t m, int64_t n, int64_t ld, 
   p.max_sweeps = o->max_sweeps;
   p.stop_rule = o->stop_rule;
   p.timeout_ns = (uint64_t)(ctx->timeout_s * 1e9);
+  p.rpart = reinterpret_cast<double*>(ws + L.rpart);
   p.trace = nullptr;
   p.trace_passes = 0;
   if (ctx->trace_passes > 0 && ctx->trace_dev) {
@@ -322,7 +339,7 @@ int solve_wide(hpscd_ctx* ctx, const void* X, int64_t m, int64_t n, int64_t ld, 
       c.sweeps = total;
       break;
     }
-    if (launch_wide_confirm(static_cast<const float*>(X), m, n, ld, y, a, p.e,
+    if (launch_wide_confirm(static_cast<const float*>(X), m, n, ld, y, a, p.e, p.rpart,
                             reinterpret_cast<double*>(ws + L.r2), tsum, st) != cudaSuccess ||
         cudaMemcpyAsync(ctx->host_scratch, tsum, sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaMemcpyAsync(ctx->host_scratch + 1, p.ysq, sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||

@@ -58,6 +58,7 @@ struct GramTCParams {
   uint64_t timeout_ns;
   int nstages;
   const float* y;   // or null: also form X^T y and ||y||^2
+  int y_tma;        // 1: y's K blocks arrive by TMA with the stages (y 16-byte aligned)
   double* hpart;    // [ksplit][npad] per-split X^T y (the diagonal tiles' workers)
   double* y2part;   // [ksplit] per-split ||y||^2
 };
@@ -68,7 +69,8 @@ bool gram_tc_plan(int dtype, int64_t m, int n, int sms, int max_smem, GramTCPlan
 cudaError_t launch_gram_tc(const CUtensorMap* tmap, int dtype, int64_t m, const GramTCPlan& gp,
                            float* partial, int* err, uint64_t timeout_ns, float* G, int ldG,
                            cudaStream_t stream, int n, float* Gt, float* dvec,
-                           const float* y = nullptr, double* h0 = nullptr, double* y2 = nullptr);
+                           const float* y = nullptr, double* h0 = nullptr, double* y2 = nullptr,
+                           const CUtensorMap* ymap = nullptr);
 
 // ---- persistent tall sweep (column-major X, n <= 512) ----
 constexpr int MODE_COPY = 0, MODE_NORMAL = 1, MODE_REFRESH = 2;
@@ -153,6 +155,7 @@ struct WideParams {
   unsigned long long* trace;  // optional: per-block phase stamps of the first blocks
   int trace_passes;
   int continuing;             // 1: a continuation after a failed confirmation (no stop at sweep 0)
+  double* rpart;              // [m][32] per-row float64 partials of a true-residual pass
 };
 struct WideConfig {
   int csize, rows_box, nstages, smem_bytes;
@@ -163,7 +166,8 @@ cudaError_t launch_wide(const float* X, int64_t m, int64_t n, int64_t ld, const 
                         int warm, float* a_tmp, cudaStream_t stream);
 // e = y - X·a (Dot2, float64-grade) for the float32 a, and *sum = ||y - X·a||^2 (float64)
 cudaError_t launch_wide_confirm(const float* X, int64_t m, int64_t n, int64_t ld, const float* y,
-                                const float* a, float* e, double* r2, double* sum, cudaStream_t stream);
+                                const float* a, float* e, double* part, double* r2, double* sum,
+                                cudaStream_t stream);
 // sweeps on from the residual p.e of the coefficients p.a_out (after launch_wide_confirm)
 cudaError_t launch_wide_continue(int64_t n, const WideConfig& cfg, const CUtensorMap* tmap,
                                  WideParams p, float* a_tmp, cudaStream_t stream);

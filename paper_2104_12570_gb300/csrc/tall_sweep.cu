@@ -497,7 +497,9 @@ __global__ void __launch_bounds__(NT, 1)
   double r_prev = 0.0, ynorm = 0.0;
   int64_t pass = 0, sweeps = 0;
   int64_t sw = 0;          // sweeps (or selection steps) reflected in the residual of a pass
-  bool confirm_next = false;
+  // what the next pass is: 0 a sweep, 1 a confirmation (no step), 2 the
+  // predicted last sweep, whose pass forms the true residual
+  int next_kind = 0;
   uint64_t qbase = 0;
 
   // optional trace: CTA 0 records, per pass, the global time at the start of
@@ -515,13 +517,15 @@ __global__ void __launch_bounds__(NT, 1)
   // coefficients that would be returned, and the rule is tested on that.
   for (pass = 0;; ++pass) {
     stamp(pass, 0);
-    const bool conf = confirm_next;
-    confirm_next = false;
+    const bool conf = next_kind == 1;
+    const bool fin = next_kind == 2;
+    next_kind = 0;
     if (pass > 0 && !conf) ++sw;
     const bool virt = pass == 0 && p.h0 != nullptr && !p.warm;
     const int mode = (pass == 0) ? (p.warm ? MODE_REFRESH : MODE_COPY)
-                     : (conf || (p.refresh_every > 0 && sw % p.refresh_every == 0)) ? MODE_REFRESH
-                                                                                      : MODE_NORMAL;
+                     : (conf || fin || (p.refresh_every > 0 && sw % p.refresh_every == 0))
+                         ? MODE_REFRESH
+                         : MODE_NORMAL;
     // the residual the pass starts from (y until a pass has written e)
     const float* __restrict__ ein_src = (pass == 0 || (pass == 1 && p.h0 && !p.warm)) ? p.y : p.e;
     const int buf = (int)(pass & 1);
@@ -731,7 +735,7 @@ __global__ void __launch_bounds__(NT, 1)
     sweeps = sw;
     // e_out is y - X·a for exactly the float32 coefficients a_out would get:
     // pass 0 (a = 0, or the float32 guess) and a confirmation pass
-    const bool exact = pass == 0 || conf;
+    const bool exact = pass == 0 || conf || fin;
     // after the selection steps of Algorithm 3, up to swap_rounds swap steps
     const bool swap_phase = SEL && p.swap_rounds > 0 && sw >= p.max_sweeps;
     bool stop = false;
@@ -739,18 +743,25 @@ __global__ void __launch_bounds__(NT, 1)
       status = HPSCD_ERR_NONFINITE; stop = true;
     } else if (!swap_phase && p.stop_rule == HPSCD_STOP_REL_RES && rel <= p.tol) {
       if (exact || !p.confirm) { status = HPSCD_OK; stop = true; }
-      else confirm_next = true;
+      else next_kind = 1;
     } else if (!swap_phase && p.stop_rule == HPSCD_STOP_REL_CHANGE && sw >= 1 &&
                (r_prev == 0.0 || fabs(r_prev - rel) < p.tol * r_prev)) {
       status = HPSCD_OK; stop = true;
     }
-    if (!stop && !confirm_next && sw == p.max_sweeps + (SEL ? p.swap_rounds : 0)) {
+    if (!stop && next_kind != 1 && sw == p.max_sweeps + (SEL ? p.swap_rounds : 0)) {
       status = (p.stop_rule == HPSCD_STOP_NONE || swap_phase) ? HPSCD_OK : HPSCD_ERR_NOT_CONVERGED;
       stop = true;
     }
+    // When the residual's decay predicts that the next sweep ends at half the
+    // tolerance or below, that sweep's pass forms y - X·a of the returned
+    // coefficients itself (and the rule is tested on it), in place of a
+    // separate confirmation pass after it.
+    if (!stop && next_kind == 0 && p.confirm && p.stop_rule == HPSCD_STOP_REL_RES && sw >= 1 &&
+        r_prev > 0.0 && rel * (rel / r_prev) <= 0.5 * p.tol)
+      next_kind = 2;
     r_prev = rel;
     if (stop) break;
-    if (confirm_next) {
+    if (next_kind == 1) {
       // the next pass recomputes e = y - X·a for a = fl32(a64), the coefficients
       // that would be returned, and applies no step (da = 0)
       for (int c = tid; c < NPAD; c += NT) {
@@ -837,10 +848,12 @@ __global__ void __launch_bounds__(NT, 1)
     for (int c = tid; c < NPAD; c += NT) {
       if constexpr (SEL) a64_s[c] = (c == removed) ? 0.0 : a64_s[c] + (double)da_s[c];
       else a64_s[c] += (double)da_s[c];
-      // a refresh forms y - X·a from a itself: a = hi + lo, both float32
+      // a refresh forms y - X·a from a itself: a = hi + lo, both float32; the
+      // predicted last sweep forms it for the float32 coefficients returned
       const float hi = (float)a64_s[c];
-      vsm[c] = next_refresh ? hi : da_s[c];
-      vlo[c] = next_refresh ? (float)(a64_s[c] - (double)hi) : 0.f;
+      if (next_kind == 2) a64_s[c] = (double)hi;
+      vsm[c] = (next_refresh || next_kind == 2) ? hi : da_s[c];
+      vlo[c] = (next_refresh && next_kind != 2) ? (float)(a64_s[c] - (double)hi) : 0.f;
     }
     named_sync(NT);
     if constexpr (V_IN_REGS) {

@@ -128,19 +128,26 @@ __global__ void __launch_bounds__(256) wide_gram_blocks_kernel(const float* __re
   }
 }
 
-// ---- residual e = y - X·a for row-major X, Dot2 accumulation (float64-grade) ----
-// one warp per row
-__global__ void __launch_bounds__(256) wide_residual_kernel(const float* __restrict__ X,
-                                                            int64_t m, int64_t n, int64_t ld,
-                                                            const float* __restrict__ y,
-                                                            const float* __restrict__ a,
-                                                            float* __restrict__ e) {
+// ---- the true residual e = y - X·a of a row-major X (float64-grade) ----
+// Stage 1: grid (rows / 8, WS slices of the columns); warp w of a CTA takes
+// row blockIdx.x·8 + w over its column slice with Dot2 accumulation (Ogita,
+// Rump, Oishi 2005) per lane, then sums the 32 lanes' (s + c) in float64:
+// part[row][slice].  Stage 2: per row, the WS slices summed in a fixed order,
+// e = y - sum (float32) and (y - sum)^2 in float64 before the rounding.
+// Splitting each row over the grid keeps tens of thousands of warps reading X.
+constexpr int WS = 32;
+
+__global__ void __launch_bounds__(256) wide_dot2_rows_kernel(const float* __restrict__ X, int64_t m,
+                                                             int64_t n, int64_t ld,
+                                                             const float* __restrict__ a,
+                                                             double* __restrict__ part) {
   const int64_t row = (int64_t)blockIdx.x * 8 + threadIdx.x / 32;
   const int lane = threadIdx.x & 31;
   if (row >= m) return;
+  const int64_t j0 = n * blockIdx.y / WS, j1 = n * (blockIdx.y + 1) / WS;
   const float* xr = X + row * ld;
   float s = 0.f, c = 0.f;
-  for (int64_t j = lane; j < n; j += 32) {
+  for (int64_t j = j0 + lane; j < j1; j += 32) {
     const float xv = __ldg(xr + j), av = __ldg(a + j);
     const float p = xv * av, pe = fmaf(xv, av, -p);
     const float t = s + p, z = t - s;
@@ -150,38 +157,20 @@ __global__ void __launch_bounds__(256) wide_residual_kernel(const float* __restr
   double v = (double)s + (double)c;
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(FULL_MASK, v, off);
-  if (lane == 0) e[row] = (float)((double)y[row] - v);
+  if (lane == 0) part[row * WS + blockIdx.y] = v;
 }
 
-// ---- the true residual of the returned coefficients ----
-// e = y - X·a with Dot2 accumulation per row (one warp per row) and the row's
-// (y - X·a)^2 in float64 before e is rounded to float32.
-__global__ void __launch_bounds__(256) wide_true_residual_kernel(const float* __restrict__ X,
-                                                                 int64_t m, int64_t n, int64_t ld,
-                                                                 const float* __restrict__ y,
-                                                                 const float* __restrict__ a,
-                                                                 float* __restrict__ e,
-                                                                 double* __restrict__ r2) {
-  const int64_t row = (int64_t)blockIdx.x * 8 + threadIdx.x / 32;
-  const int lane = threadIdx.x & 31;
+__global__ void wide_residual_rows_kernel(const double* __restrict__ part, int64_t m,
+                                          const float* __restrict__ y, float* __restrict__ e,
+                                          double* __restrict__ r2) {
+  const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (row >= m) return;
-  const float* xr = X + row * ld;
-  float s = 0.f, c = 0.f;
-  for (int64_t j = lane; j < n; j += 32) {
-    const float xv = __ldg(xr + j), av = __ldg(a + j);
-    const float p = xv * av, pe = fmaf(xv, av, -p);
-    const float t = s + p, z = t - s;
-    c += ((s - (t - z)) + (p - z)) + pe;
-    s = t;
-  }
-  double v = (double)s + (double)c;
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(FULL_MASK, v, off);
-  if (lane == 0) {
-    const double ed = (double)y[row] - v;
-    e[row] = (float)ed;
-    r2[row] = ed * ed;
-  }
+  double v = 0.0;
+#pragma unroll 8
+  for (int k = 0; k < WS; ++k) v += part[row * WS + k];
+  const double ed = (double)y[row] - v;
+  e[row] = (float)ed;
+  if (r2) r2[row] = ed * ed;
 }
 
 // *out = sum of r2[0..m) in a fixed order (one CTA)
@@ -541,6 +530,14 @@ bool wide_config(int64_t m, int max_smem, WideConfig* cfg) {
 }
 
 namespace {
+cudaError_t launch_true_residual(const float* X, int64_t m, int64_t n, int64_t ld, const float* y,
+                                 const float* a, float* e, double* part, double* r2,
+                                 cudaStream_t stream) {
+  wide_dot2_rows_kernel<<<dim3((unsigned)((m + 7) / 8), WS), 256, 0, stream>>>(X, m, n, ld, a, part);
+  wide_residual_rows_kernel<<<(unsigned)((m + 255) / 256), 256, 0, stream>>>(part, m, y, e, r2);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_sweep_cluster(const WideConfig& cfg, const CUtensorMap* tmap, WideParams p,
                                  cudaStream_t stream) {
   cudaError_t e = cudaFuncSetAttribute(wide_sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -576,8 +573,9 @@ cudaError_t launch_wide(const float* X, int64_t m, int64_t n, int64_t ld, const 
   if (e != cudaSuccess) return e;
   wide_init_kernel<<<256, 256, 0, stream>>>(a_in, warm, p.a64, a_tmp, n);
   wide_ynorm_kernel<<<1, 256, 0, stream>>>(y, m, p.ysq);
-  wide_residual_kernel<<<(unsigned)((m + 7) / 8), 256, 0, stream>>>(X, m, n, ld, y, a_tmp, p.e);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = launch_true_residual(X, m, n, ld, y, a_tmp, p.e, p.rpart, nullptr, stream)) != cudaSuccess)
+    return e;
   p.continuing = 0;
   if ((e = launch_sweep_cluster(cfg, tmap, p, stream)) != cudaSuccess) return e;
   wide_finish_kernel<<<256, 256, 0, stream>>>(p.a64, p.a_out, n);
@@ -585,8 +583,10 @@ cudaError_t launch_wide(const float* X, int64_t m, int64_t n, int64_t ld, const 
 }
 
 cudaError_t launch_wide_confirm(const float* X, int64_t m, int64_t n, int64_t ld, const float* y,
-                                const float* a, float* e, double* r2, double* sum, cudaStream_t stream) {
-  wide_true_residual_kernel<<<(unsigned)((m + 7) / 8), 256, 0, stream>>>(X, m, n, ld, y, a, e, r2);
+                                const float* a, float* e, double* part, double* r2, double* sum,
+                                cudaStream_t stream) {
+  cudaError_t err = launch_true_residual(X, m, n, ld, y, a, e, part, r2, stream);
+  if (err != cudaSuccess) return err;
   wide_sum_kernel<<<1, 256, 0, stream>>>(r2, m, sum);
   return cudaGetLastError();
 }

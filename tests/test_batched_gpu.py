@@ -40,24 +40,32 @@ def rel(a, b):
 
 def residual_floor(s, sweeps):
     """Absolute bound on |hist_gpu[s] - hist_oracle[s]| from float32 residual
-    arithmetic: a column step e - X_j·da_j rounds each entry by at most
-    u·(|e_i| + |X_ij·da_j|), i.e. by <= 2u·||e_{k-1}|| in norm (the projection
-    never lengthens e), and later steps are projections, which do not grow an
-    error already in e.  So the bound after sweep s is 2u·sum over the steps so
-    far of ||e_{k-1}|| / ||y||, with the step norms of Algorithm 1 in float64."""
-    u = 2.0 ** -24
+    arithmetic.  A pass of the batched kernel applies its whole sweep to each
+    row at once, e_i <- e_i - sum_j X_ij·da_j, summed in float32 to a depth of
+    at most D = 33 (16 columns per lane, then 16 warps, then e_i), so it rounds
+    row i by at most D·u·(|e_i| + sum_j |X_ij|·|da_j|), u = 2^-24; the next
+    sweeps take their steps from the perturbed residual and do not lengthen
+    that error.  So the bound after sweep s sums, over the sweeps so far,
+    D·u·|| |e_{s-1}| + |X|·|da_s| || / ||y||, with Algorithm 1's iterates in
+    float64."""
+    u, D = 2.0 ** -24, 33
     X = s.dense_f64()
     y = s.y.astype(np.float64)
     e = y.copy()
+    a = np.zeros(s.n)
     d = (X * X).sum(axis=0)
     ny = np.linalg.norm(y) or 1.0
+    aX = np.abs(X)
     acc, out = 0.0, [0.0]
     for _ in range(sweeps):
+        e0, a0 = np.abs(e), a.copy()
         for j in range(s.n):
-            acc += np.linalg.norm(e)
             if d[j] > 0:
-                e -= X[:, j] * (X[:, j] @ e / d[j])
-        out.append(2 * u * acc / ny)
+                da = X[:, j] @ e / d[j]
+                e -= X[:, j] * da
+                a[j] += da
+        acc += D * u * np.linalg.norm(e0 + aX @ np.abs(a - a0)) / ny
+        out.append(acc)
     return np.array(out)
 
 

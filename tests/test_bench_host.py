@@ -17,19 +17,21 @@ def bench():
     return mod
 
 
-def test_sweep_kernel_bytes_of_the_benchmark_solve(bench):
-    # 6 streaming passes over 1,000,000 x 256 float32 X, each reading and writing e
-    assert bench.sweep_kernel_bytes(1_000_000, 256, 4, 6) == 6 * (4 * 256 + 8) * 1_000_000
-    assert bench.sweep_kernel_bytes(1_000_000, 256, 4, 6) == 6_192_000_000
+def test_sweep_bytes_of_the_benchmark_solve(bench):
+    # X once per sweep (4 bytes x 1,000,000 x 256) plus the read and write of e (8m)
+    assert bench.sweep_bytes(1_000_000, 256, 4, 5) == 5 * (4 * 256 + 8) * 1_000_000
+    assert bench.sweep_bytes(1_000_000, 256, 4, 5) == 5_160_000_000
+    # e kept on chip (the wide and batched kernels): X alone
+    assert bench.sweep_bytes(2000, 200_000, 4, 2, e_in_hbm=False) == 2 * 4 * 2000 * 200_000
 
 
-def test_algorithmic_bytes_add_the_setup_read(bench):
+def test_solve_bytes_add_the_setup_read(bench):
     m, n = 4_000_000, 512
     for esz in (2, 4):
-        for passes in (1, 4, 9):
-            setup = esz * m * n + 4 * m  # one read of X (Gram) and of y
-            assert bench.algorithmic_bytes(m, n, esz, passes) == \
-                setup + bench.sweep_kernel_bytes(m, n, esz, passes)
+        for sweeps in (1, 4, 9):
+            setup = esz * m * n + 4 * m  # one read of X (Gram, X^T y) and of y
+            assert bench.setup_bytes(m, n, esz) == setup
+            assert bench.solve_bytes(m, n, esz, sweeps) == setup + bench.sweep_bytes(m, n, esz, sweeps)
 
 
 def _line(sm, mx, hw="Not Active", hwt="Not Active", swt="Not Active", pcap="Not Active"):

@@ -300,8 +300,7 @@ def test_full_size_precision_mode_4Mx512_bf16(ctx):
     X, y = to_gpu(s)
     r = ctx.solve(X, y, tol=1e-6, max_sweeps=100, stop="rel_res", refresh_every=4)
     assert r.status == "ok" and r.rel_res <= 1e-6
-    assert_true_residual(s, r, 1e-6)
-    assert r.timing["passes"] > r.sweeps  # the confirmation pass ran (a true-residual pass)
+    assert_true_residual(s, r, 1e-6)  # the last sweep's pass formed y - X·a (predicted last sweep)
     r1 = ctx.solve(X, y, tol=0, max_sweeps=1, stop="none", refresh_every=4)
     o1 = oracle_same(s, 1)
     assert rel(r1.a.cpu().numpy(), o1.a) <= RTOL_BF16
