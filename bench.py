@@ -603,9 +603,11 @@ def profile_wide(hp, synth, cols, blocks=512):
     """The wide cluster kernel alone on a 2,000 x `cols` float32 row-major
     consistent system, solved to relative residual 1e-6 (profiler captures and
     the kernel's own trace; not a bench line).  The trace stamps CTA 0's global
-    timer at five points of each of the first `blocks` column blocks: after the
-    copy wait and partial dots, after the CTA's reduction, after the cluster
-    exchange, after the block's chain, after the residual update."""
+    timer at six points of each of the first `blocks` column blocks: after the
+    wait for the block's exchange round and its sum, after the block's steps
+    (da = M q - N da_prev), after the next block's M/N copies are issued, after
+    the wait for the lookahead slab, after the row pass (update and lookahead
+    dots), after the push of the lookahead partials."""
     import torch
     s = synth.workload("wide_2000x200k_f32", seed=0, n=int(cols))
     dev = torch.device("cuda", 0)
@@ -616,7 +618,7 @@ def profile_wide(hp, synth, cols, blocks=512):
     ctx.set_trace(blocks)
     r = ctx.solve(X, y, tol=1e-6, max_sweeps=200, stop="rel_res")
     t = ctx.trace_raw()[: 6 * blocks].reshape(blocks, 6)
-    t = t[t[:, 4] > 0]
+    t = t[t[:, 5] > 0]
     ctx.set_trace(0)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -628,10 +630,11 @@ def profile_wide(hp, synth, cols, blocks=512):
            "ms_to_tol": e0.elapsed_time(e1), "sweep_kernel_ms": float(r.timing["sweep_ms"]),
            "blocks_per_sweep": -(-s.n // 64)}
     if len(t) > 2:
-        prev = t[:-1, 4]
-        ph = {"copy_wait_and_dots_us": t[1:, 0] - prev, "cta_reduce_us": t[1:, 1] - t[1:, 0],
-              "cluster_exchange_us": t[1:, 2] - t[1:, 1], "chain_us": t[1:, 3] - t[1:, 2],
-              "residual_update_us": t[1:, 4] - t[1:, 3], "block_us": t[1:, 4] - prev}
+        prev = t[:-1, 5]
+        ph = {"round_wait_and_sum_us": t[1:, 0] - prev, "chain_us": t[1:, 1] - t[1:, 0],
+              "next_copies_us": t[1:, 2] - t[1:, 1], "slab_wait_us": t[1:, 3] - t[1:, 2],
+              "row_pass_us": t[1:, 4] - t[1:, 3], "push_us": t[1:, 5] - t[1:, 4],
+              "block_us": t[1:, 5] - prev}
         out["trace_blocks"] = int(len(t) - 1)
         out["median_per_block"] = {k: float(np.median(v)) / 1e3 for k, v in ph.items()}
     print(json.dumps(out), flush=True)

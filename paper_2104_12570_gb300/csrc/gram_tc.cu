@@ -247,10 +247,6 @@ __global__ void __launch_bounds__(GT_THREADS, 1)
       }
     };
     load_y(0, yv);
-    // X^T y is needed only for the columns of this group's diagonal tiles
-    bool dsl[MAXQ / 8];
-#pragma unroll
-    for (int k = 0; k < MAXQ / 8; ++k) dsl[k] = want_y && k < nload && p.grp.diag_slot[g][k] != 0;
     auto flush = [&]() {
 #pragma unroll
       for (int q = 0; q < MAXQ; ++q) {
@@ -301,8 +297,7 @@ __global__ void __launch_bounds__(GT_THREADS, 1)
             const float a0 = __uint_as_float(x.x), a1 = __uint_as_float(x.y);
             const float a2 = __uint_as_float(x.z), a3 = __uint_as_float(x.w);
             dsq[q] = fmaf(a0, a0, fmaf(a1, a1, fmaf(a2, a2, fmaf(a3, a3, dsq[q]))));
-            if (dsl[q >> 3])
-              xy[q] = fmaf(a0, yv[0], fmaf(a1, yv[1], fmaf(a2, yv[2], fmaf(a3, yv[3], xy[q]))));
+            xy[q] = fmaf(a0, yv[0], fmaf(a1, yv[1], fmaf(a2, yv[2], fmaf(a3, yv[3], xy[q]))));
             // split in place: hi over x, lo in the second half
             uint4 h, l;
             split_tf32(x, h, l);
@@ -314,7 +309,7 @@ __global__ void __launch_bounds__(GT_THREADS, 1)
             for (int h = 0; h < 4; ++h) {
               const float lo16 = __uint_as_float(w4[h] << 16), hi16 = __uint_as_float(w4[h] & 0xffff0000u);
               dsq[q] = fmaf(lo16, lo16, fmaf(hi16, hi16, dsq[q]));
-              if (dsl[q >> 3]) xy[q] = fmaf(lo16, yv[2 * h], fmaf(hi16, yv[2 * h + 1], xy[q]));
+              xy[q] = fmaf(lo16, yv[2 * h], fmaf(hi16, yv[2 * h + 1], xy[q]));
             }
           }
         }

@@ -227,7 +227,7 @@ int run_gram(hpscd_ctx* ctx, const void* X, int dtype, int64_t m, int64_t n, int
 
 // ---- wide systems: row-major X, m <= 4096 (the cluster sweep) ----
 struct WideLayout {
-  size_t Gb = 0, e = 0, a64 = 0, dsw = 0, atmp = 0, ysq = 0, hist = 0, ctl = 0, r2 = 0, tsum = 0,
+  size_t Mb = 0, Nb = 0, e = 0, a64 = 0, dsw = 0, atmp = 0, ysq = 0, hist = 0, ctl = 0, r2 = 0, tsum = 0,
          rpart = 0, xcopy = 0, ycopy = 0, acopy = 0, total = 0;
 };
 
@@ -235,14 +235,15 @@ int make_wide_plan(const hpscd_ctx* ctx, int dtype, int64_t m, int64_t n, int64_
                    const hpscd_opts* o, bool host_copies, WideConfig* cfg, WideLayout* L) {
   if (dtype != HPSCD_F32) return HPSCD_ERR_UNSUPPORTED;
   if (!wide_config(m, ctx->max_smem, cfg)) return HPSCD_ERR_UNSUPPORTED;
-  const int64_t nblk = (n + 63) / 64;
+  const int64_t nblk = (n + cfg->W - 1) / cfg->W;
   size_t off = 0;
   auto take = [&](size_t bytes) {
     const size_t at = off;
     off = align_up(off + bytes, 256);
     return at;
   };
-  L->Gb = take((size_t)nblk * 64 * 64 * sizeof(float));
+  L->Mb = take((size_t)nblk * cfg->W * cfg->W * sizeof(float));
+  L->Nb = take((size_t)nblk * cfg->W * cfg->W * sizeof(float));
   L->e = take((size_t)m * sizeof(float));
   L->a64 = take((size_t)n * sizeof(double));
   L->dsw = take((size_t)n * sizeof(float));
@@ -273,7 +274,7 @@ int solve_wide(hpscd_ctx* ctx, const void* X, int64_t m, int64_t n, int64_t ld, 
   memset(&map, 0, sizeof(map));
   cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)m};
   cuuint64_t strides[1] = {(cuuint64_t)ld * 4};
-  cuuint32_t box[2] = {64, (cuuint32_t)cfg.rows_box};
+  cuuint32_t box[2] = {(cuuint32_t)cfg.W, (cuuint32_t)cfg.rows_box};
   cuuint32_t estr[2] = {1, 1};
   const int use_tma =
       aligned && ctx->encode(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(X), dims,
@@ -288,7 +289,8 @@ int solve_wide(hpscd_ctx* ctx, const void* X, int64_t m, int64_t n, int64_t ld, 
   p.m = m;
   p.n = n;
   p.ld = ld;
-  p.Gb = reinterpret_cast<float*>(ws + L.Gb);
+  p.Mb = reinterpret_cast<float*>(ws + L.Mb);
+  p.Nb = reinterpret_cast<float*>(ws + L.Nb);
   p.e = reinterpret_cast<float*>(ws + L.e);
   p.a64 = reinterpret_cast<double*>(ws + L.a64);
   p.dsw = reinterpret_cast<float*>(ws + L.dsw);

@@ -139,7 +139,8 @@ struct WideParams {
   const float* X;    // row-major X (plain-load path)
   int use_tma;
   int64_t m, n, ld;
-  float* Gb;         // [nblk][64][64] Gram blocks (set-up)
+  float* Mb;         // [nblk][W][W] M_b = (I + D^-1 L_b)^-1 D^-1 of each column block (set-up)
+  float* Nb;         // [nblk][W][W] N_b = M_b·(X_b^T X_{b-1}), the coupling to the previous block
   float* e;          // [m] residual (in: initial; out: final)
   double* a64;       // [n] coefficients
   float* dsw;        // [n] da of the current sweep
@@ -159,6 +160,7 @@ struct WideParams {
 };
 struct WideConfig {
   int csize, rows_box, nstages, smem_bytes;
+  int W;  // columns per block: 64, or 32 when a CTA owns more than 128 rows
 };
 bool wide_config(int64_t m, int max_smem, WideConfig* cfg);
 cudaError_t launch_wide(const float* X, int64_t m, int64_t n, int64_t ld, const WideConfig& cfg,

@@ -5,31 +5,51 @@
 // chain of n dependent column steps.  One thread-block cluster of WC CTAs
 // walks that chain: CTA c owns rows [r0_c, r1_c) and keeps its slice of e in
 // shared memory for the whole solve.  The columns are taken in the paper's
-// order in blocks of W = 64.  TMA re-tiles row-major X on the fly: the box
-// {64 columns, rows of this CTA} is the block's slab for this CTA.  Per block:
-//   1. each CTA forms its partial <X_j, e> (j in the block) over its rows;
-//   2. the partials are pushed to every CTA of the cluster through
-//      distributed shared memory, with a release-arrive on the receiver's
-//      mbarrier (bounded waits, no cluster-wide hardware barrier);
-//   3. every CTA sums them in a fixed order and solves the block's chain
-//      da_j = (<X_j, e> - sum_{l<j in block} G_jl da_l) / G_jj (Eq. da2 and
-//      Eq. ek1-ek inside the block) as s = <X_., e> ⊘ d (the elementwise form
-//      of the ⊘ step) followed by da_j = s_j - sum_{l<j} (G_jl / G_jj) da_l,
-//      which keeps the division off the dependency chain; the set-up kernel
-//      stores each block's Gram with its rows pre-divided by G_jj;
-//   4. each CTA applies e <- e - X_block·da to its rows (Eq. ek1-ek) and CTA 0
-//      adds da to a.
-// After each sweep the cluster forms ||e|| (float64) and tests the stopping
-// rule; the chain is latency-bound by construction (n dependent steps).
+// order in blocks of W (64, or 32 when a CTA owns more than 128 rows); TMA
+// re-tiles row-major X on the fly: the box {W columns, rows of this CTA} is
+// the block's slab for this CTA.
+//
+// The steps of block b (Eq. da2 and Eq. ek1-ek inside the block) are
+//     da_j = (<X_j, e> - sum_{l<j in block} G_jl da_l) / G_jj,
+// a forward substitution with the block's unit lower triangle.  The set-up
+// writes it as a matrix: M_b = (I + D_b^{-1} L_b)^{-1} D_b^{-1} (L_b the strict
+// lower triangle of G_bb = X_b^T X_b, D_b its diagonal; a zero column gives a
+// zero row), so da_b = M_b·(X_b^T e_{b-1}), where e_{b-1} is the residual
+// after block b-1.  Two blocks of lookahead take the exchange of the dot
+// products off the chain: each CTA forms X_{b+2}^T e_b over its rows right
+// after block b's update and pushes the partials to every CTA then; they are
+// used two blocks later, corrected for the one block applied in between by
+// Eq. ek1-ek: X_b^T e_{b-1} = X_b^T e_{b-2} - P_b·da_{b-1} with the coupling
+// P_b = X_b^T X_{b-1}.  The set-up stores N_b = M_b·P_b, so the chain is
+//     da_b = M_b·q_b - N_b·da_{b-1},   q_b = sum over the CTAs of X_b^T e_{b-2},
+// two W×W products per block on the dependency chain (the paper's column
+// order is kept; only the association of the sums differs).  One iteration
+// of a CTA, for block b:
+//   1. wait (bounded) for round b of the exchange, sum its WC partials in a
+//      fixed order (every CTA holds identical values);
+//   2. da_b = M_b·q_b - N_b·da_{b-1}  (8 threads per row; M_b and N_b are
+//      staged in shared memory by cp.async one block ahead);
+//   3. one pass over the CTA's rows: e_r -= X_b[r]·da_b, then the partial
+//      X_{b+2}^T e over the new e_r (the two slabs are both in shared memory);
+//   4. the partials summed over the CTA's warps and pushed into slot (b+2) % 4
+//      of every CTA of the cluster by st.async (distributed shared memory; the
+//      bytes complete on the receiver's mbarrier, which the receiver arms with
+//      the round's byte count, so the sender does not wait).  A CTA can run at
+//      most two blocks ahead of the slowest one (it waits for round b, which
+//      every CTA pushes two blocks earlier), so four slots are never
+//      overwritten unread; slot s is re-armed for round b+4 right after round
+//      b is consumed, which every push of round b+4 follows.
+// After the last block of a sweep the cluster forms ||e|| (float64) and tests
+// the stopping rule.
 #include "kernels.h"
 
 namespace hpscd {
 
 namespace {
 
-constexpr int WW = 64;        // columns per block
 constexpr int WNT = 512;      // threads per CTA
 constexpr int WNW = WNT / 32;
+constexpr int XSLOTS = 4;     // exchange slots of the dot products (lookahead 2 + slack)
 
 __device__ __forceinline__ void st_cluster_f64(uint32_t addr, double v) {
   asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(addr), "d"(v) : "memory");
@@ -39,6 +59,19 @@ __device__ __forceinline__ void arrive_remote(uint32_t bar_cluster_addr) {
                    bar_cluster_addr)
                : "memory");
 }
+// Asynchronous store of 16 bytes into another CTA's shared memory; the bytes
+// complete (complete_tx) on that CTA's mbarrier at `bar` (both cluster addresses).
+__device__ __forceinline__ void st_async_v4(uint32_t addr, float4 v, uint32_t bar) {
+  asm volatile(
+      "st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.f32 [%0], {%1, %2, %3, %4}, [%5];" ::"r"(
+          addr),
+      "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+
 __device__ __forceinline__ bool try_wait_cluster(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
@@ -63,68 +96,160 @@ __device__ __forceinline__ bool wait_cluster_bounded(uint64_t* bar, uint32_t par
 
 }  // namespace
 
-// ---- set-up: the 64x64 Gram block of every column block, and d ----
-// grid: one CTA per column block; rows streamed with plain loads.
-__global__ void __launch_bounds__(256) wide_gram_blocks_kernel(const float* __restrict__ X,
-                                                               int64_t m, int64_t n, int64_t ld,
-                                                               float* __restrict__ Gb) {
-  __shared__ float tile[32][WW + 1];
+// ---- set-up: M_b and N_b of every column block ----
+// One CTA per block b: D = X_b^T [X_b | X_{b-1}] (W x 2W: G = X_b^T X_b and the
+// coupling P = X_b^T X_{b-1} to the previous block, cyclically: block 0's is
+// the last block, which precedes it in the next sweep) over all m rows.  X is
+// staged through shared memory 32 rows at a time (the next rows already in
+// registers); 16 x 16 threads each hold a (W/16) x (2W/16) tile of D, float32
+// products summed in float32 over 256 rows and those sums in float32 again.
+// Then, in shared memory: d = diag(G), H = D^{-1}·strict_lower(G),
+// T = (I + H)^{-1} (column k by forward substitution in thread k),
+// M = T·D^{-1}, N = M·P; M and N are stored row-major [W][W].
+template <int W>
+__global__ void __launch_bounds__(256, 1) wide_setup_kernel(const float* __restrict__ X, int64_t m,
+                                                            int64_t n, int64_t ld, int64_t nblk,
+                                                            float* __restrict__ Mb,
+                                                            float* __restrict__ Nb) {
+  constexpr int W2 = 2 * W;
+  constexpr int TR = W / 16;    // rows of D per thread
+  constexpr int TC = W2 / 16;   // columns of D per thread
+  constexpr int XP = W2 + 4;    // tile pitch (16-byte rows)
+  constexpr int WP = W + 4;     // pitch of the W x W matrices
+  constexpr int F4 = 32 * W2 / 4 / 256;  // float4 of a tile per thread
+  extern __shared__ float wsm[];
+  float* xs = wsm;              // [32][XP]: columns 0..W-1 block b, W..2W-1 block b-1
+  float* Gs = xs + 32 * XP;     // [W][WP]
+  float* Ps = Gs + W * WP;      // [W][WP]
+  float* Ts = Ps + W * WP;      // [W][WP] T, then M
+  float* dsv = Ts + W * WP;     // [W]
   const int64_t b = blockIdx.x;
-  const int64_t c0 = b * WW;
+  const int64_t bp = (b + nblk - 1) % nblk;
+  const int64_t c0 = b * W, cp0 = bp * W;
   const int tid = threadIdx.x;
-  const int ty = tid / 16, tx = tid % 16;  // 16x16 threads, 4x4 outputs each
-  float acc[4][4];
-  double acc64[4][4];
+  const int ty = tid / 16, tx = tid % 16;
+  const bool vec = (reinterpret_cast<uintptr_t>(X) & 15) == 0 && (ld & 3) == 0;
+  // float4 q of a tile: row (tid + 256 q) / (W2 / 4), columns 4·((tid + 256 q) % (W2 / 4))
+  auto fetch = [&](int64_t rbase, float4 (&v)[F4]) {
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+    for (int q = 0; q < F4; ++q) {
+      const int i = tid + 256 * q;
+      const int r = i / (W2 / 4), c = 4 * (i % (W2 / 4));
+      const int64_t row = rbase + r;
+      const int64_t col = c < W ? c0 + c : cp0 + (c - W);
+      const float* src = X + row * ld + col;
+      if (row < m && vec && col + 3 < n) {
+        v[q] = __ldg(reinterpret_cast<const float4*>(src));
+      } else {
+        v[q].x = (row < m && col < n) ? __ldg(src) : 0.f;
+        v[q].y = (row < m && col + 1 < n) ? __ldg(src + 1) : 0.f;
+        v[q].z = (row < m && col + 2 < n) ? __ldg(src + 2) : 0.f;
+        v[q].w = (row < m && col + 3 < n) ? __ldg(src + 3) : 0.f;
+      }
+    }
+  };
+  float acc[TR][TC], acc2[TR][TC];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) { acc[i][j] = 0.f; acc64[i][j] = 0.0; }
-  int chunks = 0;
+  for (int i = 0; i < TR; ++i)
+#pragma unroll
+    for (int j = 0; j < TC; ++j) { acc[i][j] = 0.f; acc2[i][j] = 0.f; }
+  float4 nxt[F4];
+  fetch(0, nxt);
+  int tiles = 0;
   for (int64_t r0 = 0; r0 < m; r0 += 32) {
-    for (int idx = tid; idx < 32 * WW; idx += 256) {
-      const int r = idx / WW, c = idx % WW;
-      const int64_t row = r0 + r, col = c0 + c;
-      tile[r][c] = (row < m && col < n) ? X[row * ld + col] : 0.f;
+#pragma unroll
+    for (int q = 0; q < F4; ++q) {
+      const int i = tid + 256 * q;
+      const int r = i / (W2 / 4), c = 4 * (i % (W2 / 4));
+      *reinterpret_cast<float4*>(xs + r * XP + c) = nxt[q];
     }
     __syncthreads();
+    if (r0 + 32 < m) fetch(r0 + 32, nxt);  // in flight while this tile is used
 #pragma unroll 4
     for (int r = 0; r < 32; ++r) {
-      float av[4], bv[4];
+      float av[TR], bv[TC];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) { av[i] = tile[r][ty * 4 + i]; bv[i] = tile[r][tx * 4 + i]; }
+      for (int i = 0; i < TR; i += 2) {
+        const float2 t = *reinterpret_cast<const float2*>(xs + r * XP + ty * TR + i);
+        av[i] = t.x; av[i + 1] = t.y;
+      }
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int j = 0; j < TC; j += 4) {
+        const float4 t = *reinterpret_cast<const float4*>(xs + r * XP + tx * TC + j);
+        bv[j] = t.x; bv[j + 1] = t.y; bv[j + 2] = t.z; bv[j + 3] = t.w;
+      }
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+      for (int i = 0; i < TR; ++i)
+#pragma unroll
+        for (int j = 0; j < TC; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
     }
     __syncthreads();
-    if (++chunks == 8) {
-      chunks = 0;
+    if (++tiles == 8) {
+      tiles = 0;
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < TR; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) { acc64[i][j] += acc[i][j]; acc[i][j] = 0.f; }
+        for (int j = 0; j < TC; ++j) { acc2[i][j] += acc[i][j]; acc[i][j] = 0.f; }
     }
   }
-  // store the block as  d_i on the diagonal and H_ik = G_ik / d_i below it
-  // (the couplings pre-divided by the row's denominator; 0 for a zero column),
-  // transposed: entry (i, k) at [k][i], so the chain's lanes (one row each)
-  // read consecutive words of column k
-  __shared__ float gs[WW][WW + 1];
+  // columns tx·TC.. of D: G for tx < 8, P for tx >= 8
+  float* dst = tx < 8 ? Gs : Ps;
+  const int cbase = (tx % 8) * TC;
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < TR; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) gs[ty * 4 + i][tx * 4 + j] = (float)(acc64[i][j] + acc[i][j]);
+    for (int j = 0; j < TC; ++j) dst[(ty * TR + i) * WP + cbase + j] = acc2[i][j] + acc[i][j];
   __syncthreads();
-  float* out = Gb + b * (WW * WW);
-  for (int idx = tid; idx < WW * WW; idx += 256) {
-    const int k = idx / WW, i = idx % WW;
-    const float di = gs[i][i];
-    float v;
-    if (k == i) v = di;
-    else if (k < i) v = di > 0.f ? gs[i][k] / di : 0.f;
-    else v = 0.f;
-    out[idx] = v;
+  if (tid < W) dsv[tid] = Gs[tid * WP + tid];
+  __syncthreads();
+  // H = D^{-1}·strict_lower(G) in place of G's lower triangle (a zero row for d_i = 0)
+  for (int idx = tid; idx < W * W; idx += 256) {
+    const int i = idx / W, l = idx % W;
+    if (l < i) {
+      const float di = dsv[i];
+      Gs[i * WP + l] = di > 0.f ? Gs[i * WP + l] / di : 0.f;
+    }
+  }
+  __syncthreads();
+  // T = (I + H)^{-1}, column k in thread k, held in registers:
+  // T_ik = delta_ik - sum_{l<i} H_il T_lk (T_lk = 0 for l < k)
+  if (tid < W) {
+    const int k = tid;
+    float t[W];
+#pragma unroll
+    for (int i = 0; i < W; ++i) {
+      float acc_t = 0.f;
+#pragma unroll
+      for (int l = 0; l < i; ++l) acc_t = fmaf(Gs[i * WP + l], t[l], acc_t);
+      t[i] = i < k ? 0.f : (i == k ? 1.f : -acc_t);
+    }
+#pragma unroll
+    for (int i = 0; i < W; ++i) Ts[i * WP + k] = t[i];
+  }
+  __syncthreads();
+  // M = T·D^{-1} (in place; a zero column gives a zero column of M)
+  for (int idx = tid; idx < W * W; idx += 256) {
+    const int i = idx / W, j = idx % W;
+    const float dj = dsv[j];
+    Ts[i * WP + j] = dj > 0.f ? Ts[i * WP + j] / dj : 0.f;
+  }
+  __syncthreads();
+  // N = M·P, four consecutive columns per thread and step
+  float* Mo = Mb + b * (W * W);
+  float* No = Nb + b * (W * W);
+  for (int idx = tid; idx < W * W / 4; idx += 256) {
+    const int i = idx / (W / 4), j = 4 * (idx % (W / 4));
+    float4 a4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int l = 0; l <= i; ++l) {
+      const float mil = Ts[i * WP + l];
+      const float4 pv = *reinterpret_cast<const float4*>(Ps + l * WP + j);
+      a4.x = fmaf(mil, pv.x, a4.x);
+      a4.y = fmaf(mil, pv.y, a4.y);
+      a4.z = fmaf(mil, pv.z, a4.z);
+      a4.w = fmaf(mil, pv.w, a4.w);
+    }
+    *reinterpret_cast<float4*>(No + i * W + j) = a4;
+    *reinterpret_cast<float4*>(Mo + i * W + j) = *reinterpret_cast<const float4*>(Ts + i * WP + j);
   }
 }
 
@@ -190,8 +315,38 @@ __global__ void wide_sum_kernel(const double* __restrict__ r2, int64_t m, double
 }
 
 // ---- the cluster sweep ----
+// Shared memory of a CTA (byte offsets from a 1024-aligned base).
+struct WSmem {
+  int stages, es, xbuf, red, mn, qs, da, dap, nbuf, wsum, bars, total;
+};
+__host__ __device__ inline WSmem wide_smem_plan(int W, int rows_box, int nst) {
+  WSmem s;
+  int off = 0;
+  auto take = [&](int bytes) {
+    const int at = off;
+    off += (bytes + 127) / 128 * 128;
+    return at;
+  };
+  s.stages = take(nst * rows_box * W * 4);
+  s.es = take(rows_box * 4);
+  s.xbuf = take(XSLOTS * 16 * W * 4);  // [slot][source CTA][W] partial dots
+  s.red = take(WNW * W * 4);           // [warp][W]
+  s.mn = take(2 * 2 * W * W * 4);      // [buffer][M, N][W][W] of the current and next block
+  s.qs = take(W * 4);
+  s.da = take(W * 4);
+  s.dap = take(W * 4);
+  s.nbuf = take(16 * 8);
+  s.wsum = take(WNW * 8);
+  s.bars = take((8 + XSLOTS + 2) * 8);  // full[<= 8], dot slots, norm rounds
+  s.total = off + 1024;                 // alignment slack
+  return s;
+}
+
+template <int W>
 __global__ void __launch_bounds__(WNT, 1)
     wide_sweep_kernel(const __grid_constant__ CUtensorMap tmap, const WideParams p) {
+  constexpr int CPL = W / 32;  // columns per lane in the row pass (2 or 1)
+  constexpr int CPT = W / 8;   // columns per thread in the chain (8 threads per row)
   extern __shared__ unsigned char smem_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -203,58 +358,86 @@ __global__ void __launch_bounds__(WNT, 1)
   const int rows = (int)(r1 - r0);
   const int rows_box = p.rows_box;  // box height (>= rows of every CTA)
   const int nst = p.nstages;
-  const int stage_bytes = rows_box * WW * 4;
-  float* stages = reinterpret_cast<float*>(base);
-  float* es = reinterpret_cast<float*>(base + (size_t)nst * stage_bytes);  // [rows_box, padded to 4]
-  float* xbuf = es + ((rows_box + 3) & ~3);    // [2][16][WW] partial dots from each CTA
-  float* red = xbuf + 2 * 16 * WW;             // [WNW][WW]
-  float* gsum = red + WNW * WW;                // [WW]
-  float* da_s = gsum + WW;                     // [WW]
-  float* psum = da_s + WW;                     // [WW] this CTA's partial dots
-  float* gblk = psum + WW;                     // [2][WW][WW] Gram blocks (double-buffered)
-  double* nbuf = reinterpret_cast<double*>(gblk + 2 * WW * WW);  // [16] norm partials
-  double* wsum = nbuf + 16;                    // [WNW]
-  uint64_t* full = reinterpret_cast<uint64_t*>(wsum + WNW);
-  uint64_t* xbar = full + 8;                   // [2] dots exchange, [2] norm exchange
+  const WSmem L = wide_smem_plan(W, rows_box, nst);
+  float* stages = reinterpret_cast<float*>(base + L.stages);
+  float* es = reinterpret_cast<float*>(base + L.es);
+  float* xbuf = reinterpret_cast<float*>(base + L.xbuf);
+  float* red = reinterpret_cast<float*>(base + L.red);
+  float* mn = reinterpret_cast<float*>(base + L.mn);
+  float* qs = reinterpret_cast<float*>(base + L.qs);
+  float* da_s = reinterpret_cast<float*>(base + L.da);
+  float* dap_s = reinterpret_cast<float*>(base + L.dap);
+  double* nbuf = reinterpret_cast<double*>(base + L.nbuf);
+  double* wsum = reinterpret_cast<double*>(base + L.wsum);
+  uint64_t* full = reinterpret_cast<uint64_t*>(base + L.bars);
+  uint64_t* xbar = full + 8;       // [XSLOTS] dot exchange
+  uint64_t* nbar = xbar + XSLOTS;  // [2] norm exchange
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int64_t nblk = (n + WW - 1) / WW;
+  const int64_t nblk = (n + W - 1) / W;
   // optional trace (CTA 0, thread 0): for the first trace_passes blocks, the
-  // global time after the copy wait, the dots, the exchange, the chain, the update
+  // global time after the round's wait and sum, after the chain, after the
+  // next block's copies are issued, after the slab wait, after the row pass,
+  // after the push
   uint64_t trace_k = 0;
   auto stamp = [&](int f) {
     if (p.trace && me == 0 && tid == 0 && trace_k < (uint64_t)p.trace_passes)
       p.trace[trace_k * 6 + f] = global_timer_ns();
   };
 
+  const uint32_t round_bytes = (uint32_t)(WC * W * 4);  // every CTA's W partials
   if (tid == 0) {
     for (int s = 0; s < nst; ++s) mbar_init(&full[s], 1);
-    for (int k = 0; k < 4; ++k) mbar_init(&xbar[k], WC);
+    // one arrival (this CTA's, with the round's byte count) per round
+    for (int k = 0; k < XSLOTS; ++k) {
+      mbar_init(&xbar[k], 1);
+      mbar_arrive_expect_tx(&xbar[k], round_bytes);
+    }
+    for (int k = 0; k < 2; ++k) mbar_init(&nbar[k], WC);
     fence_mbar_init();
   }
   for (int r = tid; r < rows_box; r += WNT) es[r] = (r < rows) ? p.e[r0 + r] : 0.f;
+  for (int c = tid; c < W; c += WNT) dap_s[c] = 0.f;
   __syncthreads();
   cluster_sync_all();  // every CTA's barriers are initialised before anyone arrives remotely
 
+  // stage ring: sequence number k (block k % nblk of the whole solve) in stage k % nst
+  const bool tma = p.use_tma != 0;
   uint64_t issued = 0, waited = 0;
   auto issue = [&](uint64_t k) {
     const int s = (int)(k % nst);
     const int64_t b = (int64_t)(k % (uint64_t)nblk);
-    mbar_arrive_expect_tx(&full[s], (uint32_t)stage_bytes);
-    tma_load_2d(stages + (size_t)s * rows_box * WW, &tmap, &full[s], (int32_t)(b * WW),
-                (int32_t)r0);
+    mbar_arrive_expect_tx(&full[s], (uint32_t)(rows_box * W * 4));
+    tma_load_2d(stages + (size_t)s * rows_box * W, &tmap, &full[s], (int32_t)(b * W), (int32_t)r0);
   };
-  const bool tma = p.use_tma != 0;
   if (tid == 0 && tma)
     while (issued < (uint64_t)nst) issue(issued++);
+  // the slab of sequence k in shared memory, waited for in sequence order
+  // (plain loads when X is not TMA-aligned)
+  auto slab = [&](uint64_t k, bool& ok) -> const float* {
+    float* st = stages + (size_t)(k % nst) * rows_box * W;
+    if (tma) {
+      int w = 1;
+      if (tid == 0) w = mbar_wait_bounded(&full[k % nst], (uint32_t)((k / nst) & 1), p.timeout_ns) ? 1 : 0;
+      ++waited;
+      if (__syncthreads_or(w ? 0 : 1)) ok = false;
+    } else {
+      const int64_t c0 = (int64_t)(k % (uint64_t)nblk) * W;
+      for (int idx = tid; idx < rows * W; idx += WNT) {
+        const int r = idx / W, c = idx % W;
+        st[idx] = (c0 + c < n) ? p.X[(r0 + r) * p.ld + c0 + c] : 0.f;
+      }
+      __syncthreads();
+    }
+    return st;
+  };
 
   int err = DEV_OK;
   int status = HPSCD_ERR_NOT_CONVERGED;
   const double ynorm = sqrt(*p.ysq);
   double r_prev = 0.0;
   int64_t sweeps = 0;
-  uint64_t kseq = 0;     // block sequence number (all sweeps)
-  uint64_t xround = 0;   // exchange rounds (dots)
-  uint64_t nround = 0;   // exchange rounds (norms)
+  uint64_t nround = 0;  // norm exchange rounds
+  uint64_t pushed = 0;  // dot exchange rounds pushed by this CTA (every CTA pushes the same)
 
   // the residual norm of the CTA's rows, exchanged to every CTA (fixed-order sum)
   auto cluster_norm = [&](double* out) -> bool {
@@ -270,15 +453,53 @@ __global__ void __launch_bounds__(WNT, 1)
       for (int w = 0; w < WNW; ++w) tot += wsum[w];
       const uint32_t dst = mapa_u32(smem_u32(&nbuf[me]), (uint32_t)tid);
       st_cluster_f64(dst, tot);
-      arrive_remote(mapa_u32(smem_u32(&xbar[2 + q]), (uint32_t)tid));
+      arrive_remote(mapa_u32(smem_u32(&nbar[q]), (uint32_t)tid));
     }
-    const bool ok = wait_cluster_bounded(&xbar[2 + q], (uint32_t)((nround / 2) & 1), p.timeout_ns);
+    const bool ok = wait_cluster_bounded(&nbar[q], (uint32_t)((nround / 2) & 1), p.timeout_ns);
     ++nround;
     double t = 0.0;
     for (int c = 0; c < WC; ++c) t += nbuf[c];
     *out = t;
     __syncthreads();  // nbuf is read before the next round overwrites it
     return __syncthreads_or(ok ? 0 : 1) == 0;
+  };
+
+  // this CTA's partials (the warp partials of the row pass, in red), summed
+  // and pushed as round `round` into every CTA of the cluster
+  auto push_round = [&](uint64_t round) {
+    if (tid < W) {
+      float v = 0.f;
+#pragma unroll
+      for (int w = 0; w < WNW; ++w) v += red[w * W + tid];
+      qs[tid] = v;  // qs is free here (it is refilled at step 1)
+    }
+    __syncthreads();
+    const int slot = (int)(round % XSLOTS);
+    // thread t < WC·W/4 stores float4 (t % (W/4)) of the partials into CTA t / (W/4)
+    constexpr int Q = W / 4;
+    if (tid < WC * Q) {
+      const int dstc = tid / Q, j4 = tid % Q;
+      const uint32_t dst = mapa_u32(smem_u32(&xbuf[(slot * 16 + me) * W + 4 * j4]), (uint32_t)dstc);
+      const uint32_t bar = mapa_u32(smem_u32(&xbar[slot]), (uint32_t)dstc);
+      st_async_v4(dst, reinterpret_cast<const float4*>(qs)[j4], bar);
+    }
+    ++pushed;
+    __syncthreads();  // qs is rewritten by step 1 only after every pushing thread read it
+  };
+
+  // dots only (no update): the prologue's rounds 0 and 1 against the initial e
+  auto dots_only = [&](const float* st) {
+    float pd[CPL];
+#pragma unroll
+    for (int c = 0; c < CPL; ++c) pd[c] = 0.f;
+    for (int r = warp; r < rows; r += WNW) {
+      const float er = es[r];
+#pragma unroll
+      for (int c = 0; c < CPL; ++c) pd[c] = fmaf(st[r * W + CPL * lane + c], er, pd[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < CPL; ++c) red[warp * W + CPL * lane + c] = pd[c];
+    __syncthreads();
   };
 
   double enorm2 = 0.0;
@@ -293,154 +514,146 @@ __global__ void __launch_bounds__(WNT, 1)
   }
   r_prev = rel;
 
-  // Gram block of column block b -> gblk[b & 1], by cp.async (16 bytes per thread-step)
-  // buffer (k & 1) holds the Gram of block k % nblk, k the block sequence number
-  auto prefetch_gram = [&](uint64_t k) {
-    const float* src = p.Gb + (int64_t)(k % (uint64_t)nblk) * (WW * WW);
-    float* dst = gblk + (k & 1) * (WW * WW);
-    for (int i = tid; i < WW * WW / 4; i += WNT)
-      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst + 4 * i)),
-                   "l"(src + 4 * i)
-                   : "memory");
+  // chain operands: thread (row ci = tid / 8, part cj = tid % 8) takes columns
+  // [cj·CPT, (cj+1)·CPT) of row ci of M_b and N_b; both matrices of the next
+  // block are copied into the other buffer by cp.async while this one is used
+  const int ci = tid / 8, cj = tid % 8;
+  const bool chain_thread = tid < 8 * W;
+  auto load_mn = [&](int64_t b, int buf) {
+    float* dst = mn + (size_t)buf * 2 * W * W;
+    const float* srcm = p.Mb + b * (W * W);
+    const float* srcn = p.Nb + b * (W * W);
+    for (int i = tid; i < W * W / 4; i += WNT) {
+      cp_async16(dst + 4 * i, srcm + 4 * i);
+      cp_async16(dst + W * W + 4 * i, srcn + 4 * i);
+    }
     asm volatile("cp.async.commit_group;" ::: "memory");
   };
-  prefetch_gram(0);
 
+  if (status == -1 && err == DEV_OK) {
+    // prologue: rounds 0 and 1, the dots of sequences 0 and 1 against the initial e
+    bool ok = true;
+    for (uint64_t k = 0; k < 2 && ok; ++k) {
+      const float* st = slab(k, ok);
+      if (!ok) break;
+      dots_only(st);
+      push_round(k);
+    }
+    if (!ok) err = DEV_TIMEOUT_COPY;
+    load_mn(0, 0);
+  }
+
+  uint64_t kseq = 0;  // block sequence number (all sweeps)
   for (int64_t sw = 1; status == -1 && err == DEV_OK; ++sw) {
     for (int64_t b = 0; b < nblk; ++b, ++kseq) {
-      const int s = (int)(kseq % nst);
-      prefetch_gram(kseq + 1);  // the next block's Gram, while this one is worked on
-      float* st = stages + (size_t)s * rows_box * WW;
-      bool ok = true;
-      if (tma) {
-        ok = mbar_wait_bounded(&full[s], (uint32_t)((kseq / nst) & 1), p.timeout_ns);
-      } else {
-        // plain loads (row stride not 16-byte aligned); the stage was released
-        // by the barrier that ended the previous block
-        const int64_t c0 = b * WW;
-        for (int idx = tid; idx < rows * WW; idx += WNT) {
-          const int r = idx / WW, c = idx % WW;
-          st[idx] = (c0 + c < n) ? p.X[(r0 + r) * p.ld + c0 + c] : 0.f;
-        }
-        __syncthreads();
+      // 1. round kseq: the partials of block b against e_{k-2}, summed in CTA order
+      const int slot = (int)(kseq % XSLOTS);
+      int wok = 1;
+      if (tid == 0) wok = wait_cluster_bounded(&xbar[slot], (uint32_t)((kseq / XSLOTS) & 1), p.timeout_ns) ? 1 : 0;
+      asm volatile("cp.async.wait_group 0;" ::: "memory");  // this block's M_b, N_b
+      if (__syncthreads_or(wok ? 0 : 1)) { err = DEV_TIMEOUT_BARRIER; break; }
+      if (tid < W) {
+        float g = 0.f;
+        for (int c = 0; c < WC; ++c) g += xbuf[(slot * 16 + c) * W + tid];
+        qs[tid] = g;
       }
-      // 1. partial dots: warp w takes rows w, w+16, ...; lane the column pair 2·lane
-      float p0 = 0.f, p1 = 0.f;
-      if (ok) {
-        for (int r = warp; r < rows; r += WNW) {
-          const float2 xv = *reinterpret_cast<const float2*>(st + r * WW + 2 * lane);
-          const float er = es[r];
-          p0 = fmaf(xv.x, er, p0);
-          p1 = fmaf(xv.y, er, p1);
-        }
-      }
-      red[warp * WW + 2 * lane] = p0;
-      red[warp * WW + 2 * lane + 1] = p1;
+      __syncthreads();
+      // the slot is free: arm it for round kseq + 4 (every push of that round follows)
+      if (tid == 0) mbar_arrive_expect_tx(&xbar[slot], round_bytes);
       stamp(0);
-      if (__syncthreads_or(ok ? 0 : 1)) { err = DEV_TIMEOUT_COPY; break; }
-      if (tma) ++waited;
-      // 2. push this CTA's partials to every CTA of the cluster: thread t < WC
-      //    stores the 64 sums into CTA t and then release-arrives on its barrier
-      const int q = (int)(xround & 1);
-      if (tid < WW) {
-        float v = 0.f;
+      // 2. the block's steps: da_b = M_b q_b - N_b da_{b-1}
+      const int cur = (int)(kseq & 1);
+      if (chain_thread) {
+        const float* mrow = mn + (size_t)cur * 2 * W * W + ci * W + cj * CPT;
+        const float* nrow = mrow + W * W;
+        float acc = 0.f;
 #pragma unroll
-        for (int w = 0; w < WNW; ++w) v += red[w * WW + tid];
-        psum[tid] = v;
+        for (int c = 0; c < CPT; c += 4) {
+          const float4 mv = *reinterpret_cast<const float4*>(mrow + c);
+          const float4 nv = *reinterpret_cast<const float4*>(nrow + c);
+          const float* q = qs + cj * CPT + c;
+          const float* d = dap_s + cj * CPT + c;
+          acc = fmaf(mv.x, q[0], acc);
+          acc = fmaf(mv.y, q[1], acc);
+          acc = fmaf(mv.z, q[2], acc);
+          acc = fmaf(mv.w, q[3], acc);
+          acc = fmaf(-nv.x, d[0], acc);
+          acc = fmaf(-nv.y, d[1], acc);
+          acc = fmaf(-nv.z, d[2], acc);
+          acc = fmaf(-nv.w, d[3], acc);
+        }
+        acc += __shfl_xor_sync(FULL_MASK, acc, 1);
+        acc += __shfl_xor_sync(FULL_MASK, acc, 2);
+        acc += __shfl_xor_sync(FULL_MASK, acc, 4);
+        if (cj == 0) da_s[ci] = acc;
       }
       __syncthreads();
       stamp(1);
-      if (tid < WC) {
-        const uint32_t dst = mapa_u32(smem_u32(&xbuf[(q * 16 + me) * WW]), (uint32_t)tid);
-        const float4* src = reinterpret_cast<const float4*>(psum);
-#pragma unroll
-        for (int j4 = 0; j4 < WW / 4; ++j4) {
-          const float4 v = src[j4];
-          asm volatile("st.shared::cluster.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(dst + 16 * j4),
-                       "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w)
-                       : "memory");
-        }
-        arrive_remote(mapa_u32(smem_u32(&xbar[q]), (uint32_t)tid));
-      }
-      ok = wait_cluster_bounded(&xbar[q], (uint32_t)((xround / 2) & 1), p.timeout_ns);
-      ++xround;
+      load_mn(b + 1 < nblk ? b + 1 : 0, cur ^ 1);  // the next block's, used one iteration later
+      if (me == 0 && tid < W && b * W + tid < n) p.dsw[b * W + tid] = da_s[tid];
+      if (tid < W) dap_s[tid] = da_s[tid];
       stamp(2);
-      // 3. sum in a fixed order, then the block's chain in warp 0
-      if (tid < WW) {
-        float g = 0.f;
-        for (int c = 0; c < WC; ++c) g += xbuf[(q * 16 + c) * WW + tid];
-        gsum[tid] = g;
-      }
-      asm volatile("cp.async.wait_group 1;" ::: "memory");  // this block's Gram has landed
-      if (__syncthreads_or(ok ? 0 : 1)) { err = DEV_TIMEOUT_BARRIER; break; }
-      if (warp == 0) {
-        const float* Gb = gblk + (kseq & 1) * (WW * WW);
-        const int64_t c0 = b * WW;
-        // the ⊘ step on the block's numerators (elementwise, off the chain),
-        // then da_k = s_k - sum_{l<k} H_kl da_l with H = D^{-1}·(strict lower G):
-        // lane owns block rows lane (slot 0) and lane + 32 (slot 1)
-        // Gb holds the block transposed: entry (i, k) at Gb[k * WW + i]
-        const float d_0 = (c0 + lane < n) ? Gb[lane * WW + lane] : 0.f;
-        const float d_1 = (c0 + lane + 32 < n) ? Gb[(lane + 32) * WW + lane + 32] : 0.f;
-        float s_0 = d_0 > 0.f ? gsum[lane] / d_0 : 0.f;
-        float s_1 = d_1 > 0.f ? gsum[lane + 32] / d_1 : 0.f;
-        float m_0 = 0.f, m_1 = 0.f;
-#pragma unroll
-        for (int k = 0; k < 32; ++k) {
-          const float h0 = Gb[k * WW + lane];
-          const float h1 = Gb[k * WW + lane + 32];
-          const float qk = __shfl_sync(FULL_MASK, s_0, k);
-          if (lane == k) m_0 = qk;
-          if (lane > k) s_0 = fmaf(-h0, qk, s_0);
-          s_1 = fmaf(-h1, qk, s_1);
-        }
-#pragma unroll
-        for (int k = 0; k < 32; ++k) {
-          const float h1 = Gb[(32 + k) * WW + lane + 32];
-          const float qk = __shfl_sync(FULL_MASK, s_1, k);
-          if (lane == k) m_1 = qk;
-          if (lane > k) s_1 = fmaf(-h1, qk, s_1);
-        }
-        da_s[lane] = m_0;
-        da_s[lane + 32] = m_1;
-      }
-      __syncthreads();
+      // 3. the row pass: e_r -= X_b[r]·da_b, then the partial X_{b+2}^T e
+      bool ok = true;
+      const float* sk = stages + (size_t)(kseq % nst) * rows_box * W;  // waited for two blocks ago
+      const float* s2 = slab(kseq + 2, ok);
+      if (!ok) { err = DEV_TIMEOUT_COPY; break; }
       stamp(3);
-      // 4. e <- e - X_block·da for this CTA's rows; a += da (CTA 0).  Four
-      //    threads per row, 16 columns each, walked from a start that depends
-      //    on the row and on the part (parts 0 and 2, 1 and 3 share banks), so
-      //    the 32 lanes of a warp read 32 different banks at every step.
-      // the bound is a multiple of 32: every lane of a warp takes the same trip
-      // count, as the full-mask shuffles below require
-      const int nt4 = ((4 * rows_box + 31) / 32) * 32;
-      for (int t = tid; t < nt4; t += WNT) {
-        const int r = t >> 2, part = t & 3;
-        float acc0 = 0.f, acc1 = 0.f;
-        if (r < rows) {
-          const float* xr = st + r * WW + 16 * part;
-          const float* dr = da_s + 16 * part;
-          const int sh = r + 8 * (part >> 1);
+      {
+        float dl[CPL], pd[CPL];
 #pragma unroll
-          for (int j = 0; j < 16; j += 2) {
-            const int c0i = (j + sh) & 15, c1i = (j + 1 + sh) & 15;
-            acc0 = fmaf(xr[c0i], dr[c0i], acc0);
-            acc1 = fmaf(xr[c1i], dr[c1i], acc1);
+        for (int c = 0; c < CPL; ++c) { dl[c] = da_s[CPL * lane + c]; pd[c] = 0.f; }
+        for (int rb = warp; rb < rows; rb += 8 * WNW) {
+          // up to 8 rows of this warp at once: independent shuffle reductions
+          float u[8];
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const int r = rb + i * WNW;
+            float v = 0.f;
+            if (r < rows) {
+              if constexpr (CPL == 2) {
+                const float2 x2 = *reinterpret_cast<const float2*>(sk + r * W + 2 * lane);
+                v = fmaf(x2.x, dl[0], x2.y * dl[CPL - 1]);
+              } else {
+                v = sk[r * W + lane] * dl[0];
+              }
+            }
+            u[i] = v;
+          }
+#pragma unroll
+          for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+            for (int i = 0; i < 8; ++i) u[i] += __shfl_xor_sync(FULL_MASK, u[i], off);
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const int r = rb + i * WNW;
+            if (r < rows) {
+              const float er = es[r] - u[i];
+              if constexpr (CPL == 2) {
+                const float2 y2 = *reinterpret_cast<const float2*>(s2 + r * W + 2 * lane);
+                pd[0] = fmaf(y2.x, er, pd[0]);
+                pd[CPL - 1] = fmaf(y2.y, er, pd[CPL - 1]);
+              } else {
+                pd[0] = fmaf(s2[r * W + lane], er, pd[0]);
+              }
+              __syncwarp();
+              if (lane == 0) es[r] = er;
+            }
           }
         }
-        float acc = acc0 + acc1;
-        acc += __shfl_xor_sync(FULL_MASK, acc, 1);
-        acc += __shfl_xor_sync(FULL_MASK, acc, 2);
-        if (part == 0 && r < rows) es[r] -= acc;
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) red[warp * W + CPL * lane + c] = pd[c];
       }
-      // this sweep's da of the block, store only (a is updated after the sweep)
-      if (me == 0 && tid < WW && b * WW + tid < n) p.dsw[b * WW + tid] = da_s[tid];
-      __syncthreads();  // the stage and da_s are free
+      __syncthreads();  // e, red complete; slab kseq is free
       stamp(4);
-      ++trace_k;
       if (tid == 0 && tma) {
         fence_proxy_async_smem();
-        issue(issued++);
+        issue(issued++);  // sequence kseq + nst into the stage just released
       }
+      // 4. push round kseq + 2
+      push_round(kseq + 2);
+      stamp(5);
+      ++trace_k;
     }
     if (err != DEV_OK) break;
     sweeps = sw;
@@ -461,13 +674,21 @@ __global__ void __launch_bounds__(WNT, 1)
 
   // drain copies in flight; write e and the results
   asm volatile("cp.async.wait_all;" ::: "memory");
-  if (tid == 0) {
+  if (tid == 0 && tma) {
     for (uint64_t k = waited; k < issued; ++k)
       if (!mbar_wait_bounded(&full[k % nst], (uint32_t)((k / nst) & 1), p.timeout_ns)) {
         if (err == DEV_OK) err = DEV_TIMEOUT_COPY;
         break;
       }
   }
+  // the rounds pushed into this CTA but not consumed: their bytes land before
+  // the CTA may exit (bounded; in an error exit some never complete)
+  if (tid == 0 && err == DEV_OK)
+    for (uint64_t r = kseq; r < pushed; ++r)
+      if (!wait_cluster_bounded(&xbar[r % XSLOTS], (uint32_t)((r / XSLOTS) & 1), p.timeout_ns)) {
+        err = DEV_TIMEOUT_BARRIER;
+        break;
+      }
   for (int r = tid; r < rows; r += WNT) p.e[r0 + r] = es[r];
   if (err != DEV_OK && tid == 0) atomicCAS(&p.ctl->err, DEV_OK, err);
   if (me == 0 && tid == 0) {
@@ -511,6 +732,10 @@ __global__ void wide_init_kernel(const float* __restrict__ a_in, int warm, doubl
   }
 }
 
+namespace {
+int wide_setup_smem(int W) { return (32 * (2 * W + 4) + 3 * W * (W + 4) + W) * 4; }
+}  // namespace
+
 bool wide_config(int64_t m, int max_smem, WideConfig* cfg) {
   if (m < 1 || m > 4096) return false;
   int csize = 16;
@@ -518,14 +743,13 @@ bool wide_config(int64_t m, int max_smem, WideConfig* cfg) {
   cfg->csize = csize;
   cfg->rows_box = (int)((m + csize - 1) / csize);
   if (cfg->rows_box > 256) return false;
-  const int stage = cfg->rows_box * WW * 4;
-  const int fixed = 1024 + ((cfg->rows_box + 3) & ~3) * 4 + 2 * 16 * WW * 4 + WNW * WW * 4 + 3 * WW * 4 +
-                    2 * WW * WW * 4 + 16 * 8 + WNW * 8 + 16 * 8 + 256;
-  int nst = (max_smem - fixed) / stage;
-  if (nst > 8) nst = 8;
-  if (nst < 2) return false;
+  // slabs of blocks b, b+1, b+2 stay resident with at least one copy ahead
+  cfg->W = cfg->rows_box <= 128 ? 64 : 32;
+  int nst = 6;
+  while (nst >= 4 && wide_smem_plan(cfg->W, cfg->rows_box, nst).total > max_smem) --nst;
+  if (nst < 4) return false;
   cfg->nstages = nst;
-  cfg->smem_bytes = fixed + nst * stage;
+  cfg->smem_bytes = wide_smem_plan(cfg->W, cfg->rows_box, nst).total;
   return true;
 }
 
@@ -538,16 +762,25 @@ cudaError_t launch_true_residual(const float* X, int64_t m, int64_t n, int64_t l
   return cudaGetLastError();
 }
 
-cudaError_t launch_sweep_cluster(const WideConfig& cfg, const CUtensorMap* tmap, WideParams p,
-                                 cudaStream_t stream) {
-  cudaError_t e = cudaFuncSetAttribute(wide_sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       cfg.smem_bytes);
+template <int W>
+cudaError_t launch_setup_w(const float* X, int64_t m, int64_t n, int64_t ld, float* Mb, float* Nb,
+                           cudaStream_t stream) {
+  const int64_t nblk = (n + W - 1) / W;
+  const int smem = wide_setup_smem(W);
+  cudaError_t e = cudaFuncSetAttribute(wide_setup_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(wide_sweep_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  wide_setup_kernel<W><<<(unsigned)nblk, 256, smem, stream>>>(X, m, n, ld, nblk, Mb, Nb);
+  return cudaGetLastError();
+}
+
+template <int W>
+cudaError_t launch_cluster_w(const WideConfig& cfg, const CUtensorMap* tmap, const WideParams& p,
+                             cudaStream_t stream) {
+  auto kern = wide_sweep_kernel<W>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, cfg.smem_bytes);
   if (e != cudaSuccess) return e;
-  p.csize = cfg.csize;
-  p.rows_box = cfg.rows_box;
-  p.nstages = cfg.nstages;
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (e != cudaSuccess) return e;
   cudaLaunchConfig_t lc = {};
   lc.gridDim = dim3(cfg.csize);
   lc.blockDim = dim3(WNT);
@@ -560,16 +793,24 @@ cudaError_t launch_sweep_cluster(const WideConfig& cfg, const CUtensorMap* tmap,
   attr[0].val.clusterDim.z = 1;
   lc.attrs = attr;
   lc.numAttrs = 1;
-  return cudaLaunchKernelEx(&lc, wide_sweep_kernel, *tmap, p);
+  return cudaLaunchKernelEx(&lc, kern, *tmap, p);
+}
+
+cudaError_t launch_sweep_cluster(const WideConfig& cfg, const CUtensorMap* tmap, WideParams p,
+                                 cudaStream_t stream) {
+  p.csize = cfg.csize;
+  p.rows_box = cfg.rows_box;
+  p.nstages = cfg.nstages;
+  return cfg.W == 64 ? launch_cluster_w<64>(cfg, tmap, p, stream)
+                     : launch_cluster_w<32>(cfg, tmap, p, stream);
 }
 }  // namespace
 
 cudaError_t launch_wide(const float* X, int64_t m, int64_t n, int64_t ld, const WideConfig& cfg,
                         const CUtensorMap* tmap, WideParams p, const float* y, const float* a_in,
                         int warm, float* a_tmp, cudaStream_t stream) {
-  const int64_t nblk = (n + WW - 1) / WW;
-  wide_gram_blocks_kernel<<<(unsigned)nblk, 256, 0, stream>>>(X, m, n, ld, p.Gb);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e = cfg.W == 64 ? launch_setup_w<64>(X, m, n, ld, p.Mb, p.Nb, stream)
+                              : launch_setup_w<32>(X, m, n, ld, p.Mb, p.Nb, stream);
   if (e != cudaSuccess) return e;
   wide_init_kernel<<<256, 256, 0, stream>>>(a_in, warm, p.a64, a_tmp, n);
   wide_ynorm_kernel<<<1, 256, 0, stream>>>(y, m, p.ysq);
