@@ -100,14 +100,14 @@ __device__ __forceinline__ bool wait_cluster_bounded(uint64_t* bar, uint32_t par
 // One CTA per block b: D = X_b^T [X_b | X_{b-1}] (W x 2W: G = X_b^T X_b and the
 // coupling P = X_b^T X_{b-1} to the previous block, cyclically: block 0's is
 // the last block, which precedes it in the next sweep) over all m rows.  X is
-// staged through shared memory 32 rows at a time (the next rows already in
-// registers); 16 x 16 threads each hold a (W/16) x (2W/16) tile of D, float32
-// products summed in float32 over 256 rows and those sums in float32 again.
+// staged through shared memory 32 rows at a time, double-buffered by cp.async
+// (two CTAs per SM); 16 x 16 threads each hold a (W/16) x (2W/16) tile of D,
+// float32 products summed in float32 over 256 rows and those sums in float32.
 // Then, in shared memory: d = diag(G), H = D^{-1}·strict_lower(G),
 // T = (I + H)^{-1} (column k by forward substitution in thread k),
 // M = T·D^{-1}, N = M·P; M and N are stored row-major [W][W].
 template <int W>
-__global__ void __launch_bounds__(256, 1) wide_setup_kernel(const float* __restrict__ X, int64_t m,
+__global__ void __launch_bounds__(256, 2) wide_setup_kernel(const float* __restrict__ X, int64_t m,
                                                             int64_t n, int64_t ld, int64_t nblk,
                                                             float* __restrict__ Mb,
                                                             float* __restrict__ Nb) {
@@ -118,8 +118,8 @@ __global__ void __launch_bounds__(256, 1) wide_setup_kernel(const float* __restr
   constexpr int WP = W + 4;     // pitch of the W x W matrices
   constexpr int F4 = 32 * W2 / 4 / 256;  // float4 of a tile per thread
   extern __shared__ float wsm[];
-  float* xs = wsm;              // [32][XP]: columns 0..W-1 block b, W..2W-1 block b-1
-  float* Gs = xs + 32 * XP;     // [W][WP]
+  float* xs = wsm;              // [2][32][XP]: columns 0..W-1 block b, W..2W-1 block b-1
+  float* Gs = xs + 2 * 32 * XP; // [W][WP]
   float* Ps = Gs + W * WP;      // [W][WP]
   float* Ts = Ps + W * WP;      // [W][WP] T, then M
   float* dsv = Ts + W * WP;     // [W]
@@ -129,8 +129,9 @@ __global__ void __launch_bounds__(256, 1) wide_setup_kernel(const float* __restr
   const int tid = threadIdx.x;
   const int ty = tid / 16, tx = tid % 16;
   const bool vec = (reinterpret_cast<uintptr_t>(X) & 15) == 0 && (ld & 3) == 0;
-  // float4 q of a tile: row (tid + 256 q) / (W2 / 4), columns 4·((tid + 256 q) % (W2 / 4))
-  auto fetch = [&](int64_t rbase, float4 (&v)[F4]) {
+  // float4 q of a tile: row (tid + 256 q) / (W2 / 4), columns 4·((tid + 256 q) % (W2 / 4));
+  // 16-byte cp.async where the four columns exist and X is aligned, else plain loads
+  auto fetch = [&](int64_t rbase, float* dst) {
 #pragma unroll
     for (int q = 0; q < F4; ++q) {
       const int i = tid + 256 * q;
@@ -138,44 +139,42 @@ __global__ void __launch_bounds__(256, 1) wide_setup_kernel(const float* __restr
       const int64_t row = rbase + r;
       const int64_t col = c < W ? c0 + c : cp0 + (c - W);
       const float* src = X + row * ld + col;
+      float* d = dst + r * XP + c;
       if (row < m && vec && col + 3 < n) {
-        v[q] = __ldg(reinterpret_cast<const float4*>(src));
+        cp_async16(d, src);
       } else {
-        v[q].x = (row < m && col < n) ? __ldg(src) : 0.f;
-        v[q].y = (row < m && col + 1 < n) ? __ldg(src + 1) : 0.f;
-        v[q].z = (row < m && col + 2 < n) ? __ldg(src + 2) : 0.f;
-        v[q].w = (row < m && col + 3 < n) ? __ldg(src + 3) : 0.f;
+        d[0] = (row < m && col < n) ? __ldg(src) : 0.f;
+        d[1] = (row < m && col + 1 < n) ? __ldg(src + 1) : 0.f;
+        d[2] = (row < m && col + 2 < n) ? __ldg(src + 2) : 0.f;
+        d[3] = (row < m && col + 3 < n) ? __ldg(src + 3) : 0.f;
       }
     }
+    asm volatile("cp.async.commit_group;" ::: "memory");
   };
   float acc[TR][TC], acc2[TR][TC];
 #pragma unroll
   for (int i = 0; i < TR; ++i)
 #pragma unroll
     for (int j = 0; j < TC; ++j) { acc[i][j] = 0.f; acc2[i][j] = 0.f; }
-  float4 nxt[F4];
-  fetch(0, nxt);
+  fetch(0, xs);
   int tiles = 0;
-  for (int64_t r0 = 0; r0 < m; r0 += 32) {
-#pragma unroll
-    for (int q = 0; q < F4; ++q) {
-      const int i = tid + 256 * q;
-      const int r = i / (W2 / 4), c = 4 * (i % (W2 / 4));
-      *reinterpret_cast<float4*>(xs + r * XP + c) = nxt[q];
-    }
-    __syncthreads();
-    if (r0 + 32 < m) fetch(r0 + 32, nxt);  // in flight while this tile is used
+  int buf = 0;
+  for (int64_t r0 = 0; r0 < m; r0 += 32, buf ^= 1) {
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    __syncthreads();  // tile r0 landed in buffer buf; buffer buf ^ 1 is free
+    if (r0 + 32 < m) fetch(r0 + 32, xs + (buf ^ 1) * 32 * XP);  // in flight while this tile is used
+    const float* xt = xs + buf * 32 * XP;
 #pragma unroll 4
     for (int r = 0; r < 32; ++r) {
       float av[TR], bv[TC];
 #pragma unroll
       for (int i = 0; i < TR; i += 2) {
-        const float2 t = *reinterpret_cast<const float2*>(xs + r * XP + ty * TR + i);
+        const float2 t = *reinterpret_cast<const float2*>(xt + r * XP + ty * TR + i);
         av[i] = t.x; av[i + 1] = t.y;
       }
 #pragma unroll
       for (int j = 0; j < TC; j += 4) {
-        const float4 t = *reinterpret_cast<const float4*>(xs + r * XP + tx * TC + j);
+        const float4 t = *reinterpret_cast<const float4*>(xt + r * XP + tx * TC + j);
         bv[j] = t.x; bv[j + 1] = t.y; bv[j + 2] = t.z; bv[j + 3] = t.w;
       }
 #pragma unroll
@@ -183,7 +182,6 @@ __global__ void __launch_bounds__(256, 1) wide_setup_kernel(const float* __restr
 #pragma unroll
         for (int j = 0; j < TC; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
     }
-    __syncthreads();
     if (++tiles == 8) {
       tiles = 0;
 #pragma unroll
@@ -411,15 +409,18 @@ __global__ void __launch_bounds__(WNT, 1)
   };
   if (tid == 0 && tma)
     while (issued < (uint64_t)nst) issue(issued++);
-  // the slab of sequence k in shared memory, waited for in sequence order
-  // (plain loads when X is not TMA-aligned)
+  // the slab of sequence k in shared memory, waited for in sequence order by
+  // every warp itself (lane 0 polls the copy's mbarrier); plain loads and a CTA
+  // barrier when X is not TMA-aligned.  ok turns false when a wait gave up.
   auto slab = [&](uint64_t k, bool& ok) -> const float* {
     float* st = stages + (size_t)(k % nst) * rows_box * W;
     if (tma) {
       int w = 1;
-      if (tid == 0) w = mbar_wait_bounded(&full[k % nst], (uint32_t)((k / nst) & 1), p.timeout_ns) ? 1 : 0;
+      if (lane == 0) w = mbar_wait_bounded(&full[k % nst], (uint32_t)((k / nst) & 1), p.timeout_ns) ? 1 : 0;
+      w = __shfl_sync(FULL_MASK, w, 0);
+      __syncwarp();
       ++waited;
-      if (__syncthreads_or(w ? 0 : 1)) ok = false;
+      if (!w) ok = false;
     } else {
       const int64_t c0 = (int64_t)(k % (uint64_t)nblk) * W;
       for (int idx = tid; idx < rows * W; idx += WNT) {
@@ -464,31 +465,31 @@ __global__ void __launch_bounds__(WNT, 1)
     return __syncthreads_or(ok ? 0 : 1) == 0;
   };
 
-  // this CTA's partials (the warp partials of the row pass, in red), summed
-  // and pushed as round `round` into every CTA of the cluster
+  // this CTA's partials (the warp partials of the row pass, in red, complete
+  // after a CTA barrier), pushed as round `round` into every CTA of the
+  // cluster: thread j < W/4 of warp 0 sums float4 j over the warps and stores
+  // it into every CTA by st.async (no barrier: red is next written after two)
   auto push_round = [&](uint64_t round) {
-    if (tid < W) {
-      float v = 0.f;
-#pragma unroll
-      for (int w = 0; w < WNW; ++w) v += red[w * W + tid];
-      qs[tid] = v;  // qs is free here (it is refilled at step 1)
-    }
-    __syncthreads();
-    const int slot = (int)(round % XSLOTS);
-    // thread t < WC·W/4 stores float4 (t % (W/4)) of the partials into CTA t / (W/4)
     constexpr int Q = W / 4;
-    if (tid < WC * Q) {
-      const int dstc = tid / Q, j4 = tid % Q;
-      const uint32_t dst = mapa_u32(smem_u32(&xbuf[(slot * 16 + me) * W + 4 * j4]), (uint32_t)dstc);
-      const uint32_t bar = mapa_u32(smem_u32(&xbar[slot]), (uint32_t)dstc);
-      st_async_v4(dst, reinterpret_cast<const float4*>(qs)[j4], bar);
+    if (tid < Q) {
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int w = 0; w < WNW; ++w) {
+        const float4 t = *reinterpret_cast<const float4*>(red + w * W + 4 * tid);
+        v.x += t.x; v.y += t.y; v.z += t.z; v.w += t.w;
+      }
+      const int slot = (int)(round % XSLOTS);
+      const uint32_t src = smem_u32(&xbuf[(slot * 16 + me) * W + 4 * tid]);
+      const uint32_t bar = smem_u32(&xbar[slot]);
+      for (int dstc = 0; dstc < WC; ++dstc)
+        st_async_v4(mapa_u32(src, (uint32_t)dstc), v, mapa_u32(bar, (uint32_t)dstc));
     }
     ++pushed;
-    __syncthreads();  // qs is rewritten by step 1 only after every pushing thread read it
   };
 
   // dots only (no update): the prologue's rounds 0 and 1 against the initial e
   auto dots_only = [&](const float* st) {
+    __syncthreads();  // the previous round's push has read red
     float pd[CPL];
 #pragma unroll
     for (int c = 0; c < CPL; ++c) pd[c] = 0.f;
@@ -535,7 +536,7 @@ __global__ void __launch_bounds__(WNT, 1)
     bool ok = true;
     for (uint64_t k = 0; k < 2 && ok; ++k) {
       const float* st = slab(k, ok);
-      if (!ok) break;
+      if (__syncthreads_or(ok ? 0 : 1)) { ok = false; break; }  // the same decision in every warp
       dots_only(st);
       push_round(k);
     }
@@ -546,18 +547,27 @@ __global__ void __launch_bounds__(WNT, 1)
   uint64_t kseq = 0;  // block sequence number (all sweeps)
   for (int64_t sw = 1; status == -1 && err == DEV_OK; ++sw) {
     for (int64_t b = 0; b < nblk; ++b, ++kseq) {
-      // 1. round kseq: the partials of block b against e_{k-2}, summed in CTA order
+      // 1. round kseq: the partials of block b against e_{k-2}, summed in CTA
+      //    order by the warps of threads < W, which wait for the round themselves
       const int slot = (int)(kseq % XSLOTS);
       int wok = 1;
-      if (tid == 0) wok = wait_cluster_bounded(&xbar[slot], (uint32_t)((kseq / XSLOTS) & 1), p.timeout_ns) ? 1 : 0;
+      if (warp * 32 < W) {
+        if (lane == 0) wok = wait_cluster_bounded(&xbar[slot], (uint32_t)((kseq / XSLOTS) & 1), p.timeout_ns) ? 1 : 0;
+        wok = __shfl_sync(FULL_MASK, wok, 0);
+        __syncwarp();
+        if (wok && tid < W) {
+          // loads issued together (WC <= 16), summed in CTA order
+          float v[16];
+#pragma unroll
+          for (int c = 0; c < 16; ++c) v[c] = c < WC ? xbuf[(slot * 16 + c) * W + tid] : 0.f;
+          float g = 0.f;
+#pragma unroll
+          for (int c = 0; c < 16; ++c) g += v[c];
+          qs[tid] = g;
+        }
+      }
       asm volatile("cp.async.wait_group 0;" ::: "memory");  // this block's M_b, N_b
       if (__syncthreads_or(wok ? 0 : 1)) { err = DEV_TIMEOUT_BARRIER; break; }
-      if (tid < W) {
-        float g = 0.f;
-        for (int c = 0; c < WC; ++c) g += xbuf[(slot * 16 + c) * W + tid];
-        qs[tid] = g;
-      }
-      __syncthreads();
       // the slot is free: arm it for round kseq + 4 (every push of that round follows)
       if (tid == 0) mbar_arrive_expect_tx(&xbar[slot], round_bytes);
       stamp(0);
@@ -596,8 +606,7 @@ __global__ void __launch_bounds__(WNT, 1)
       // 3. the row pass: e_r -= X_b[r]·da_b, then the partial X_{b+2}^T e
       bool ok = true;
       const float* sk = stages + (size_t)(kseq % nst) * rows_box * W;  // waited for two blocks ago
-      const float* s2 = slab(kseq + 2, ok);
-      if (!ok) { err = DEV_TIMEOUT_COPY; break; }
+      const float* s2 = slab(kseq + 2, ok);  // a failed wait is acted on after the pass
       stamp(3);
       {
         float dl[CPL], pd[CPL];
@@ -644,7 +653,8 @@ __global__ void __launch_bounds__(WNT, 1)
 #pragma unroll
         for (int c = 0; c < CPL; ++c) red[warp * W + CPL * lane + c] = pd[c];
       }
-      __syncthreads();  // e, red complete; slab kseq is free
+      // e, red complete; slab kseq is free
+      if (__syncthreads_or(ok ? 0 : 1)) { err = DEV_TIMEOUT_COPY; break; }
       stamp(4);
       if (tid == 0 && tma) {
         fence_proxy_async_smem();
@@ -733,7 +743,7 @@ __global__ void wide_init_kernel(const float* __restrict__ a_in, int warm, doubl
 }
 
 namespace {
-int wide_setup_smem(int W) { return (32 * (2 * W + 4) + 3 * W * (W + 4) + W) * 4; }
+int wide_setup_smem(int W) { return (2 * 32 * (2 * W + 4) + 3 * W * (W + 4) + W) * 4; }
 }  // namespace
 
 bool wide_config(int64_t m, int max_smem, WideConfig* cfg) {
