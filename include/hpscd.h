@@ -64,7 +64,10 @@ typedef enum {
   HPSCD_ERR_NO_MEMORY = 7      /* workspace allocation failed or is too small */
 } hpscd_status;
 
-typedef enum { HPSCD_F32 = 0, HPSCD_BF16 = 1 } hpscd_dtype;
+/* Storage type of X.  Every type is widened exactly to float32 when read; the
+ * arithmetic is the same for all three (float32 products and sums, float64
+ * where stated). */
+typedef enum { HPSCD_F32 = 0, HPSCD_BF16 = 1, HPSCD_F16 = 2 } hpscd_dtype;
 typedef enum { HPSCD_COL_MAJOR = 0, HPSCD_ROW_MAJOR = 1 } hpscd_layout;
 typedef enum {
   HPSCD_STOP_REL_RES = 0,
@@ -146,13 +149,20 @@ int hpscd_set_workspace(hpscd_ctx* ctx, void* ptr, size_t bytes);
 
 /*
  * Solve X·a ≈ y by sweeps of Algorithm 1 (Sec. 2) on the GPU.
- *   X      device, dtype HPSCD_F32 (float) or HPSCD_BF16 (bfloat16), layout/ld
- *          as above.  Column-major: any m, n <= 512 (tall and square systems;
- *          float32 or bfloat16).  Row-major: float32, any n, m <= 4096 (wide
- *          systems; TMA tiles when X is 16-byte aligned and ld a multiple
- *          of 4, plain loads otherwise): one
- *          thread-block cluster walks the column chain with TMA-re-tiled
- *          row-major blocks).  Other combinations return HPSCD_ERR_UNSUPPORTED.
+ *   X      device, dtype HPSCD_F32, HPSCD_BF16 or HPSCD_F16, layout/ld as above;
+ *          every shape is taken (m, n >= 0), by one of three sweeps:
+ *            column-major, n <= 512: the persistent tall sweep (tall and
+ *              square systems; TMA tiles when X is 16-byte aligned and ld·size
+ *              a multiple of 16, plain loads otherwise);
+ *            column-major, n > 512: the persistent panel sweep (the columns in
+ *              panels of 512 in the paper's order; X is read twice per sweep);
+ *            row-major, m <= 4096: one thread-block cluster walks the column
+ *              chain (wide systems); 16-bit X is first widened to a float32
+ *              copy in the workspace (m·n·4 bytes, values exact);
+ *            row-major, m > 4096: X is first transposed to a column-major
+ *              copy in the workspace (n·m bytes of its own type), then as
+ *              column-major.
+ *          The copies are made once per call, as part of the set-up.
  *   y      device float[m].
  *   a      device float[n]; in: the initial guess when a_is_guess != 0
  *          (Algorithm 2's "or initial guess"), ignored otherwise (0_n);

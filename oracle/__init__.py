@@ -19,7 +19,7 @@ _LIB = os.path.join(_HERE, "_build", "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-DTYPES = {"f32": 0, "bf16": 1, "f64": 2}
+DTYPES = {"f32": 0, "bf16": 1, "f64": 2, "f16": 3}
 LAYOUTS = {"col": 0, "row": 1}
 STOP = {"rel_res": 0, "rel_change": 1, "none": 2}
 STATUS = {0: "ok", 1: "invalid", 2: "not_converged", 3: "nonfinite", 4: "nomem"}
@@ -86,7 +86,7 @@ def _ptr(a):
 
 
 def _check_x(X, m, n, layout, dtype):
-    exp = {"f32": np.float32, "bf16": np.uint16, "f64": np.float64}[dtype]
+    exp = {"f32": np.float32, "bf16": np.uint16, "f64": np.float64, "f16": np.float16}[dtype]
     if X.dtype != exp or not X.flags.c_contiguous:
         raise TypeError(f"X must be C-contiguous {exp}")
     shape = (n, m) if layout == "col" else (m, n)

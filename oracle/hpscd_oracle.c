@@ -8,8 +8,8 @@
  *
  * Arithmetic: IEEE float64 throughout, strictly sequential summation order
  * (i = 0..m-1), true division.  X is read in its stored type (float32,
- * bfloat16 bit patterns or float64) and promoted exactly to float64, so the
- * system being solved is exactly the stored one.
+ * bfloat16 or IEEE binary16 bit patterns, or float64) and promoted exactly to
+ * float64, so the system being solved is exactly the stored one.
  *
  * Readings of the paper taken here (each is listed in the design notes):
  *   - the residual is e = y - X·a (Algorithm 1, the initialisation of e, and
@@ -35,6 +35,7 @@
 #define OR_F32 0
 #define OR_BF16 1
 #define OR_F64 2
+#define OR_F16 3
 #define OR_COL 0
 #define OR_ROW 1
 #define OR_STOP_REL_RES 0
@@ -53,11 +54,25 @@ static double bf16_to_f64(uint16_t b) {
   return (double)f;
 }
 
+/* IEEE 754 binary16 bit pattern to float64, from the format's definition:
+ * sign, 5 exponent bits (bias 15), 10 fraction bits; exponent 0 holds the
+ * subnormals fraction·2^-24, exponent 31 the infinities and NaNs.  Every
+ * binary16 value is exact in float64. */
+static double f16_to_f64(uint16_t h) {
+  const int ex = (h >> 10) & 31, fr = h & 1023;
+  double v;
+  if (ex == 0) v = ldexp((double)fr, -24);
+  else if (ex == 31) v = fr ? NAN : INFINITY;
+  else v = ldexp((double)(fr + 1024), ex - 25);
+  return (h & 0x8000) ? -v : v;
+}
+
 /* Element X(i, j) promoted to float64. */
 static double x_elem(const void* X, int dt, int lay, int64_t ld, int64_t i, int64_t j) {
   int64_t idx = (lay == OR_COL) ? j * ld + i : i * ld + j;
   if (dt == OR_F32) return (double)((const float*)X)[idx];
   if (dt == OR_BF16) return bf16_to_f64(((const uint16_t*)X)[idx]);
+  if (dt == OR_F16) return f16_to_f64(((const uint16_t*)X)[idx]);
   return ((const double*)X)[idx];
 }
 
@@ -72,6 +87,9 @@ static void load_column(const void* X, int dt, int lay, int64_t ld, int64_t m, i
     } else if (dt == OR_BF16) {
       const uint16_t* p = (const uint16_t*)X + base;
       for (int64_t i = 0; i < m; ++i) col[i] = bf16_to_f64(p[i]);
+    } else if (dt == OR_F16) {
+      const uint16_t* p = (const uint16_t*)X + base;
+      for (int64_t i = 0; i < m; ++i) col[i] = f16_to_f64(p[i]);
     } else {
       memcpy(col, (const double*)X + base, (size_t)m * sizeof(double));
     }
@@ -88,7 +106,7 @@ static double norm2(const double* v, int64_t m) {
 
 static int valid_args(const void* X, int dt, int lay, int64_t m, int64_t n, int64_t ld) {
   if (m < 0 || n < 0) return 0;
-  if (dt != OR_F32 && dt != OR_BF16 && dt != OR_F64) return 0;
+  if (dt != OR_F32 && dt != OR_BF16 && dt != OR_F64 && dt != OR_F16) return 0;
   if (lay != OR_COL && lay != OR_ROW) return 0;
   if (lay == OR_COL && ld < (m > 1 ? m : 1)) return 0;
   if (lay == OR_ROW && ld < (n > 1 ? n : 1)) return 0;
@@ -297,6 +315,9 @@ static double dot_rows(const void* X, int dt, int64_t base, const double* e, int
   } else if (dt == OR_BF16) {
     const uint16_t* p = (const uint16_t*)X + base;
     for (int64_t i = i0; i < i1; ++i) s += bf16_to_f64(p[i]) * e[i];
+  } else if (dt == OR_F16) {
+    const uint16_t* p = (const uint16_t*)X + base;
+    for (int64_t i = i0; i < i1; ++i) s += f16_to_f64(p[i]) * e[i];
   } else {
     const double* p = (const double*)X + base;
     for (int64_t i = i0; i < i1; ++i) s += p[i] * e[i];
@@ -311,6 +332,9 @@ static void axpy_rows(const void* X, int dt, int64_t base, double da, double* e,
   } else if (dt == OR_BF16) {
     const uint16_t* p = (const uint16_t*)X + base;
     for (int64_t i = i0; i < i1; ++i) e[i] -= bf16_to_f64(p[i]) * da;
+  } else if (dt == OR_F16) {
+    const uint16_t* p = (const uint16_t*)X + base;
+    for (int64_t i = i0; i < i1; ++i) e[i] -= f16_to_f64(p[i]) * da;
   } else {
     const double* p = (const double*)X + base;
     for (int64_t i = i0; i < i1; ++i) e[i] -= p[i] * da;
@@ -375,6 +399,9 @@ int hpscd_oracle_solve_mt(const void* X, int dt, int lay, int64_t m, int64_t n, 
       } else if (dtc == OR_BF16) {
         const uint16_t* p = (const uint16_t*)Xc + j * ldc;
         for (int64_t i = i0; i < i1; ++i) sq += bf16_to_f64(p[i]) * bf16_to_f64(p[i]);
+      } else if (dtc == OR_F16) {
+        const uint16_t* p = (const uint16_t*)Xc + j * ldc;
+        for (int64_t i = i0; i < i1; ++i) sq += f16_to_f64(p[i]) * f16_to_f64(p[i]);
       } else {
         const double* p = (const double*)Xc + j * ldc;
         for (int64_t i = i0; i < i1; ++i) sq += p[i] * p[i];

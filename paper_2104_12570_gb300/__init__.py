@@ -8,7 +8,8 @@ be built or loaded, every call raises.
 X is a 2-D (m, n) array: a torch tensor on the GPU for solve(), a host array
 (numpy or CPU torch tensor) for solve_host().  Its strides pick the layout:
 stride (1, ld) is column-major, stride (ld, 1) is row-major.  dtypes: float32,
-bfloat16 (torch.bfloat16, or numpy uint16 bit patterns for solve_host).
+bfloat16 (torch.bfloat16, or numpy uint16 bit patterns for solve_host) and IEEE
+binary16 (torch.float16 / numpy float16).
 """
 from __future__ import annotations
 
@@ -27,7 +28,8 @@ __all__ = ["Context", "Batch", "MLP", "solve", "solve_host", "HpscdError", "load
 STATUS = {0: "ok", 1: "invalid_arg", 2: "not_converged", 3: "nonfinite", 4: "timeout",
           5: "cuda_error", 6: "unsupported", 7: "no_memory"}
 STOP = {"rel_res": 0, "rel_change": 1, "none": 2}
-F32, BF16 = 0, 1
+F32, BF16, F16 = 0, 1, 2
+DTYPE_CODES = {"f32": F32, "bf16": BF16, "f16": F16}
 COL, ROW = 0, 1
 
 _lock = threading.Lock()
@@ -219,8 +221,10 @@ def _describe(X):
             dt = F32
         elif X.dtype == torch.bfloat16:
             dt = BF16
+        elif X.dtype == torch.float16:
+            dt = F16
         else:
-            raise TypeError("X dtype must be float32 or bfloat16")
+            raise TypeError("X dtype must be float32, bfloat16 or float16")
         m, n = X.shape
         s0, s1 = X.stride()
         ptr = X.data_ptr()
@@ -232,8 +236,10 @@ def _describe(X):
             dt = F32
         elif X.dtype == np.uint16:
             dt = BF16
+        elif X.dtype == np.float16:
+            dt = F16
         else:
-            raise TypeError("X dtype must be float32 or uint16 (bfloat16 bits)")
+            raise TypeError("X dtype must be float32, uint16 (bfloat16 bits) or float16")
         m, n = X.shape
         s0, s1 = (s // X.itemsize for s in X.strides)
         ptr = X.ctypes.data
@@ -434,10 +440,17 @@ class Context:
         return [{"setup_ms": t.setup_ms, "sweep_ms": t.sweep_ms, "x_bytes": t.x_bytes, "grid": t.grid,
                  "kernel_launches": t.kernel_launches} for t in ts]
 
+    def set_workspace(self, ptr: int, nbytes: int):
+        """Install caller-owned device memory (256-byte aligned) as the workspace;
+        ptr = 0 returns the context to allocating its own."""
+        rc = self._lib.hpscd_set_workspace(self._h, ctypes.c_void_p(int(ptr) or None), int(nbytes))
+        if rc:
+            raise HpscdError(rc)
+
     def workspace_size(self, m, n, dtype="f32", layout="col", **opt_kw) -> int:
         o = make_opts(**opt_kw)
         b = ctypes.c_size_t(0)
-        rc = self._lib.hpscd_workspace_size(self._h, F32 if dtype == "f32" else BF16,
+        rc = self._lib.hpscd_workspace_size(self._h, DTYPE_CODES[dtype],
                                             COL if layout == "col" else ROW, int(m), int(n),
                                             ctypes.byref(o), ctypes.byref(b))
         if rc:

@@ -15,6 +15,7 @@ struct hpscd_ctx {
   bool ws_owned = true;
   double timeout_s = 5.0;
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+  cudaEvent_t ev_rl[2] = {nullptr, nullptr};  // around a set-up relayout of X
   hpscd::GridCtl* ctl_host = nullptr;  // pinned
   double* host_scratch = nullptr;      // pinned, 2 doubles (the wide path's confirmation)
   hpscd_timing last{};

@@ -9,6 +9,8 @@
 //
 // Tiles of 64x64 outputs, split over rows; float32 products accumulated in
 // float32 over 1024-row blocks, then in float64 across blocks and splits.
+#include <cuda_fp16.h>
+
 #include "kernels.h"
 
 namespace hpscd {
@@ -25,6 +27,8 @@ template <>
 __device__ __forceinline__ float to_f<float>(float v) { return v; }
 template <>
 __device__ __forceinline__ float to_f<uint16_t>(uint16_t v) { return bf16_bits_to_float(v); }
+template <>
+__device__ __forceinline__ float to_f<__half>(__half v) { return __half2float(v); }
 
 // grid: (ntile, ksplit); block 256.  Tile t enumerates (I >= J) 64-column blocks.
 template <typename T>
@@ -144,9 +148,12 @@ cudaError_t launch_gram(const void* X, int dtype, int64_t m, int n, int64_t ld, 
   if (dtype == HPSCD_F32)
     gram_partial_kernel<float><<<grid, 256, 0, stream>>>((const float*)X, m, n, ld,
                                                          gp.rows_per_split, partial);
-  else
+  else if (dtype == HPSCD_BF16)
     gram_partial_kernel<uint16_t><<<grid, 256, 0, stream>>>((const uint16_t*)X, m, n, ld,
                                                             gp.rows_per_split, partial);
+  else
+    gram_partial_kernel<__half><<<grid, 256, 0, stream>>>((const __half*)X, m, n, ld,
+                                                          gp.rows_per_split, partial);
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return err;
   const int64_t total = (int64_t)gp.npad * gp.npad;

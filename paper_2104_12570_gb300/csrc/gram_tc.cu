@@ -8,8 +8,9 @@
 // need (at most four; two for float32, whose split doubles a stage) through
 // shared memory by TMA (128-byte swizzle: each column's K elements are the
 // operand's contiguous K-major rows), and accumulates D_IJ = X_I^T X_J in
-// tensor memory (128 columns per tile) with tcgen05.mma issued by one thread.  bfloat16 X: kind::f16 (exact
-// products, float32 accumulation).  float32 X: kind::tf32 on a two-term split
+// tensor memory (128 columns per tile) with tcgen05.mma issued by one thread.
+// bfloat16 or IEEE binary16 X: kind::f16 (exact products, float32
+// accumulation).  float32 X: kind::tf32 on a two-term split
 // x = hi + lo (hi = x rounded to the nearest tf32, written back in place;
 // lo = x - hi rounded to tf32), accumulating hi·hi + hi·lo + lo·hi, which
 // leaves ~2^-22 relative error per product, of either sign.  The tensor-core accumulation loses accuracy on long sums of
@@ -19,6 +20,7 @@
 // the symmetric G.  The same workers also form X^T y and ||y||^2 from those
 // tiles (y read alongside), the dot products of the sweep's starting residual
 // e = y of a cold start, so the sweep does not need a pass over X to form them.
+#include <cuda_fp16.h>
 #include <string.h>
 
 #include "kernels.h"
@@ -56,12 +58,16 @@ __device__ __forceinline__ void tma_load_1d(void* dst, const CUtensorMap* map, u
 
 constexpr int YSTAGE_BYTES = 256;  // one K block of y (64 floats at most)
 
-template <bool TF32>
+// DT: the storage type of X (HPSCD_F32, HPSCD_BF16 or HPSCD_F16).
+template <int DT>
 __global__ void __launch_bounds__(GT_THREADS, 1)
     gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap ymap,
                    const GramTCParams p) {
+  constexpr bool TF32 = DT == HPSCD_F32;
   constexpr int KB = TF32 ? 32 : 64;         // rows of X per 128-byte K block
-  constexpr uint32_t FMT = TF32 ? 2u : 1u;
+  // operand format of the instruction descriptor: tf32 (kind::tf32), else
+  // bf16 or f16 (kind::f16, A and B of the same type)
+  constexpr uint32_t FMT = TF32 ? 2u : (DT == HPSCD_BF16 ? 1u : 0u);
   extern __shared__ unsigned char smem_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -307,7 +313,14 @@ __global__ void __launch_bounds__(GT_THREADS, 1)
             const uint32_t w4[4] = {x.x, x.y, x.z, x.w};
 #pragma unroll
             for (int h = 0; h < 4; ++h) {
-              const float lo16 = __uint_as_float(w4[h] << 16), hi16 = __uint_as_float(w4[h] & 0xffff0000u);
+              float lo16, hi16;  // rows 2h and 2h+1 of the chunk
+              if constexpr (DT == HPSCD_BF16) {
+                lo16 = __uint_as_float(w4[h] << 16);
+                hi16 = __uint_as_float(w4[h] & 0xffff0000u);
+              } else {
+                lo16 = __half2float(__ushort_as_half((unsigned short)(w4[h] & 0xffffu)));
+                hi16 = __half2float(__ushort_as_half((unsigned short)(w4[h] >> 16)));
+              }
               dsq[q] = fmaf(lo16, lo16, fmaf(hi16, hi16, dsq[q]));
               xy[q] = fmaf(lo16, yv[2 * h], fmaf(hi16, yv[2 * h + 1], xy[q]));
             }
@@ -575,17 +588,12 @@ cudaError_t launch_gram_tc(const CUtensorMap* tmap, int dtype, int64_t m, const 
   p.y2part = p.hpart + (size_t)gp.ksplit * gp.npad;
   dim3 grid(gp.ksplit, gp.grp.ngroups);
   cudaError_t e;
-  if (dtype == HPSCD_F32) {
-    e = cudaFuncSetAttribute(gram_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             gp.smem_bytes);
-    if (e != cudaSuccess) return e;
-    gram_tc_kernel<true><<<grid, GT_THREADS, gp.smem_bytes, stream>>>(*tmap, ym, p);
-  } else {
-    e = cudaFuncSetAttribute(gram_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             gp.smem_bytes);
-    if (e != cudaSuccess) return e;
-    gram_tc_kernel<false><<<grid, GT_THREADS, gp.smem_bytes, stream>>>(*tmap, ym, p);
-  }
+  auto kern = dtype == HPSCD_F32    ? gram_tc_kernel<HPSCD_F32>
+              : dtype == HPSCD_BF16 ? gram_tc_kernel<HPSCD_BF16>
+                                    : gram_tc_kernel<HPSCD_F16>;
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, gp.smem_bytes);
+  if (e != cudaSuccess) return e;
+  kern<<<grid, GT_THREADS, gp.smem_bytes, stream>>>(*tmap, ym, p);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int64_t t1 = (int64_t)RED_SLICES * gp.npad * (gp.npad / 4);

@@ -60,7 +60,7 @@ int check_opts(const hpscd_opts* o) {
 }
 
 int check_shape(int dtype, int layout, int64_t m, int64_t n, int64_t ld) {
-  if (dtype != HPSCD_F32 && dtype != HPSCD_BF16) return HPSCD_ERR_INVALID_ARG;
+  if (dtype != HPSCD_F32 && dtype != HPSCD_BF16 && dtype != HPSCD_F16) return HPSCD_ERR_INVALID_ARG;
   if (layout != HPSCD_COL_MAJOR && layout != HPSCD_ROW_MAJOR) return HPSCD_ERR_INVALID_ARG;
   if (m < 0 || n < 0) return HPSCD_ERR_INVALID_ARG;
   if (m > ((int64_t)1 << 31) - 1024 || n > ((int64_t)1 << 31) - 1024) return HPSCD_ERR_INVALID_ARG;
@@ -148,8 +148,7 @@ int encode_tall_map(hpscd_ctx* ctx, const void* X, int dtype, int64_t m, int64_t
   cuuint64_t strides[1] = {(cuuint64_t)ld * es};
   cuuint32_t box[2] = {(cuuint32_t)cfg.rows, (cuuint32_t)cfg.box_cols};
   cuuint32_t estr[2] = {1, 1};
-  CUresult r = ctx->encode(map, dtype == HPSCD_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
-                                                   : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+  CUresult r = ctx->encode(map, x_tmap_type(dtype),
                            2, const_cast<void*>(X), dims, strides, box, estr,
                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -168,8 +167,7 @@ int encode_gram_map(hpscd_ctx* ctx, const void* X, int dtype, int64_t m, int64_t
   cuuint64_t strides[1] = {(cuuint64_t)ld * es};
   cuuint32_t box[2] = {(cuuint32_t)(128 / es), 128};
   cuuint32_t estr[2] = {1, 1};
-  CUresult r = ctx->encode(map, dtype == HPSCD_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
-                                                   : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+  CUresult r = ctx->encode(map, x_tmap_type(dtype),
                            2, const_cast<void*>(X), dims, strides, box, estr,
                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -561,6 +559,263 @@ int solve_device(hpscd_ctx* ctx, const void* X, int dtype, int layout, int64_t m
   return c.status;
 }
 
+
+// ---- column-major X with n > 512: the panel sweep ----
+struct PanelPlan {
+  Plan full, last;  // Gram plans of a full panel and of the last (ragged) one
+  int npanels = 0;
+  int grid = 0;
+  size_t G = 0, Gt = 0, dvec = 0, partial = 0, e = 0, a64 = 0, hacc = 0, npart = 0, ypart = 0,
+         hist = 0, ctl = 0, total = 0;
+};
+
+void panel_gram_plan(const hpscd_ctx* ctx, int dtype, int64_t m, int nq, Plan* g) {
+  g->gp = gram_plan(m, nq, ctx->sms);
+  g->tc_ok = gram_tc_plan(dtype, m, nq, ctx->sms, ctx->max_smem, &g->gtc);
+  g->ldG = PANEL_W;
+}
+
+int make_panel_plan(const hpscd_ctx* ctx, int dtype, int64_t m, int64_t n, const hpscd_opts* o,
+                    PanelPlan* P) {
+  if (n <= 512 || n > ((int64_t)1 << 30)) return HPSCD_ERR_UNSUPPORTED;
+  P->npanels = (int)((n + PANEL_W - 1) / PANEL_W);
+  const int nlast = (int)(n - (int64_t)(P->npanels - 1) * PANEL_W);
+  panel_gram_plan(ctx, dtype, m, PANEL_W, &P->full);
+  panel_gram_plan(ctx, dtype, m, nlast, &P->last);
+  P->grid = ctx->sms;
+  auto pbytes = [](const Plan& g) {
+    return g.tc_ok && g.gtc.partial_bytes > g.gp.partial_bytes ? g.gtc.partial_bytes : g.gp.partial_bytes;
+  };
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = off;
+    off = align_up(off + bytes, 256);
+    return at;
+  };
+  const size_t pw2 = (size_t)PANEL_W * PANEL_W * sizeof(float);
+  P->G = take(pw2);
+  P->Gt = take(pw2 * P->npanels);
+  P->dvec = take((size_t)P->npanels * PANEL_W * sizeof(float));
+  P->partial = take(pbytes(P->full) > pbytes(P->last) ? pbytes(P->full) : pbytes(P->last));
+  P->e = take((size_t)((m + 127) / 128 * 128) * sizeof(float));
+  P->a64 = take((size_t)n * sizeof(double));
+  P->hacc = take((size_t)3 * PANEL_W * sizeof(double));
+  P->npart = take((size_t)2 * P->grid * sizeof(double));
+  P->ypart = take((size_t)P->grid * sizeof(double));
+  P->hist = take((size_t)(o->max_sweeps + 1) * sizeof(double));
+  P->ctl = take(sizeof(GridCtl));
+  P->total = off;
+  return HPSCD_OK;
+}
+
+int solve_panel(hpscd_ctx* ctx, const void* X, int dtype, int64_t m, int64_t n, int64_t ld,
+                const float* y, float* a, int a_is_guess, const hpscd_opts* o, double* hist,
+                int64_t* sweeps_done, double* final_rel_res, const PanelPlan& P) {
+  if (m == 0) return solve_empty_rows(ctx, n, a, a_is_guess, o, hist, sweeps_done, final_rel_res);
+  char* ws = static_cast<char*>(ctx->ws);
+  cudaStream_t st = ctx->stream;
+  GridCtl* ctl = reinterpret_cast<GridCtl*>(ws + P.ctl);
+  float* G = reinterpret_cast<float*>(ws + P.G);
+  float* Gt = reinterpret_cast<float*>(ws + P.Gt);
+  float* dvec = reinterpret_cast<float*>(ws + P.dvec);
+  if (cudaMemsetAsync(ctl, 0, sizeof(GridCtl), st) != cudaSuccess) return HPSCD_ERR_CUDA;
+  if (cudaEventRecord(ctx->ev[0], st) != cudaSuccess) return HPSCD_ERR_CUDA;
+  // the panels' diagonal Gram blocks: G~ = D^{-1} G_QQ and d, panel by panel
+  const int es = esize(dtype);
+  int launches = 0;
+  for (int q = 0; q < P.npanels; ++q) {
+    const int64_t q0 = (int64_t)q * PANEL_W;
+    const int nq = (int)(n - q0 < PANEL_W ? n - q0 : PANEL_W);
+    const Plan& g = (q == P.npanels - 1) ? P.last : P.full;
+    const void* Xq = static_cast<const char*>(X) + (size_t)q0 * (size_t)ld * es;
+    int gl = 0;
+    const int rcg = run_gram(ctx, Xq, dtype, m, nq, ld, g, ws + P.partial, G, PANEL_W, &ctl->err,
+                             (o->debug_flags & HPSCD_DEBUG_SIMT_GRAM) != 0, &gl,
+                             Gt + (size_t)q * PANEL_W * PANEL_W, dvec + q0);
+    if (rcg != HPSCD_OK) return rcg;
+    launches += gl;
+  }
+  if (cudaMemsetAsync(ws + P.hacc, 0, (size_t)3 * PANEL_W * sizeof(double), st) != cudaSuccess)
+    return HPSCD_ERR_CUDA;
+  if (cudaEventRecord(ctx->ev[1], st) != cudaSuccess) return HPSCD_ERR_CUDA;
+  PanelParams p{};
+  p.X = X;
+  p.m = m;
+  p.n = (int)n;
+  p.ld = ld;
+  const uintptr_t vec_align = dtype == HPSCD_F32 ? 16 : 8;
+  p.vec = ((reinterpret_cast<uintptr_t>(X) % vec_align) == 0 && ld % 4 == 0) ? 1 : 0;
+  p.y = y;
+  p.e = reinterpret_cast<float*>(ws + P.e);
+  p.a_in = a;
+  p.warm = a_is_guess ? 1 : 0;
+  p.a_out = a;
+  p.a64 = reinterpret_cast<double*>(ws + P.a64);
+  p.Gt = Gt;
+  p.dvec = dvec;
+  p.npanels = P.npanels;
+  p.hacc = reinterpret_cast<double*>(ws + P.hacc);
+  p.npart = reinterpret_cast<double*>(ws + P.npart);
+  p.ypart = reinterpret_cast<double*>(ws + P.ypart);
+  p.hist = reinterpret_cast<double*>(ws + P.hist);
+  p.ctl = ctl;
+  p.tol = o->tol;
+  p.max_sweeps = o->max_sweeps;
+  p.stop_rule = o->stop_rule;
+  p.refresh_every = o->refresh_every;
+  p.timeout_ns = (uint64_t)(ctx->timeout_s * 1e9);
+  p.stall_barrier = (o->debug_flags & HPSCD_DEBUG_STALL_BARRIER) ? 1 : 0;
+  if (launch_panel_sweep(dtype, p, P.grid, st) != cudaSuccess) {
+    cudaGetLastError();
+    return HPSCD_ERR_CUDA;
+  }
+  if (cudaEventRecord(ctx->ev[2], st) != cudaSuccess) return HPSCD_ERR_CUDA;
+  if (cudaMemcpyAsync(ctx->ctl_host, ctl, sizeof(GridCtl), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return HPSCD_ERR_CUDA;
+  const GridCtl c = *ctx->ctl_host;
+  if (hist && c.sweeps >= 0 && c.sweeps <= o->max_sweeps &&
+      cudaMemcpy(hist, p.hist, (size_t)(c.sweeps + 1) * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return HPSCD_ERR_CUDA;
+  if (sweeps_done) *sweeps_done = c.sweeps;
+  if (final_rel_res) *final_rel_res = c.final_res;
+  hpscd_timing t{};
+  cudaEventElapsedTime(&t.setup_ms, ctx->ev[0], ctx->ev[1]);
+  cudaEventElapsedTime(&t.sweep_ms, ctx->ev[1], ctx->ev[2]);
+  t.passes = c.passes;
+  t.x_bytes = m * n * es;
+  t.grid = P.grid;
+  t.kernel_launches = launches + 1;
+  ctx->last = t;
+  if (c.err != DEV_OK) return HPSCD_ERR_TIMEOUT;
+  return c.status;
+}
+
+// ---- routing: which sweep runs a solve, after which one-off relayout of X ----
+//   column-major, n <= 512          the tall sweep
+//   column-major, n > 512           the panel sweep
+//   row-major, m <= 4096            the cluster sweep (16-bit X widened to float32 first)
+//   row-major, m > 4096             transposed once to column-major, then as above
+enum RouteKind { ROUTE_EMPTY, ROUTE_TALL, ROUTE_PANEL, ROUTE_WIDE };
+enum Relayout { RL_NONE, RL_TRANSPOSE, RL_WIDEN };
+
+struct Route {
+  RouteKind kind = ROUTE_TALL;
+  int relayout = RL_NONE;
+  int dtype_k = HPSCD_F32;  // element type the sweep reads
+  int64_t ld_k = 0;         // leading dimension the sweep reads
+  Plan tall;
+  PanelPlan panel;
+  WideConfig wc{};
+  WideLayout wl;
+  size_t xk = 0;            // the relaid copy of X
+  size_t xh = 0, yh = 0, ah = 0;  // host entry point: device copies of X, y and a
+  size_t total = 0;
+};
+
+int make_route(const hpscd_ctx* ctx, int dtype, int layout, int64_t m, int64_t n, int64_t ld,
+               const hpscd_opts* o, bool host_copies, Route* R) {
+  int rc;
+  R->dtype_k = dtype;
+  R->ld_k = ld;
+  int lay = layout;
+  size_t inner = 0;
+  if (m == 0) {
+    R->kind = ROUTE_EMPTY;
+  } else if (n == 0) {
+    R->kind = ROUTE_TALL;
+    R->ld_k = m;
+    if ((rc = make_plan(ctx, dtype, HPSCD_COL_MAJOR, m, n, m, o, false, &R->tall))) return rc;
+    inner = R->tall.L.total;
+  } else {
+    if (lay == HPSCD_ROW_MAJOR) {
+      if (wide_config(m, ctx->max_smem, &R->wc)) {
+        R->kind = ROUTE_WIDE;
+        if (dtype != HPSCD_F32) {
+          R->relayout = RL_WIDEN;
+          R->dtype_k = HPSCD_F32;
+          R->ld_k = (n + 3) / 4 * 4;  // float32 rows on 16-byte boundaries
+        }
+        if ((rc = make_wide_plan(ctx, R->dtype_k, m, n, R->ld_k, o, false, &R->wc, &R->wl))) return rc;
+        inner = R->wl.total;
+      } else {
+        R->relayout = RL_TRANSPOSE;
+        R->ld_k = (m + 31) / 32 * 32;  // columns on 128-byte boundaries (the sweeps' TMA boxes)
+        lay = HPSCD_COL_MAJOR;
+      }
+    }
+    if (lay == HPSCD_COL_MAJOR) {
+      if (n <= 512) {
+        R->kind = ROUTE_TALL;
+        if ((rc = make_plan(ctx, dtype, HPSCD_COL_MAJOR, m, n, R->ld_k, o, false, &R->tall))) return rc;
+        inner = R->tall.L.total;
+      } else {
+        R->kind = ROUTE_PANEL;
+        if ((rc = make_panel_plan(ctx, dtype, m, n, o, &R->panel))) return rc;
+        inner = R->panel.total;
+      }
+    }
+  }
+  size_t off = align_up(inner, 256);
+  auto take = [&](size_t bytes) {
+    const size_t at = off;
+    off = align_up(off + bytes, 256);
+    return at;
+  };
+  if (R->relayout == RL_TRANSPOSE) R->xk = take((size_t)n * (size_t)R->ld_k * esize(dtype));
+  if (R->relayout == RL_WIDEN) R->xk = take((size_t)m * (size_t)R->ld_k * sizeof(float));
+  if (host_copies) {
+    const size_t xe = layout == HPSCD_COL_MAJOR ? (size_t)(n > 0 ? n : 1) * (size_t)ld
+                                                : (size_t)(m > 0 ? m : 1) * (size_t)ld;
+    R->xh = take(xe * esize(dtype));
+    R->yh = take((size_t)(m > 0 ? m : 1) * sizeof(float));
+    R->ah = take((size_t)(n > 0 ? n : 1) * sizeof(float));
+  }
+  R->total = off;
+  return HPSCD_OK;
+}
+
+// Runs a routed solve on device buffers (X as given by the caller, or its
+// device copy for the host entry point); the workspace holds R.total bytes.
+int run_route(hpscd_ctx* ctx, const Route& R, const void* X, int dtype, int64_t m, int64_t n,
+              int64_t ld, const float* y, float* a, int a_is_guess, const hpscd_opts* o, double* hist,
+              int64_t* sweeps_done, double* final_rel_res) {
+  if (R.kind == ROUTE_EMPTY) return solve_empty_rows(ctx, n, a, a_is_guess, o, hist, sweeps_done, final_rel_res);
+  char* ws = static_cast<char*>(ctx->ws);
+  cudaStream_t st = ctx->stream;
+  const void* Xk = X;
+  float rl_ms = 0.f;
+  if (R.relayout != RL_NONE) {
+    Xk = ws + R.xk;
+    if (cudaEventRecord(ctx->ev_rl[0], st) != cudaSuccess) return HPSCD_ERR_CUDA;
+    const cudaError_t e =
+        R.relayout == RL_TRANSPOSE
+            ? launch_transpose_to_col(X, dtype, m, n, ld, ws + R.xk, R.ld_k, ctx->sms, st)
+            : launch_widen_rows(X, dtype, m, n, ld, reinterpret_cast<float*>(ws + R.xk), R.ld_k, ctx->sms, st);
+    if (e != cudaSuccess || cudaEventRecord(ctx->ev_rl[1], st) != cudaSuccess) {
+      cudaGetLastError();
+      return HPSCD_ERR_CUDA;
+    }
+  }
+  int rc;
+  if (R.kind == ROUTE_WIDE)
+    rc = solve_wide(ctx, Xk, m, n, R.ld_k, y, a, a_is_guess, o, hist, sweeps_done, final_rel_res, R.wc, R.wl);
+  else if (R.kind == ROUTE_PANEL)
+    rc = solve_panel(ctx, Xk, R.dtype_k, m, n, R.ld_k, y, a, a_is_guess, o, hist, sweeps_done,
+                     final_rel_res, R.panel);
+  else
+    rc = solve_device(ctx, Xk, R.dtype_k, HPSCD_COL_MAJOR, m, n, R.ld_k, y, a, a_is_guess, o, hist,
+                      sweeps_done, final_rel_res, R.tall);
+  if (R.relayout != RL_NONE && rc != HPSCD_ERR_CUDA &&
+      cudaEventElapsedTime(&rl_ms, ctx->ev_rl[0], ctx->ev_rl[1]) == cudaSuccess) {
+    // the relayout is part of the set-up (the cluster sweep times its set-up with its sweeps)
+    if (R.kind == ROUTE_WIDE) ctx->last.sweep_ms += rl_ms;
+    else ctx->last.setup_ms += rl_ms;
+    ctx->last.kernel_launches += 1;
+  }
+  return rc;
+}
+
 }  // namespace
 
 namespace {
@@ -572,6 +827,8 @@ void free_ctx(hpscd_ctx* ctx) {
   if (ctx->ws && ctx->ws_owned) cudaFree(ctx->ws);
   for (int i = 0; i < 3; ++i)
     if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
+  for (int i = 0; i < 2; ++i)
+    if (ctx->ev_rl[i]) cudaEventDestroy(ctx->ev_rl[i]);
   for (int r = 0; r < hpscd_ctx::RING; ++r)
     for (int i = 0; i < 3; ++i)
       if (ctx->ring_ev[r][i]) cudaEventDestroy(ctx->ring_ev[r][i]);
@@ -612,6 +869,8 @@ int hpscd_create(hpscd_ctx** out, int device, void* stream) {
   }
   for (int i = 0; i < 3; ++i)
     if (cudaEventCreate(&c->ev[i]) != cudaSuccess) { hpscd_destroy(c); return HPSCD_ERR_CUDA; }
+  for (int i = 0; i < 2; ++i)
+    if (cudaEventCreate(&c->ev_rl[i]) != cudaSuccess) { hpscd_destroy(c); return HPSCD_ERR_CUDA; }
   if (cudaMallocHost(reinterpret_cast<void**>(&c->ctl_host), sizeof(GridCtl)) != cudaSuccess) {
     c->ctl_host = nullptr;
     hpscd_destroy(c);
@@ -663,16 +922,9 @@ int hpscd_workspace_size(hpscd_ctx* ctx, int dtype, int layout, int64_t m, int64
   if (rc) return rc;
   const int64_t ld = layout == HPSCD_COL_MAJOR ? (m > 1 ? m : 1) : (n > 1 ? n : 1);
   if ((rc = check_shape(dtype, layout, m, n, ld))) return rc;
-  if (layout == HPSCD_ROW_MAJOR && m > 0 && n > 0) {
-    WideConfig wc;
-    WideLayout wl;
-    if ((rc = make_wide_plan(ctx, dtype, m, n, ld, opts, false, &wc, &wl))) return rc;
-    *bytes = wl.total;
-    return HPSCD_OK;
-  }
-  Plan P;
-  if ((rc = make_plan(ctx, dtype, HPSCD_COL_MAJOR, m, n, m > 1 ? m : 1, opts, false, &P))) return rc;
-  *bytes = P.L.total;
+  Route R;
+  if ((rc = make_route(ctx, dtype, layout, m, n, ld, opts, false, &R))) return rc;
+  *bytes = R.total;
   return HPSCD_OK;
 }
 
@@ -698,20 +950,10 @@ int hpscd_solve(hpscd_ctx* ctx, const void* X, int dtype, int layout, int64_t m,
   if ((m > 0 && n > 0 && !X) || (m > 0 && !y) || (n > 0 && !a)) return HPSCD_ERR_INVALID_ARG;
   DeviceGuard g(ctx->device);
   if (!g.ok) return HPSCD_ERR_CUDA;
-  if (layout == HPSCD_ROW_MAJOR && m > 0 && n > 0) {
-    WideConfig wc;
-    WideLayout wl;
-    if ((rc = make_wide_plan(ctx, dtype, m, n, ld, opts, false, &wc, &wl))) return rc;
-    if ((rc = ensure_ws(ctx, wl.total))) return rc;
-    return solve_wide(ctx, X, m, n, ld, y, a, a_is_guess, opts, hist, sweeps_done, final_rel_res,
-                      wc, wl);
-  }
-  if (layout == HPSCD_ROW_MAJOR) { layout = HPSCD_COL_MAJOR; ld = m > 1 ? m : 1; }
-  Plan P;
-  if ((rc = make_plan(ctx, dtype, layout, m, n, ld, opts, false, &P))) return rc;
-  if ((rc = ensure_ws(ctx, P.L.total))) return rc;
-  return solve_device(ctx, X, dtype, layout, m, n, ld, y, a, a_is_guess, opts, hist, sweeps_done,
-                      final_rel_res, P);
+  Route R;
+  if ((rc = make_route(ctx, dtype, layout, m, n, ld, opts, false, &R))) return rc;
+  if ((rc = ensure_ws(ctx, R.total))) return rc;
+  return run_route(ctx, R, X, dtype, m, n, ld, y, a, a_is_guess, opts, hist, sweeps_done, final_rel_res);
 }
 
 int hpscd_solve_blocks(hpscd_ctx* ctx, const void* X, int dtype, int64_t m, int64_t n, int64_t ld,
@@ -862,25 +1104,17 @@ int hpscd_solve_host(hpscd_ctx* ctx, const void* X, int dtype, int layout, int64
   if ((m > 0 && n > 0 && !X) || (m > 0 && !y) || (n > 0 && !a)) return HPSCD_ERR_INVALID_ARG;
   DeviceGuard g(ctx->device);
   if (!g.ok) return HPSCD_ERR_CUDA;
-  const bool wide = layout == HPSCD_ROW_MAJOR && m > 0 && n > 0;
-  if (layout == HPSCD_ROW_MAJOR && !wide) { layout = HPSCD_COL_MAJOR; ld = m > 1 ? m : 1; }
-  Plan P;
-  WideConfig wc;
-  WideLayout wl;
-  if (wide) {
-    if ((rc = make_wide_plan(ctx, dtype, m, n, ld, opts, true, &wc, &wl))) return rc;
-    if ((rc = ensure_ws(ctx, wl.total))) return rc;
-  } else {
-    if ((rc = make_plan(ctx, dtype, layout, m, n, ld, opts, true, &P))) return rc;
-    if ((rc = ensure_ws(ctx, P.L.total))) return rc;
-  }
+  Route R;
+  if ((rc = make_route(ctx, dtype, layout, m, n, ld, opts, true, &R))) return rc;
+  if ((rc = ensure_ws(ctx, R.total))) return rc;
   char* ws = static_cast<char*>(ctx->ws);
-  void* Xd = ws + (wide ? wl.xcopy : P.L.xcopy);
-  float* yd = reinterpret_cast<float*>(ws + (wide ? wl.ycopy : P.L.ycopy));
-  float* ad = reinterpret_cast<float*>(ws + (wide ? wl.acopy : P.L.acopy));
+  void* Xd = ws + R.xh;
+  float* yd = reinterpret_cast<float*>(ws + R.yh);
+  float* ad = reinterpret_cast<float*>(ws + R.ah);
   cudaStream_t st = ctx->stream;
-  const size_t xbytes = layout == HPSCD_COL_MAJOR ? (size_t)n * ld * esize(dtype)
-                                                  : (size_t)m * ld * esize(dtype);
+  const size_t xbytes = (m > 0 && n > 0) ? (layout == HPSCD_COL_MAJOR ? (size_t)n * ld * esize(dtype)
+                                                                       : (size_t)m * ld * esize(dtype))
+                                         : 0;
   if (xbytes && cudaMemcpyAsync(Xd, X, xbytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
     return HPSCD_ERR_CUDA;
   if (m > 0 && cudaMemcpyAsync(yd, y, (size_t)m * sizeof(float), cudaMemcpyHostToDevice, st) != cudaSuccess)
@@ -888,10 +1122,7 @@ int hpscd_solve_host(hpscd_ctx* ctx, const void* X, int dtype, int layout, int64
   if (n > 0 && a_is_guess &&
       cudaMemcpyAsync(ad, a, (size_t)n * sizeof(float), cudaMemcpyHostToDevice, st) != cudaSuccess)
     return HPSCD_ERR_CUDA;
-  rc = wide ? solve_wide(ctx, Xd, m, n, ld, yd, ad, a_is_guess, opts, hist, sweeps_done,
-                         final_rel_res, wc, wl)
-            : solve_device(ctx, Xd, dtype, layout, m, n, ld, yd, ad, a_is_guess, opts, hist,
-                           sweeps_done, final_rel_res, P);
+  rc = run_route(ctx, R, Xd, dtype, m, n, ld, yd, ad, a_is_guess, opts, hist, sweeps_done, final_rel_res);
   if (rc == HPSCD_ERR_CUDA || rc == HPSCD_ERR_INVALID_ARG || rc == HPSCD_ERR_UNSUPPORTED) return rc;
   if (n > 0 && cudaMemcpyAsync(a, ad, (size_t)n * sizeof(float), cudaMemcpyDeviceToHost, st) != cudaSuccess)
     return HPSCD_ERR_CUDA;

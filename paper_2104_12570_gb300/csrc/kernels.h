@@ -8,6 +8,14 @@
 
 namespace hpscd {
 
+// Tensor-map element type of a stored X (TMA copies only its bytes; the type
+// fixes the element size).
+inline CUtensorMapDataType x_tmap_type(int dtype) {
+  return dtype == HPSCD_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+         : dtype == HPSCD_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                               : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+}
+
 // ---- Gram set-up: G = X^T X (lower triangle incl. diagonal), G_jj = <X_j, X_j> ----
 struct GramPlan {
   int npad;         // padded column count (multiple of 64)
@@ -133,6 +141,48 @@ bool tall_config(int dtype, int n, int max_smem, TallConfig* cfg);
 cudaError_t launch_scale_rows(const float* G, int ldG, int n, float* Gt, float* d, cudaStream_t stream);
 cudaError_t launch_tall_sweep(int dtype, const TallConfig& cfg, const CUtensorMap* tmap,
                               const TallParams& p, int grid, cudaStream_t stream);
+// The IEEE binary16 instantiations (tall_sweep_f16.cu).
+cudaError_t launch_tall_sweep_f16(const TallConfig& cfg, const CUtensorMap* tmap, const TallParams& p,
+                                  int grid, cudaStream_t stream);
+
+// ---- set-up relayouts (relayout.cu) ----
+// out (column-major, leading dimension ldo) = X (row-major, ld), element bits copied.
+cudaError_t launch_transpose_to_col(const void* X, int dtype, int64_t m, int64_t n, int64_t ld, void* out,
+                                    int64_t ldo, int sms, cudaStream_t stream);
+// out (row-major float32, ldo) = X (row-major bfloat16 or binary16, ld), widened exactly.
+cudaError_t launch_widen_rows(const void* X, int dtype, int64_t m, int64_t n, int64_t ld, float* out,
+                              int64_t ldo, int sms, cudaStream_t stream);
+
+// ---- panel sweep (column-major X, n > 512): panels of PANEL_W columns ----
+constexpr int PANEL_W = 512;
+struct PanelParams {
+  const void* X;         // column-major, leading dimension ld
+  int64_t m;
+  int n;
+  int64_t ld;
+  int vec;               // X and ld allow 16-byte (float32) / 8-byte (16-bit) row loads
+  const float* y;
+  float* e;              // [ceil(m/128)·128] residual (rows past m kept zero)
+  const float* a_in;     // the initial guess when warm
+  int warm;
+  float* a_out;          // [n] float32 coefficients returned
+  double* a64;           // [n] float64 coefficients
+  const float* Gt;       // [npanels][PANEL_W][PANEL_W] G~ = D^{-1} G of each panel's diagonal block
+  const float* dvec;     // [npanels·PANEL_W] d = diag(G)
+  int npanels;
+  double* hacc;          // [3][PANEL_W] a pass's dot products (float64 atomics); zeroed by the host
+  double* npart;         // [2][grid] ||e||^2 partials
+  double* ypart;         // [grid] ||y||^2 partials
+  double* hist;          // [max_sweeps + 1]
+  GridCtl* ctl;
+  double tol;
+  int64_t max_sweeps;
+  int stop_rule;
+  int refresh_every;
+  uint64_t timeout_ns;
+  int stall_barrier;     // test hook: the first grid barrier waits for one arrival too many
+};
+cudaError_t launch_panel_sweep(int dtype, const PanelParams& p, int grid, cudaStream_t stream);
 
 // ---- wide sweep (row-major X, m <= 4096): one thread-block cluster ----
 struct WideParams {

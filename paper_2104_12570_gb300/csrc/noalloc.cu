@@ -107,7 +107,7 @@ extern "C" int hpscd_solve_noalloc(void* stream, const void* X, int dtype, int64
     return HPSCD_ERR_INVALID_ARG;
   for (int i = 0; i < 5; ++i)
     if (o->reserved[i] != 0) return HPSCD_ERR_INVALID_ARG;
-  if (dtype != HPSCD_F32 && dtype != HPSCD_BF16) return HPSCD_ERR_INVALID_ARG;
+  if (dtype != HPSCD_F32 && dtype != HPSCD_BF16 && dtype != HPSCD_F16) return HPSCD_ERR_INVALID_ARG;
   if (m < 1 || n < 1 || ld < m || !X || !y || !a) return HPSCD_ERR_INVALID_ARG;
   if (m > NOALLOC_MAX_M || n > NOALLOC_MAX_N || o->max_sweeps > NOALLOC_MAX_SWEEPS)
     return HPSCD_ERR_UNSUPPORTED;
@@ -170,8 +170,7 @@ extern "C" int hpscd_solve_noalloc(void* stream, const void* X, int dtype, int64
     cuuint32_t box[2] = {(cuuint32_t)cfg.rows, (cuuint32_t)cfg.box_cols};
     cuuint32_t estr[2] = {1, 1};
     use_tma = g_encode(&map,
-                       dtype == HPSCD_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
-                                          : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+                       x_tmap_type(dtype),
                        2, const_cast<void*>(X), dims, strides, box, estr,
                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B,

@@ -1,0 +1,487 @@
+// Persistent column sweep of Algorithm 1 for column-major X with more than
+// 512 columns (any m): one CTA per SM, cooperative launch.
+//
+// The n columns are taken in panels of PW = 512 consecutive columns, panel by
+// panel in the paper's column order.  Inside a panel Q the steps follow, as in
+// the tall sweep, from the dot products against the residual e as it stands
+// before the panel and the panel's diagonal block of G = X^T X (Eq. ek1-ek
+// applied to the panel's own columns), by forward substitution on the
+// pre-divided couplings G~ = D^{-1} G:
+//     da_j = <X_j, e> / G_jj - sum_{l<j, l in Q} G~_jl da_l   (Eq. da2, j in Q).
+// Across panels the residual itself carries the coupling: pass t applies the
+// rank-1 corrections of the panel solved before it (e <- e - X_P·da_P, Eq.
+// ek1-ek) and forms the next panel's dot products against that updated e,
+// row segment by row segment (a segment's dots need only the segment's e), so
+// the only couplings formed in set-up are the panels' diagonal Gram blocks
+// (O(m·n·PW) work, not the O(m·n^2) of a full Gram) and every column is read
+// twice per sweep: once for its dot products, once for its corrections.
+//
+// Every CTA owns a contiguous range of 128-row chunks and walks it in segments
+// of SEG_CHUNKS chunks: first the corrections (a warp per chunk, each lane 4
+// consecutive rows, the segment's updated e kept in shared memory and written
+// back), then the dots (a warp per 32 columns of the next panel, float32 sums
+// over the segment, float64 across segments and, by atomics, across CTAs).
+// After a grid barrier every CTA reads the same float64 dot products, forms
+// r = h ⊘ d and runs the panel's substitution itself (bitwise the same in
+// every CTA), so the next pass needs no broadcast of da.
+#include <cuda_fp16.h>
+
+#include "kernels.h"
+
+namespace hpscd {
+
+namespace {
+
+constexpr int PW = PANEL_W;       // columns per panel
+constexpr int PNW = 16;           // warps per CTA
+constexpr int PNT = PNW * 32;     // threads per CTA (one per column of a panel)
+constexpr int SEG_CHUNKS = 32;    // 128-row chunks per row segment
+constexpr int SEG_ROWS = SEG_CHUNKS * 128;
+
+// what a pass does to the residual before the dot products
+enum PassKind : int {
+  PK_COPY_Y = 0,  // e = y (cold start)
+  PK_APPLY = 1,   // e -= X_P·da_P (the panel solved before this pass)
+  PK_TRUE = 2     // e = y - X·v over all n columns, compensated (Dot2)
+};
+
+// Four consecutive rows of one column, widened exactly to float32.
+template <typename T>
+struct Rows4;
+template <>
+struct Rows4<float> {
+  __device__ static void vec(const float* p, float (&v)[4]) {
+    const float4 t = __ldg(reinterpret_cast<const float4*>(p));
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+  }
+  __device__ static float one(const float* p) { return __ldg(p); }
+};
+template <>
+struct Rows4<uint16_t> {
+  __device__ static void vec(const uint16_t* p, float (&v)[4]) {
+    const uint2 t = __ldg(reinterpret_cast<const uint2*>(p));
+    v[0] = __uint_as_float(t.x << 16);
+    v[1] = __uint_as_float(t.x & 0xffff0000u);
+    v[2] = __uint_as_float(t.y << 16);
+    v[3] = __uint_as_float(t.y & 0xffff0000u);
+  }
+  __device__ static float one(const uint16_t* p) { return bf16_bits_to_float(__ldg(p)); }
+};
+template <>
+struct Rows4<__half> {
+  __device__ static void vec(const __half* p, float (&v)[4]) {
+    const uint2 t = __ldg(reinterpret_cast<const uint2*>(p));
+    const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&t.x));
+    const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&t.y));
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+  }
+  __device__ static float one(const __half* p) {
+    return __half2float(__ushort_as_half(__ldg(reinterpret_cast<const unsigned short*>(p))));
+  }
+};
+
+// Rows r0..r0+3 of column `col` (zero past m).  vec: X is aligned for vector loads.
+template <typename T>
+__device__ __forceinline__ void load_rows4(const T* __restrict__ X, int64_t ld, int64_t col, int64_t r0,
+                                           int64_t m, bool vec, float (&v)[4]) {
+  const T* p = X + col * ld + r0;
+  if (vec && r0 + 4 <= m) {
+    Rows4<T>::vec(p, v);
+  } else {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) v[i] = (r0 + i < m) ? Rows4<T>::one(p + i) : 0.f;
+  }
+}
+
+// s + c += -x·v with the error-free transformations of Dot2 (TwoProduct by
+// fma, TwoSum), so that s + c carries about twice float32's precision.
+__device__ __forceinline__ void dot2_sub(float x, float v, float& s, float& c) {
+  const float p = -x * v;
+  const float pe = fmaf(-x, v, -p);
+  const float t = s + p;
+  const float bb = t - s;
+  const float err = (s - (t - bb)) + (p - bb);
+  s = t;
+  c += err + pe;
+}
+
+// Forward substitution of one panel: on entry r_s[i] = h_i / d_i (i < nq); on
+// exit da_s[i] = da_i (0 for nq <= i < PW).  Gq: the panel's G~ block, row-major
+// with row stride PW.  Blocks of 32 steps: warp 0 solves the block's unit lower
+// triangle with shuffles (lane l owns step 32b + l and keeps its row of the
+// block in registers), then every thread applies the block to its later row.
+__device__ void panel_substitution(const float* __restrict__ Gq, int nq, float* r_s, float* da_s) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nb = (nq + 31) / 32;
+  for (int b = 0; b < nb; ++b) {
+    const int i0 = 32 * b;
+    if (warp == 0) {
+      const int i = i0 + lane;
+      float g[32];
+      if (i < nq) {
+        const float4* row = reinterpret_cast<const float4*>(Gq + (size_t)i * PW + i0);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const float4 t = __ldg(row + k);
+          g[4 * k] = t.x; g[4 * k + 1] = t.y; g[4 * k + 2] = t.z; g[4 * k + 3] = t.w;
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < 32; ++k) g[k] = 0.f;
+      }
+      float v = (i < nq) ? r_s[i] : 0.f;
+#pragma unroll
+      for (int k = 0; k < 32; ++k) {
+        const float dk = __shfl_sync(FULL_MASK, v, k);
+        if (lane > k) v = fmaf(-g[k], dk, v);
+      }
+      da_s[i] = (i < nq) ? v : 0.f;
+    }
+    __syncthreads();
+    const int i = tid;
+    if (i >= i0 + 32 && i < nq) {
+      const float4* row = reinterpret_cast<const float4*>(Gq + (size_t)i * PW + i0);
+      float acc = r_s[i];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const float4 t = __ldg(row + k);
+        acc = fmaf(-t.x, da_s[i0 + 4 * k], acc);
+        acc = fmaf(-t.y, da_s[i0 + 4 * k + 1], acc);
+        acc = fmaf(-t.z, da_s[i0 + 4 * k + 2], acc);
+        acc = fmaf(-t.w, da_s[i0 + 4 * k + 3], acc);
+      }
+      r_s[i] = acc;
+    }
+    __syncthreads();
+  }
+  for (int i = 32 * nb + tid; i < PW; i += PNT) da_s[i] = 0.f;
+  __syncthreads();
+}
+
+// Sum over the CTAs of one partial per CTA, in a fixed order (the same value
+// in every CTA).  Called by all threads; the result is in every thread.
+__device__ double sum_partials(const double* __restrict__ part, int count, double* red) {
+  if (threadIdx.x < 32) {
+    double s = 0.0;
+    for (int i = threadIdx.x; i < count; i += 32) s += __ldcg(part + i);
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) s += __shfl_xor_sync(FULL_MASK, s, o);
+    if (threadIdx.x == 0) red[0] = s;
+  }
+  __syncthreads();
+  const double v = red[0];
+  __syncthreads();
+  return v;
+}
+
+__device__ __forceinline__ double rel_of(double e2, double y2) {
+  const double en = sqrt(e2), yn = sqrt(y2);
+  return yn > 0.0 ? en / yn : en;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(PNT, 1) panel_sweep_kernel(const PanelParams p) {
+  __shared__ __align__(16) float e_sm[SEG_ROWS];
+  __shared__ __align__(16) float r_s[PW];
+  __shared__ __align__(16) float da_s[PW];
+  __shared__ double red[PNW];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const T* __restrict__ X = static_cast<const T*>(p.X);
+  const int64_t m = p.m, ld = p.ld;
+  const int n = p.n, npan = p.npanels;
+  const bool vec = p.vec != 0;
+  // the CTA's contiguous range of 128-row chunks
+  const int64_t nchunks = (m + 127) / 128;
+  const int64_t c_begin = nchunks * blockIdx.x / gridDim.x;
+  const int64_t c_end = nchunks * (blockIdx.x + 1) / gridDim.x;
+  const unsigned G = gridDim.x;
+  const bool lead = blockIdx.x == 0;
+  int err = DEV_OK;
+
+  if (lead)
+    for (int j = tid; j < n; j += PNT) p.a64[j] = p.warm ? (double)p.a_in[j] : 0.0;
+
+  // One pass: the residual step of `kind`, then the dot products of panel qd
+  // into hacc[hb]; the CTA's ||e||^2 (and, on the first pass, ||y||^2) partials.
+  auto run_pass = [&](int kind, int qp, int qd, int hb, int nb, bool first) {
+    const int p0 = qp * PW, np = min(PW, n - p0);
+    const int d0 = qd * PW, nd = min(PW, n - d0);
+    double e2 = 0.0, y2 = 0.0, acc64 = 0.0;
+    const int dcol = 32 * warp;  // this warp's first column of the dot panel
+    for (int64_t s0 = c_begin; s0 < c_end; s0 += SEG_CHUNKS) {
+      const int nc = (int)min((int64_t)SEG_CHUNKS, c_end - s0);
+      // residual step, a warp per chunk
+      for (int c = warp; c < nc; c += PNW) {
+        const int64_t r0 = (s0 + c) * 128 + 4 * lane;
+        float ev[4];
+        if (kind == PK_APPLY) {
+          const float4 t = *reinterpret_cast<const float4*>(p.e + r0);
+          float a0[4] = {0.f, 0.f, 0.f, 0.f}, a1[4] = {0.f, 0.f, 0.f, 0.f};
+          int j = 0;
+          for (; j + 1 < np; j += 2) {
+            float x0[4], x1[4];
+            load_rows4<T>(X, ld, p0 + j, r0, m, vec, x0);
+            load_rows4<T>(X, ld, p0 + j + 1, r0, m, vec, x1);
+            const float v0 = da_s[j], v1 = da_s[j + 1];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+              a0[i] = fmaf(x0[i], v0, a0[i]);
+              a1[i] = fmaf(x1[i], v1, a1[i]);
+            }
+          }
+          if (j < np) {
+            float x0[4];
+            load_rows4<T>(X, ld, p0 + j, r0, m, vec, x0);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a0[i] = fmaf(x0[i], da_s[j], a0[i]);
+          }
+          ev[0] = t.x - (a0[0] + a1[0]);
+          ev[1] = t.y - (a0[1] + a1[1]);
+          ev[2] = t.z - (a0[2] + a1[2]);
+          ev[3] = t.w - (a0[3] + a1[3]);
+        } else {
+          float yv[4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) yv[i] = (r0 + i < m) ? __ldg(p.y + r0 + i) : 0.f;
+          if (first) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) y2 += (double)yv[i] * (double)yv[i];
+          }
+          if (kind == PK_COPY_Y) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) ev[i] = yv[i];
+          } else {
+            // e = y - X·v, v = hi + lo of the float64 coefficients (lo = 0 for the
+            // float32 coefficients of a confirmation, or a warm start's guess)
+            float s[4], cc[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) { s[i] = yv[i]; cc[i] = 0.f; }
+            for (int j = 0; j < n; ++j) {
+              float vh, vl;
+              if (first) {
+                vh = __ldg(p.a_in + j);
+                vl = 0.f;
+              } else {
+                const double a = __ldcg(p.a64 + j);
+                vh = (float)a;
+                vl = (float)(a - (double)vh);
+              }
+              float x[4];
+              load_rows4<T>(X, ld, j, r0, m, vec, x);
+#pragma unroll
+              for (int i = 0; i < 4; ++i) {
+                dot2_sub(x[i], vh, s[i], cc[i]);
+                cc[i] = fmaf(-x[i], vl, cc[i]);
+              }
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) ev[i] = s[i] + cc[i];
+          }
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          if (r0 + i >= m) ev[i] = 0.f;
+          e2 += (double)ev[i] * (double)ev[i];
+        }
+        *reinterpret_cast<float4*>(p.e + r0) = make_float4(ev[0], ev[1], ev[2], ev[3]);
+        *reinterpret_cast<float4*>(e_sm + c * 128 + 4 * lane) = make_float4(ev[0], ev[1], ev[2], ev[3]);
+      }
+      __syncthreads();
+      // dot products of the dot panel's columns dcol..dcol+31 over the segment
+      if (dcol < nd) {
+        float acc[32];
+#pragma unroll
+        for (int k = 0; k < 32; ++k) acc[k] = 0.f;
+        for (int c = 0; c < nc; ++c) {
+          const int64_t r0 = (s0 + c) * 128 + 4 * lane;
+          const float4 et = *reinterpret_cast<const float4*>(e_sm + c * 128 + 4 * lane);
+#pragma unroll
+          for (int k = 0; k < 32; ++k) {
+            if (dcol + k < nd) {
+              float x[4];
+              load_rows4<T>(X, ld, d0 + dcol + k, r0, m, vec, x);
+              acc[k] = fmaf(x[0], et.x, fmaf(x[1], et.y, fmaf(x[2], et.z, fmaf(x[3], et.w, acc[k]))));
+            }
+          }
+        }
+        // lane k ends with the segment's sum for column dcol + k
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) {
+          const bool upper = (lane & o) != 0;
+#pragma unroll
+          for (int k = 0; k < o; ++k) {
+            const float send = upper ? acc[k] : acc[k + o];
+            const float keep = upper ? acc[k + o] : acc[k];
+            acc[k] = keep + __shfl_xor_sync(FULL_MASK, send, o);
+          }
+        }
+        acc64 += (double)acc[0];
+      }
+      __syncthreads();
+    }
+    if (dcol + lane < nd && c_end > c_begin) atomicAdd(p.hacc + (size_t)hb * PW + dcol + lane, acc64);
+    // the CTA's ||e||^2 and ||y||^2 partials
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+      e2 += __shfl_xor_sync(FULL_MASK, e2, o);
+      y2 += __shfl_xor_sync(FULL_MASK, y2, o);
+    }
+    if (lane == 0) red[warp] = e2;
+    __syncthreads();
+    if (tid == 0) {
+      double s = 0.0;
+      for (int w = 0; w < PNW; ++w) s += red[w];
+      p.npart[(size_t)nb * G + blockIdx.x] = s;
+    }
+    __syncthreads();
+    if (first) {
+      if (lane == 0) red[warp] = y2;
+      __syncthreads();
+      if (tid == 0) {
+        double s = 0.0;
+        for (int w = 0; w < PNW; ++w) s += red[w];
+        p.ypart[blockIdx.x] = s;
+      }
+      __syncthreads();
+    }
+  };
+
+  // After a pass's barrier: r = h ⊘ d of the dot panel, hacc[hb] left for the
+  // next-but-one pass zeroed by CTA 0.
+  auto take_dots = [&](int qd, int hb) {
+    const int d0 = qd * PW, nd = min(PW, n - d0);
+    if (tid < PW) {
+      float r = 0.f;
+      if (tid < nd) {
+        const float dj = p.dvec[d0 + tid];
+        if (dj > 0.f) r = (float)(__ldcg(p.hacc + (size_t)hb * PW + tid) / (double)dj);
+      }
+      r_s[tid] = r;
+    }
+    if (lead && tid < PW) p.hacc[(size_t)((hb + 2) % 3) * PW + tid] = 0.0;
+    __syncthreads();
+  };
+
+  auto solve_panel = [&](int q) {
+    const int q0 = q * PW, nq = min(PW, n - q0);
+    panel_substitution(p.Gt + (size_t)q * PW * PW, nq, r_s, da_s);
+    if (lead && tid < nq) p.a64[q0 + tid] += (double)da_s[tid];
+  };
+
+  int64_t t = 0;         // passes made
+  int64_t s = 0;         // sweeps completed
+  int status = HPSCD_ERR_NOT_CONVERGED;
+  double r_prev = 0.0, r = 0.0, y2 = 0.0;
+  int nconf = 0;
+  bool stall = p.stall_barrier != 0;
+  auto sync_grid = [&]() -> bool {
+    const unsigned expect = G + (stall ? 1u : 0u);
+    stall = false;
+    if (!grid_barrier(p.ctl, expect, p.timeout_ns)) {
+      err = DEV_TIMEOUT_BARRIER;
+      return false;
+    }
+    return true;
+  };
+
+  // pass 0: the initial residual (y, or y - X·a0 of a warm start) and the
+  // first panel's dot products
+  run_pass(p.warm ? PK_TRUE : PK_COPY_Y, 0, 0, 0, 0, true);
+  bool done = false;
+  if (!sync_grid()) done = true;
+  if (!done) {
+    take_dots(0, 0);
+    y2 = sum_partials(p.ypart, G, red);
+    r = rel_of(sum_partials(p.npart, G, red), y2);
+    if (lead && tid == 0) p.hist[0] = r;
+    if (!isfinite(r)) {
+      status = HPSCD_ERR_NONFINITE;
+      done = true;
+    } else if (p.max_sweeps == 0) {
+      status = (p.stop_rule == HPSCD_STOP_REL_CHANGE || (p.stop_rule == HPSCD_STOP_REL_RES && r > p.tol))
+                   ? HPSCD_ERR_NOT_CONVERGED
+                   : HPSCD_OK;
+      done = true;
+    } else if (p.stop_rule == HPSCD_STOP_REL_RES && r <= p.tol) {
+      status = HPSCD_OK;  // e_0 is a true residual already
+      done = true;
+    }
+    r_prev = r;
+  }
+  int q = 0;  // the panel whose dot products are in r_s
+  if (!done) solve_panel(q);
+  while (!done) {
+    ++t;
+    const int qn = (q + 1) % npan;
+    const bool boundary = qn == 0;
+    const bool refresh = boundary && p.refresh_every > 0 && ((s + 1) % p.refresh_every) == 0;
+    if (refresh && !sync_grid()) break;  // the coefficients of the last panel are visible
+    const int hb = (int)(t % 3), nb = (int)(t & 1);
+    run_pass(refresh ? PK_TRUE : PK_APPLY, q, qn, hb, nb, false);
+    if (!sync_grid()) break;
+    take_dots(qn, hb);
+    q = qn;
+    if (boundary) {
+      ++s;
+      r = rel_of(sum_partials(p.npart + (size_t)nb * G, G, red), y2);
+      if (lead && tid == 0) p.hist[s] = r;
+      if (!isfinite(r)) {
+        status = HPSCD_ERR_NONFINITE;
+        break;
+      }
+      bool met = false;
+      if (p.stop_rule == HPSCD_STOP_REL_RES) met = r <= p.tol;
+      else if (p.stop_rule == HPSCD_STOP_REL_CHANGE) met = r_prev == 0.0 || fabs(r_prev - r) < p.tol * r_prev;
+      const bool last = s >= p.max_sweeps;
+      if ((met || last) && p.stop_rule != HPSCD_STOP_NONE && nconf < 8) {
+        // the stop is taken on y - X·a of the float32 coefficients returned
+        ++nconf;
+        if (lead)
+          for (int j = tid; j < n; j += PNT) p.a64[j] = (double)(float)p.a64[j];
+        if (!sync_grid()) break;
+        ++t;
+        const int hb2 = (int)(t % 3), nb2 = (int)(t & 1);
+        run_pass(PK_TRUE, 0, 0, hb2, nb2, false);
+        if (!sync_grid()) break;
+        take_dots(0, hb2);
+        r = rel_of(sum_partials(p.npart + (size_t)nb2 * G, G, red), y2);
+        if (lead && tid == 0) p.hist[s] = r;
+        if (!isfinite(r)) {
+          status = HPSCD_ERR_NONFINITE;
+          break;
+        }
+        if (p.stop_rule == HPSCD_STOP_REL_RES) met = r <= p.tol;
+      }
+      if (met || last) {
+        status = (met || p.stop_rule == HPSCD_STOP_NONE) ? HPSCD_OK : HPSCD_ERR_NOT_CONVERGED;
+        break;
+      }
+      r_prev = r;
+    }
+    solve_panel(q);
+  }
+  if (err != DEV_OK && tid == 0) atomicCAS(&p.ctl->err, DEV_OK, err);
+  if (lead) {
+    __syncthreads();
+    for (int j = tid; j < n; j += PNT) p.a_out[j] = (float)p.a64[j];
+    if (tid == 0) {
+      p.ctl->status = status;
+      p.ctl->sweeps = s;
+      p.ctl->final_res = r;
+      p.ctl->passes = t + 1;
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_panel_sweep(int dtype, const PanelParams& p, int grid, cudaStream_t stream) {
+  PanelParams pp = p;
+  void* args[] = {(void*)&pp};
+  const void* kern = dtype == HPSCD_F32    ? (const void*)panel_sweep_kernel<float>
+                     : dtype == HPSCD_BF16 ? (const void*)panel_sweep_kernel<uint16_t>
+                                           : (const void*)panel_sweep_kernel<__half>;
+  return cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(PNT), args, 0, stream);
+}
+
+}  // namespace hpscd

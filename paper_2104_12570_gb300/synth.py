@@ -68,13 +68,13 @@ def bf16_bits_to_f32(b: np.ndarray) -> np.ndarray:
 @dataclass
 class System:
     """One synthetic system.  X is stored as described in the module docstring."""
-    X: np.ndarray          # float32 / uint16(bf16) / float64 storage array
+    X: np.ndarray          # float32 / uint16(bf16) / float16 / float64 storage array
     y: np.ndarray          # float32 (or float64 for the float64 tiny case), length m
     a_true: np.ndarray     # float64, length n
     m: int
     n: int
     layout: str            # "col" or "row"
-    dtype: str             # "f32", "bf16", "f64"
+    dtype: str             # "f32", "bf16", "f16", "f64"
 
     @property
     def ld(self) -> int:
@@ -116,7 +116,7 @@ def make_system(m: int, n: int, seed: int = 0, *, layout: str = "col", dtype: st
     The system solved is the STORED X (after rounding to the storage dtype);
     y is formed from those stored values in float64 and then rounded to
     float32 (or kept float64 when consistent_rhs_dtype == "f64")."""
-    if layout not in ("col", "row") or dtype not in ("f32", "bf16", "f64"):
+    if layout not in ("col", "row") or dtype not in ("f32", "bf16", "f16", "f64"):
         raise ValueError("bad layout/dtype")
     shape = (n, m) if layout == "col" else (m, n)
 
@@ -136,7 +136,12 @@ def make_system(m: int, n: int, seed: int = 0, *, layout: str = "col", dtype: st
         Xf = np.empty(shape, dtype=np.float32)
         _fill_chunks(Xf.reshape(-1), seed, 1, "normal")
         Xf = shaped(Xf)
-        X = f32_to_bf16_bits(Xf).reshape(shape) if dtype == "bf16" else Xf
+        if dtype == "bf16":
+            X = f32_to_bf16_bits(Xf).reshape(shape)
+        elif dtype == "f16":
+            X = Xf.astype(np.float16)  # IEEE binary16, round to nearest even
+        else:
+            X = Xf
     a_true = np.empty(n, dtype=np.float64)
     _fill_chunks(a_true, seed, 2, "uniform", -1.0, 1.0)
     s = System(X=X, y=np.empty(0), a_true=a_true, m=m, n=n, layout=layout, dtype=dtype)

@@ -4,7 +4,8 @@ ABI, against float64 X^T X computed on the host.
 
 Bound: each entry within 4e-6·sqrt(G_ii G_jj) (float32-grade: float32
 accumulation of products that are exact for bfloat16 X and carry ~2^-21
-relative error for float32 X split into two tf32 terms)."""
+relative error for float32 X split into two tf32 terms; binary16 products are
+exact as well)."""
 import numpy as np
 import pytest
 
@@ -26,7 +27,7 @@ def ctx():
 def gpu_X(s):
     if s.dtype == "bf16":
         return torch.from_numpy(s.X.view(np.int16)).view(torch.bfloat16).cuda().T
-    return torch.from_numpy(s.X).cuda().T
+    return torch.from_numpy(s.X).cuda().T  # float32 or float16
 
 
 def check(G, s, tol=4e-6):
@@ -41,7 +42,8 @@ def check(G, s, tol=4e-6):
 @pytest.mark.parametrize("m,n,dtype", [(64, 1, "f32"), (200, 50, "f32"), (1000, 37, "f32"),
                                        (5000, 256, "f32"), (4099, 129, "f32"),
                                        (777, 300, "bf16"), (3333, 100, "bf16"),
-                                       (20000, 512, "bf16"), (130, 256, "bf16")])
+                                       (20000, 512, "bf16"), (130, 256, "bf16"),
+                                       (777, 300, "f16"), (20000, 512, "f16"), (4099, 129, "f16")])
 def test_gram_matches_float64(ctx, m, n, dtype):
     s = synth.make_system(m, n, seed=m + n, dtype=dtype)
     X = gpu_X(s)

@@ -258,6 +258,35 @@ def test_layouts_and_bf16_promote_exactly():
     np.testing.assert_array_equal(r_bf.a, r_row.a)
 
 
+def test_binary16_decode_is_exact_for_every_finite_pattern():
+    """The oracle widens IEEE binary16 from the format's definition: for all
+    63,488 finite bit patterns (normals, subnormals, both zeros) the residual
+    y - X·a with y = 0, a = 1 returns -x exactly as numpy's float16 -> float64
+    conversion gives it, through the column-major and row-major readers."""
+    bits = np.arange(1 << 16, dtype=np.uint32).astype(np.uint16)
+    bits = bits[((bits >> 10) & 31) != 31]
+    x16 = bits.view(np.float16)
+    m = len(x16)
+    want = -x16.astype(np.float64)
+    for layout in ("col", "row"):
+        X = np.ascontiguousarray(x16.reshape((1, m) if layout == "col" else (m, 1)))
+        e, _ = oracle.residual(X, np.zeros(m), np.ones(1), m=m, n=1, layout=layout, dtype="f16")
+        np.testing.assert_array_equal(e, want)
+    assert want[bits == 0x0001][0] == -2.0 ** -24 and want[bits == 0x7bff][0] == -65504.0
+
+
+def test_binary16_storage_is_the_float32_system():
+    """A binary16 system solves exactly like the float32 system of the same
+    values (every binary16 value is a float32)."""
+    s = synth.make_system(50, 11, seed=13, layout="col", dtype="f16")
+    vals = s.X.astype(np.float32)
+    r16 = oracle.solve_system(s, tol=0, max_sweeps=4, stop="none")
+    r32 = oracle.solve(np.ascontiguousarray(vals), s.y, m=50, n=11, layout="col", dtype="f32",
+                       tol=0, max_sweeps=4, stop="none")
+    np.testing.assert_array_equal(r16.a, r32.a)
+    np.testing.assert_array_equal(r16.hist, r32.hist)
+
+
 def test_empty_and_degenerate_shapes():
     y = np.array([1.0, 2.0, 3.0])
     r = oracle.solve(np.zeros((0, 3)), y, m=3, n=0, layout="col", dtype="f64", tol=1e-6,
@@ -287,7 +316,7 @@ def test_nonfinite_inputs_are_reported():
 
 
 @pytest.mark.parametrize("layout,dtype,stop", [("col", "f32", "rel_change"), ("col", "bf16", "rel_res"),
-                                               ("row", "f32", "none")])
+                                               ("col", "f16", "rel_res"), ("row", "f32", "none")])
 def test_threaded_oracle_is_algorithm_1(layout, dtype, stop):
     """The CPU baseline's threaded Algorithm 1 (row loops split over threads,
     column order sequential): bitwise the sequential oracle at one thread, and

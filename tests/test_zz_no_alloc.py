@@ -104,6 +104,20 @@ def test_refuses_host_pointers():
     assert rc == 1  # HPSCD_ERR_INVALID_ARG, nothing launched
 
 
+@pytest.mark.parametrize("dtype", ["f16"])
+def test_f16_matches_hpscd_solve(dtype):
+    s = synth.make_system(30_001, 64, seed=23, dtype=dtype)
+    X, y = gpu_system(s)
+    assert X.dtype == torch.float16
+    ctx = hp.Context(0)
+    ref = ctx.solve(X, y, tol=0, max_sweeps=5, stop="none")
+    ctx.close()
+    a = torch.empty(s.n, device="cuda")
+    rc, hist, sweeps = solve_noalloc(X, y, a, tol=0, max_sweeps=5, stop="none")
+    assert rc == 0 and sweeps == 5
+    assert rel(a.cpu().numpy(), ref.a.cpu().numpy()) <= RTOL_F32
+
+
 def test_bf16_and_limits():
     s = synth.make_system(40_000, 96, seed=22, dtype="bf16")
     X, y = gpu_system(s)
