@@ -310,8 +310,10 @@ def run_reference(args, rank, world):
 def precision_comparison(hp, synth, ctx, dev, peak, peak_kind, steps=5, warmup=3, cpu=True):
     """Time to relative residual 1e-6 on the 4,000,000 x 512 consistent system: X
     stored bfloat16 (float32 accumulation, true-residual refresh every 4 sweeps)
-    against the same values stored float32 (plain float32 sweep).  The stop is
-    confirmed on y - X·a of the returned float32 coefficients (a Dot2 pass)."""
+    and IEEE binary16 (the same values converted, exact but for the entries below
+    2^-17 in magnitude, about 6 per million) against the same values stored
+    float32 (plain float32 sweep).  The stop is confirmed on y - X·a of the
+    returned float32 coefficients (a Dot2 pass)."""
     import torch
     s = synth.workload("tall_4Mx512_bf16", seed=0)
     Xb = torch.from_numpy(s.X.view(np.int16)).view(torch.bfloat16).to(dev).T
@@ -320,9 +322,12 @@ def precision_comparison(hp, synth, ctx, dev, peak, peak_kind, steps=5, warmup=3
            "stop": "rel_res<=1e-6 (confirmed on the true residual)",
            "bytes": "set-up: elem·m·n + 4m; per sweep: elem·m·n + 8m (e in HBM)"}
     results = {}
+    Xh = Xb.T.half().T
     for name, X, kw in (("bf16_refresh4", Xb, dict(refresh_every=4)),
+                        ("f16_refresh4", Xh, dict(refresh_every=4)),
                         ("f32_plain", None, {})):
         if X is None:
+            del Xh
             X = Xb.T.float().contiguous().T
             del Xb
         for _ in range(warmup):
@@ -335,7 +340,7 @@ def precision_comparison(hp, synth, ctx, dev, peak, peak_kind, steps=5, warmup=3
         e1.record()
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / steps
-        esz = 2 if X.dtype == torch.bfloat16 else 4
+        esz = 4 if X.dtype == torch.float32 else 2
         sw = int(r.sweeps)
         out[name] = {"ms_to_tol": ms, "GBps": solve_bytes(s.m, s.n, esz, sw) / (ms * 1e-3) / 1e9,
                      "sweeps": sw, "passes": int(r.timing["passes"]), "rel_res": float(r.rel_res),
@@ -346,6 +351,7 @@ def precision_comparison(hp, synth, ctx, dev, peak, peak_kind, steps=5, warmup=3
         results[name] = r.a.cpu().numpy()
         del X
     out["bf16_speedup_time_to_tol"] = out["f32_plain"]["ms_to_tol"] / out["bf16_refresh4"]["ms_to_tol"]
+    out["f16_speedup_time_to_tol"] = out["f32_plain"]["ms_to_tol"] / out["f16_refresh4"]["ms_to_tol"]
     if cpu:
         cb, ro = cpu_baseline(s, 2, "rel_res", 1e-6, 100, one_core_sweeps=1, what="tall_4Mx512_bf16")
         out["cpu_baseline"] = cb
@@ -599,6 +605,49 @@ def rowmajor_line(hp, synth, ctx, dev, name, desc, peak, peak_kind, reps=3, flus
     return out
 
 
+def panel_line(hp, synth, ctx, dev, peak, peak_kind, reps=3, cpu=True, rows=0):
+    """The column-major 1,000,000 x 1024 consistent float32 system (more than 512
+    columns: the panel sweep) solved to relative residual 1e-6, the stop
+    confirmed on the true residual of the returned a.  Bytes are the method's:
+    set-up 4·m·n + 4m, per sweep 4·m·n + 8m; the panel design reads X twice per
+    sweep, so its fraction of the copy peak on those bytes is at most about 1/2."""
+    import torch
+    name = "tall_1Mx1024_f32"
+    s = synth.workload(name, seed=0, **({"m": rows} if rows else {}))
+    X = torch.from_numpy(s.X).to(dev).T  # (m, n) column-major
+    y = torch.from_numpy(s.y).to(dev)
+    r = ctx.solve(X, y, tol=1e-6, max_sweeps=100, stop="rel_res")
+    times = []
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        r = ctx.solve(X, y, tol=1e-6, max_sweeps=100, stop="rel_res")
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    ms = sorted(times)[len(times) // 2]
+    sw = int(r.sweeps)
+    nb = solve_bytes(s.m, s.n, 4, sw)
+    out = {"workload": f"{name} (column-major, consistent, n > 512: the panel sweep)" +
+                       (f", m overridden to {s.m}" if rows else ""),
+           "stop": "rel_res<=1e-6 (confirmed on the true residual)", "l2": "X larger than L2",
+           "status": r.status, "sweeps": sw, "passes": int(r.timing["passes"]),
+           "rel_res": float(r.rel_res), "ms_to_tol": ms, "setup_ms": float(r.timing["setup_ms"]),
+           "ms_per_sweep": float(r.timing["sweep_ms"]) / max(1, sw),
+           "GBps": nb / (ms * 1e-3) / 1e9, "frac_of_peak": nb / (ms * 1e-3) / 1e9 / peak,
+           "bytes": "set-up 4·m·n + 4m, per sweep 4·m·n + 8m (X is read twice per sweep)",
+           "roofline": roofline_block(sweep_bytes(s.m, s.n, 4, sw), float(r.timing["sweep_ms"]), peak,
+                                      peak_kind, "panel_sweep_kernel")}
+    a_gpu = r.a.cpu().numpy()
+    del X
+    if cpu:
+        cb, ro = cpu_baseline(s, 4, "rel_res", 1e-6, 100, one_core_sweeps=1, what=name)
+        out["cpu_baseline"] = cb
+        out["oracle_check"] = oracle_check(s, a_gpu, sw, r.rel_res, ro)
+    return out
+
+
 def profile_wide(hp, synth, cols, blocks=512):
     """The wide cluster kernel alone on a 2,000 x `cols` float32 row-major
     consistent system, solved to relative residual 1e-6 (profiler captures and
@@ -659,6 +708,8 @@ def main():
                     help="skip the batched cold-vs-learned-warm-start comparison (4096 RBF systems)")
     ap.add_argument("--rows", type=int, default=0,
                     help="override m (smaller case for profiler captures; not a bench line)")
+    ap.add_argument("--profile-panel", action="store_true",
+                    help="the panel sweep alone on the 1,000,000 x 1024 system (not a bench line)")
     ap.add_argument("--profile-small", action="store_true",
                     help="run only the small batched + MLP case used for profiler captures")
     ap.add_argument("--profile-wide", type=int, default=0, metavar="COLS",
@@ -673,6 +724,17 @@ def main():
         import paper_2104_12570_gb300 as hp
         from paper_2104_12570_gb300 import synth
         profile_small(hp, synth)
+        return
+    if args.profile_panel:
+        import torch
+        import paper_2104_12570_gb300 as hp
+        from paper_2104_12570_gb300 import synth
+        ctx = hp.Context(0)
+        peak, peak_kind = peaks()
+        out = panel_line(hp, synth, ctx, torch.device("cuda", 0), peak, peak_kind, cpu=False,
+                         rows=args.rows)
+        print(json.dumps({"profile_panel": True, **out}), flush=True)
+        ctx.close()
         return
     if args.warmup < 3:
         args.warmup = 3
@@ -780,9 +842,12 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "m": s.m, "n": s.n, "layout": "col-major",
+            "config": {"workload": WORKLOAD if not args.rows else f"{WORKLOAD} with m overridden to {s.m}",
+                       "m": s.m, "n": s.n, "layout": "col-major",
                        "stop": f"{STOP}<{TOL}", "sweeps": sweeps_timed,
-                       "passes_per_solve": p_mean, "l2": "inputs larger than L2 (1.02 GB X)",
+                       "passes_per_solve": p_mean,
+                       "l2": f"inputs larger than L2 ({s.m * s.n * esz / 1e9:.2f} GB X)" if s.m * s.n * esz > 129e6
+                       else f"X of {s.m * s.n * esz / 1e6:.0f} MB, below L2",
                        "bytes": "set-up 4·m·n + 4m, per sweep 4·m·n + 8m (e in HBM)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -808,6 +873,9 @@ def main():
             out["square"] = rowmajor_line(hp, synth, ctx, dev, "square_4096_f32",
                                           "square_4096_f32 (row-major, consistent, I + 0.5·Z/64)",
                                           peak, peak_kind, reps=3, flush=True, cpu=cpu)
+        if not args.no_wide and not args.rows:
+            torch.cuda.empty_cache()
+            out["panel"] = panel_line(hp, synth, ctx, dev, peak, peak_kind, cpu=cpu)
         if not args.no_compare and not args.rows:
             del X
             torch.cuda.empty_cache()

@@ -216,20 +216,24 @@ __global__ void __launch_bounds__(PNT, 1) panel_sweep_kernel(const PanelParams p
         float ev[4];
         if (kind == PK_APPLY) {
           const float4 t = *reinterpret_cast<const float4*>(p.e + r0);
+          // eight columns' loads in flight per step, two accumulator sets
           float a0[4] = {0.f, 0.f, 0.f, 0.f}, a1[4] = {0.f, 0.f, 0.f, 0.f};
           int j = 0;
-          for (; j + 1 < np; j += 2) {
-            float x0[4], x1[4];
-            load_rows4<T>(X, ld, p0 + j, r0, m, vec, x0);
-            load_rows4<T>(X, ld, p0 + j + 1, r0, m, vec, x1);
-            const float v0 = da_s[j], v1 = da_s[j + 1];
+          for (; j + 8 <= np; j += 8) {
+            float x[8][4];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-              a0[i] = fmaf(x0[i], v0, a0[i]);
-              a1[i] = fmaf(x1[i], v1, a1[i]);
+            for (int u = 0; u < 8; ++u) load_rows4<T>(X, ld, p0 + j + u, r0, m, vec, x[u]);
+#pragma unroll
+            for (int u = 0; u < 8; u += 2) {
+              const float v0 = da_s[j + u], v1 = da_s[j + u + 1];
+#pragma unroll
+              for (int i = 0; i < 4; ++i) {
+                a0[i] = fmaf(x[u][i], v0, a0[i]);
+                a1[i] = fmaf(x[u + 1][i], v1, a1[i]);
+              }
             }
           }
-          if (j < np) {
+          for (; j < np; ++j) {
             float x0[4];
             load_rows4<T>(X, ld, p0 + j, r0, m, vec, x0);
 #pragma unroll
@@ -256,23 +260,35 @@ __global__ void __launch_bounds__(PNT, 1) panel_sweep_kernel(const PanelParams p
             float s[4], cc[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i) { s[i] = yv[i]; cc[i] = 0.f; }
-            for (int j = 0; j < n; ++j) {
-              float vh, vl;
-              if (first) {
-                vh = __ldg(p.a_in + j);
-                vl = 0.f;
-              } else {
-                const double a = __ldcg(p.a64 + j);
-                vh = (float)a;
-                vl = (float)(a - (double)vh);
-              }
-              float x[4];
-              load_rows4<T>(X, ld, j, r0, m, vec, x);
+            // four columns' loads in flight per step
+            for (int j0 = 0; j0 < n; j0 += 4) {
+              float x[4][4], vh[4], vl[4];
 #pragma unroll
-              for (int i = 0; i < 4; ++i) {
-                dot2_sub(x[i], vh, s[i], cc[i]);
-                cc[i] = fmaf(-x[i], vl, cc[i]);
+              for (int u = 0; u < 4; ++u) {
+                const int j = j0 + u;
+                vh[u] = 0.f;
+                vl[u] = 0.f;
+                if (j < n) {
+                  load_rows4<T>(X, ld, j, r0, m, vec, x[u]);
+                  if (first) {
+                    vh[u] = __ldg(p.a_in + j);
+                  } else {
+                    const double a = __ldcg(p.a64 + j);
+                    vh[u] = (float)a;
+                    vl[u] = (float)(a - (double)vh[u]);
+                  }
+                } else {
+#pragma unroll
+                  for (int i = 0; i < 4; ++i) x[u][i] = 0.f;
+                }
               }
+#pragma unroll
+              for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                  dot2_sub(x[u][i], vh[u], s[i], cc[i]);
+                  cc[i] = fmaf(-x[u][i], vl[u], cc[i]);
+                }
             }
 #pragma unroll
             for (int i = 0; i < 4; ++i) ev[i] = s[i] + cc[i];

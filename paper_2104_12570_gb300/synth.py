@@ -164,6 +164,9 @@ WORKLOADS = {
     "tall_1Mx256_f32": dict(m=1_000_000, n=256, layout="col", dtype="f32", noise=0.01),
     # wide, consistent, float32 row-major (1.6 GB of X)
     "wide_2000x200k_f32": dict(m=2000, n=200_000, layout="row", dtype="f32", noise=0.0),
+    # tall, consistent, float32 column-major with more than 512 columns (4.1 GB
+    # of X): the panel sweep
+    "tall_1Mx1024_f32": dict(m=1_000_000, n=1024, layout="col", dtype="f32", noise=0.0),
     # tall, consistent, bfloat16 storage (4.1 GB of X)
     "tall_4Mx512_bf16": dict(m=4_000_000, n=512, layout="col", dtype="bf16", noise=0.0),
     # square, consistent, float32 row-major (67 MB of X): I + 0.5·Z/sqrt(n), whose
