@@ -96,6 +96,9 @@ typedef struct {
 /* Bit 1: form G = X^T X with the CUDA-core kernel even where the tensor-core
  * (tcgen05) kernel applies (cross-checking the two). */
 #define HPSCD_DEBUG_SIMT_GRAM 2
+/* Bit 2: keep the residual e in HBM even where the tall sweep would keep the
+ * rows of each CTA in shared memory (measuring the difference). */
+#define HPSCD_DEBUG_E_IN_HBM 4
 
 /* Timings of the last solve on a context, from CUDA events on its stream. */
 typedef struct {

@@ -42,6 +42,7 @@ struct Plan {
   int ldG = 0;
   int64_t ntiles = 0;
   int grid = 0;
+  int e_smem = 0;  // the tall sweep keeps e in shared memory
   Layout L;
 };
 
@@ -53,7 +54,8 @@ int check_opts(const hpscd_opts* o) {
   if (o->max_sweeps < 0 || o->max_sweeps > (int64_t)1 << 40) return HPSCD_ERR_INVALID_ARG;
   if (o->stop_rule < HPSCD_STOP_REL_RES || o->stop_rule > HPSCD_STOP_NONE) return HPSCD_ERR_INVALID_ARG;
   if (o->refresh_every < 0) return HPSCD_ERR_INVALID_ARG;
-  if (o->debug_flags & ~(HPSCD_DEBUG_STALL_BARRIER | HPSCD_DEBUG_SIMT_GRAM)) return HPSCD_ERR_INVALID_ARG;
+  if (o->debug_flags & ~(HPSCD_DEBUG_STALL_BARRIER | HPSCD_DEBUG_SIMT_GRAM | HPSCD_DEBUG_E_IN_HBM))
+    return HPSCD_ERR_INVALID_ARG;
   for (int i = 0; i < 5; ++i)
     if (o->reserved[i] != 0) return HPSCD_ERR_INVALID_ARG;
   return HPSCD_OK;
@@ -84,6 +86,23 @@ int make_plan(const hpscd_ctx* ctx, int dtype, int layout, int64_t m, int64_t n,
   if (P->ntiles < grid) grid = P->ntiles;
   if (grid < 1) grid = 1;
   P->grid = (int)grid;
+  // The residual of each CTA's row panels stays in shared memory when it fits
+  // beside at least four TMA stages (the kernel's other buffers are fixed).
+  P->e_smem = 0;
+  if (!(o->debug_flags & HPSCD_DEBUG_E_IN_HBM) && m > 0) {
+    const int64_t npan_max = (P->ntiles + P->grid - 1) / P->grid;
+    const int64_t e_bytes = npan_max * P->cfg.rows * (int64_t)sizeof(float) + 16;
+    int nst = P->cfg.nstages, smem = P->cfg.smem_bytes;
+    while ((int64_t)smem + e_bytes > ctx->max_smem - 256 && nst > 4) {
+      --nst;
+      smem -= P->cfg.stage_bytes;
+    }
+    if ((int64_t)smem + e_bytes <= ctx->max_smem - 256) {
+      P->cfg.nstages = nst;
+      P->cfg.smem_bytes = smem + (int)e_bytes;
+      P->e_smem = 1;
+    }
+  }
   Layout& L = P->L;
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -497,6 +516,7 @@ int solve_device(hpscd_ctx* ctx, const void* X, int dtype, int layout, int64_t m
   p.h0 = got_h0 ? h0 : nullptr;
   p.y2 = got_h0 ? y2 : nullptr;
   p.confirm = select ? 0 : 1;
+  p.e_smem = P.e_smem;
   p.trace = nullptr;
   p.trace_passes = 0;
   if (ctx->trace_passes > 0 && ctx->trace_dev) {

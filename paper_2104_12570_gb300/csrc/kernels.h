@@ -129,6 +129,8 @@ struct TallParams {
   const double* y2;   // ||y||^2 (float64), given with h0
   int confirm;        // 1: under REL_RES a tracked residual at the tolerance is confirmed
                       // by a pass that recomputes e = y - X·a of the returned a
+  int e_smem;         // 1: the residual of the CTA's rows stays in shared memory (after the
+                      // kernel's other buffers); 0: e lives in HBM (p.e)
 };
 
 struct TallConfig {

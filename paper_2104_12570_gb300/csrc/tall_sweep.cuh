@@ -442,6 +442,9 @@ __global__ void __launch_bounds__(NT, 1)
   uint64_t* empty = full + 16;
   int* flags = reinterpret_cast<int*>(empty + 16);  // [1]: grid barrier result
   float* diag_s = reinterpret_cast<float*>(flags + 4);  // [max(1, NPAD/32)][DIAG_PACK]
+  // with p.e_smem: e of the CTA's row panels, [panels of this CTA][PR]
+  float* e_res = reinterpret_cast<float*>(
+      (reinterpret_cast<uintptr_t>(diag_s + (NPAD >= 32 ? NPAD / 32 : 1) * DIAG_PACK) + 15) & ~uintptr_t(15));
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int grid = gridDim.x;
@@ -540,8 +543,12 @@ __global__ void __launch_bounds__(NT, 1)
                      : (conf || fin || (p.refresh_every > 0 && sw % p.refresh_every == 0))
                          ? MODE_REFRESH
                          : MODE_NORMAL;
-    // the residual the pass starts from (y until a pass has written e)
-    const float* __restrict__ ein_src = (pass == 0 || (pass == 1 && p.h0 && !p.warm)) ? p.y : p.e;
+    // the residual the pass starts from (y until a pass has written e), at row
+    // `row`, local index `li` among the CTA's rows
+    // (e_rows: the shared-memory copy indexed by the row itself, a generic pointer)
+    const bool from_y = pass == 0 || (pass == 1 && p.h0 && !p.warm);
+    float* const e_rows = p.e_smem ? e_res - pn0 * PR : p.e;
+    const float* __restrict__ ein_src = from_y ? p.y : e_rows;
     const int buf = (int)(pass & 1);
     const int hb = (int)(pass % 3);
     double nrm = 0.0, ysq = 0.0;
@@ -635,7 +642,7 @@ __global__ void __launch_bounds__(NT, 1)
           e64 = ((double)red_y - (double)sh) - ((double)sc + (double)sl);
           e_new = (float)e64;
         }
-        p.e[rrow] = e_new;
+        e_rows[rrow] = e_new;
         // a true-residual pass takes the norm of y - X·a before e is rounded to float32
         if (mode != MODE_REFRESH) e64 = (double)e_new;
         nrm = fma(e64, e64, nrm);

@@ -151,6 +151,23 @@ def test_f16_refresh_and_true_residual_stop(ctx):
     assert_true_residual(s, r, 1e-6)
 
 
+@pytest.mark.parametrize("m,n,dtype", [(200_003, 256, "f32"), (1_000_000, 64, "f32"), (300_001, 512, "bf16")])
+def test_residual_on_chip_matches_residual_in_hbm(ctx, m, n, dtype):
+    """Where it fits, each CTA keeps the residual of its rows in shared memory;
+    the debug bit HPSCD_DEBUG_E_IN_HBM keeps it in HBM.  Both give the oracle's
+    iterate at equal sweeps, and the same stop and residual under REL_RES."""
+    s = synth.make_system(m, n, seed=m % 97 + n, dtype=dtype, noise=0.01)
+    X, y = to_gpu(s)
+    o = oracle_same(s, 3)
+    for flags in (0, 4):
+        r = ctx.solve(X, y, tol=0, max_sweeps=3, stop="none", debug_flags=flags)
+        assert rel(r.a.cpu().numpy(), o.a) <= RTOL_F32, (flags, rel(r.a.cpu().numpy(), o.a))
+        np.testing.assert_allclose(r.hist, o.hist, rtol=1e-5, atol=1e-7)
+    on = ctx.solve(X, y, tol=1e-7, max_sweeps=50, stop="rel_change")
+    off = ctx.solve(X, y, tol=1e-7, max_sweeps=50, stop="rel_change", debug_flags=4)
+    assert on.sweeps == off.sweeps and on.rel_res == pytest.approx(off.rel_res, rel=1e-9)
+
+
 def test_unaligned_leading_dimension_uses_plain_loads(ctx):
     m, n = 1001, 17
     s = synth.make_system(m, n, seed=4)
