@@ -71,7 +71,10 @@ __global__ void __launch_bounds__(GT_THREADS, 1)
   extern __shared__ unsigned char smem_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  const int g = blockIdx.y;
+  // this CTA's group and row split (the splits of group g are CTAs split_base[g]..)
+  int g = 0;
+  while (g + 1 < p.grp.ngroups && (int)blockIdx.x >= p.grp.split_base[g + 1]) ++g;
+  const int split = (int)blockIdx.x - p.grp.split_base[g];
   const int nload = p.grp.nload[g];
   const int ntile = p.grp.ntile[g];
   const int stage_raw = nload * ATOM_BYTES;
@@ -87,8 +90,8 @@ __global__ void __launch_bounds__(GT_THREADS, 1)
   int* s_fail = reinterpret_cast<int*>(tmem_slot + 1);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int64_t r0 = (int64_t)blockIdx.x * p.rows_per_split;
-  const int64_t r1 = min(p.m, r0 + p.rows_per_split);
+  const int64_t r0 = (int64_t)split * p.grp.rows_per[g];
+  const int64_t r1 = min(p.m, r0 + p.grp.rows_per[g]);
   const int64_t nkb = r1 > r0 ? (r1 - r0 + KB - 1) / KB : 0;
 
   if (tid == 0) {
@@ -360,7 +363,7 @@ __global__ void __launch_bounds__(GT_THREADS, 1)
     for (int k = 0; k < MAXQ / 8; ++k) {
       const int lcol = wt / 8 + 16 * jl;  // column within slot k
       if (k < nload && p.grp.diag_slot[g][k]) {
-        const size_t at = (size_t)blockIdx.x * p.npad + p.grp.load_blk[g][k] * BLK + lcol;
+        const size_t at = (size_t)split * p.npad + p.grp.load_blk[g][k] * BLK + lcol;
         p.dpart[at] = dsq64[k];
         if (p.y) p.hpart[at] = xy64[k];
       }
@@ -371,11 +374,11 @@ __global__ void __launch_bounds__(GT_THREADS, 1)
       v += __shfl_xor_sync(0xffu, v, 1);
       v += __shfl_xor_sync(0xffu, v, 2);
       v += __shfl_xor_sync(0xffu, v, 4);
-      if (wt == 0) p.y2part[blockIdx.x] = v;
+      if (wt == 0) p.y2part[split] = v;
     }
     // tensor memory: worker warp w reads lane quarter w % 4 (rows 32·(w%4)..+31)
     const int quarter = warp & 3;
-    float* out = p.partial + (size_t)blockIdx.x * p.npad * p.npad;
+    float* out = p.partial + (size_t)split * p.npad * p.npad;
     for (int t = 0; t < ntile; ++t) {
       const int row = BLK * p.grp.tile_i[g][t] + 32 * quarter + lane;
       float* orow = out + (size_t)row * p.npad + BLK * p.grp.tile_j[g][t];
@@ -406,14 +409,15 @@ __global__ void __launch_bounds__(GT_THREADS, 1)
 // gives the same G):
 //   stage 1: tmp[s][i][j..j+3] = sum over the splits of slice s of the lower
 //            partials (float4 loads, independent across threads; one thread
-//            per slice, row and 4 columns), and d_i = sum_k dpart[k][i] (the
-//            CUDA-core diagonal, float64), and when asked (X^T y)_i and ||y||^2
-//            summed over the splits the same way;
+//            per slice, row and 4 columns; a tile's splits are those of the
+//            group that holds it), and d_i = sum_k dpart[k][i] (the CUDA-core
+//            diagonal, float64), and when asked (X^T y)_i and ||y||^2 summed over
+//            the splits the same way;
 //   stage 2: G_ij = G_ji = sum_s tmp[s][i][j], G_ii = d_i; optionally
 //            G~ = D^{-1} G in both triangles and d as float32.
 constexpr int RED_SLICES = 16;
 __global__ void gram_tc_reduce1_kernel(const float* __restrict__ partial,
-                                       const double* __restrict__ dpart, int ksplit, int npad,
+                                       const double* __restrict__ dpart, const GramTCGroups grp, int npad,
                                        float* __restrict__ tmp, double* __restrict__ d64,
                                        const double* __restrict__ hpart, const double* __restrict__ y2part,
                                        double* __restrict__ h0, double* __restrict__ y2) {
@@ -425,7 +429,8 @@ __global__ void gram_tc_reduce1_kernel(const float* __restrict__ partial,
     const int i = (int)((idx / n4) % npad);
     const int sl = (int)(idx / ((int64_t)n4 * npad));
     if (4 * j4 > i) continue;
-    const int k0 = ksplit * sl / RED_SLICES, k1 = ksplit * (sl + 1) / RED_SLICES;
+    const int ks = grp.tile_splits[i / BLK][(4 * j4) / BLK];
+    const int k0 = ks * sl / RED_SLICES, k1 = ks * (sl + 1) / RED_SLICES;
     double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
 #pragma unroll 4
     for (int k = k0; k < k1; ++k) {
@@ -435,16 +440,19 @@ __global__ void gram_tc_reduce1_kernel(const float* __restrict__ partial,
     *reinterpret_cast<float4*>(tmp + ((size_t)sl * npad + i) * npad + 4 * j4) =
         make_float4((float)a0, (float)a1, (float)a2, (float)a3);
     if (sl == 0 && j4 == 0) {
+      // the diagonal and X^T y of block i / BLK come from the group holding tile (I, I);
+      // ||y||^2 from group 0, whose splits cover every row
+      const int kd = grp.tile_splits[i / BLK][i / BLK];
       double dd = 0.0;
-      for (int k = 0; k < ksplit; ++k) dd += dpart[(size_t)k * npad + i];
+      for (int k = 0; k < kd; ++k) dd += dpart[(size_t)k * npad + i];
       d64[i] = dd;
       if (h0) {
         double hh = 0.0;
-        for (int k = 0; k < ksplit; ++k) hh += hpart[(size_t)k * npad + i];
+        for (int k = 0; k < kd; ++k) hh += hpart[(size_t)k * npad + i];
         h0[i] = hh;
         if (i == 0) {
           double yy = 0.0;
-          for (int k = 0; k < ksplit; ++k) yy += y2part[k];
+          for (int k = 0; k < grp.nsplit[0]; ++k) yy += y2part[k];
           *y2 = yy;
         }
       }
@@ -545,12 +553,33 @@ bool gram_tc_plan(int dtype, int64_t m, int n, int sms, int max_smem, GramTCPlan
   gp->smem_bytes = nst * stage + nst * YSTAGE_BYTES + 1024 + 256;
   // one CTA per SM: each CTA allocates all 512 tensor-memory columns
   if (gp->smem_bytes < max_smem / 2 + 4096) gp->smem_bytes = max_smem / 2 + 4096;
-  int ksplit = sms / G.ngroups;
-  if (ksplit < 1) ksplit = 1;
-  int64_t rps = (m + ksplit - 1) / ksplit;
-  rps = (rps + kb_rows - 1) / kb_rows * kb_rows;
-  gp->rows_per_split = rps;
-  gp->ksplit = (int)((m + rps - 1) / rps);
+  // row splits per group in proportion to its work per K block: for float32 the
+  // column blocks it streams (and splits into hi/lo), for 16-bit X its tiles
+  // (measured on 4,000,000 x 512: float32 9.6 ms by blocks, 15.6 ms by tiles;
+  // bfloat16 2.38 ms by tiles, 2.67 ms by blocks, 2.47 ms with equal splits);
+  // at most one CTA per SM in all
+  auto weight = [&](int g) { return f32 ? G.nload[g] : G.ntile[g]; };
+  int wsum = 0;
+  for (int g = 0; g < G.ngroups; ++g) wsum += weight(g);
+  const int64_t maxsplit = (m + kb_rows - 1) / kb_rows;
+  int total = 0, ksmax = 0;
+  for (int g = 0; g < G.ngroups; ++g) {
+    int64_t ns = (int64_t)sms * weight(g) / wsum;
+    if (ns < 1) ns = 1;
+    if (ns > maxsplit) ns = maxsplit;
+    int64_t rps = (m + ns - 1) / ns;
+    rps = (rps + kb_rows - 1) / kb_rows * kb_rows;
+    ns = (m + rps - 1) / rps;
+    G.nsplit[g] = (int)ns;
+    G.rows_per[g] = rps;
+    G.split_base[g] = total;
+    total += (int)ns;
+    if (ns > ksmax) ksmax = (int)ns;
+    for (int t = 0; t < G.ntile[g]; ++t) G.tile_splits[G.tile_i[g][t]][G.tile_j[g][t]] = (int)ns;
+  }
+  gp->ksplit = ksmax;
+  gp->nctas = total;
+  gp->rows_per_split = G.rows_per[0];
   gp->partial_bytes = (size_t)gp->ksplit * gp->npad * gp->npad * sizeof(float) +
                       (size_t)gp->ksplit * gp->npad * sizeof(double) +
                       (size_t)RED_SLICES * gp->npad * gp->npad * sizeof(float) +
@@ -586,7 +615,7 @@ cudaError_t launch_gram_tc(const CUtensorMap* tmap, int dtype, int64_t m, const 
   else memset(&ym, 0, sizeof(ym));
   p.hpart = d64 + gp.npad;
   p.y2part = p.hpart + (size_t)gp.ksplit * gp.npad;
-  dim3 grid(gp.ksplit, gp.grp.ngroups);
+  dim3 grid(gp.nctas);
   cudaError_t e;
   auto kern = dtype == HPSCD_F32    ? gram_tc_kernel<HPSCD_F32>
               : dtype == HPSCD_BF16 ? gram_tc_kernel<HPSCD_BF16>
@@ -598,7 +627,7 @@ cudaError_t launch_gram_tc(const CUtensorMap* tmap, int dtype, int64_t m, const 
   if (e != cudaSuccess) return e;
   const int64_t t1 = (int64_t)RED_SLICES * gp.npad * (gp.npad / 4);
   gram_tc_reduce1_kernel<<<(unsigned)((t1 + 255) / 256), 256, 0, stream>>>(
-      partial, p.dpart, gp.ksplit, gp.npad, tmp, d64, p.hpart, p.y2part, with_y ? h0 : nullptr,
+      partial, p.dpart, gp.grp, gp.npad, tmp, d64, p.hpart, p.y2part, with_y ? h0 : nullptr,
       with_y ? y2 : nullptr);
   const int64_t t2 = (int64_t)gp.npad * gp.npad;
   gram_tc_reduce2_kernel<<<(unsigned)((t2 + 255) / 256), 256, 0, stream>>>(tmp, d64, gp.npad, n, G, ldG,

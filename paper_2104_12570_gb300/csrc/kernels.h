@@ -44,12 +44,19 @@ struct GramTCGroups {
   int nload[GTC_MAX_GROUPS];
   int load_blk[GTC_MAX_GROUPS][4];  // column block streamed into each slot
   int diag_slot[GTC_MAX_GROUPS][4]; // 1 when the group holds tile (b, b) of the block in that slot
+  // row splits: group g runs nsplit[g] CTAs (linear indices split_base[g]..), each over
+  // rows_per[g] rows, in proportion to its work per K block
+  int nsplit[GTC_MAX_GROUPS];
+  int split_base[GTC_MAX_GROUPS];
+  int64_t rows_per[GTC_MAX_GROUPS];
+  int tile_splits[4][4];            // nsplit of the group that holds lower tile (I, J)
 };
 struct GramTCPlan {
   int npad;                 // multiple of 128
   GramTCGroups grp;
   int maxload;
-  int ksplit;
+  int ksplit;               // the most row splits of a group (partial buffers per split)
+  int nctas;                // CTAs of the launch (the splits of every group)
   int64_t rows_per_split;
   int nstages;
   int smem_bytes;
