@@ -685,7 +685,29 @@ int solve_panel(hpscd_ctx* ctx, const void* X, int dtype, int64_t m, int64_t n, 
   p.refresh_every = o->refresh_every;
   p.timeout_ns = (uint64_t)(ctx->timeout_s * 1e9);
   p.stall_barrier = (o->debug_flags & HPSCD_DEBUG_STALL_BARRIER) ? 1 : 0;
-  if (launch_panel_sweep(dtype, p, P.grid, st) != cudaSuccess) {
+  // TMA boxes of 128 rows x 64 KB of columns where X allows (16-byte base, ld·elem a
+  // multiple of 16), as many stages (at most 4) as fit beside the rest
+  CUtensorMap map;
+  memset(&map, 0, sizeof(map));
+  p.use_tma = 0;
+  p.nstages = 0;
+  if (ctx->encode && (reinterpret_cast<uintptr_t>(X) & 15) == 0 && ((uint64_t)ld * es) % 16 == 0 &&
+      (uint64_t)ld * es < ((uint64_t)1 << 40)) {
+    int nst = 4;
+    while (nst > 1 && panel_tma_smem(nst) + 8192 > ctx->max_smem) --nst;
+    cuuint64_t dims[2] = {(cuuint64_t)m, (cuuint64_t)n};
+    cuuint64_t strides[1] = {(cuuint64_t)ld * es};
+    cuuint32_t box[2] = {128, (cuuint32_t)(PANEL_BOX_BYTES / (128 * es))};
+    cuuint32_t estr[2] = {1, 1};
+    if (nst >= 2 && ctx->encode(&map, x_tmap_type(dtype), 2, const_cast<void*>(X), dims, strides, box, estr,
+                               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                               CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS) {
+      p.use_tma = 1;
+      p.nstages = nst;
+    }
+  }
+  if (launch_panel_sweep(dtype, p, p.use_tma ? &map : nullptr, P.grid, st) != cudaSuccess) {
     cudaGetLastError();
     return HPSCD_ERR_CUDA;
   }

@@ -164,6 +164,7 @@ cudaError_t launch_widen_rows(const void* X, int dtype, int64_t m, int64_t n, in
 
 // ---- panel sweep (column-major X, n > 512): panels of PANEL_W columns ----
 constexpr int PANEL_W = 512;
+constexpr int PANEL_BOX_BYTES = 65536;  // TMA box of the panel sweep: 128 rows x 64 KB of columns
 struct PanelParams {
   const void* X;         // column-major, leading dimension ld
   int64_t m;
@@ -190,8 +191,13 @@ struct PanelParams {
   int refresh_every;
   uint64_t timeout_ns;
   int stall_barrier;     // test hook: the first grid barrier waits for one arrival too many
+  int use_tma;           // 1: X streams by TMA (tensor map: dims {m, n}, boxes of 128 rows x
+                         // PANEL_BOX_BYTES / (128·elem) columns), else plain loads
+  int nstages;           // TMA stages (PANEL_BOX_BYTES each)
 };
-cudaError_t launch_panel_sweep(int dtype, const PanelParams& p, int grid, cudaStream_t stream);
+int panel_tma_smem(int nst);  // dynamic shared memory of the TMA kernel
+cudaError_t launch_panel_sweep(int dtype, const PanelParams& p, const CUtensorMap* tmap, int grid,
+                               cudaStream_t stream);
 
 // ---- wide sweep (row-major X, m <= 4096): one thread-block cluster ----
 struct WideParams {

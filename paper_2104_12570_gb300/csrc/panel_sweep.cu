@@ -17,7 +17,7 @@
 // twice per sweep: once for its dot products, once for its corrections.
 //
 // Every CTA owns a contiguous range of 128-row chunks and walks it in segments
-// of SEG_CHUNKS chunks: first the corrections (a warp per chunk, each lane 4
+// of SEG_CHUNKS chunks (plain loads) or box by box (TMA): first the corrections (a warp per chunk, each lane 4
 // consecutive rows, the segment's updated e kept in shared memory and written
 // back), then the dots (a warp per 32 columns of the next panel, float32 sums
 // over the segment, float64 across segments and, by atomics, across CTAs).
@@ -25,6 +25,7 @@
 // r = h ⊘ d and runs the panel's substitution itself (bitwise the same in
 // every CTA), so the next pass needs no broadcast of da.
 #include <cuda_fp16.h>
+#include <string.h>
 
 #include "kernels.h"
 
@@ -77,6 +78,37 @@ struct Rows4<__half> {
   }
   __device__ static float one(const __half* p) {
     return __half2float(__ushort_as_half(__ldg(reinterpret_cast<const unsigned short*>(p))));
+  }
+};
+
+// Four consecutive rows of a column of a TMA box in shared memory (plain
+// loads: __ldg is for global memory only), widened exactly to float32.
+template <typename T>
+struct BoxRows4;
+template <>
+struct BoxRows4<float> {
+  __device__ static void load(const float* p, float (&v)[4]) {
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+  }
+};
+template <>
+struct BoxRows4<uint16_t> {
+  __device__ static void load(const uint16_t* p, float (&v)[4]) {
+    const uint2 t = *reinterpret_cast<const uint2*>(p);
+    v[0] = __uint_as_float(t.x << 16);
+    v[1] = __uint_as_float(t.x & 0xffff0000u);
+    v[2] = __uint_as_float(t.y << 16);
+    v[3] = __uint_as_float(t.y & 0xffff0000u);
+  }
+};
+template <>
+struct BoxRows4<__half> {
+  __device__ static void load(const __half* p, float (&v)[4]) {
+    const uint2 t = *reinterpret_cast<const uint2*>(p);
+    const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&t.x));
+    const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&t.y));
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
   }
 };
 
@@ -179,9 +211,12 @@ __device__ __forceinline__ double rel_of(double e2, double y2) {
   return yn > 0.0 ? en / yn : en;
 }
 
-template <typename T>
-__global__ void __launch_bounds__(PNT, 1) panel_sweep_kernel(const PanelParams p) {
-  __shared__ __align__(16) float e_sm[SEG_ROWS];
+// TMA: X streams through shared memory by TMA in boxes of 128 rows x BC
+// columns (32 KB) instead of plain loads.
+template <typename T, bool TMA>
+__global__ void __launch_bounds__(PNT, 1)
+    panel_sweep_kernel(const __grid_constant__ CUtensorMap tmap, const PanelParams p) {
+  __shared__ __align__(16) float e_sm[TMA ? 4 : SEG_ROWS];
   __shared__ __align__(16) float r_s[PW];
   __shared__ __align__(16) float da_s[PW];
   __shared__ double red[PNW];
@@ -362,6 +397,231 @@ __global__ void __launch_bounds__(PNT, 1) panel_sweep_kernel(const PanelParams p
     }
   };
 
+  // ---- the same pass streamed by TMA ----
+  // Per 128-row chunk of the CTA: the apply boxes (the previous panel's columns,
+  // or all columns for y - X·v), each warp its BC/16 columns and each lane 4
+  // rows, keeping the lane's row partials (Dot2 pairs for y - X·v); a cross-warp
+  // reduction gives the chunk's new e (threads 0..127, one row each); then the
+  // dot boxes of the next panel against that e, each lane keeping its 32 column
+  // partials over the chunks (float64 every 8 chunks).  Box s of a pass is
+  // sequence qbase + s of the stage ring (stage and parity from it); the ring is
+  // refilled after each box's CTA barrier and drains at the end of the pass.
+  constexpr int BC = PANEL_BOX_BYTES / (128 * (int)sizeof(T));  // box columns: 128 (float32) or 256 (16-bit)
+  constexpr int CWB = BC / 16;                          // columns of a box per warp
+  constexpr int NBP = PW / BC;                          // boxes of a full panel
+  constexpr int BOXB = 128 * BC * (int)sizeof(T);
+  extern __shared__ unsigned char dyn_smem[];
+  unsigned char* dbase = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(dyn_smem) + 1023) & ~uintptr_t(1023));
+  const int nst = p.nstages;
+  T* stages = reinterpret_cast<T*>(dbase);
+  float* red_h = reinterpret_cast<float*>(dbase + (size_t)nst * BOXB);  // [PNW][128]
+  float* red_l = red_h + PNW * 128;                                     // [PNW][128]
+  float* ech = red_l + PNW * 128;                                       // [128]
+  uint64_t* full = reinterpret_cast<uint64_t*>(ech + 128);              // [nst]
+  uint64_t qbase = 0, issued_g = 0, waited_g = 0;
+  bool tma_fail = false;
+  if (TMA && tid == 0) {
+    for (int i = 0; i < nst; ++i) mbar_init(&full[i], 1);
+    fence_mbar_init();
+  }
+  if (TMA) __syncthreads();
+  auto run_pass_tma = [&](int kind, int qp, int qd, int hb, int nb, bool first) -> bool {
+    const int p0 = qp * PW, np = min(PW, n - p0);
+    const int d0 = qd * PW, nd = min(PW, n - d0);
+    const int nA = kind == PK_APPLY ? (np + BC - 1) / BC : (kind == PK_TRUE ? (n + BC - 1) / BC : 0);
+    const int a0c = kind == PK_APPLY ? p0 : 0;  // first column of the apply boxes
+    const int nD = (nd + BC - 1) / BC;
+    const int bpc = nA + nD;                    // boxes per chunk
+    const int64_t nch = c_end - c_begin;
+    const uint64_t total = (uint64_t)(nch > 0 ? nch : 0) * (uint64_t)bpc;
+    auto issue = [&](uint64_t s) {  // box s of the pass (thread 0)
+      const uint64_t gs = qbase + s;
+      const int st = (int)(gs % nst);
+      const int64_t ch = c_begin + (int64_t)(s / bpc);
+      const int idx = (int)(s % bpc);
+      const int col = idx < nA ? a0c + idx * BC : d0 + (idx - nA) * BC;
+      mbar_arrive_expect_tx(&full[st], (uint32_t)BOXB);
+      tma_load_2d(stages + (size_t)st * 128 * BC, &tmap, &full[st], (int32_t)(ch * 128), col);
+    };
+    if (tid == 0)
+      for (uint64_t s = 0; s < total && s < (uint64_t)nst; ++s) { issue(s); ++issued_g; }
+    // one box of the pass: wait for it (every thread), hand it to f, release it
+    auto box = [&](uint64_t s, auto f) -> bool {
+      const uint64_t gs = qbase + s;
+      const int st = (int)(gs % nst);
+      const bool ok = mbar_wait_bounded(&full[st], (uint32_t)((gs / nst) & 1), p.timeout_ns);
+      ++waited_g;
+      if (ok) f(stages + (size_t)st * 128 * BC);
+      if (__syncthreads_or(ok ? 0 : 1)) return false;
+      if (tid == 0 && s + nst < total) {
+        fence_proxy_async_smem();
+        issue(s + nst);
+        ++issued_g;
+      }
+      return true;
+    };
+    double e2 = 0.0, y2 = 0.0, acc64 = 0.0;
+    float gacc[NBP][CWB];
+#pragma unroll
+    for (int b = 0; b < NBP; ++b)
+#pragma unroll
+      for (int c = 0; c < CWB; ++c) gacc[b][c] = 0.f;
+    int since_flush = 0;
+    // lane l ends with the warp's total of accumulator l = b·CWB + c
+    auto flush = [&]() {
+      float v[32];
+#pragma unroll
+      for (int b = 0; b < NBP; ++b)
+#pragma unroll
+        for (int c = 0; c < CWB; ++c) { v[b * CWB + c] = gacc[b][c]; gacc[b][c] = 0.f; }
+#pragma unroll
+      for (int o = 16; o >= 1; o >>= 1) {
+        const bool upper = (lane & o) != 0;
+#pragma unroll
+        for (int k = 0; k < o; ++k) {
+          const float send = upper ? v[k] : v[k + o];
+          const float keep = upper ? v[k + o] : v[k];
+          v[k] = keep + __shfl_xor_sync(FULL_MASK, send, o);
+        }
+      }
+      acc64 += (double)v[0];
+    };
+    for (int64_t ci = 0; ci < nch; ++ci) {
+      const int64_t ch = c_begin + ci;
+      // the reducers' inputs of this chunk, loaded before its boxes are worked on
+      const int64_t rrow = ch * 128 + tid;
+      float e_in = 0.f, y_in = 0.f;
+      if (tid < 128 && rrow < m) {
+        if (kind == PK_APPLY) e_in = p.e[rrow];
+        else y_in = __ldg(p.y + rrow);
+      }
+      float ph[4] = {0.f, 0.f, 0.f, 0.f}, pl[4] = {0.f, 0.f, 0.f, 0.f};
+      for (int b = 0; b < nA; ++b) {
+        const int colw = a0c + b * BC + warp * CWB;  // this warp's first column of the box
+        const bool ok = box((uint64_t)ci * bpc + b, [&](const T* bx) {
+#pragma unroll
+          for (int c = 0; c < CWB; ++c) {
+            const int j = colw + c;
+            float x[4];
+            BoxRows4<T>::load(bx + (warp * CWB + c) * 128 + 4 * lane, x);  // zero past m and n
+            if (kind == PK_APPLY) {
+              const float v = (j - p0 < np) ? da_s[j - p0] : 0.f;
+#pragma unroll
+              for (int r = 0; r < 4; ++r) ph[r] = fmaf(x[r], v, ph[r]);
+            } else if (j < n) {
+              float vh, vl;
+              if (first) {
+                vh = __ldg(p.a_in + j);
+                vl = 0.f;
+              } else {
+                const double a = __ldcg(p.a64 + j);
+                vh = (float)a;
+                vl = (float)(a - (double)vh);
+              }
+              // ph, pl: the Dot2 pair (s, c) of sum x·v
+#pragma unroll
+              for (int r = 0; r < 4; ++r) {
+                const float pr = x[r] * vh, pe = fmaf(x[r], vh, -pr);
+                const float t = ph[r] + pr, bb = t - ph[r];
+                pl[r] += ((ph[r] - (t - bb)) + (pr - bb)) + pe;
+                ph[r] = t;
+                pl[r] = fmaf(x[r], vl, pl[r]);
+              }
+            }
+          }
+        });
+        if (!ok) return false;
+      }
+      // the chunk's new residual: one reducer thread per row
+      *reinterpret_cast<float4*>(red_h + warp * 128 + 4 * lane) = make_float4(ph[0], ph[1], ph[2], ph[3]);
+      *reinterpret_cast<float4*>(red_l + warp * 128 + 4 * lane) = make_float4(pl[0], pl[1], pl[2], pl[3]);
+      __syncthreads();
+      if (tid < 128) {
+        const int64_t row = rrow;
+        float en = 0.f;
+        if (row < m) {
+          double e64;
+          if (kind == PK_APPLY) {
+            float sacc = 0.f;
+#pragma unroll
+            for (int w = 0; w < PNW; ++w) sacc += red_h[w * 128 + tid];
+            en = e_in - sacc;
+            e64 = (double)en;
+          } else if (kind == PK_COPY_Y) {
+            en = y_in;
+            e64 = (double)en;
+          } else {
+            double tot = 0.0;
+#pragma unroll
+            for (int w = 0; w < PNW; ++w) tot += (double)red_h[w * 128 + tid] + (double)red_l[w * 128 + tid];
+            e64 = (double)y_in - tot;
+            en = (float)e64;
+          }
+          p.e[row] = en;
+          e2 = fma(e64, e64, e2);
+          if (first) y2 = fma((double)y_in, (double)y_in, y2);
+        }
+        ech[tid] = en;
+      }
+      __syncthreads();
+      const float4 ev = *reinterpret_cast<const float4*>(ech + 4 * lane);
+#pragma unroll
+      for (int b = 0; b < NBP; ++b) {
+        if (b >= nD) break;
+        const bool ok = box((uint64_t)ci * bpc + nA + b, [&](const T* bx) {
+#pragma unroll
+          for (int c = 0; c < CWB; ++c) {
+            float x[4];
+            BoxRows4<T>::load(bx + (warp * CWB + c) * 128 + 4 * lane, x);
+            gacc[b][c] = fmaf(x[0], ev.x, fmaf(x[1], ev.y, fmaf(x[2], ev.z, fmaf(x[3], ev.w, gacc[b][c]))));
+          }
+        });
+        if (!ok) return false;
+      }
+      if (++since_flush == 8) {
+        flush();
+        since_flush = 0;
+      }
+    }
+    if (since_flush) flush();
+    qbase += total;
+    {
+      const int b = lane / CWB, c = lane % CWB;
+      const int col = b * BC + warp * CWB + c;  // within the dot panel
+      if (col < nd && nch > 0) atomicAdd(p.hacc + (size_t)hb * PW + col, acc64);
+    }
+    // the CTA's ||e||^2 (and ||y||^2) partials: the reducer threads' sums
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+      e2 += __shfl_xor_sync(FULL_MASK, e2, o);
+      y2 += __shfl_xor_sync(FULL_MASK, y2, o);
+    }
+    if (lane == 0 && warp < 4) {
+      red[warp] = e2;
+      red[4 + warp] = y2;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      p.npart[(size_t)nb * G + blockIdx.x] = red[0] + red[1] + red[2] + red[3];
+      if (first) p.ypart[blockIdx.x] = red[4] + red[5] + red[6] + red[7];
+    }
+    __syncthreads();
+    return true;
+  };
+  auto pass = [&](int kind, int qp, int qd, int hb, int nb, bool first) -> bool {
+    if constexpr (TMA) {
+      if (!run_pass_tma(kind, qp, qd, hb, nb, first)) {
+        tma_fail = true;
+        return false;
+      }
+      return true;
+    } else {
+      run_pass(kind, qp, qd, hb, nb, first);
+      return true;
+    }
+  };
+
   // After a pass's barrier: r = h ⊘ d of the dot panel, hacc[hb] left for the
   // next-but-one pass zeroed by CTA 0.
   auto take_dots = [&](int qd, int hb) {
@@ -402,9 +662,8 @@ __global__ void __launch_bounds__(PNT, 1) panel_sweep_kernel(const PanelParams p
 
   // pass 0: the initial residual (y, or y - X·a0 of a warm start) and the
   // first panel's dot products
-  run_pass(p.warm ? PK_TRUE : PK_COPY_Y, 0, 0, 0, 0, true);
-  bool done = false;
-  if (!sync_grid()) done = true;
+  bool done = !pass(p.warm ? PK_TRUE : PK_COPY_Y, 0, 0, 0, 0, true);
+  if (!done && !sync_grid()) done = true;
   if (!done) {
     take_dots(0, 0);
     y2 = sum_partials(p.ypart, G, red);
@@ -433,7 +692,7 @@ __global__ void __launch_bounds__(PNT, 1) panel_sweep_kernel(const PanelParams p
     const bool refresh = boundary && p.refresh_every > 0 && ((s + 1) % p.refresh_every) == 0;
     if (refresh && !sync_grid()) break;  // the coefficients of the last panel are visible
     const int hb = (int)(t % 3), nb = (int)(t & 1);
-    run_pass(refresh ? PK_TRUE : PK_APPLY, q, qn, hb, nb, false);
+    if (!pass(refresh ? PK_TRUE : PK_APPLY, q, qn, hb, nb, false)) break;
     if (!sync_grid()) break;
     take_dots(qn, hb);
     q = qn;
@@ -457,7 +716,7 @@ __global__ void __launch_bounds__(PNT, 1) panel_sweep_kernel(const PanelParams p
         if (!sync_grid()) break;
         ++t;
         const int hb2 = (int)(t % 3), nb2 = (int)(t & 1);
-        run_pass(PK_TRUE, 0, 0, hb2, nb2, false);
+        if (!pass(PK_TRUE, 0, 0, hb2, nb2, false)) break;
         if (!sync_grid()) break;
         take_dots(0, hb2);
         r = rel_of(sum_partials(p.npart + (size_t)nb2 * G, G, red), y2);
@@ -476,6 +735,11 @@ __global__ void __launch_bounds__(PNT, 1) panel_sweep_kernel(const PanelParams p
     }
     solve_panel(q);
   }
+  if (tma_fail) err = DEV_TIMEOUT_COPY;
+  // copies still in flight land before the CTA retires
+  if (TMA && tid == 0)
+    for (uint64_t g = waited_g; g < issued_g; ++g)
+      if (!mbar_wait_bounded(&full[g % nst], (uint32_t)((g / nst) & 1), p.timeout_ns)) break;
   if (err != DEV_OK && tid == 0) atomicCAS(&p.ctl->err, DEV_OK, err);
   if (lead) {
     __syncthreads();
@@ -491,13 +755,32 @@ __global__ void __launch_bounds__(PNT, 1) panel_sweep_kernel(const PanelParams p
 
 }  // namespace
 
-cudaError_t launch_panel_sweep(int dtype, const PanelParams& p, int grid, cudaStream_t stream) {
+// Dynamic shared memory of the TMA instantiation with nst stages.
+int panel_tma_smem(int nst) { return nst * PANEL_BOX_BYTES + 2 * PNW * 128 * 4 + 128 * 4 + 8 * 8 + 1024; }
+
+cudaError_t launch_panel_sweep(int dtype, const PanelParams& p, const CUtensorMap* tmap, int grid,
+                               cudaStream_t stream) {
   PanelParams pp = p;
-  void* args[] = {(void*)&pp};
-  const void* kern = dtype == HPSCD_F32    ? (const void*)panel_sweep_kernel<float>
-                     : dtype == HPSCD_BF16 ? (const void*)panel_sweep_kernel<uint16_t>
-                                           : (const void*)panel_sweep_kernel<__half>;
-  return cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(PNT), args, 0, stream);
+  CUtensorMap map;
+  if (tmap) map = *tmap;
+  else memset(&map, 0, sizeof(map));
+  void* args[] = {(void*)&map, (void*)&pp};
+  const bool tma = p.use_tma != 0 && tmap != nullptr;
+  const void* kern;
+  if (tma)
+    kern = dtype == HPSCD_F32    ? (const void*)panel_sweep_kernel<float, true>
+           : dtype == HPSCD_BF16 ? (const void*)panel_sweep_kernel<uint16_t, true>
+                                 : (const void*)panel_sweep_kernel<__half, true>;
+  else
+    kern = dtype == HPSCD_F32    ? (const void*)panel_sweep_kernel<float, false>
+           : dtype == HPSCD_BF16 ? (const void*)panel_sweep_kernel<uint16_t, false>
+                                 : (const void*)panel_sweep_kernel<__half, false>;
+  const int smem = tma ? panel_tma_smem(p.nstages) : 0;
+  if (tma) {
+    const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(PNT), args, (size_t)smem, stream);
 }
 
 }  // namespace hpscd
