@@ -410,17 +410,19 @@ __global__ void __launch_bounds__(GT_THREADS, 1)
 //   stage 1: tmp[s][i][j..j+3] = sum over the splits of slice s of the lower
 //            partials (float4 loads, independent across threads; one thread
 //            per slice, row and 4 columns; a tile's splits are those of the
-//            group that holds it), and d_i = sum_k dpart[k][i] (the CUDA-core
-//            diagonal, float64), and when asked (X^T y)_i and ||y||^2 summed over
-//            the splits the same way;
+//            group that holds it), and slice s of d_i = sum_k dpart[k][i] (the
+//            CUDA-core diagonal, float64) and, when asked, of (X^T y)_i and
+//            ||y||^2, over the same slices of the splits;
+//   stage 1b: d, X^T y and ||y||^2: the 16 slice sums added in order;
 //   stage 2: G_ij = G_ji = sum_s tmp[s][i][j], G_ii = d_i; optionally
 //            G~ = D^{-1} G in both triangles and d as float32.
 constexpr int RED_SLICES = 16;
+// dsl, hsl: [RED_SLICES][npad] slice sums of the diagonal and X^T y; ysl: [RED_SLICES]
 __global__ void gram_tc_reduce1_kernel(const float* __restrict__ partial,
                                        const double* __restrict__ dpart, const GramTCGroups grp, int npad,
-                                       float* __restrict__ tmp, double* __restrict__ d64,
+                                       float* __restrict__ tmp, double* __restrict__ dsl,
                                        const double* __restrict__ hpart, const double* __restrict__ y2part,
-                                       double* __restrict__ h0, double* __restrict__ y2) {
+                                       double* __restrict__ hsl, double* __restrict__ ysl) {
   const int n4 = npad / 4;
   const int64_t total = (int64_t)RED_SLICES * npad * n4;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
@@ -439,23 +441,48 @@ __global__ void gram_tc_reduce1_kernel(const float* __restrict__ partial,
     }
     *reinterpret_cast<float4*>(tmp + ((size_t)sl * npad + i) * npad + 4 * j4) =
         make_float4((float)a0, (float)a1, (float)a2, (float)a3);
-    if (sl == 0 && j4 == 0) {
-      // the diagonal and X^T y of block i / BLK come from the group holding tile (I, I);
-      // ||y||^2 from group 0, whose splits cover every row
+    if (j4 == 0) {
+      // slice sl of the diagonal and X^T y of block i / BLK (from the group holding
+      // tile (I, I)) and of ||y||^2 (from group 0, whose splits cover every row)
       const int kd = grp.tile_splits[i / BLK][i / BLK];
+      const int d0 = kd * sl / RED_SLICES, d1 = kd * (sl + 1) / RED_SLICES;
       double dd = 0.0;
-      for (int k = 0; k < kd; ++k) dd += dpart[(size_t)k * npad + i];
-      d64[i] = dd;
-      if (h0) {
+      for (int k = d0; k < d1; ++k) dd += dpart[(size_t)k * npad + i];
+      dsl[(size_t)sl * npad + i] = dd;
+      if (hsl) {
         double hh = 0.0;
-        for (int k = 0; k < kd; ++k) hh += hpart[(size_t)k * npad + i];
-        h0[i] = hh;
+        for (int k = d0; k < d1; ++k) hh += hpart[(size_t)k * npad + i];
+        hsl[(size_t)sl * npad + i] = hh;
         if (i == 0) {
+          const int ky = grp.nsplit[0];
           double yy = 0.0;
-          for (int k = 0; k < grp.nsplit[0]; ++k) yy += y2part[k];
-          *y2 = yy;
+          for (int k = ky * sl / RED_SLICES; k < ky * (sl + 1) / RED_SLICES; ++k) yy += y2part[k];
+          ysl[sl] = yy;
         }
       }
+    }
+  }
+}
+
+// d_i, (X^T y)_i and ||y||^2: the slice sums in slice order (one thread per row)
+__global__ void gram_tc_reduce1b_kernel(const double* __restrict__ dsl, const double* __restrict__ hsl,
+                                        const double* __restrict__ ysl, int npad, double* __restrict__ d64,
+                                        double* __restrict__ h0, double* __restrict__ y2) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= npad) return;
+  double dd = 0.0, hh = 0.0;
+#pragma unroll
+  for (int sl = 0; sl < RED_SLICES; ++sl) {
+    dd += dsl[(size_t)sl * npad + i];
+    if (h0) hh += hsl[(size_t)sl * npad + i];
+  }
+  d64[i] = dd;
+  if (h0) {
+    h0[i] = hh;
+    if (i == 0) {
+      double yy = 0.0;
+      for (int sl = 0; sl < RED_SLICES; ++sl) yy += ysl[sl];
+      *y2 = yy;
     }
   }
 }
@@ -585,7 +612,9 @@ bool gram_tc_plan(int dtype, int64_t m, int n, int sms, int max_smem, GramTCPlan
                       (size_t)RED_SLICES * gp->npad * gp->npad * sizeof(float) +
                       (size_t)gp->npad * sizeof(double) +
                       (size_t)gp->ksplit * gp->npad * sizeof(double) +  // X^T y partials
-                      (size_t)gp->ksplit * sizeof(double);              // ||y||^2 partials
+                      (size_t)gp->ksplit * sizeof(double) +             // ||y||^2 partials
+                      (size_t)2 * RED_SLICES * gp->npad * sizeof(double) +  // slice sums of d, X^T y
+                      (size_t)RED_SLICES * sizeof(double);              // and of ||y||^2
   return true;
 }
 
@@ -615,6 +644,9 @@ cudaError_t launch_gram_tc(const CUtensorMap* tmap, int dtype, int64_t m, const 
   else memset(&ym, 0, sizeof(ym));
   p.hpart = d64 + gp.npad;
   p.y2part = p.hpart + (size_t)gp.ksplit * gp.npad;
+  double* dsl = p.y2part + gp.ksplit;               // [RED_SLICES][npad]
+  double* hsl = dsl + (size_t)RED_SLICES * gp.npad;  // [RED_SLICES][npad]
+  double* ysl = hsl + (size_t)RED_SLICES * gp.npad;  // [RED_SLICES]
   dim3 grid(gp.nctas);
   cudaError_t e;
   auto kern = dtype == HPSCD_F32    ? gram_tc_kernel<HPSCD_F32>
@@ -627,8 +659,9 @@ cudaError_t launch_gram_tc(const CUtensorMap* tmap, int dtype, int64_t m, const 
   if (e != cudaSuccess) return e;
   const int64_t t1 = (int64_t)RED_SLICES * gp.npad * (gp.npad / 4);
   gram_tc_reduce1_kernel<<<(unsigned)((t1 + 255) / 256), 256, 0, stream>>>(
-      partial, p.dpart, gp.grp, gp.npad, tmp, d64, p.hpart, p.y2part, with_y ? h0 : nullptr,
-      with_y ? y2 : nullptr);
+      partial, p.dpart, gp.grp, gp.npad, tmp, dsl, p.hpart, p.y2part, with_y ? hsl : nullptr, ysl);
+  gram_tc_reduce1b_kernel<<<(unsigned)((gp.npad + 127) / 128), 128, 0, stream>>>(
+      dsl, with_y ? hsl : nullptr, ysl, gp.npad, d64, with_y ? h0 : nullptr, with_y ? y2 : nullptr);
   const int64_t t2 = (int64_t)gp.npad * gp.npad;
   gram_tc_reduce2_kernel<<<(unsigned)((t2 + 255) / 256), 256, 0, stream>>>(tmp, d64, gp.npad, n, G, ldG,
                                                                           Gt, dvec);

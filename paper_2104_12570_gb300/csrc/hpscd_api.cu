@@ -229,7 +229,7 @@ int run_gram(hpscd_ctx* ctx, const void* X, int dtype, int64_t m, int64_t n, int
       return HPSCD_ERR_CUDA;
     }
     if (got_h0) *got_h0 = y && h0 && y2;
-    *launches = 3;
+    *launches = 4;  // the Gram kernel and its three reduce kernels
     return HPSCD_OK;
   }
   if (launch_gram(X, dtype, m, (int)n, ld, P.gp, static_cast<double*>(partial), G, ldG,
