@@ -433,14 +433,15 @@ __global__ void gram_tc_reduce1_kernel(const float* __restrict__ partial,
     if (4 * j4 > i) continue;
     const int ks = grp.tile_splits[i / BLK][(4 * j4) / BLK];
     const int k0 = ks * sl / RED_SLICES, k1 = ks * (sl + 1) / RED_SLICES;
-    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    // float32 over a slice's few splits (the float64 pipe is a small fraction of
+    // the float32 one on this part); the 16 slices are added in float64
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
 #pragma unroll 4
     for (int k = k0; k < k1; ++k) {
-      const float4 v = __ldg(reinterpret_cast<const float4*>(partial + ((size_t)k * npad + i) * npad) + j4);
+      const float4 v = *(reinterpret_cast<const float4*>(partial + ((size_t)k * npad + i) * npad) + j4);
       a0 += v.x; a1 += v.y; a2 += v.z; a3 += v.w;
     }
-    *reinterpret_cast<float4*>(tmp + ((size_t)sl * npad + i) * npad + 4 * j4) =
-        make_float4((float)a0, (float)a1, (float)a2, (float)a3);
+    *reinterpret_cast<float4*>(tmp + ((size_t)sl * npad + i) * npad + 4 * j4) = make_float4(a0, a1, a2, a3);
     if (j4 == 0) {
       // slice sl of the diagonal and X^T y of block i / BLK (from the group holding
       // tile (I, I)) and of ||y||^2 (from group 0, whose splits cover every row)

@@ -101,8 +101,10 @@ __device__ __forceinline__ bool wait_cluster_bounded(uint64_t* bar, uint32_t par
 // coupling P = X_b^T X_{b-1} to the previous block, cyclically: block 0's is
 // the last block, which precedes it in the next sweep) over all m rows.  X is
 // staged through shared memory 32 rows at a time, double-buffered by cp.async
-// (two CTAs per SM); 16 x 16 threads each hold a (W/16) x (2W/16) tile of D,
-// float32 products summed in float32 over 256 rows and those sums in float32.
+// (two CTAs per SM); 16 x 16 threads each hold W/16 rows x 2W/16 columns of D
+// (thread tx: columns 4·tx.. of G's half and of P's half, W/32 groups of four
+// each, so that eight consecutive threads read 128 contiguous bytes), float32
+// products summed in float32 over 256 rows and those sums in float32.
 // Then, in shared memory: d = diag(G), H = D^{-1}·strict_lower(G),
 // T = (I + H)^{-1} (column k by forward substitution in thread k),
 // M = T·D^{-1}, N = M·P; M and N are stored row-major [W][W].
@@ -174,7 +176,8 @@ __global__ void __launch_bounds__(256, 2) wide_setup_kernel(const float* __restr
       }
 #pragma unroll
       for (int j = 0; j < TC; j += 4) {
-        const float4 t = *reinterpret_cast<const float4*>(xt + r * XP + tx * TC + j);
+        // group j / 4 of this thread's columns: 64·(j / 4) + 4·tx (W = 64), 32·(j / 4) + 4·tx (W = 32)
+        const float4 t = *reinterpret_cast<const float4*>(xt + r * XP + (j / 4) * (W2 / (TC / 4)) + 4 * tx);
         bv[j] = t.x; bv[j + 1] = t.y; bv[j + 2] = t.z; bv[j + 3] = t.w;
       }
 #pragma unroll
@@ -190,13 +193,15 @@ __global__ void __launch_bounds__(256, 2) wide_setup_kernel(const float* __restr
         for (int j = 0; j < TC; ++j) { acc2[i][j] += acc[i][j]; acc[i][j] = 0.f; }
     }
   }
-  // columns tx·TC.. of D: G for tx < 8, P for tx >= 8
-  float* dst = tx < 8 ? Gs : Ps;
-  const int cbase = (tx % 8) * TC;
+  // this thread's columns of D (see the loads): G for columns < W, P above
 #pragma unroll
   for (int i = 0; i < TR; ++i)
 #pragma unroll
-    for (int j = 0; j < TC; ++j) dst[(ty * TR + i) * WP + cbase + j] = acc2[i][j] + acc[i][j];
+    for (int j = 0; j < TC; ++j) {
+      const int col = (j / 4) * (W2 / (TC / 4)) + 4 * tx + (j % 4);
+      float* dst = col < W ? Gs : Ps;
+      dst[(ty * TR + i) * WP + (col % W)] = acc2[i][j] + acc[i][j];
+    }
   __syncthreads();
   if (tid < W) dsv[tid] = Gs[tid * WP + tid];
   __syncthreads();
