@@ -334,7 +334,7 @@ __host__ __device__ inline WSmem wide_smem_plan(int W, int rows_box, int nst) {
   s.es = take(rows_box * 4);
   s.xbuf = take(XSLOTS * 16 * W * 4);  // [slot][source CTA][W] partial dots
   s.red = take(WNW * W * 4);           // [warp][W]
-  s.mn = take(2 * 2 * W * W * 4);      // [buffer][M, N][W][W] of the current and next block
+  s.mn = take(2 * W * W * 4);          // [M, N][W][W] of the block (the next one's copied in after its use)
   s.qs = take(W * 4);
   s.da = take(W * 4);
   s.dap = take(W * 4);
@@ -522,7 +522,8 @@ __global__ void __launch_bounds__(WNT, 1)
 
   // chain operands: thread (row ci = tid / 8, part cj = tid % 8) takes columns
   // [cj·CPT, (cj+1)·CPT) of row ci of M_b and N_b; both matrices of the next
-  // block are copied into the other buffer by cp.async while this one is used
+  // block are copied into the buffer by cp.async as soon as this block's
+  // products are done (one buffer: the space goes to one more TMA stage)
   const int ci = tid / 8, cj = tid % 8;
   const bool chain_thread = tid < 8 * W;
   auto load_mn = [&](int64_t b, int buf) {
@@ -577,7 +578,7 @@ __global__ void __launch_bounds__(WNT, 1)
       if (tid == 0) mbar_arrive_expect_tx(&xbar[slot], round_bytes);
       stamp(0);
       // 2. the block's steps: da_b = M_b q_b - N_b da_{b-1}
-      const int cur = (int)(kseq & 1);
+      const int cur = 0;  // one M/N buffer
       if (chain_thread) {
         const float* mrow = mn + (size_t)cur * 2 * W * W + ci * W + cj * CPT;
         const float* nrow = mrow + W * W;
@@ -604,7 +605,7 @@ __global__ void __launch_bounds__(WNT, 1)
       }
       __syncthreads();
       stamp(1);
-      load_mn(b + 1 < nblk ? b + 1 : 0, cur ^ 1);  // the next block's, used one iteration later
+      load_mn(b + 1 < nblk ? b + 1 : 0, 0);  // the next block's into the buffer just used, landing before its products
       if (me == 0 && tid < W && b * W + tid < n) p.dsw[b * W + tid] = da_s[tid];
       if (tid < W) dap_s[tid] = da_s[tid];
       stamp(2);
