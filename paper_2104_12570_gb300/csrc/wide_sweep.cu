@@ -28,7 +28,7 @@
 //   1. wait (bounded) for round b of the exchange, sum its WC partials in a
 //      fixed order (every CTA holds identical values);
 //   2. da_b = M_b·q_b - N_b·da_{b-1}  (8 threads per row; M_b and N_b are
-//      staged in shared memory by cp.async one block ahead);
+//      staged in shared memory by two bulk copies one block ahead);
 //   3. one pass over the CTA's rows: e_r -= X_b[r]·da_b, then the partial
 //      X_{b+2}^T e over the new e_r (the two slabs are both in shared memory);
 //   4. the partials summed over the CTA's warps and pushed into slot (b+2) % 4
@@ -67,6 +67,14 @@ __device__ __forceinline__ void st_async_v4(uint32_t addr, float4 v, uint32_t ba
           addr),
       "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "r"(bar)
       : "memory");
+}
+// 1-D bulk copy of `bytes` (a multiple of 16, both addresses 16-byte aligned)
+// from global into this CTA's shared memory, completing on `bar`
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
 }
 __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
@@ -340,7 +348,7 @@ __host__ __device__ inline WSmem wide_smem_plan(int W, int rows_box, int nst) {
   s.dap = take(W * 4);
   s.nbuf = take(16 * 8);
   s.wsum = take(WNW * 8);
-  s.bars = take((8 + XSLOTS + 2) * 8);  // full[<= 8], dot slots, norm rounds
+  s.bars = take((8 + XSLOTS + 2 + 1) * 8);  // full[<= 8], dot slots, norm rounds, M/N
   s.total = off + 1024;                 // alignment slack
   return s;
 }
@@ -375,6 +383,7 @@ __global__ void __launch_bounds__(WNT, 1)
   uint64_t* full = reinterpret_cast<uint64_t*>(base + L.bars);
   uint64_t* xbar = full + 8;       // [XSLOTS] dot exchange
   uint64_t* nbar = xbar + XSLOTS;  // [2] norm exchange
+  uint64_t* mnbar = nbar + 2;      // M_b, N_b of the block landed (one phase per block)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t nblk = (n + W - 1) / W;
   // optional trace (CTA 0, thread 0): for the first trace_passes blocks, the
@@ -396,6 +405,7 @@ __global__ void __launch_bounds__(WNT, 1)
       mbar_arrive_expect_tx(&xbar[k], round_bytes);
     }
     for (int k = 0; k < 2; ++k) mbar_init(&nbar[k], WC);
+    mbar_init(mnbar, 1);
     fence_mbar_init();
   }
   for (int r = tid; r < rows_box; r += WNT) es[r] = (r < rows) ? p.e[r0 + r] : 0.f;
@@ -522,19 +532,22 @@ __global__ void __launch_bounds__(WNT, 1)
 
   // chain operands: thread (row ci = tid / 8, part cj = tid % 8) takes columns
   // [cj·CPT, (cj+1)·CPT) of row ci of M_b and N_b; both matrices of the next
-  // block are copied into the buffer by cp.async as soon as this block's
-  // products are done (one buffer: the space goes to one more TMA stage)
+  // block are copied into the buffer as soon as this block's products are done
+  // (one buffer: the space goes to one more TMA stage)
   const int ci = tid / 8, cj = tid % 8;
   const bool chain_thread = tid < 8 * W;
+  // M_b and N_b by two bulk copies issued by thread 0 (one instruction each,
+  // not thousands of per-thread 16-byte copies in the memory pipe)
+  uint64_t mn_issued = 0;  // M/N copies issued (thread 0)
   auto load_mn = [&](int64_t b, int buf) {
-    float* dst = mn + (size_t)buf * 2 * W * W;
-    const float* srcm = p.Mb + b * (W * W);
-    const float* srcn = p.Nb + b * (W * W);
-    for (int i = tid; i < W * W / 4; i += WNT) {
-      cp_async16(dst + 4 * i, srcm + 4 * i);
-      cp_async16(dst + W * W + 4 * i, srcn + 4 * i);
+    (void)buf;
+    if (tid == 0) {
+      fence_proxy_async_smem();  // the buffer's last reads (the previous block's products) come first
+      mbar_arrive_expect_tx(mnbar, (uint32_t)(2 * W * W * 4));
+      bulk_g2s(mn, p.Mb + b * (W * W), (uint32_t)(W * W * 4), mnbar);
+      bulk_g2s(mn + W * W, p.Nb + b * (W * W), (uint32_t)(W * W * 4), mnbar);
+      ++mn_issued;
     }
-    asm volatile("cp.async.commit_group;" ::: "memory");
   };
 
   if (status == -1 && err == DEV_OK) {
@@ -572,7 +585,8 @@ __global__ void __launch_bounds__(WNT, 1)
           qs[tid] = g;
         }
       }
-      asm volatile("cp.async.wait_group 0;" ::: "memory");  // this block's M_b, N_b
+      // this block's M_b and N_b (phase kseq of mnbar)
+      if (wok && !mbar_wait_bounded(mnbar, (uint32_t)(kseq & 1), p.timeout_ns)) wok = 0;
       if (__syncthreads_or(wok ? 0 : 1)) { err = DEV_TIMEOUT_BARRIER; break; }
       // the slot is free: arm it for round kseq + 4 (every push of that round follows)
       if (tid == 0) mbar_arrive_expect_tx(&xbar[slot], round_bytes);
@@ -690,6 +704,9 @@ __global__ void __launch_bounds__(WNT, 1)
 
   // drain copies in flight; write e and the results
   asm volatile("cp.async.wait_all;" ::: "memory");
+  // the M/N copy issued last lands before the CTA may retire
+  if (tid == 0 && mn_issued > 0)
+    mbar_wait_bounded(mnbar, (uint32_t)((mn_issued - 1) & 1), p.timeout_ns);
   if (tid == 0 && tma) {
     for (uint64_t k = waited; k < issued; ++k)
       if (!mbar_wait_bounded(&full[k % nst], (uint32_t)((k / nst) & 1), p.timeout_ns)) {
