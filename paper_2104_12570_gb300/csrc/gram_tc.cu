@@ -32,11 +32,19 @@ namespace {
 
 using namespace tc;
 
-constexpr int GT_THREADS = 192;  // 6 warps: producer, MMA issuer, 4 workers
+// Worker warps: two per SM sub-partition, so that the split's dependent
+// arithmetic of one warp overlaps the other's (with one worker warp per
+// sub-partition the split of a float32 stage took about as long as its MMAs).
+#ifndef GRAM_WORKER_WARPS
+#define GRAM_WORKER_WARPS 8
+#endif
+constexpr int GT_NWW = GRAM_WORKER_WARPS;
+static_assert(GT_NWW == 4 || GT_NWW == 8, "4 or 8 worker warps");
+constexpr int GT_THREADS = 64 + 32 * GT_NWW;  // producer, MMA issuer, workers
 // Warp roles: warp 0 lane 0 feeds the stages by TMA; warp 1 lane 0 issues
-// the MMAs; warps 2..5 (the workers, one per tensor-memory lane quarter) sum
-// the squares of every column (the diagonal), split float32 tiles into tf32
-// hi/lo, and run the epilogue.  Per stage s and K block kb:
+// the MMAs; warps 2.. (the workers; worker warp w reads tensor-memory lane
+// quarter w % 4) sum the squares of every column (the diagonal), split
+// float32 tiles into tf32 hi/lo, and run the epilogue.  Per stage s and K block kb:
 //   full[s]  : TMA bytes landed                 (producer -> workers, MMA for bf16)
 //   ready[s] : the workers are done with the tile (workers -> MMA issuer)
 //   empty[s] : the MMAs that read the tile completed (tcgen05.commit -> producer)
@@ -44,7 +52,8 @@ constexpr int GT_THREADS = 192;  // 6 warps: producer, MMA issuer, 4 workers
 // of block kb.  Every wait is bounded; a wait that gives up raises s_fail, which
 // every role polls, and the CTA drains its copies and frees tensor memory.
 constexpr int GT_WORK_WARP0 = 2;
-constexpr int GT_WORKERS = 128;
+constexpr int GT_WORKERS = 32 * GT_NWW;
+constexpr int GT_CPS = 1024 / GT_WORKERS;  // 16-byte chunks of a worker per 128-column slot
 
 // 1-D tiled TMA load of `box` elements of `map` from coordinate c0 (rows past
 // the tensor's end read as zero), completing on `bar`.
@@ -204,19 +213,19 @@ __global__ void __launch_bounds__(GT_THREADS, 1)
 
   // ---------------- workers: warps 2..5 ----------------
   // <X_j, X_j> on the CUDA cores: worker w sums the squares of the 16-byte
-  // chunks w + 128q of every stage, i.e. of column w/8 + 16q (the swizzle only
-  // permutes chunks within a column's 128 bytes); float32 per 64 K blocks,
-  // float64 across them.  The tensor-core accumulation drifts on long sums of
+  // chunks w + W·q of every stage (W workers), i.e. of column w/8 + (W/8)·(q %
+  // GT_CPS) of slot q / GT_CPS (the swizzle only permutes chunks within a
+  // column's 128 bytes); float32 per 64 K blocks, float64 across them.  The tensor-core accumulation drifts on long sums of
   // positive terms, so these replace its diagonal.
   // <X_j, y> (when p.y is given): the chunk a worker reads holds K rows
   // 4c..4c+3 (float32; 8c..8c+7 for bfloat16) of its column, c = the logical
   // chunk (w & 7) XOR (column & 7) of the 128-byte swizzle; the column index
-  // w/8 + 16q has (column & 7) = (w/8) & 7 for every q, so each worker needs
-  // the same YR values of y per K block, loaded one block ahead.
+  // w/8 + (W/8)·q' has (column & 7) = (w/8) & 7 for every q', so each worker
+  // needs the same YR values of y per K block, loaded one block ahead.
   // Float64 accumulation: every 64 K blocks the 8 workers that share a column
   // (8 consecutive lanes) sum their float32 partials with shuffles, and lane j
-  // of the 8 keeps the float64 totals of q = j, j+8, j+16, j+24.
-  constexpr int MAXQ = 32;  // 16-byte chunks per worker per stage (nload <= 4)
+  // of the 8 keeps the float64 totals of q = j, j+8, ...
+  constexpr int MAXQ = 4 * GT_CPS;  // 16-byte chunks per worker per stage (nload <= 4)
   constexpr int YR = TF32 ? 4 : 8;  // rows of a 16-byte chunk
   const int wt = tid - GT_WORK_WARP0 * 32;
   const bool worker = warp >= GT_WORK_WARP0 && warp < GT_WORK_WARP0 + GT_WORKERS / 32;
@@ -231,7 +240,7 @@ __global__ void __launch_bounds__(GT_THREADS, 1)
     float dsq[MAXQ], xy[MAXQ], y2 = 0.f;
 #pragma unroll
     for (int q = 0; q < MAXQ; ++q) { dsq[q] = 0.f; xy[q] = 0.f; }
-    const int nq = 8 * nload;
+    const int nq = GT_CPS * nload;
     const int yoff = YR * ((wt & 7) ^ ((wt >> 3) & 7));  // first K row of the worker's chunk
     float yv[YR], yn[YR];
     // without the TMA copy of y (y not 16-byte aligned): rows r0 + kb·KB + yoff..
@@ -357,15 +366,16 @@ __global__ void __launch_bounds__(GT_THREADS, 1)
   tc_fence_after();
   const int fail = __syncthreads_or((!ok || *vfail) ? 1 : 0);
   if (!fail && worker) {
-    // column totals: lane j of each 8-lane group holds q = 8k + j, the
-    // column wt/8 + 16j of stage slot k
+    // column totals: lane j of each 8-lane group holds q = 8h + j: slot
+    // k = q / GT_CPS, column wt/8 + (W/8)·(q % GT_CPS) of the slot
 #pragma unroll
-    for (int k = 0; k < MAXQ / 8; ++k) {
-      const int lcol = wt / 8 + 16 * jl;  // column within slot k
+    for (int h = 0; h < MAXQ / 8; ++h) {
+      const int q = 8 * h + jl, k = q / GT_CPS;
+      const int lcol = wt / 8 + (GT_WORKERS / 8) * (q % GT_CPS);  // column within slot k
       if (k < nload && p.grp.diag_slot[g][k]) {
         const size_t at = (size_t)split * p.npad + p.grp.load_blk[g][k] * BLK + lcol;
-        p.dpart[at] = dsq64[k];
-        if (p.y) p.hpart[at] = xy64[k];
+        p.dpart[at] = dsq64[h];
+        if (p.y) p.hpart[at] = xy64[h];
       }
     }
     // ||y||^2 of the split: workers 0..7 of group 0 read every K row once
@@ -376,13 +386,16 @@ __global__ void __launch_bounds__(GT_THREADS, 1)
       v += __shfl_xor_sync(0xffu, v, 4);
       if (wt == 0) p.y2part[split] = v;
     }
-    // tensor memory: worker warp w reads lane quarter w % 4 (rows 32·(w%4)..+31)
+    // tensor memory: worker warp w reads lane quarter w % 4 (rows 32·(w%4)..+31);
+    // the GT_NWW / 4 warps of a quarter take equal column ranges of each tile
     const int quarter = warp & 3;
+    constexpr int CW = BLK / (GT_NWW / 4);
+    const int cbeg = CW * ((warp - GT_WORK_WARP0) / 4);
     float* out = p.partial + (size_t)split * p.npad * p.npad;
     for (int t = 0; t < ntile; ++t) {
       const int row = BLK * p.grp.tile_i[g][t] + 32 * quarter + lane;
       float* orow = out + (size_t)row * p.npad + BLK * p.grp.tile_j[g][t];
-      for (int c0 = 0; c0 < BLK; c0 += 32) {
+      for (int c0 = cbeg; c0 < cbeg + CW; c0 += 32) {
         float v[32];
         if (nkb > 0) {
           tmem_ld32(tmem + ((uint32_t)(32 * quarter) << 16) + BLK * t + c0, v);
