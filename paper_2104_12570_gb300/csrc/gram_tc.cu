@@ -307,9 +307,11 @@ __global__ void __launch_bounds__(GT_THREADS, 1)
       }
 #pragma unroll
       for (int r = 0; r < YR; ++r) y2 = fmaf(yv[r], yv[r], y2);
+      // 16-bit X: only the slots of diagonal tiles carry sums that are kept
+      // (float32 splits every slot)
 #pragma unroll
       for (int q = 0; q < MAXQ; ++q) {
-        if (q < nq) {
+        if (q < nq && (TF32 || p.grp.diag_slot[g][q / GT_CPS])) {
           const uint4 x = raw4[wt + GT_WORKERS * q];
           if constexpr (TF32) {
             const float a0 = __uint_as_float(x.x), a1 = __uint_as_float(x.y);
