@@ -11,9 +11,10 @@
 // tensor memory (128 columns per tile) with tcgen05.mma issued by one thread.
 // bfloat16 or IEEE binary16 X: kind::f16 (exact products, float32
 // accumulation).  float32 X: kind::tf32 on a two-term split
-// x = hi + lo (hi = x rounded to the nearest tf32, written back in place;
-// lo = x - hi rounded to tf32), accumulating hi·hi + hi·lo + lo·hi, which
-// leaves ~2^-22 relative error per product, of either sign.  The tensor-core accumulation loses accuracy on long sums of
+// x = hi + lo (hi = x with the low 13 mantissa bits dropped, which is what a
+// tf32 operand reads of x, so the stage keeps x in place; lo = x - hi, exact,
+// rounded to tf32), accumulating hi·hi + hi·lo + lo·hi, which leaves ~2^-21
+// relative error per product, of either sign.  The tensor-core accumulation loses accuracy on long sums of
 // positive terms, so the diagonal <X_j, X_j> is summed on the CUDA cores from
 // the same shared-memory tiles (float32, float64 across blocks).  Per-split
 // float32 partials are summed in a fixed order by gram_tc_reduce_kernel into
@@ -318,10 +319,14 @@ __global__ void __launch_bounds__(GT_THREADS, 1)
             const float a2 = __uint_as_float(x.z), a3 = __uint_as_float(x.w);
             dsq[q] = fmaf(a0, a0, fmaf(a1, a1, fmaf(a2, a2, fmaf(a3, a3, dsq[q]))));
             xy[q] = fmaf(a0, yv[0], fmaf(a1, yv[1], fmaf(a2, yv[2], fmaf(a3, yv[3], xy[q]))));
-            // split in place: hi over x, lo in the second half
-            uint4 h, l;
-            split_tf32(x, h, l);
-            raw4[wt + GT_WORKERS * q] = h;
+            // split: a tf32 operand is x with its low 13 mantissa bits ignored,
+            // so x itself stays in place as hi = x & ~0x1fff (no store); lo =
+            // x - hi, exact in float32, rounded to tf32 into the second half
+            uint4 l;
+            l.x = tf32_rna(a0 - __uint_as_float(x.x & 0xffffe000u));
+            l.y = tf32_rna(a1 - __uint_as_float(x.y & 0xffffe000u));
+            l.z = tf32_rna(a2 - __uint_as_float(x.z & 0xffffe000u));
+            l.w = tf32_rna(a3 - __uint_as_float(x.w & 0xffffe000u));
             lo4[wt + GT_WORKERS * q] = l;
           } else {
             const uint32_t w4[4] = {x.x, x.y, x.z, x.w};

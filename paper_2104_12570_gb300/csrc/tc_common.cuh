@@ -80,17 +80,6 @@ __device__ __forceinline__ uint32_t tf32_rna(float x) {
   return r;
 }
 
-__device__ __forceinline__ void split_tf32(const uint4& x, uint4& hi, uint4& lo) {
-  hi.x = tf32_rna(__uint_as_float(x.x));
-  hi.y = tf32_rna(__uint_as_float(x.y));
-  hi.z = tf32_rna(__uint_as_float(x.z));
-  hi.w = tf32_rna(__uint_as_float(x.w));
-  lo.x = tf32_rna(__uint_as_float(x.x) - __uint_as_float(hi.x));
-  lo.y = tf32_rna(__uint_as_float(x.y) - __uint_as_float(hi.y));
-  lo.z = tf32_rna(__uint_as_float(x.z) - __uint_as_float(hi.z));
-  lo.w = tf32_rna(__uint_as_float(x.w) - __uint_as_float(hi.w));
-}
-
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
   uint32_t r[32];
   asm volatile(

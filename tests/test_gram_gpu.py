@@ -93,3 +93,22 @@ def test_gram_one_signed_columns(ctx):
     err = np.abs(Gt - G64) / nrm
     assert err.max() <= L * 2.0 ** -23 + 4e-6, (err.max(), L)
     assert np.abs(np.diag(Gt) - np.diag(G64)).max() / np.diag(G64).min() <= 4e-6
+
+
+def test_gram_float32_low_bits_reach_the_product(ctx):
+    """The float32 split keeps x in place as its high part and relies on a tf32
+    operand reading x with its low 13 mantissa bits dropped (hi = x & ~0x1fff);
+    lo = x - hi carries those bits.  Elements whose low 13 bits are all ones
+    are where dropping and rounding to nearest differ by a full tf32 ulp
+    (2^-10 relative): had the operand rounded x instead, every product would
+    be off by ~1e-3 and G with it.  Signs and the high bits vary, so the
+    entries are sums of products of both signs."""
+    m, n = 4096, 160
+    g = np.random.default_rng(21)
+    hi_bits = (g.integers(0x3f000000, 0x40800000, (n, m), dtype=np.int64) & ~0x1fff).astype(np.uint32)
+    Xh = (hi_bits | np.uint32(0x1fff)).view(np.float32) * g.choice([-1.0, 1.0], (n, m)).astype(np.float32)
+    Xd = Xh.astype(np.float64)
+    G64 = Xd @ Xd.T
+    nrm = np.sqrt(np.outer(np.diag(G64), np.diag(G64)))
+    Gt = ctx.gram(torch.from_numpy(Xh).cuda().T).cpu().numpy().astype(np.float64)
+    assert (np.abs(Gt - G64) / nrm).max() <= 4e-6
