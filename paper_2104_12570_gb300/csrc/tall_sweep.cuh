@@ -129,12 +129,14 @@ __device__ __forceinline__ bool warp_wait_flag(const int* flag, int want, uint64
 //   da_j = r_j - sum_{l<j} G~_jl da_l, j = 0..n-1 (r = g ⊘ d; da_j = 0 when d_j = 0,
 //   where row j of G~ is zero).
 // Dataflow over blocks of 32 columns, no CTA barrier between blocks: warp w
-// owns rows 32w..32w+31.  Warp 0 solves block c (shuffles along the block's
-// strictly lower triangle, staged in diag_s) as soon as warp c has applied
-// blocks 0..c-1 to its rows, then publishes da of the block; every warp w
+// owns rows 32w..32w+31.  Warp 0 solves block c as soon as warp c has applied
+// blocks 0..c-1 to its rows (da_c = M_c r_c with the block's inverse
+// M_c = (I + L_c)^{-1} in diag_s: 32 independent shuffles; formed once per
+// launch, or every sweep for a given column order, whose blocks change with
+// the order), then publishes da of the block; every warp w
 // applies each published block b < w to its rows (its G~ segment of block b+1
 // loaded while it waits) and, after block w-1, signals warp 0.  The critical
-// path is one block's walk plus one hand-off per block.  With thr > 1
+// path is one block's solve plus one hand-off per block.  With thr > 1
 // (Algorithm 2) the couplings inside a block of thr columns are masked.
 // flags: [0] blocks solved, [1 + w] warp w's rows ready; r (in: g ⊘ d) and da
 // are shared arrays of length npad.  Returns false when a wait gave up.
@@ -161,11 +163,12 @@ __device__ bool forward_substitution(const float* __restrict__ Gt, int ldG, int 
       for (int k = 0; k < 32; ++k) seg[k] = (k < lane) ? dl[k] : 0.f;
       if (b > 0 && !warp_wait_flag(&flags[1 + b], 1, timeout_ns)) { ok = false; break; }
       float ri = (i < n) ? r[i] : 0.f;
+      // diag_s: the strictly lower part of M_b = (I + L_b)^{-1}, so the block's
+      // da = M_b r takes 32 independent shuffles instead of a dependent walk
+      float acc[4] = {ri, 0.f, 0.f, 0.f};
 #pragma unroll
-      for (int k = 0; k < 32; ++k) {
-        const float q = __shfl_sync(FULL_MASK, ri, k);  // lane k's value is final
-        if (lane > k) ri = fmaf(-seg[k], q, ri);
-      }
+      for (int k = 0; k < 32; ++k) acc[k & 3] = fmaf(seg[k], __shfl_sync(FULL_MASK, ri, k), acc[k & 3]);
+      ri = (acc[0] + acc[1]) + (acc[2] + acc[3]);
       if (i < npad) da[i] = (i < n) ? ri : 0.f;
       __syncwarp();
       if (lane == 0) st_release_cta(&flags[0], b + 1);
@@ -208,6 +211,33 @@ __device__ bool forward_substitution(const float* __restrict__ Gt, int ldG, int 
     if (lane == 0) st_release_cta(&flags[1 + warp], 1);
   }
   return named_sync_or(NT, ok ? 0 : 1) == 0;  // da complete (or a wait gave up)
+}
+
+// diag_s holds, per 32-column block b, the strictly lower triangle L_b of the
+// unit lower triangular diagonal block I + L_b of G~ (packed by rows).  Replaced
+// in place by the strictly lower triangle of M_b = (I + L_b)^{-1}, again unit
+// lower triangular, so the substitution of a block becomes a product with M_b
+// (the same da in exact arithmetic).  Warp w takes blocks w, w + NW, ...; lane j
+// forms column j: M_ij = -sum_{k<i} L_ik M_kj for i > j, in float32.
+__device__ void invert_diag_blocks(float* diag_s, int nb) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int b = warp; b < nb; b += NW) {
+    float* blk = diag_s + b * DIAG_PACK;
+    float mcol[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+      const float* li = blk + (i * (i - 1)) / 2;
+      float s = 0.f;
+#pragma unroll
+      for (int k = 0; k < i; ++k) s = fmaf(li[k], mcol[k], s);  // mcol[k] = 0 for k < lane
+      mcol[i] = i < lane ? 0.f : (i == lane ? 1.f : -s);
+    }
+    __syncwarp();
+#pragma unroll
+    for (int i = 1; i < 32; ++i)
+      if (i > lane) blk[(i * (i - 1)) / 2 + lane] = mcol[i];
+    __syncwarp();
+  }
 }
 
 // Algorithm 3's step (Sec. 8): with r = (X^T e) ⊘ d (every column's da against
@@ -479,6 +509,10 @@ __global__ void __launch_bounds__(NT, 1)
     diag_s[idx] = (32 * b + i < n && keep) ? p.Gt[(int64_t)(32 * b + i) * p.ldG + 32 * b + k] : 0.f;
   }
   __syncthreads();
+  if constexpr (!SEL) {  // a given column order (ORD) regathers and inverts every sweep
+    invert_diag_blocks(diag_s, (n + 31) / 32);
+    __syncthreads();
+  }
 
   // ---------------- TMA issue (thread 0) ----------------
   // chunk sequence q = pass·nchunk + panel·NCH + ch, periodic over passes;
@@ -842,6 +876,8 @@ __global__ void __launch_bounds__(NT, 1)
         diag_s[idx] = (32 * b + i < n) ? __ldg(p.Gt + (int64_t)o_s[32 * b + i] * p.ldG + o_s[32 * b + k])
                                        : 0.f;
       }
+      named_sync(NT);
+      invert_diag_blocks(diag_s, (n + 31) / 32);
       if (!forward_substitution<true>(p.Gt, p.ldG, n, NPAD, rstep, dstep, diag_s, 1,
                                       reinterpret_cast<int*>(red_lo), p.timeout_ns, o_s)) {
         err = DEV_TIMEOUT_BARRIER;
