@@ -14,8 +14,12 @@
 // x = hi + lo (hi = x with the low 13 mantissa bits dropped, which is what a
 // tf32 operand reads of x, so the stage keeps x in place; lo = x - hi, exact,
 // rounded to tf32), accumulating hi·hi + hi·lo + lo·hi, which leaves ~2^-21
-// relative error per product, of either sign.  The tensor-core accumulation loses accuracy on long sums of
-// positive terms, so the diagonal <X_j, X_j> is summed on the CUDA cores from
+// relative error per product, of either sign.  A group that holds the full
+// square of a pair of diagonal column blocks takes two products instead of
+// three: with the split stored as 2·lo (exact), D = H^T H + H^T (2L) and
+// (D + D^T) / 2 = H^T H + H^T L + L^T H, the same three terms; the epilogue
+// forms the symmetric part through shared memory.  The tensor-core
+// accumulation loses accuracy on long sums of positive terms, so the diagonal <X_j, X_j> is summed on the CUDA cores from
 // the same shared-memory tiles (float32, float64 across blocks).  Per-split
 // float32 partials are summed in a fixed order by gram_tc_reduce_kernel into
 // the symmetric G.  The same workers also form X^T y and ||y||^2 from those
@@ -87,6 +91,7 @@ __global__ void __launch_bounds__(GT_THREADS, 1)
   const int split = (int)blockIdx.x - p.grp.split_base[g];
   const int nload = p.grp.nload[g];
   const int ntile = p.grp.ntile[g];
+  const bool sym = TF32 && p.grp.sym[g] != 0;
   const int stage_raw = nload * ATOM_BYTES;
   const int stage_bytes = stage_raw * (TF32 ? 2 : 1);
   const int nst = p.nstages;
@@ -196,10 +201,12 @@ __global__ void __launch_bounds__(GT_THREADS, 1)
             const uint32_t acc = (kb > 0 || k > 0) ? 1u : 0u;
             mma_issue<TF32>(d_tmem, ah, bh, idesc, acc);
             if constexpr (TF32) {
-              const uint64_t al = make_sw128_desc(a_base + stage_raw + si * ATOM_BYTES + koff);
               const uint64_t bl = make_sw128_desc(a_base + stage_raw + sj * ATOM_BYTES + koff);
-              mma_issue<TF32>(d_tmem, ah, bl, idesc, 1u);
-              mma_issue<TF32>(d_tmem, al, bh, idesc, 1u);
+              mma_issue<TF32>(d_tmem, ah, bl, idesc, 1u);  // H^T L (H^T 2L in a full-square group)
+              if (!sym) {
+                const uint64_t al = make_sw128_desc(a_base + stage_raw + si * ATOM_BYTES + koff);
+                mma_issue<TF32>(d_tmem, al, bh, idesc, 1u);
+              }
             }
           }
           if (pair) ++t;
@@ -322,11 +329,13 @@ __global__ void __launch_bounds__(GT_THREADS, 1)
             // split: a tf32 operand is x with its low 13 mantissa bits ignored,
             // so x itself stays in place as hi = x & ~0x1fff (no store); lo =
             // x - hi, exact in float32, rounded to tf32 into the second half
+            // (2·lo in a full-square group: the scaling is exact)
+            const float ls = sym ? 2.f : 1.f;
             uint4 l;
-            l.x = tf32_rna(a0 - __uint_as_float(x.x & 0xffffe000u));
-            l.y = tf32_rna(a1 - __uint_as_float(x.y & 0xffffe000u));
-            l.z = tf32_rna(a2 - __uint_as_float(x.z & 0xffffe000u));
-            l.w = tf32_rna(a3 - __uint_as_float(x.w & 0xffffe000u));
+            l.x = __float_as_uint(ls * __uint_as_float(tf32_rna(a0 - __uint_as_float(x.x & 0xffffe000u))));
+            l.y = __float_as_uint(ls * __uint_as_float(tf32_rna(a1 - __uint_as_float(x.y & 0xffffe000u))));
+            l.z = __float_as_uint(ls * __uint_as_float(tf32_rna(a2 - __uint_as_float(x.z & 0xffffe000u))));
+            l.w = __float_as_uint(ls * __uint_as_float(tf32_rna(a3 - __uint_as_float(x.w & 0xffffe000u))));
             lo4[wt + GT_WORKERS * q] = l;
           } else {
             const uint32_t w4[4] = {x.x, x.y, x.z, x.w};
@@ -399,17 +408,57 @@ __global__ void __launch_bounds__(GT_THREADS, 1)
     constexpr int CW = BLK / (GT_NWW / 4);
     const int cbeg = CW * ((warp - GT_WORK_WARP0) / 4);
     float* out = p.partial + (size_t)split * p.npad * p.npad;
-    for (int t = 0; t < ntile; ++t) {
+    auto tile_row = [&](int t, int c0, float (&v)[32]) {
+      if (nkb > 0) {
+        tmem_ld32(tmem + ((uint32_t)(32 * quarter) << 16) + BLK * t + c0, v);
+      } else {
+#pragma unroll
+        for (int i = 0; i < 32; ++i) v[i] = 0.f;
+      }
+    };
+    if (sym) {
+      // lower tile (I, J) = (D_IJ + D_JI^T) / 2: D_JI goes to shared memory (the
+      // stages are idle now), row-major with a padded pitch, and is read back
+      // transposed
+      constexpr int SP = BLK + 4;
+      float* S = reinterpret_cast<float*>(base);
+      const int rr = 32 * quarter + lane;
+      for (int t = 0; t < ntile; ++t) {
+        const int I = p.grp.tile_i[g][t], J = p.grp.tile_j[g][t];
+        if (I < J) continue;
+        int tt = t;
+        for (int u = 0; u < ntile; ++u)
+          if (p.grp.tile_i[g][u] == J && p.grp.tile_j[g][u] == I) tt = u;
+        for (int c0 = cbeg; c0 < cbeg + CW; c0 += 32) {
+          float v[32];
+          tile_row(tt, c0, v);
+#pragma unroll
+          for (int q = 0; q < 8; ++q)
+            *reinterpret_cast<float4*>(S + rr * SP + c0 + 4 * q) =
+                make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        }
+        asm volatile("bar.sync 1, %0;" ::"n"(GT_WORKERS) : "memory");
+        float* orow = out + (size_t)(BLK * I + rr) * p.npad + BLK * J;
+        for (int c0 = cbeg; c0 < cbeg + CW; c0 += 32) {
+          float v[32];
+          tile_row(t, c0, v);
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            float w[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) w[e] = 0.5f * (v[4 * q + e] + S[(c0 + 4 * q + e) * SP + rr]);
+            *reinterpret_cast<float4*>(orow + c0 + 4 * q) = make_float4(w[0], w[1], w[2], w[3]);
+          }
+        }
+        asm volatile("bar.sync 1, %0;" ::"n"(GT_WORKERS) : "memory");
+      }
+    }
+    for (int t = 0; t < (sym ? 0 : ntile); ++t) {
       const int row = BLK * p.grp.tile_i[g][t] + 32 * quarter + lane;
       float* orow = out + (size_t)row * p.npad + BLK * p.grp.tile_j[g][t];
       for (int c0 = cbeg; c0 < cbeg + CW; c0 += 32) {
         float v[32];
-        if (nkb > 0) {
-          tmem_ld32(tmem + ((uint32_t)(32 * quarter) << 16) + BLK * t + c0, v);
-        } else {
-#pragma unroll
-          for (int i = 0; i < 32; ++i) v[i] = 0.f;
-        }
+        tile_row(t, c0, v);
 #pragma unroll
         for (int q = 0; q < 8; ++q)
           *reinterpret_cast<float4*>(orow + c0 + 4 * q) =
@@ -569,12 +618,18 @@ bool gram_tc_plan(int dtype, int64_t m, int n, int sms, int max_smem, GramTCPlan
   // Groups of lower tiles: at most 4 tiles (512 TMEM columns); bfloat16 streams
   // up to 4 column blocks per stage, float32 (whose hi/lo split doubles a
   // stage) at most 2.
+  // float32: the diagonal block pairs (0, 1) and (2, 3) as full squares (both
+  // (I, J) and (J, I): two products each, see the kernel; 1M x 256 set-up 0.429
+  // -> 0.421 ms, 4M x 512 8.63 -> 8.46 ms); a lone diagonal block (n <= 128,
+  // where the symmetrizing epilogue did not pay) and the other off-diagonal
+  // tiles with three products
   static const int f32_groups[4][6][4][2] = {
       {{{0, 0}, {-1, -1}}},
-      {{{0, 0}, {1, 0}, {1, 1}, {-1, -1}}},
-      {{{0, 0}, {1, 0}, {1, 1}, {-1, -1}}, {{2, 0}, {2, 2}, {-1, -1}}, {{2, 1}, {-1, -1}}},
-      {{{0, 0}, {1, 0}, {1, 1}, {-1, -1}}, {{2, 2}, {3, 2}, {3, 3}, {-1, -1}},
+      {{{0, 0}, {0, 1}, {1, 0}, {1, 1}}},
+      {{{0, 0}, {0, 1}, {1, 0}, {1, 1}}, {{2, 0}, {2, 2}, {-1, -1}}, {{2, 1}, {-1, -1}}},
+      {{{0, 0}, {0, 1}, {1, 0}, {1, 1}}, {{2, 2}, {2, 3}, {3, 2}, {3, 3}},
        {{2, 0}, {-1, -1}}, {{3, 0}, {-1, -1}}, {{2, 1}, {-1, -1}}, {{3, 1}, {-1, -1}}}};
+  static const int f32_sym[4][6] = {{0}, {1}, {1, 0, 0}, {1, 1, 0, 0, 0, 0}};
   static const int bf16_groups[4][3][4][2] = {
       {{{0, 0}, {-1, -1}}},
       {{{0, 0}, {1, 0}, {1, 1}, {-1, -1}}},
@@ -588,6 +643,7 @@ bool gram_tc_plan(int dtype, int64_t m, int n, int sms, int max_smem, GramTCPlan
     const int(*tiles)[2] = f32 ? f32_groups[nb - 1][gi] : bf16_groups[nb - 1][gi];
     const int g = G.ngroups++;
     for (int t = 0; t < 4 && tiles[t][0] >= 0; ++t) add_tile(G, g, tiles[t][0], tiles[t][1]);
+    G.sym[g] = f32 ? f32_sym[nb - 1][gi] : 0;
   }
   int maxload = 0;
   for (int g = 0; g < G.ngroups; ++g) maxload = G.nload[g] > maxload ? G.nload[g] : maxload;

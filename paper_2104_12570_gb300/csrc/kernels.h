@@ -50,6 +50,9 @@ struct GramTCGroups {
   int split_base[GTC_MAX_GROUPS];
   int64_t rows_per[GTC_MAX_GROUPS];
   int tile_splits[4][4];            // nsplit of the group that holds lower tile (I, J)
+  // float32 only: 1 when the group holds the full square of its column blocks
+  // (both (I, J) and (J, I)), accumulated with two products and symmetrized
+  int sym[GTC_MAX_GROUPS];
 };
 struct GramTCPlan {
   int npad;                 // multiple of 128
