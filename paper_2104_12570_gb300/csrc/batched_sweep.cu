@@ -310,9 +310,9 @@ __device__ double true_residual_rows(const float* __restrict__ X, int64_t ld, in
 }
 
 // Forward substitution da_j = r_j - sum_{l<j} G~_jl da_l in blocks of 32
-// columns: warp 0 walks each diagonal block with shuffles (its strictly lower
-// part staged in diag_s); every thread t >= 32 owns row t and applies each
-// finished block to it.  r is overwritten.
+// columns: warp 0 solves each diagonal block as a product with its inverse
+// (staged in diag_s by invert_diag_blocks, once per system); every thread
+// t >= 32 owns row t and applies each finished block to it.  r is overwritten.
 __device__ __forceinline__ void cp_async16(float* dst, const float* src) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
 }
@@ -322,6 +322,32 @@ __device__ __forceinline__ void cp_async16(float* dst, const float* src) {
 // cp.async before the walk (no registers held), so the copy overlaps the walk.
 constexpr int SEGP = 36;  // row pitch of the staged segments (16-byte rows, conflict-free float4 reads)
 static_assert(BMAXN * SEGP <= 2 * REDF, "the staged segments fit the pass scratch");
+// diag_s holds, per 32-column block b, the strictly lower triangle L_b of the
+// unit lower triangular diagonal block I + L_b of G~ (packed by rows); it is
+// replaced in place by the strictly lower triangle of M_b = (I + L_b)^{-1}, so
+// that the substitution of a block is a product with M_b.  Warp w takes blocks
+// w, w + BNW, ...; lane j forms column j: M_ij = -sum_{k<i} L_ik M_kj, i > j.
+__device__ void invert_diag_blocks(float* diag_s, int nb) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int b = warp; b < nb; b += BNW) {
+    float* blk = diag_s + b * DIAGP;
+    float mcol[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+      const float* li = blk + (i * (i - 1)) / 2;
+      float s = 0.f;
+#pragma unroll
+      for (int k = 0; k < i; ++k) s = fmaf(li[k], mcol[k], s);  // mcol[k] = 0 for k < lane
+      mcol[i] = i < lane ? 0.f : (i == lane ? 1.f : -s);
+    }
+    __syncwarp();
+#pragma unroll
+    for (int i = 1; i < 32; ++i)
+      if (i > lane) blk[(i * (i - 1)) / 2 + lane] = mcol[i];
+    __syncwarp();
+  }
+}
+
 __device__ void forward_sub_scaled(const float* __restrict__ Gt, int n, float* r, float* da,
                                    const float* diag_s, float* stage) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -342,13 +368,13 @@ __device__ void forward_sub_scaled(const float* __restrict__ Gt, int n, float* r
       const float* dl = diag_s + b * DIAGP + (lane * (lane - 1)) / 2;
 #pragma unroll
       for (int k = 0; k < 32; ++k) seg[k] = (k < lane) ? dl[k] : 0.f;
-      float ri = (i < n) ? r[i] : 0.f;
+      // diag_s holds the strictly lower part of M_b = (I + L_b)^{-1}: the block's
+      // da = M_b r, 32 independent shuffles
+      const float ri = (i < n) ? r[i] : 0.f;
+      float acc[4] = {ri, 0.f, 0.f, 0.f};
 #pragma unroll
-      for (int k = 0; k < 32; ++k) {
-        const float q = __shfl_sync(FULL_MASK, ri, k);
-        if (lane > k) ri = fmaf(-seg[k], q, ri);
-      }
-      da[i] = (i < n) ? ri : 0.f;
+      for (int k = 0; k < 32; ++k) acc[k & 3] = fmaf(seg[k], __shfl_sync(FULL_MASK, ri, k), acc[k & 3]);
+      da[i] = (i < n) ? (acc[0] + acc[1]) + (acc[2] + acc[3]) : 0.f;
     }
     __syncthreads();
     if (mine) {
@@ -471,6 +497,8 @@ __global__ void __launch_bounds__(BNT, 1) batched_sweep_kernel(const BatchParams
       const int row = 32 * b + i, col = 32 * b + k;
       diag_s[idx] = (row < n) ? __ldcg(Gt + (size_t)row * BLDG + col) : 0.f;
     }
+    __syncthreads();
+    invert_diag_blocks(diag_s, (n + 31) / 32);
     // residual slice e = y, coefficients, v
     double ysq = 0.0;
     for (int t = tid; t < p.ecap; t += BNT) {
