@@ -655,6 +655,12 @@ int solve_panel(hpscd_ctx* ctx, const void* X, int dtype, int64_t m, int64_t n, 
     if (rcg != HPSCD_OK) return rcg;
     launches += gl;
   }
+  // the substitution solves each 32-column diagonal block with its inverse
+  if (launch_invert_panel_diag(Gt, P.npanels, st) != cudaSuccess) {
+    cudaGetLastError();
+    return HPSCD_ERR_CUDA;
+  }
+  ++launches;
   if (cudaMemsetAsync(ws + P.hacc, 0, (size_t)3 * PANEL_W * sizeof(double), st) != cudaSuccess)
     return HPSCD_ERR_CUDA;
   if (cudaEventRecord(ctx->ev[1], st) != cudaSuccess) return HPSCD_ERR_CUDA;

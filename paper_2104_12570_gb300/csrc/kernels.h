@@ -199,6 +199,9 @@ struct PanelParams {
   int nstages;           // TMA stages (PANEL_BOX_BYTES each)
 };
 int panel_tma_smem(int nst);  // dynamic shared memory of the TMA kernel
+// The panels' G~ blocks (npanels × PANEL_W²): each 32 × 32 diagonal block's
+// strictly lower part replaced in place by that of its unit lower triangular inverse.
+cudaError_t launch_invert_panel_diag(float* Gt, int npanels, cudaStream_t stream);
 cudaError_t launch_panel_sweep(int dtype, const PanelParams& p, const CUtensorMap* tmap, int grid,
                                cudaStream_t stream);
 

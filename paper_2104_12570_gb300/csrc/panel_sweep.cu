@@ -139,9 +139,11 @@ __device__ __forceinline__ void dot2_sub(float x, float v, float& s, float& c) {
 
 // Forward substitution of one panel: on entry r_s[i] = h_i / d_i (i < nq); on
 // exit da_s[i] = da_i (0 for nq <= i < PW).  Gq: the panel's G~ block, row-major
-// with row stride PW.  Blocks of 32 steps: warp 0 solves the block's unit lower
-// triangle with shuffles (lane l owns step 32b + l and keeps its row of the
-// block in registers), then every thread applies the block to its later row.
+// with row stride PW, whose 32 x 32 diagonal blocks hold (below the diagonal)
+// M_b = (I + L_b)^{-1} in place of L_b (invert_panel_diag_kernel, in the
+// set-up).  Blocks of 32 steps: warp 0 solves a block as da_b = M_b r_b (lane l
+// owns step 32b + l and keeps its row of M_b in registers: 32 independent
+// shuffles), then every thread applies the block to its later row.
 __device__ void panel_substitution(const float* __restrict__ Gq, int nq, float* r_s, float* da_s) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nb = (nq + 31) / 32;
@@ -161,13 +163,14 @@ __device__ void panel_substitution(const float* __restrict__ Gq, int nq, float* 
 #pragma unroll
         for (int k = 0; k < 32; ++k) g[k] = 0.f;
       }
-      float v = (i < nq) ? r_s[i] : 0.f;
+      const float v = (i < nq) ? r_s[i] : 0.f;
+      float acc[4] = {v, 0.f, 0.f, 0.f};
 #pragma unroll
       for (int k = 0; k < 32; ++k) {
         const float dk = __shfl_sync(FULL_MASK, v, k);
-        if (lane > k) v = fmaf(-g[k], dk, v);
+        acc[k & 3] = fmaf(lane > k ? g[k] : 0.f, dk, acc[k & 3]);
       }
-      da_s[i] = (i < nq) ? v : 0.f;
+      da_s[i] = (i < nq) ? (acc[0] + acc[1]) + (acc[2] + acc[3]) : 0.f;
     }
     __syncthreads();
     const int i = tid;
@@ -188,6 +191,29 @@ __device__ void panel_substitution(const float* __restrict__ Gq, int nq, float* 
   }
   for (int i = 32 * nb + tid; i < PW; i += PNT) da_s[i] = 0.f;
   __syncthreads();
+}
+
+// Set-up of the panel substitution: each 32 x 32 diagonal block I + L_b of a
+// panel's G~ block (unit lower triangular below the diagonal) gets M_b =
+// (I + L_b)^{-1} written over L_b, in place; the diagonal and the upper part
+// stay.  One warp per block (blockIdx.x = panel · PW/32 + b); lane j forms
+// column j: M_ij = -sum_{k<i} L_ik M_kj for i > j, reading L before any write.
+__global__ void __launch_bounds__(32) invert_panel_diag_kernel(float* __restrict__ Gt) {
+  const int lane = threadIdx.x;
+  const int q = blockIdx.x / (PW / 32), b = blockIdx.x % (PW / 32);
+  float* blk = Gt + (size_t)q * PW * PW + (size_t)(32 * b) * PW + 32 * b;
+  float mcol[32];
+#pragma unroll
+  for (int i = 0; i < 32; ++i) {
+    float s = 0.f;
+#pragma unroll
+    for (int k = 0; k < i; ++k) s = fmaf(blk[(size_t)i * PW + k], mcol[k], s);  // mcol[k] = 0 for k < lane
+    mcol[i] = i < lane ? 0.f : (i == lane ? 1.f : -s);
+  }
+  __syncwarp();
+#pragma unroll
+  for (int i = 1; i < 32; ++i)
+    if (i > lane) blk[(size_t)i * PW + lane] = mcol[i];
 }
 
 // Sum over the CTAs of one partial per CTA, in a fixed order (the same value
@@ -757,6 +783,12 @@ __global__ void __launch_bounds__(PNT, 1)
 
 // Dynamic shared memory of the TMA instantiation with nst stages.
 int panel_tma_smem(int nst) { return nst * PANEL_BOX_BYTES + 2 * PNW * 128 * 4 + 128 * 4 + 8 * 8 + 1024; }
+
+cudaError_t launch_invert_panel_diag(float* Gt, int npanels, cudaStream_t stream) {
+  if (npanels <= 0) return cudaSuccess;
+  invert_panel_diag_kernel<<<npanels * (PW / 32), 32, 0, stream>>>(Gt);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_panel_sweep(int dtype, const PanelParams& p, const CUtensorMap* tmap, int grid,
                                cudaStream_t stream) {
